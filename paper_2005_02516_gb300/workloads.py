@@ -1,0 +1,148 @@
+"""Seeded synthetic workloads: problem definitions and random inputs.
+
+This module holds no arithmetic of the ESDG method.  It defines the five
+problem configurations (mesh size, degree, warp, analytic bathymetry and
+initial data as plain functions of (x, y)) and seeded random inputs.  The
+tests, the benchmark and the oracle-side CPU baseline all draw their inputs
+from here; the library and the oracle are each handed the same arrays or
+evaluate the same analytic functions at their own points.
+
+Base seed 20050251; instance i of an ensemble uses seed 20050251 + i.
+"""
+
+import dataclasses
+import math
+
+import numpy as np
+
+BASE_SEED = 20050251
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    N: int
+    nx: int
+    ny: int
+    warp: float            # ax = ay (0 -> affine)
+    g: float
+    cfl: float
+    steps: int
+    forcing: str           # "none" or "mms_sine"
+    x0: float = -1.0
+    x1: float = 1.0
+    y0: float = -1.0
+    y1: float = 1.0
+    surface_init: bool = False   # initial q[0] is the free surface H = h + b
+
+    @property
+    def K(self):
+        return 2 * self.nx * self.ny
+
+    @property
+    def Np(self):
+        return (self.N + 1) * (self.N + 2) // 2
+
+    def bathymetry(self, x, y):
+        return _BATHY[self.name](x, y)
+
+    def initial(self, x, y):
+        """Initial (h or H, hu, hv) at points (x, y); shape (3, ...)."""
+        return _INIT[self.name](x, y)
+
+    def exact(self, x, y, t):
+        """Closed-form solution where the workload has one (else None)."""
+        f = _EXACT.get(self.name)
+        return None if f is None else f(x, y, t)
+
+
+def _lake_bump_bathy(x, y):
+    return 0.2 * np.sin(np.pi * x) * np.sin(np.pi * y)
+
+
+def _lake_bump_init(x, y):
+    # H = 2 plus a Gaussian bump in h (given as the free surface)
+    r2 = x * x + y * y
+    return np.stack([2.0 + 0.01 * np.exp(-25.0 * r2), 0 * x, 0 * x])
+
+
+def _mms_bathy(x, y):
+    return 0.1 * np.cos(np.pi * x) * np.cos(np.pi * y)
+
+
+def _mms_exact(x, y, t):
+    h = 2.0 + 0.1 * np.sin(np.pi * (x + y - t))
+    return np.stack([h, 0.5 * h, 0.5 * h])
+
+
+def _dam_bathy(x, y):
+    return 0.05 * np.exp(-10.0 * ((x - 0.4) ** 2 + y * y))
+
+
+def _dam_init(x, y):
+    r = np.sqrt(x * x + y * y)
+    return np.stack([1.0 + 0.5 * np.tanh(40.0 * (0.3 - r)), 0 * x, 0 * x])
+
+
+_BATHY = {"lake_bump_k128_n2": _lake_bump_bathy,
+          "mms_k8192_n3": _mms_bathy,
+          "dam_k131072_n4": _dam_bathy}
+_INIT = {"lake_bump_k128_n2": _lake_bump_init,
+         "mms_k8192_n3": lambda x, y: _mms_exact(x, y, 0.0),
+         "dam_k131072_n4": _dam_init}
+_EXACT = {"mms_k8192_n3": _mms_exact}
+
+# Config 1: plain FP64, N=2, 8x8 quads -> K=128 affine, g=1, lake at rest H=2
+# plus a bump; 200 steps at CFL 0.25.
+LAKE_BUMP = Workload("lake_bump_k128_n2", N=2, nx=8, ny=8, warp=0.0, g=1.0, cfl=0.25,
+                     steps=200, forcing="none", surface_init=True)
+# Config 2: N=3, 64x64 -> K=8192 curved, manufactured solution, 1000 steps.
+MMS = Workload("mms_k8192_n3", N=3, nx=64, ny=64, warp=0.05, g=1.0, cfl=0.25,
+               steps=1000, forcing="mms_sine")
+# Config 3: N=4, 256x256 -> K=131072 curved, smoothed dam break.
+DAM = Workload("dam_k131072_n4", N=4, nx=256, ny=256, warp=0.05, g=1.0, cfl=0.25,
+               steps=50, forcing="none")
+
+WORKLOADS = {w.name: w for w in (LAKE_BUMP, MMS, DAM)}
+
+
+def scaled(w, nx, ny=None, N=None, steps=None):
+    """Same problem on another grid or degree (for small parity cases)."""
+    ny = nx if ny is None else ny
+    return dataclasses.replace(w, nx=nx, ny=ny, N=w.N if N is None else N,
+                               steps=w.steps if steps is None else steps)
+
+
+def random_modal_state(K, Np, seed, c0=2.8, amp_h=0.05, amp_m=0.05):
+    """Random modal coefficients [3][K][Np]: i.i.d. normal, scaled by
+    amp / (1 + mode index), with c0 added to the first (constant) mode of h.
+    For an orthonormal basis on the reference triangle (area 2) the constant
+    mode is 1/sqrt(2), so c0 = 2.8 gives a mean depth near 1.98 and keeps the
+    depth positive everywhere for the default amplitudes."""
+    rng = np.random.default_rng(seed)
+    decay = 1.0 / (1.0 + np.arange(Np))
+    u = rng.standard_normal((3, K, Np)) * decay[None, None, :]
+    u[0] *= amp_h
+    u[1:] *= amp_m
+    u[0, :, 0] += c0
+    return u
+
+
+def ensemble(n=64, seed=BASE_SEED):
+    """Batched-ensemble instances: N ~ U{2,3,4}, K ~ U{512,2048,8192,32768},
+    bathymetry amplitude ~ U[0.02,0.2], bump centre ~ U[-0.5,0.5]^2."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        N = int(rng.integers(2, 5))
+        nx = int(rng.choice([16, 32, 64, 128]))
+        amp = float(rng.uniform(0.02, 0.2))
+        c = rng.uniform(-0.5, 0.5, size=2)
+        out.append(dict(N=N, nx=nx, ny=nx, amp=amp, cx=float(c[0]), cy=float(c[1])))
+    return out
+
+
+def lake_at_rest_table_bathymetry(x, y):
+    """Bathymetry of the lake-at-rest experiment of Sec. 4.1 as printed:
+    b = 0.1 sin(2 pi x) cos(2 pi x) + 0.5 (periodic on [-1,1]^2)."""
+    return 0.1 * np.sin(2 * math.pi * x) * np.cos(2 * math.pi * x) + 0.5

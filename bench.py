@@ -1,0 +1,348 @@
+"""Benchmark: ESDG shallow-water right-hand side + LSRK45 on GB300.
+
+Workload (single large solve): N = 4, 256 x 256 quads -> K = 131072 curved
+triangles, smoothed dam break h = 1 + 0.5 tanh(40 (0.3 - r)), u = v = 0,
+b = 0.05 exp(-10((x-0.4)^2 + y^2)); FP32 right-hand side with FP64 RK
+accumulation.  A step is one LSRK45 step (five stages, each one pass of the
+whole per-stage path).  Metric: GDOF-stage/s = K * Np * 5 * steps / time / 1e9.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank runs an
+independent replica (the path has no exchange between separate solves), and
+value is the sum over ranks divided by the max time over ranks.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+# the CPU baseline is timed single-threaded; set before numpy is imported
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2005_02516_gb300 import workloads as W  # noqa: E402
+
+METRIC = "GDOF-stage/s FP32 vs FP64 per GB300 at stated L2 error; served p50/p99 latency"
+UNIT = "GDOF-stage/s"
+WL = W.DAM
+
+# Algorithmic work of one element-stage at degree N ("roofline").
+def algorithmic_flops(N):
+    Np = (N + 1) * (N + 2) // 2
+    Nq = (N + 1) ** 2
+    Nfq = 3 * (N + 1)
+    Nh = Nq + Nfq
+    pairs = Nq * (Nq - 1) // 2 + Nq * Nfq            # unique non-zero pairs of Q_skew
+    flops = 0
+    flops += 2 * Nq * Np * 3                          # u_q = Vq u
+    flops += 10 * Nq                                  # entropy variables
+    flops += 2 * Np * Nq * 3 + 3 * Nq + 2 * Np * Np * 3   # J-weighted projection
+    flops += 2 * Nh * Np * 3 + 6 * Nh                 # v~ = Vh v_h, u~ = u(v~)
+    flops += 35 * pairs                               # flux differencing (35 flops / unique pair)
+    flops += 40 * Nfq                                 # interface flux + Lax-Friedrichs
+    flops += 2 * Np * Nh * 3 + 2 * Np * Np * 3        # lift + inverse mass
+    flops += 4 * 3 * Np                               # RK stage (FP64)
+    return flops
+
+
+def algorithmic_bytes(N, real_bytes=4):
+    Np = (N + 1) * (N + 2) // 2
+    Nq = (N + 1) ** 2
+    Nfq = 3 * (N + 1)
+    Nh = Nq + Nfq
+    NpP = Np * (Np + 1) // 2
+    b = 0
+    b += 4 * 3 * Np * 8                 # u, res read + write (FP64)
+    b += 2 * Nh * 4 * real_bytes        # u~ read (own) + write (next stage)
+    b += Nfq * 3 * real_bytes           # neighbour traces (h, u, v)
+    b += Nh * 4 * real_bytes            # metrics rxJ sxJ ryJ syJ
+    b += Nq * real_bytes                # w_q J_q
+    b += NpP * real_bytes               # packed inverse mass matrix
+    b += Nh * real_bytes                # bathymetry at hybrid nodes
+    b += 3 * 4                          # neighbour ids
+    return b
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_solver(precision):
+    from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
+    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl)
+    xb, yb = s.points(ESDG_POINTS_NODAL)
+    xq, yq = s.points(ESDG_POINTS_VOLQ)
+    s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
+    return s
+
+
+def time_steps(s, steps, warmup, world):
+    """Device time of `steps` LSRK45 steps (CUDA events on the library's stream)."""
+    import torch
+    dt = s.dt()
+    s.step(warmup, dt, 0.0)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(s.stream)
+    s.step_async(steps, dt, warmup * dt)
+    ev1.record(s.stream)
+    ev1.synchronize()
+    s.check()
+    torch.cuda.synchronize()
+    barrier(world)
+    return ev0.elapsed_time(ev1) / 1e3
+
+
+def time_e2e(s, steps, warmup):
+    """Same metric through the public API with host buffers: per step, the
+    state goes host -> device, one LSRK45 step runs, and the state comes back."""
+    import torch
+    host_in = torch.empty((3, s.K, s.Np), dtype=torch.float64, pin_memory=True).numpy()
+    host_out = torch.empty((3, s.K, s.Np), dtype=torch.float64, pin_memory=True).numpy()
+    s.get_state(host_in)
+    dt = s.dt()
+    for _ in range(max(1, warmup)):
+        s.set_state(host_in)
+        s.step(1, dt, 0.0)
+        s.get_state(host_out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.set_state(host_in)
+        s.step(1, dt, 0.0)
+        s.get_state(host_out)
+        host_in, host_out = host_out, host_in
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    nbytes = host_in.nbytes
+    return el, nbytes
+
+
+def cpu_baseline(seconds_target=15.0):
+    """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
+    on a sample of 2048 consecutive elements of the same workload, repeated
+    until about `seconds_target` seconds of CPU work."""
+    from oracle import Oracle
+    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(WL.bathymetry(xb, yb))
+    xq, yq = o.points("volq")
+    u = o.init_state(WL.initial(xq, yq))
+    ks = np.arange(0, 2048)
+    o.rhs_elements(u, ks)
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        o.rhs_elements(u, ks)
+        n += 1
+        el = time.perf_counter() - t0
+        if el > seconds_target:
+            break
+    gdof = ks.size * o.Np * n / el / 1e9
+    return {"value": gdof, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d right-hand-side evaluations of elements 0..2047 of the K=131072 N=4 workload "
+                      "(FP64 numpy oracle, single thread), %.1f s" % (n, el)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cb = cpu_baseline(seconds_target=max(5.0, min(60.0, 3.0 * args.steps)))
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WL.name, "N": WL.N, "K": WL.K, "curved": True},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    peaks, peak_kind = load_peaks()
+
+    s = make_solver("fp32")
+    steps = args.steps
+    clocks = ClockSampler(local)
+    clocks.start()
+    el = time_steps(s, steps, args.warmup, world)
+    clk = clocks.stop()
+    el_max = max_over_ranks(el, world)
+    K, Np = s.K, s.Np
+    units = K * Np * 5 * steps
+    value = units * world / el_max / 1e9
+    launches = 5 * steps
+    t_launch = el / launches
+    flops = algorithmic_flops(WL.N) * K
+    nbytes = algorithmic_bytes(WL.N, 4) * K
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
+    alu = flops / t_launch / 1e12
+    hbm = nbytes / t_launch / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "stage_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("kernel_version") == "k_stage-v1":
+            traffic = tj.get("dram_bytes_per_launch")
+    roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
+                "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
+    roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": hbm / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind}
+    roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
+    other = roof_hbm if roofline is roof_alu else roof_alu
+
+    # FP64 right-hand side on the same workload (the plain FP64 path), a few steps
+    fp64 = None
+    s.close()
+    del s
+    s64 = make_solver("fp64")
+    st64 = max(2, steps // 10)
+    el64 = time_steps(s64, st64, 1, world)
+    fp64 = {"value": K * Np * 5 * st64 / el64 / 1e9, "unit": UNIT, "ms_per_step": el64 / st64 * 1e3,
+            "steps": st64}
+    s64.close()
+    del s64
+
+    e2e = None
+    if not args.no_e2e:
+        s = make_solver("fp32")
+        e_steps = max(5, steps // 5)
+        el_e, nb = time_e2e(s, e_steps, 2)
+        el_e = max_over_ranks(el_e, world)
+        e2e = {"value": K * Np * 5 * e_steps * world / el_e / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e_steps}
+        s.close()
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
+                "warmup": args.warmup, "ms_per_step": el_max / steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WL.name, "N": WL.N, "K": K, "Np": Np, "curved": True,
+                           "rhs_precision": "fp32", "rk_accumulation": "fp64",
+                           "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
+                           "parallelism": "replicas" if world > 1 else "single"},
+                "roofline": roofline, "roofline_other": other,
+                "fp64": fp64, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
+                "gpu_launches": launches, "peaks": peak_kind}
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

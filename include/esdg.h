@@ -1,0 +1,181 @@
+/*
+ * esdg.h -- C ABI of the GB300 entropy-stable DG (ESDG) shallow-water library.
+ *
+ * Method: Wu, Kubatko, Chan, "High-order entropy stable discontinuous Galerkin
+ * methods for the shallow water equations: curved triangular meshes and GPU
+ * acceleration" (arXiv 2005.02516).  The library evaluates the per-stage
+ * right-hand side of the modal ESDG scheme, eq. (dgform) of Sec. 2.8, and
+ * advances it with the low-storage RK45 scheme named in Sec. 4, on one GPU.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: ESDG_OK (0) or a negative code
+ *     below.  No call throws or aborts; esdg_last_error() gives a message.
+ *   - Host pointers are owned by the caller and are only read or written
+ *     during the call.  Device pointers named as such are owned by the caller
+ *     unless stated otherwise; library-owned device memory is released by
+ *     esdg_destroy().
+ *   - Arrays are dense, C order.  The state is u[field][element][mode], FP64,
+ *     fields (h, hu, hv), modes of the orthonormal Dubiner basis in the order
+ *     i = 0..N, j = 0..N-i (phi_ij = sqrt(2) P_i(a) P_j^(2i+1,0)(b) (1-b)^i,
+ *     a = 2(1+r)/(1-s) - 1, b = s).
+ *   - All work is enqueued on the stream given to esdg_attach_device(); calls
+ *     that return host data synchronise that stream.
+ */
+#ifndef ESDG_H
+#define ESDG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define ESDG_OK            0
+#define ESDG_EINVAL       -1  /* bad argument, unsupported size, malformed mesh */
+#define ESDG_ENOMEM       -2  /* host or device allocation failed / buffer too small */
+#define ESDG_ECUDA        -3  /* a CUDA runtime call failed (message names it) */
+#define ESDG_ENONPOSITIVE -4  /* the device found an entropy-projected depth <= 0 */
+#define ESDG_ENONFINITE   -5  /* the device found a non-finite value */
+#define ESDG_ESTATE       -6  /* call out of order (e.g. no device memory attached) */
+
+/* arithmetic of the right-hand side; state and RK accumulation are always FP64 */
+#define ESDG_FP64 0
+#define ESDG_FP32 1
+
+/* built-in forcing terms */
+#define ESDG_FORCING_NONE     0
+#define ESDG_FORCING_MMS_SINE 1  /* manufactured solution h = 2 + a sin(pi(x+y-t)), u=u0, v=v0,
+                                    b = bamp cos(pi x) cos(pi y): forcing added to du/dt */
+
+/* point sets for esdg_get_points */
+#define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
+#define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
+#define ESDG_POINTS_FACEQ 2  /* face quadrature points,    [K][Nfq] */
+
+/* esdg_init_state modes */
+#define ESDG_INIT_DEPTH   0  /* q[0] is the depth h */
+#define ESDG_INIT_SURFACE 1  /* q[0] is the free surface H = h + b (exact lake at rest) */
+
+typedef struct esdg_config {
+    int N;                  /* polynomial degree, 1..5 */
+    int precision;          /* ESDG_FP64 or ESDG_FP32 right-hand-side arithmetic */
+    int nx, ny;             /* quads of the structured grid, each >= 3; K = 2 nx ny triangles */
+    double x0, x1, y0, y1;  /* periodic domain [x0,x1] x [y0,y1] */
+    double warp_ax, warp_ay;/* curving amplitudes (0 = affine mesh), see below */
+    double g;               /* gravity */
+    double cfl;             /* dt = cfl * ((x1-x0)/nx) / ((N+1)(N+2)/2), Sec. 4 */
+    int lax_friedrichs;     /* 1: add the local Lax-Friedrichs penalty (entropy stable),
+                               0: entropy-conservative flux alone */
+    int forcing;            /* ESDG_FORCING_* */
+    double mms_amp, mms_bamp, mms_u0, mms_v0;  /* ESDG_FORCING_MMS_SINE parameters */
+} esdg_config;
+
+/*
+ * Mesh: quad (i,j), q = j*nx + i, splits along its lower-left to upper-right
+ * diagonal into elements 2q = (v(i,j), v(i+1,j), v(i+1,j+1)) and
+ * 2q+1 = (v(i,j), v(i+1,j+1), v(i,j+1)), mapped from the reference vertices
+ * (-1,-1), (1,-1), (-1,1).  Curved elements: the degree-N equispaced nodes of
+ * each affine element are moved by, with xi = 2(x-xc)/Lx, eta = 2(y-yc)/Ly,
+ *     x += warp_ax * Lx/2 * cos(pi xi / 2) cos(3 pi eta / 2)
+ *     y += warp_ay * Ly/2 * sin(2 pi xi)   cos(pi eta / 2)
+ * and the element map is their degree-N interpolant (Sec. 2.7, Sec. 4).
+ */
+
+typedef struct esdg_ctx esdg_ctx;
+
+/*
+ * esdg_build_operators -- build on the host, in FP64, the reference-element
+ * operators of Sec. 2.1-2.3 (V_q, V_f, P_q, Q-hat, hybridized Q_h), the mesh,
+ * the geometric factors and (M_h^k)^{-1} of Sec. 2.7.  Validates J > 0 at every
+ * quadrature node and that every face node has a matching neighbour node
+ * (ESDG_EINVAL otherwise).  *out receives a new context; no device work.
+ */
+int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out);
+
+/* Sizes: K elements, Np modes, Nq volume and Nfq face quadrature points, and
+ * the device bytes that esdg_attach_device() needs.  Any pointer may be NULL. */
+int esdg_sizes(const esdg_ctx* ctx, int* K, int* Np, int* Nq, int* Nfq, size_t* device_bytes);
+
+/*
+ * esdg_attach_device -- give the library its device memory and stream, and
+ * upload operators and geometry.  device_buffer: caller-owned device memory of
+ * at least esdg_sizes(...device_bytes) bytes, 256-byte aligned, kept alive
+ * until esdg_destroy(); or NULL, in which case the library allocates (and later
+ * frees) that memory itself.  stream: a cudaStream_t (NULL = legacy default).
+ */
+int esdg_attach_device(esdg_ctx* ctx, void* device_buffer, size_t bytes, void* stream);
+
+/* Physical coordinates of a point set (ESDG_POINTS_*), host arrays [K][n]. */
+int esdg_get_points(const esdg_ctx* ctx, int kind, double* x, double* y);
+
+/*
+ * esdg_init_state -- set bathymetry and initial state from host arrays.
+ * b_nodal [K][Np]: bathymetry at the ESDG_POINTS_NODAL points; b is the degree-N
+ * polynomial through these values on each element (C0 across elements when
+ * shared nodes carry equal values, Sec. 4.1).  q_volq [3][K][Nq]: (h or H, hu,
+ * hv) at the volume quadrature points, L2-projected with the J-weighted mass
+ * matrix (Sec. 2.7).  mode ESDG_INIT_SURFACE sets h = Pi(H) - b so a lake at rest
+ * is exact.  Resets the RK residual.
+ */
+int esdg_init_state(esdg_ctx* ctx, const double* b_nodal, const double* q_volq, int mode);
+
+/* Bathymetry alone (b_nodal as above); keeps the state. */
+int esdg_set_bathymetry(esdg_ctx* ctx, const double* b_nodal);
+
+/* Overwrite the modal state u [3][K][Np] FP64 from host (on_device = 0) or
+ * device (on_device = 1) memory; resets the RK residual. */
+int esdg_set_state(esdg_ctx* ctx, const double* u, int on_device);
+
+/* Copy the modal state out, to host (on_device = 0) or device memory. */
+int esdg_copy_state(const esdg_ctx* ctx, double* u, int on_device);
+
+/*
+ * esdg_rhs -- one evaluation of the semi-discrete right-hand side du/dt of
+ * eq. (dgform) (Sec. 2.8) at time t: entropy projection (Sec. 2.6), flux
+ * differencing with the entropy-conservative SWE flux and its well-balanced
+ * bathymetry term, interface flux plus Lax-Friedrichs, lift and inverse curved
+ * mass matrix, plus the forcing if configured.  u_in: device [3][K][Np] FP64 or
+ * NULL for the current state.  rhs_out: device [3][K][Np] FP64.  Synchronises
+ * the stream and returns ESDG_ENONPOSITIVE / ESDG_ENONFINITE if the device
+ * flagged a bad entropy-projected state.
+ */
+int esdg_rhs(esdg_ctx* ctx, double t, const double* u_in, double* rhs_out);
+
+/*
+ * esdg_step -- advance the current state by nsteps LSRK45 steps (five stages
+ * each, Carpenter-Kennedy 2N-storage, Sec. 4) of size dt (dt <= 0: the CFL
+ * rule of Sec. 4).  *t_inout is advanced.  The residual persists between
+ * calls.  Synchronises the stream once at the end and reports device flags.
+ */
+int esdg_step(esdg_ctx* ctx, int nsteps, double dt, double* t_inout);
+
+/* Enqueue nsteps steps without synchronising or checking flags (for timing
+ * loops and graph capture); esdg_check() reads the flags later. */
+int esdg_step_async(esdg_ctx* ctx, int nsteps, double dt, double t0);
+int esdg_check(esdg_ctx* ctx);
+
+/*
+ * esdg_entropy -- FP64 diagnostics of the current state (Sec. 2.4):
+ * entropy = sum_k sum_q w_q J_q S(u_q), mass = sum_k sum_q w_q J_q h_q, and, if
+ * entropy_rate is not NULL, the semi-discrete entropy rate
+ * sum_k sum_q w_q J_q v(u_q) . (V_q du/dt)_q at time t (zero for the
+ * entropy-conservative flux on a periodic mesh, Theorem 2.2).
+ */
+int esdg_entropy(esdg_ctx* ctx, double t, double* entropy, double* mass, double* entropy_rate);
+
+/* The CFL time step of Sec. 4 for this configuration. */
+int esdg_dt(const esdg_ctx* ctx, double* dt);
+
+/* Release the context and any library-owned device memory. */
+int esdg_destroy(esdg_ctx* ctx);
+
+/* Message for the last failing call on ctx (ctx may be NULL for
+ * esdg_build_operators failures).  The string lives until the next call. */
+const char* esdg_last_error(const esdg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESDG_H */

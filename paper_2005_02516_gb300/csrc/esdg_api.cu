@@ -1,0 +1,584 @@
+// C ABI of the ESDG shallow-water library (see include/esdg.h).
+// Host set-up builds the FP64 operators and geometry once (host_build.cpp);
+// all per-stage work runs in the kernels of esdg_kernels.cuh.
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/esdg.h"
+#include "esdg_launch.hpp"
+#include "host_build.hpp"
+
+namespace esdg {
+
+// Carpenter & Kennedy (1994) five-stage fourth-order 2N-storage coefficients
+// (the integrator of Sec. 4).
+static const double RK_A[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                               -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+static const double RK_B[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                               1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                               2277821191437.0 / 14882151754819.0};
+static const double RK_C[5] = {0.0, 1432997174477.0 / 9575080441755.0, 2526269341429.0 / 6820363962896.0,
+                               2006345519317.0 / 3224310063776.0, 2802321613138.0 / 2924317926251.0};
+
+__global__ void k_entropy_finalize(int nparts, const double* __restrict__ partial, double* __restrict__ out) {
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int i = 0; i < nparts; ++i) s += partial[i * 3 + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+}  // namespace esdg
+
+using namespace esdg;
+
+// Device memory map (offsets into one buffer, each 256-byte aligned).
+struct DevLayout {
+    size_t ops = 0, ops_bytes = 0;       // reference operators (real)
+    size_t vq64 = 0;                     // Vq FP64 (diagnostics)
+    size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
+    size_t wJq64 = 0, bq64 = 0;
+    size_t u = 0, res = 0, rhs = 0, ut0 = 0, ut1 = 0;
+    size_t partial = 0, diag = 0, status = 0;
+    size_t total = 0;
+};
+
+struct esdg_ctx {
+    esdg_config cfg;
+    RefOps ref;
+    MeshData mesh;
+    std::vector<double> b_modal;  // [K][Np]
+    std::string err;
+    // device
+    bool attached = false;
+    bool owns_buffer = false;
+    unsigned char* dbuf = nullptr;
+    cudaStream_t stream = nullptr;
+    DevLayout L;
+    LaunchGeom lg;
+    int entropy_parts = 0;
+    int num_sms = 0;
+    int cur = 0;            // which u~ buffer holds the current stage's values
+    bool ut_valid = false;  // u~ buffer current for the state u
+};
+
+static thread_local std::string g_build_error;
+
+static int fail(esdg_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg; else g_build_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                         \
+    do {                                                                                            \
+        cudaError_t e__ = (call);                                                                   \
+        if (e__ != cudaSuccess)                                                                     \
+            return fail((ctx), ESDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__));   \
+    } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static size_t real_size(const esdg_ctx* c) { return c->cfg.precision == ESDG_FP32 ? 4 : 8; }
+
+static void compute_layout(esdg_ctx* c) {
+    const RefOps& R = c->ref;
+    const size_t rs = real_size(c);
+    const size_t K = size_t(c->mesh.K);
+    const int NpP = R.Np * (R.Np + 1) / 2;
+    DevLayout& L = c->L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
+    L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq));
+    L.ops = take(L.ops_bytes);
+    L.vq64 = take(8 * size_t(R.Nq) * R.Np);
+    L.geo = take(rs * K * R.Nh * 4);
+    L.wJq = take(rs * K * R.Nq);
+    L.minv = take(rs * K * NpP);
+    L.bh = take(rs * K * R.Nh);
+    L.nbr = take(4 * K * 3);
+    const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
+    L.xq = take(forcing ? rs * K * R.Nq : 0);
+    L.yq = take(forcing ? rs * K * R.Nq : 0);
+    L.wJq64 = take(8 * K * R.Nq);
+    L.bq64 = take(8 * K * R.Nq);
+    L.u = take(8 * 3 * K * R.Np);
+    L.res = take(8 * 3 * K * R.Np);
+    L.rhs = take(8 * 3 * K * R.Np);
+    L.ut0 = take(rs * K * R.Nh * 4);
+    L.ut1 = take(rs * K * R.Nh * 4);
+    c->entropy_parts = 1024;
+    L.partial = take(8 * 3 * size_t(c->entropy_parts));
+    L.diag = take(8 * 4);
+    L.status = take(4 * 4);
+    L.total = off;
+}
+
+template <typename real>
+static std::vector<real> to_real(const std::vector<double>& v) {
+    return std::vector<real>(v.begin(), v.end());
+}
+
+template <typename real>
+static std::vector<real> pack_ops(const RefOps& R) {
+    // order must match Smem<N, real>: QsT, Vq, VqT, Vh, VhT, wf, nrs
+    std::vector<real> o;
+    o.reserve(size_t(R.Nh) * R.Nh * 2 + 4 * size_t(R.Nh) * R.Np);
+    for (int m = 0; m < R.Nh; ++m)
+        for (int l = 0; l < R.Nh; ++l) {
+            o.push_back((real)R.Qsr(l, m));
+            o.push_back((real)R.Qss(l, m));
+        }
+    for (int q = 0; q < R.Nq; ++q)
+        for (int n = 0; n < R.Np; ++n) o.push_back((real)R.Vq(q, n));
+    for (int n = 0; n < R.Np; ++n)
+        for (int q = 0; q < R.Nq; ++q) o.push_back((real)R.Vq(q, n));
+    for (int l = 0; l < R.Nh; ++l)
+        for (int n = 0; n < R.Np; ++n) o.push_back((real)R.Vh(l, n));
+    for (int n = 0; n < R.Np; ++n)
+        for (int l = 0; l < R.Nh; ++l) o.push_back((real)R.Vh(l, n));
+    for (int f = 0; f < R.Nfq; ++f) o.push_back((real)R.wf[f]);
+    for (int f = 0; f < R.Nfq; ++f) {
+        o.push_back((real)R.nr[f]);
+        o.push_back((real)R.ns[f]);
+    }
+    return o;
+}
+
+template <typename real>
+static int upload_static(esdg_ctx* c) {
+    const RefOps& R = c->ref;
+    const MeshData& M = c->mesh;
+    const size_t K = size_t(M.K);
+    unsigned char* d = c->dbuf;
+    cudaStream_t s = c->stream;
+    std::vector<real> ops = pack_ops<real>(R);
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.ops, ops.data(), ops.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.vq64, R.Vq.a.data(), R.Vq.a.size() * 8, cudaMemcpyHostToDevice, s));
+    std::vector<real> geo = to_real<real>(M.geo);
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.geo, geo.data(), geo.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    std::vector<double> wJ64(K * R.Nq);
+    for (size_t e = 0; e < K; ++e)
+        for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
+    std::vector<real> wJ = to_real<real>(wJ64);
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq, wJ.data(), wJ.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq64, wJ64.data(), wJ64.size() * 8, cudaMemcpyHostToDevice, s));
+    std::vector<real> mi = to_real<real>(M.minv);
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.minv, mi.data(), mi.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.nbr, M.nbr.data(), M.nbr.size() * 4, cudaMemcpyHostToDevice, s));
+    if (c->cfg.forcing != ESDG_FORCING_NONE) {
+        std::vector<real> xq = to_real<real>(M.xq), yq = to_real<real>(M.yq);
+        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.xq, xq.data(), xq.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.yq, yq.data(), yq.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(s));
+    return ESDG_OK;
+}
+
+template <typename real>
+static int upload_bathymetry_t(esdg_ctx* c) {
+    const RefOps& R = c->ref;
+    const size_t K = size_t(c->mesh.K);
+    std::vector<double> bh(K * R.Nh), bq(K * R.Nq);
+    for (size_t e = 0; e < K; ++e)
+        for (int l = 0; l < R.Nh; ++l) {
+            double s = 0;
+            for (int n = 0; n < R.Np; ++n) s += R.Vh(l, n) * c->b_modal[e * R.Np + n];
+            bh[e * R.Nh + l] = s;
+            if (l < R.Nq) bq[e * R.Nq + l] = s;
+        }
+    std::vector<real> bhr = to_real<real>(bh);
+    CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.bh, bhr.data(), bhr.size() * sizeof(real), cudaMemcpyHostToDevice,
+                                c->stream));
+    CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.bq64, bq.data(), bq.size() * 8, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->ut_valid = false;
+    return ESDG_OK;
+}
+
+static int upload_bathymetry(esdg_ctx* c) {
+    return c->cfg.precision == ESDG_FP32 ? upload_bathymetry_t<float>(c) : upload_bathymetry_t<double>(c);
+}
+
+template <typename real>
+static StageParams<real> make_params(esdg_ctx* c) {
+    StageParams<real> p;
+    std::memset(&p, 0, sizeof(p));
+    const RefOps& R = c->ref;
+    unsigned char* d = c->dbuf;
+    p.K = c->mesh.K;
+    p.g = (real)c->cfg.g;
+    p.lf = c->cfg.lax_friedrichs;
+    real* ops = reinterpret_cast<real*>(d + c->L.ops);
+    p.QsT = ops;
+    p.Vq = p.QsT + size_t(R.Nh) * R.Nh * 2;
+    p.VqT = p.Vq + size_t(R.Nq) * R.Np;
+    p.Vh = p.VqT + size_t(R.Np) * R.Nq;
+    p.VhT = p.Vh + size_t(R.Nh) * R.Np;
+    p.wf = p.VhT + size_t(R.Np) * R.Nh;
+    p.nrs = p.wf + R.Nfq;
+    p.geo = reinterpret_cast<const real*>(d + c->L.geo);
+    p.wJq = reinterpret_cast<const real*>(d + c->L.wJq);
+    p.minv = reinterpret_cast<const real*>(d + c->L.minv);
+    p.bh = reinterpret_cast<const real*>(d + c->L.bh);
+    p.nbr = reinterpret_cast<const int*>(d + c->L.nbr);
+    p.xq = reinterpret_cast<const real*>(d + c->L.xq);
+    p.yq = reinterpret_cast<const real*>(d + c->L.yq);
+    p.u = reinterpret_cast<double*>(d + c->L.u);
+    p.u_in = p.u;
+    p.res = reinterpret_cast<double*>(d + c->L.res);
+    p.rhs_out = reinterpret_cast<double*>(d + c->L.rhs);
+    p.forcing = c->cfg.forcing;
+    p.mms_amp = (real)c->cfg.mms_amp;
+    p.mms_bamp = (real)c->cfg.mms_bamp;
+    p.mms_u0 = (real)c->cfg.mms_u0;
+    p.mms_v0 = (real)c->cfg.mms_v0;
+    p.status = reinterpret_cast<int*>(d + c->L.status);
+    return p;
+}
+
+template <typename real>
+static real* ut_buf(esdg_ctx* c, int which) {
+    return reinterpret_cast<real*>(c->dbuf + (which == 0 ? c->L.ut0 : c->L.ut1));
+}
+
+// ---- degree dispatch ---------------------------------------------------------
+template <typename real>
+static cudaError_t d_geometry(int N, int sms, LaunchGeom& lg) {
+    switch (N) {
+        case 1: return stage_geometry<1, real>(sms, lg);
+        case 2: return stage_geometry<2, real>(sms, lg);
+        case 3: return stage_geometry<3, real>(sms, lg);
+        case 4: return stage_geometry<4, real>(sms, lg);
+        default: return stage_geometry<5, real>(sms, lg);
+    }
+}
+template <typename real>
+static cudaError_t d_project(int N, const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_project<1, real>(p, lg, s);
+        case 2: return launch_project<2, real>(p, lg, s);
+        case 3: return launch_project<3, real>(p, lg, s);
+        case 4: return launch_project<4, real>(p, lg, s);
+        default: return launch_project<5, real>(p, lg, s);
+    }
+}
+template <typename real>
+static cudaError_t d_stage(int N, const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_stage<1, real>(p, mode, lg, s);
+        case 2: return launch_stage<2, real>(p, mode, lg, s);
+        case 3: return launch_stage<3, real>(p, mode, lg, s);
+        case 4: return launch_stage<4, real>(p, mode, lg, s);
+        default: return launch_stage<5, real>(p, mode, lg, s);
+    }
+}
+static cudaError_t d_entropy(int N, int K, double g, const double* u, const double* rhs, const double* Vq,
+                             const double* wJq, const double* bq, double* partial, int nparts, double* out,
+                             cudaStream_t s) {
+    switch (N) {
+        case 1: return launch_entropy<1>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+        case 2: return launch_entropy<2>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+        case 3: return launch_entropy<3>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+        case 4: return launch_entropy<4>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+        default: return launch_entropy<5>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+    }
+}
+
+static int check_status(esdg_ctx* c) {
+    int st[1] = {0};
+    int* dst = reinterpret_cast<int*>(c->dbuf + c->L.status);
+    CUDA_TRY(c, cudaMemcpyAsync(st, dst, 4, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (st[0]) {
+        CUDA_TRY(c, cudaMemsetAsync(dst, 0, 4, c->stream));
+        if (st[0] & STATUS_NONFINITE) return fail(c, ESDG_ENONFINITE, "non-finite entropy-projected state");
+        return fail(c, ESDG_ENONPOSITIVE, "non-positive (entropy-projected) depth");
+    }
+    return ESDG_OK;
+}
+
+template <typename real>
+static int project_current(esdg_ctx* c, const double* u_in, int target) {
+    StageParams<real> p = make_params<real>(c);
+    if (u_in) p.u_in = u_in;
+    p.ut_out = ut_buf<real>(c, target);
+    CUDA_TRY(c, d_project<real>(c->cfg.N, p, c->lg, c->stream));
+    return ESDG_OK;
+}
+
+template <typename real>
+static int rhs_t(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
+    int rc = project_current<real>(c, u_in, c->cur ^ 1);
+    if (rc) return rc;
+    StageParams<real> p = make_params<real>(c);
+    p.ut_in = ut_buf<real>(c, c->cur ^ 1);
+    p.rhs_out = rhs_out;
+    p.t = t;
+    CUDA_TRY(c, d_stage<real>(c->cfg.N, p, 0, c->lg, c->stream));
+    return ESDG_OK;
+}
+
+template <typename real>
+static int step_t(esdg_ctx* c, int nsteps, double dt, double t0) {
+    if (!c->ut_valid) {
+        int rc = project_current<real>(c, nullptr, c->cur);
+        if (rc) return rc;
+        c->ut_valid = true;
+    }
+    StageParams<real> p = make_params<real>(c);
+    p.dt = dt;
+    for (int n = 0; n < nsteps; ++n)
+        for (int s = 0; s < 5; ++s) {
+            p.ut_in = ut_buf<real>(c, c->cur);
+            p.ut_out = ut_buf<real>(c, c->cur ^ 1);
+            p.rkA = RK_A[s];
+            p.rkB = RK_B[s];
+            p.t = t0 + n * dt + RK_C[s] * dt;
+            CUDA_TRY(c, d_stage<real>(c->cfg.N, p, 1, c->lg, c->stream));
+            c->cur ^= 1;
+        }
+    return ESDG_OK;
+}
+
+static bool valid(const esdg_ctx* c) { return c != nullptr; }
+
+extern "C" {
+
+int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
+    if (!cfg || !out) return fail(nullptr, ESDG_EINVAL, "null argument");
+    *out = nullptr;
+    if (cfg->N < 1 || cfg->N > 5) return fail(nullptr, ESDG_EINVAL, "N must be in 1..5");
+    if (cfg->precision != ESDG_FP32 && cfg->precision != ESDG_FP64)
+        return fail(nullptr, ESDG_EINVAL, "precision must be ESDG_FP32 or ESDG_FP64");
+    if (!(cfg->g > 0)) return fail(nullptr, ESDG_EINVAL, "g must be positive");
+    if (cfg->forcing != ESDG_FORCING_NONE && cfg->forcing != ESDG_FORCING_MMS_SINE)
+        return fail(nullptr, ESDG_EINVAL, "unknown forcing");
+    esdg_ctx* c = new (std::nothrow) esdg_ctx();
+    if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
+    c->cfg = *cfg;
+    std::string err;
+    if (!build_reference(cfg->N, c->ref, err)) {
+        delete c;
+        return fail(nullptr, ESDG_EINVAL, err);
+    }
+    MeshSpec sp{cfg->nx, cfg->ny, cfg->x0, cfg->x1, cfg->y0, cfg->y1, cfg->warp_ax, cfg->warp_ay};
+    if (!build_mesh(c->ref, sp, c->mesh, err)) {
+        delete c;
+        return fail(nullptr, ESDG_EINVAL, err);
+    }
+    c->b_modal.assign(size_t(c->mesh.K) * c->ref.Np, 0.0);
+    compute_layout(c);
+    *out = c;
+    return ESDG_OK;
+}
+
+int esdg_sizes(const esdg_ctx* c, int* K, int* Np, int* Nq, int* Nfq, size_t* device_bytes) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (K) *K = c->mesh.K;
+    if (Np) *Np = c->ref.Np;
+    if (Nq) *Nq = c->ref.Nq;
+    if (Nfq) *Nfq = c->ref.Nfq;
+    if (device_bytes) *device_bytes = c->L.total;
+    return ESDG_OK;
+}
+
+int esdg_attach_device(esdg_ctx* c, void* buffer, size_t bytes, void* stream) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (c->attached) return fail(c, ESDG_ESTATE, "device memory already attached");
+    c->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (buffer) {
+        if (bytes < c->L.total) return fail(c, ESDG_ENOMEM, "device buffer smaller than esdg_sizes() requires");
+        if (reinterpret_cast<uintptr_t>(buffer) % 256) return fail(c, ESDG_EINVAL, "device buffer not 256-byte aligned");
+        c->dbuf = reinterpret_cast<unsigned char*>(buffer);
+        c->owns_buffer = false;
+    } else {
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, c->L.total);
+        if (e != cudaSuccess) return fail(c, ESDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        c->dbuf = reinterpret_cast<unsigned char*>(p);
+        c->owns_buffer = true;
+    }
+    int dev = 0;
+    CUDA_TRY(c, cudaGetDevice(&dev));
+    CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(c, cudaMemsetAsync(c->dbuf, 0, c->L.total, c->stream));
+    int rc;
+    if (c->cfg.precision == ESDG_FP32) {
+        CUDA_TRY(c, d_geometry<float>(c->cfg.N, c->num_sms, c->lg));
+        rc = upload_static<float>(c);
+    } else {
+        CUDA_TRY(c, d_geometry<double>(c->cfg.N, c->num_sms, c->lg));
+        rc = upload_static<double>(c);
+    }
+    if (rc) return rc;
+    c->attached = true;
+    return upload_bathymetry(c);
+}
+
+int esdg_get_points(const esdg_ctx* c, int kind, double* x, double* y) {
+    if (!valid(c) || !x || !y) return fail(nullptr, ESDG_EINVAL, "null argument");
+    const MeshData& M = c->mesh;
+    const std::vector<double>*px, *py;
+    if (kind == ESDG_POINTS_NODAL) { px = &M.xeq; py = &M.yeq; }
+    else if (kind == ESDG_POINTS_VOLQ) { px = &M.xq; py = &M.yq; }
+    else if (kind == ESDG_POINTS_FACEQ) { px = &M.xf; py = &M.yf; }
+    else return fail(const_cast<esdg_ctx*>(c), ESDG_EINVAL, "unknown point set");
+    std::memcpy(x, px->data(), px->size() * 8);
+    std::memcpy(y, py->data(), py->size() * 8);
+    return ESDG_OK;
+}
+
+int esdg_set_bathymetry(esdg_ctx* c, const double* b_nodal) {
+    if (!valid(c) || !b_nodal) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    const RefOps& R = c->ref;
+    const size_t K = size_t(c->mesh.K);
+    for (size_t e = 0; e < K; ++e)
+        for (int n = 0; n < R.Np; ++n) {
+            double s = 0;
+            for (int m = 0; m < R.Np; ++m) s += R.Veq_inv(n, m) * b_nodal[e * R.Np + m];
+            c->b_modal[e * R.Np + n] = s;
+        }
+    return upload_bathymetry(c);
+}
+
+int esdg_init_state(esdg_ctx* c, const double* b_nodal, const double* q_volq, int mode) {
+    if (!valid(c) || !q_volq) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (mode != ESDG_INIT_DEPTH && mode != ESDG_INIT_SURFACE) return fail(c, ESDG_EINVAL, "unknown init mode");
+    if (b_nodal) {
+        int rc = esdg_set_bathymetry(c, b_nodal);
+        if (rc) return rc;
+    }
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    const RefOps& R = c->ref;
+    const MeshData& M = c->mesh;
+    const size_t K = size_t(M.K);
+    const int NpP = R.Np * (R.Np + 1) / 2;
+    std::vector<double> u(3 * K * R.Np), y(R.Np);
+    for (int f = 0; f < 3; ++f)
+        for (size_t e = 0; e < K; ++e) {
+            for (int n = 0; n < R.Np; ++n) {
+                double s = 0;
+                for (int q = 0; q < R.Nq; ++q)
+                    s += R.Vq(q, n) * R.wq[q] * M.Jq[e * R.Nq + q] * q_volq[(f * K + e) * R.Nq + q];
+                y[n] = s;
+            }
+            const double* mi = &M.minv[e * NpP];
+            for (int n = 0; n < R.Np; ++n) {
+                double s = 0;
+                for (int j = 0; j < R.Np; ++j) s += mi[n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n] * y[j];
+                if (f == 0 && mode == ESDG_INIT_SURFACE) s -= c->b_modal[e * R.Np + n];
+                u[(f * K + e) * R.Np + n] = s;
+            }
+        }
+    return esdg_set_state(c, u.data(), 0);
+}
+
+int esdg_set_state(esdg_ctx* c, const double* u, int on_device) {
+    if (!valid(c) || !u) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ref.Np;
+    CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.u, u, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->dbuf + c->L.res, 0, bytes, c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->ut_valid = false;
+    return ESDG_OK;
+}
+
+int esdg_copy_state(const esdg_ctx* cc, double* u, int on_device) {
+    esdg_ctx* c = const_cast<esdg_ctx*>(cc);
+    if (!valid(c) || !u) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ref.Np;
+    CUDA_TRY(c, cudaMemcpyAsync(u, c->dbuf + c->L.u, bytes,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+    if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return ESDG_OK;
+}
+
+int esdg_rhs(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
+    if (!valid(c) || !rhs_out) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    int rc = c->cfg.precision == ESDG_FP32 ? rhs_t<float>(c, t, u_in, rhs_out) : rhs_t<double>(c, t, u_in, rhs_out);
+    if (rc) return rc;
+    return check_status(c);
+}
+
+int esdg_step_async(esdg_ctx* c, int nsteps, double dt, double t0) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (nsteps < 0) return fail(c, ESDG_EINVAL, "nsteps < 0");
+    if (!(dt > 0)) esdg_dt(c, &dt);
+    return c->cfg.precision == ESDG_FP32 ? step_t<float>(c, nsteps, dt, t0) : step_t<double>(c, nsteps, dt, t0);
+}
+
+int esdg_check(esdg_ctx* c) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    return check_status(c);
+}
+
+int esdg_step(esdg_ctx* c, int nsteps, double dt, double* t_inout) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!(dt > 0)) esdg_dt(c, &dt);
+    double t0 = t_inout ? *t_inout : 0.0;
+    int rc = esdg_step_async(c, nsteps, dt, t0);
+    if (rc) return rc;
+    rc = check_status(c);
+    if (rc) return rc;
+    if (t_inout) *t_inout = t0 + nsteps * dt;
+    return ESDG_OK;
+}
+
+int esdg_entropy(esdg_ctx* c, double t, double* entropy, double* mass, double* entropy_rate) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    const double* rhs = nullptr;
+    if (entropy_rate) {
+        double* r = reinterpret_cast<double*>(c->dbuf + c->L.rhs);
+        int rc = esdg_rhs(c, t, nullptr, r);
+        if (rc) return rc;
+        rhs = r;
+    }
+    double* out = reinterpret_cast<double*>(c->dbuf + c->L.diag);
+    CUDA_TRY(c, d_entropy(c->cfg.N, c->mesh.K, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u), rhs,
+                          reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
+                          reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                          reinterpret_cast<const double*>(c->dbuf + c->L.bq64),
+                          reinterpret_cast<double*>(c->dbuf + c->L.partial), c->entropy_parts, out, c->stream));
+    double h[3];
+    CUDA_TRY(c, cudaMemcpyAsync(h, out, 24, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (entropy) *entropy = h[0];
+    if (mass) *mass = h[1];
+    if (entropy_rate) *entropy_rate = h[2];
+    return ESDG_OK;
+}
+
+int esdg_dt(const esdg_ctx* c, double* dt) {
+    if (!valid(c) || !dt) return fail(nullptr, ESDG_EINVAL, "null argument");
+    const int N = c->cfg.N;
+    double CN = 0.5 * (N + 1) * (N + 2);
+    *dt = c->cfg.cfl * ((c->cfg.x1 - c->cfg.x0) / c->cfg.nx) / CN;
+    return ESDG_OK;
+}
+
+int esdg_destroy(esdg_ctx* c) {
+    if (!c) return ESDG_OK;
+    if (c->owns_buffer && c->dbuf) cudaFree(c->dbuf);
+    delete c;
+    return ESDG_OK;
+}
+
+const char* esdg_last_error(const esdg_ctx* c) {
+    return c ? c->err.c_str() : g_build_error.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,503 @@
+// CUDA kernels of the ESDG shallow-water right-hand side and LSRK45 stage
+// (Wu, Kubatko, Chan, arXiv 2005.02516).  Written for sm_103a.
+//
+// Per RK stage one fused kernel does, per element (a warp per element):
+//   volume flux differencing with the entropy-conservative SWE flux
+//   (eqs. (SWE_flux1/2)) and its well-balanced bathymetry term, on the skew
+//   hybridized operator of Sec. 5.2 (Q_skew = Q_h - Q_h^T, whose lower-right
+//   block is zero and skipped), with the curved metric average of Sec. 2.7;
+//   the interface flux f_S(u~+, u~) with Lax-Friedrichs (Sec. 2.8);
+//   the lift V_h^T and the stored inverse curved mass matrix (Sec. 2.7, 5.1);
+//   the LSRK45 stage update in FP64 (Sec. 4);
+//   and the entropy projection (Sec. 2.6) of the updated state, written for
+//   the next stage (its face values are what neighbours read).
+//
+// Algebra used by the volume loop.  With sums over the pair (l, m)
+//   HU = hu_l + hu_m, HV = hv_l + hv_m, U = u_l + u_m, V = v_l + v_m,
+// and the metric average folded into the operator entries
+//   Qx = 1/4 Qskew^x[l,m] = qr (rx_l + rx_m) + qs (sx_l + sx_m), (metrics / 8)
+// the row-l contribution of Qskew^x o F^x + Qskew^y o F^y is
+//   h  : 2 (Qx HU + Qy HV)
+//   hu : U (Qx HU + Qy HV) + Qx * 2 g h_l H_m
+//   hv : V (Qx HU + Qy HV) + Qy * 2 g h_l H_m
+// where the pressure g{h}^2 - g{h^2}/2 = g h_l h_m / 2 and the source
+// -g h~ (1/2 Qskew b) combine into g/2 h_l (h_m + b_m) = g/2 h_l H_m.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace esdg {
+
+template <int N>
+struct Dims {
+    static constexpr int Np = (N + 1) * (N + 2) / 2;
+    static constexpr int Nq = (N + 1) * (N + 1);
+    static constexpr int Nfp = N + 1;
+    static constexpr int Nfq = 3 * (N + 1);
+    static constexpr int Nh = Nq + Nfq;
+    static constexpr int NpP = Np * (Np + 1) / 2;
+};
+
+// status bits written by the device
+constexpr int STATUS_NONPOSITIVE = 1;
+constexpr int STATUS_NONFINITE = 2;
+
+template <typename real>
+struct StageParams {
+    int K;
+    real g;
+    int lf;
+    // reference operators (global, staged into shared memory)
+    const real* QsT;   // [Nh(m)][Nh(l)][2]: (Qskew^r[l][m], Qskew^s[l][m])
+    const real* Vq;    // [Nq][Np]
+    const real* VqT;   // [Np][Nq]
+    const real* Vh;    // [Nh][Np]
+    const real* VhT;   // [Np][Nh]
+    const real* wf;    // [Nfq]
+    const real* nrs;   // [Nfq][2] scaled reference normals
+    // per element
+    const real* geo;   // [K][Nh][4] rxJ sxJ ryJ syJ
+    const real* wJq;   // [K][Nq]   w_q J_q
+    const real* minv;  // [K][NpP]  packed (M_h^k)^{-1}
+    const real* bh;    // [K][Nh]   bathymetry at hybrid nodes
+    const int* nbr;    // [K][3]    4 * neighbour element + neighbour face
+    const real* xq;    // [K][Nq]   (forcing only)
+    const real* yq;
+    // state
+    const double* u_in;  // [3][K][Np]  (projection input)
+    double* u;           // [3][K][Np]  RK state (updated in place)
+    double* res;         // [3][K][Np]  RK residual
+    double* rhs_out;     // [3][K][Np]  RHS mode output
+    const real* ut_in;   // [K][Nh][4]  entropy-projected (h, u, v, H) of this stage
+    real* ut_out;        // [K][Nh][4]  ... of the next stage
+    double rkA, rkB, dt, t;
+    int forcing;
+    real mms_amp, mms_bamp, mms_u0, mms_v0;
+    int* status;
+};
+
+template <typename real>
+struct V2;
+template <>
+struct V2<float> { typedef float2 t; };
+template <>
+struct V2<double> { typedef double2 t; };
+
+template <typename real>
+__device__ __forceinline__ real r_sqrt(real x);
+template <>
+__device__ __forceinline__ float r_sqrt<float>(float x) { return sqrtf(x); }
+template <>
+__device__ __forceinline__ double r_sqrt<double>(double x) { return sqrt(x); }
+
+template <typename real>
+__device__ __forceinline__ void r_sincospi(real x, real* s, real* c);
+template <>
+__device__ __forceinline__ void r_sincospi<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+template <>
+__device__ __forceinline__ void r_sincospi<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+
+template <typename real>
+__device__ __forceinline__ bool r_finite(real x) { return isfinite(x); }
+
+// Shared-memory layout of one CTA: reference operators, then one slab per warp.
+template <int N, typename real>
+struct Smem {
+    typedef Dims<N> D;
+    static constexpr int REC = 12;  // h hu hv u v H rx sx ry sy 2gh b
+    static constexpr int ops_QsT = 0;
+    static constexpr int ops_Vq = ops_QsT + D::Nh * D::Nh * 2;
+    static constexpr int ops_VqT = ops_Vq + D::Nq * D::Np;
+    static constexpr int ops_Vh = ops_VqT + D::Np * D::Nq;
+    static constexpr int ops_VhT = ops_Vh + D::Nh * D::Np;
+    static constexpr int ops_wf = ops_VhT + D::Np * D::Nh;
+    static constexpr int ops_nrs = ops_wf + D::Nfq;
+    static constexpr int ops_end = ((ops_nrs + 2 * D::Nfq) + 3) & ~3;
+    // per-warp slab
+    static constexpr int w_rec = 0;                              // [Nh][REC]
+    static constexpr int w_rt = w_rec + D::Nh * REC;             // [3][Nh]
+    static constexpr int w_a = w_rt + 3 * D::Nh;                 // [3][Nq]
+    static constexpr int w_b = w_a + 3 * D::Nq;                  // [3][Np]
+    static constexpr int w_c = w_b + 3 * D::Np;                  // [3][Np]
+    static constexpr int w_minv = w_c + 3 * D::Np;               // [NpP]
+    static constexpr int w_end = ((w_minv + D::NpP) + 3) & ~3;
+    static constexpr size_t bytes(int warps) { return sizeof(real) * (size_t(ops_end) + size_t(warps) * w_end); }
+};
+
+template <int N, typename real>
+__device__ __forceinline__ void stage_ops_to_smem(const StageParams<real>& p, real* sm) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    for (int i = threadIdx.x; i < D::Nh * D::Nh * 2; i += blockDim.x) sm[S::ops_QsT + i] = p.QsT[i];
+    for (int i = threadIdx.x; i < D::Nq * D::Np; i += blockDim.x) {
+        sm[S::ops_Vq + i] = p.Vq[i];
+        sm[S::ops_VqT + i] = p.VqT[i];
+    }
+    for (int i = threadIdx.x; i < D::Nh * D::Np; i += blockDim.x) {
+        sm[S::ops_Vh + i] = p.Vh[i];
+        sm[S::ops_VhT + i] = p.VhT[i];
+    }
+    for (int i = threadIdx.x; i < D::Nfq; i += blockDim.x) {
+        sm[S::ops_wf + i] = p.wf[i];
+        sm[S::ops_nrs + 2 * i] = p.nrs[2 * i];
+        sm[S::ops_nrs + 2 * i + 1] = p.nrs[2 * i + 1];
+    }
+}
+
+// Entropy projection of one element's modal state (in w_b, FP `real`) into
+// u~ at the hybrid nodes, written to ut_out[e] (Sec. 2.6, J-weighted, Sec. 2.7).
+template <int N, typename real>
+__device__ __forceinline__ void project_element(const StageParams<real>& p, const real* ops, real* ws, int e,
+                                                int lane) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    const real* Vq = ops + S::ops_Vq;
+    const real* VqT = ops + S::ops_VqT;
+    const real* Vh = ops + S::ops_Vh;
+    real* us = ws + S::w_b;     // [3][Np] modal state
+    real* ta = ws + S::w_a;     // [3][Nq]
+    real* tc = ws + S::w_c;     // [3][Np]
+    real* mi = ws + S::w_minv;  // [NpP]
+    const real g = p.g;
+    int bad = 0;
+    // u_q = Vq u_h, v_q = v(u_q), scaled by w_q J_q
+    for (int q = lane; q < D::Nq; q += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int n = 0; n < D::Np; ++n) {
+            real v = Vq[q * D::Np + n];
+            a0 += v * us[n];
+            a1 += v * us[D::Np + n];
+            a2 += v * us[2 * D::Np + n];
+        }
+        real h = a0;
+        if (!(h > real(0))) bad |= STATUS_NONPOSITIVE;
+        real ih = real(1) / h;
+        real uu = a1 * ih, vv = a2 * ih;
+        real b = p.bh[(size_t)e * D::Nh + q];
+        real w = p.wJq[(size_t)e * D::Nq + q];
+        ta[q] = w * (g * (h + b) - real(0.5) * (uu * uu + vv * vv));
+        ta[D::Nq + q] = w * uu;
+        ta[2 * D::Nq + q] = w * vv;
+    }
+    __syncwarp();
+    // y = Vq^T W J v_q
+    for (int n = lane; n < D::Np; n += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 5
+        for (int q = 0; q < D::Nq; ++q) {
+            real v = VqT[n * D::Nq + q];
+            a0 += v * ta[q];
+            a1 += v * ta[D::Nq + q];
+            a2 += v * ta[2 * D::Nq + q];
+        }
+        tc[n] = a0;
+        tc[D::Np + n] = a1;
+        tc[2 * D::Np + n] = a2;
+    }
+    __syncwarp();
+    // v_h = (M_h^k)^{-1} y   (packed symmetric)
+    for (int n = lane; n < D::Np; n += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int j = 0; j < D::Np; ++j) {
+            int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+            real m = mi[ij];
+            a0 += m * tc[j];
+            a1 += m * tc[D::Np + j];
+            a2 += m * tc[2 * D::Np + j];
+        }
+        us[n] = a0;   // us is free again: reuse for v_h
+        us[D::Np + n] = a1;
+        us[2 * D::Np + n] = a2;
+    }
+    __syncwarp();
+    // v~ = Vh v_h; u~ = u(v~): H = (v1 + (v2^2 + v3^2)/2)/g, h = H - b
+    const real ig = real(1) / g;
+    for (int l = lane; l < D::Nh; l += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int n = 0; n < D::Np; ++n) {
+            real v = Vh[l * D::Np + n];
+            a0 += v * us[n];
+            a1 += v * us[D::Np + n];
+            a2 += v * us[2 * D::Np + n];
+        }
+        real H = (a0 + real(0.5) * (a1 * a1 + a2 * a2)) * ig;
+        real h = H - p.bh[(size_t)e * D::Nh + l];
+        if (!(h > real(0))) bad |= STATUS_NONPOSITIVE;
+        if (!r_finite(H) || !r_finite(a1) || !r_finite(a2)) bad |= STATUS_NONFINITE;
+        real* o = p.ut_out + ((size_t)e * D::Nh + l) * 4;
+        o[0] = h;
+        o[1] = a1;
+        o[2] = a2;
+        o[3] = H;
+    }
+    if (bad) atomicOr(p.status, bad);
+}
+
+template <int N, typename real>
+__device__ __forceinline__ void load_minv(const StageParams<real>& p, real* ws, int e, int lane) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * D::NpP + i];
+}
+
+// Standalone projection: u_in (FP64 modal) -> ut_out.
+template <int N, typename real>
+__global__ void __launch_bounds__(256) k_project(StageParams<real> p) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* ops = reinterpret_cast<real*>(smem_raw);
+    stage_ops_to_smem<N, real>(p, ops);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    real* ws = ops + S::ops_end + warp * S::w_end;
+    for (int e = blockIdx.x * wpb + warp; e < p.K; e += gridDim.x * wpb) {
+        load_minv<N, real>(p, ws, e, lane);
+        for (int i = lane; i < 3 * D::Np; i += 32) {
+            int c = i / D::Np, n = i - c * D::Np;
+            ws[S::w_b + i] = (real)p.u_in[((size_t)c * p.K + e) * D::Np + n];
+        }
+        __syncwarp();
+        project_element<N, real>(p, ops, ws, e, lane);
+        __syncwarp();
+    }
+}
+
+// MODE 0: write du/dt to rhs_out.  MODE 1: LSRK45 stage update of (u, res)
+// followed by the entropy projection of the new state into ut_out.
+template <int N, typename real, int MODE>
+__global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    typedef typename V2<real>::t real2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* ops = reinterpret_cast<real*>(smem_raw);
+    stage_ops_to_smem<N, real>(p, ops);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wpb = blockDim.x >> 5;
+    real* ws = ops + S::ops_end + warp * S::w_end;
+    real* rec = ws + S::w_rec;
+    real* rt = ws + S::w_rt;
+    const real2* QsT = reinterpret_cast<const real2*>(ops + S::ops_QsT);
+    const real g = p.g;
+    const real eighth = real(0.125);
+
+    for (int e = blockIdx.x * wpb + warp; e < p.K; e += gridDim.x * wpb) {
+        // ---- load u~ and geometry of the element -------------------------------
+        for (int l = lane; l < D::Nh; l += 32) {
+            const real* ut = p.ut_in + ((size_t)e * D::Nh + l) * 4;
+            const real* gg = p.geo + ((size_t)e * D::Nh + l) * 4;
+            real h = ut[0], uu = ut[1], vv = ut[2], H = ut[3];
+            real* r = rec + l * S::REC;
+            r[0] = h;
+            r[1] = h * uu;
+            r[2] = h * vv;
+            r[3] = uu;
+            r[4] = vv;
+            r[5] = H;
+            r[6] = gg[0] * eighth;
+            r[7] = gg[1] * eighth;
+            r[8] = gg[2] * eighth;
+            r[9] = gg[3] * eighth;
+            r[10] = real(2) * g * h;
+            r[11] = H - h;
+        }
+        load_minv<N, real>(p, ws, e, lane);
+        __syncwarp();
+        // ---- volume flux differencing + interface flux, row l = lane ----------
+        for (int l = lane; l < D::Nh; l += 32) {
+            const real* rl = rec + l * S::REC;
+            const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
+            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real a0 = 0, a1 = 0, a2 = 0;
+            const int mEnd = (l < D::Nq) ? D::Nh : D::Nq;
+            for (int m = 0; m < mEnd; ++m) {
+                const real2 q = QsT[m * D::Nh + l];
+                const real* rm = rec + m * S::REC;
+                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                const real U = u_l + rm[3], V = v_l + rm[4];
+                const real T = Qx * HU + Qy * HV;
+                const real P = gh2_l * rm[5];
+                a0 += T;
+                a1 += U * T + Qx * P;
+                a2 += V * T + Qy * P;
+            }
+            real r0 = real(2) * a0, r1 = a1, r2 = a2;
+            if (l >= D::Nq) {
+                // interface: f_S(u~+, u~) with the well-balanced pressure
+                // g/2 h (h+ + b), and Lax-Friedrichs on the jump of u~
+                const int f = l - D::Nq;
+                const int face = f / D::Nfp, i = f - face * D::Nfp;
+                const int nb = p.nbr[(size_t)e * 3 + face];
+                const int en = nb >> 2, fn = nb & 3;
+                const real* up = p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4;
+                const real hP = up[0], uP = up[1], vP = up[2];
+                const real huP = hP * uP, hvP = hP * vP;
+                const real nr = ops[S::ops_nrs + 2 * f], ns = ops[S::ops_nrs + 2 * f + 1];
+                const real nxJ = real(8) * (rx_l * nr + sx_l * ns);
+                const real nyJ = real(8) * (ry_l * nr + sy_l * ns);
+                const real w = ops[S::ops_wf + f];
+                const real b_l = rl[11];
+                const real huA = real(0.5) * (hu_l + huP), hvA = real(0.5) * (hv_l + hvP);
+                const real uA = real(0.5) * (u_l + uP), vA = real(0.5) * (v_l + vP);
+                const real pw = real(0.5) * g * h_l * (hP + b_l);
+                const real Fn0 = nxJ * huA + nyJ * hvA;
+                const real Fn1 = uA * Fn0 + nxJ * pw;
+                const real Fn2 = vA * Fn0 + nyJ * pw;
+                r0 += w * Fn0;
+                r1 += w * Fn1;
+                r2 += w * Fn2;
+                if (p.lf) {
+                    const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
+                    const real inx = nxJ / sJ, iny = nyJ / sJ;
+                    const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
+                    const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
+                    const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
+                    r0 -= c * (hP - h_l);
+                    r1 -= c * (huP - hu_l);
+                    r2 -= c * (hvP - hv_l);
+                }
+            }
+            rt[l] = r0;
+            rt[D::Nh + l] = r1;
+            rt[2 * D::Nh + l] = r2;
+        }
+        // forcing at the volume nodes, J-weighted: added as + Vq^T W J f
+        real* fa = ws + S::w_a;
+        if (p.forcing) {
+            for (int q = lane; q < D::Nq; q += 32) {
+                const real x = p.xq[(size_t)e * D::Nq + q], y = p.yq[(size_t)e * D::Nq + q];
+                const real w = p.wJq[(size_t)e * D::Nq + q];
+                real sth, cth, sx, cx, sy, cy;
+                r_sincospi<real>(x + y - real(p.t), &sth, &cth);
+                r_sincospi<real>(x, &sx, &cx);
+                r_sincospi<real>(y, &sy, &cy);
+                const real pi = real(3.14159265358979323846);
+                const real h = real(2) + p.mms_amp * sth;
+                const real c = p.mms_amp * pi * cth;
+                const real ht = -c, hx = c, hy = c;
+                const real bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
+                const real u0 = p.mms_u0, v0 = p.mms_v0;
+                fa[q] = w * (ht + u0 * hx + v0 * hy);
+                fa[D::Nq + q] = w * (u0 * ht + (u0 * u0 + g * h) * hx + u0 * v0 * hy + g * h * bx);
+                fa[2 * D::Nq + q] = w * (v0 * ht + u0 * v0 * hx + (v0 * v0 + g * h) * hy + g * h * by);
+            }
+        }
+        __syncwarp();
+        // ---- lift: s = Vh^T r - Vq^T W J f --------------------------------------
+        const real* VhT = ops + S::ops_VhT;
+        const real* VqT = ops + S::ops_VqT;
+        real* sb = ws + S::w_b;
+        for (int n = lane; n < D::Np; n += 32) {
+            real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 8
+            for (int l = 0; l < D::Nh; ++l) {
+                const real v = VhT[n * D::Nh + l];
+                a0 += v * rt[l];
+                a1 += v * rt[D::Nh + l];
+                a2 += v * rt[2 * D::Nh + l];
+            }
+            if (p.forcing) {
+                for (int q = 0; q < D::Nq; ++q) {
+                    const real v = VqT[n * D::Nq + q];
+                    a0 -= v * fa[q];
+                    a1 -= v * fa[D::Nq + q];
+                    a2 -= v * fa[2 * D::Nq + q];
+                }
+            }
+            sb[n] = a0;
+            sb[D::Np + n] = a1;
+            sb[2 * D::Np + n] = a2;
+        }
+        __syncwarp();
+        // ---- du/dt = -(M_h^k)^{-1} s; then output or RK update --------------------
+        const real* mi = ws + S::w_minv;
+        real* sc = ws + S::w_c;
+        for (int n = lane; n < D::Np; n += 32) {
+            real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+            for (int j = 0; j < D::Np; ++j) {
+                const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+                const real m = mi[ij];
+                a0 += m * sb[j];
+                a1 += m * sb[D::Np + j];
+                a2 += m * sb[2 * D::Np + j];
+            }
+            sc[n] = -a0;
+            sc[D::Np + n] = -a1;
+            sc[2 * D::Np + n] = -a2;
+        }
+        __syncwarp();
+        for (int i = lane; i < 3 * D::Np; i += 32) {
+            const int c = i / D::Np, n = i - c * D::Np;
+            const size_t gi = ((size_t)c * p.K + e) * D::Np + n;
+            const double r = (double)sc[i];
+            if (MODE == 0) {
+                p.rhs_out[gi] = r;
+            } else {
+                const double rs = p.rkA * p.res[gi] + p.dt * r;
+                p.res[gi] = rs;
+                const double un = p.u[gi] + p.rkB * rs;
+                p.u[gi] = un;
+                sb[i] = (real)un;
+            }
+        }
+        __syncwarp();
+        if (MODE == 1) {
+            project_element<N, real>(p, ops, ws, e, lane);
+            __syncwarp();
+        }
+    }
+}
+
+// FP64 diagnostics: per-CTA partial sums of (entropy, mass, entropy rate).
+template <int N>
+__global__ void __launch_bounds__(256) k_entropy(int K, double g, const double* __restrict__ u,
+                                                 const double* __restrict__ rhs, const double* __restrict__ Vq,
+                                                 const double* __restrict__ wJq, const double* __restrict__ bq,
+                                                 double* __restrict__ partial) {
+    typedef Dims<N> D;
+    double s_ent = 0, s_mass = 0, s_rate = 0;
+    const int total = K * D::Nq;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        const int e = idx / D::Nq, q = idx - e * D::Nq;
+        double a[3] = {0, 0, 0}, d[3] = {0, 0, 0};
+        for (int n = 0; n < D::Np; ++n) {
+            const double v = Vq[q * D::Np + n];
+            for (int c = 0; c < 3; ++c) {
+                a[c] += v * u[((size_t)c * K + e) * D::Np + n];
+                if (rhs) d[c] += v * rhs[((size_t)c * K + e) * D::Np + n];
+            }
+        }
+        const double w = wJq[idx], b = bq[idx];
+        const double h = a[0], uu = a[1] / h, vv = a[2] / h;
+        s_ent += w * (0.5 * (a[1] * uu + a[2] * vv) + 0.5 * g * h * h + g * h * b);
+        s_mass += w * h;
+        if (rhs) s_rate += w * ((g * (h + b) - 0.5 * (uu * uu + vv * vv)) * d[0] + uu * d[1] + vv * d[2]);
+    }
+    __shared__ double red[3][256];
+    red[0][threadIdx.x] = s_ent;
+    red[1][threadIdx.x] = s_mass;
+    red[2][threadIdx.x] = s_rate;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s)
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) partial[blockIdx.x * 3 + c] = red[c][0];
+}
+
+// Sum the per-CTA partials in a fixed order (deterministic).
+__global__ void k_entropy_finalize(int nparts, const double* __restrict__ partial, double* __restrict__ out);
+
+}  // namespace esdg

@@ -1,0 +1,63 @@
+// Definitions of the launch wrappers for one degree N (ESDG_N).
+#include "esdg_launch.hpp"
+
+namespace esdg {
+
+template <int N, typename real>
+cudaError_t stage_geometry(int num_sms, LaunchGeom& lg) {
+    lg.block = 256;
+    lg.smem = Smem<N, real>::bytes(lg.block / 32);
+    cudaError_t err;
+    err = cudaFuncSetAttribute(k_stage<N, real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_stage<N, real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
+    if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_project<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<N, real, 1>, lg.block, lg.smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) per_sm = 1;
+    lg.grid = per_sm * num_sms;
+    return cudaSuccess;
+}
+
+template <int N, typename real>
+cudaError_t launch_project(const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
+    int need = (p.K + lg.block / 32 - 1) / (lg.block / 32);
+    int grid = need < lg.grid ? need : lg.grid;
+    k_project<N, real><<<grid, lg.block, lg.smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t launch_stage(const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s) {
+    int need = (p.K + lg.block / 32 - 1) / (lg.block / 32);
+    int grid = need < lg.grid ? need : lg.grid;
+    if (mode == 0)
+        k_stage<N, real, 0><<<grid, lg.block, lg.smem, s>>>(p);
+    else
+        k_stage<N, real, 1><<<grid, lg.block, lg.smem, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_entropy(int K, double g, const double* u, const double* rhs, const double* Vq, const double* wJq,
+                           const double* bq, double* partial, int nparts, double* out, cudaStream_t s) {
+    k_entropy<N><<<nparts, 256, 0, s>>>(K, g, u, rhs, Vq, wJq, bq, partial);
+    cudaError_t err = cudaGetLastError();
+    if (err != cudaSuccess) return err;
+    k_entropy_finalize<<<1, 32, 0, s>>>(nparts, partial, out);
+    return cudaGetLastError();
+}
+
+template cudaError_t stage_geometry<ESDG_N, float>(int, LaunchGeom&);
+template cudaError_t stage_geometry<ESDG_N, double>(int, LaunchGeom&);
+template cudaError_t launch_project<ESDG_N, float>(const StageParams<float>&, const LaunchGeom&, cudaStream_t);
+template cudaError_t launch_project<ESDG_N, double>(const StageParams<double>&, const LaunchGeom&, cudaStream_t);
+template cudaError_t launch_stage<ESDG_N, float>(const StageParams<float>&, int, const LaunchGeom&, cudaStream_t);
+template cudaError_t launch_stage<ESDG_N, double>(const StageParams<double>&, int, const LaunchGeom&, cudaStream_t);
+template cudaError_t launch_entropy<ESDG_N>(int, double, const double*, const double*, const double*, const double*,
+                                            const double*, double*, int, double*, cudaStream_t);
+
+}  // namespace esdg

@@ -1,0 +1,431 @@
+// Host-side construction of the ESDG operators, mesh and geometry (FP64).
+// Reference element: Sec. 2.1 (basis, quadrature, V_q, V_f, M, P_q, D^i),
+// Sec. 2.2 (Q-hat^i = M D^i, B^i, Q^i, E, V_h), Sec. 2.3 (hybridized Q_h^i).
+// Curved geometry: Sec. 2.7 (J, J-scaled G_ij, B^{i,k}, M_h^k); mesh warp: Sec. 4.
+//
+// Choices the paper leaves open (basis, rules, mesh) follow the conventions
+// documented in esdg.h: orthonormal Dubiner basis, collapsed Gauss rule with
+// (N+1)^2 points (exact to degree 2N+1), N+1 Gauss-Legendre points per face.
+
+#include "host_build.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <utility>
+
+namespace esdg {
+
+// ---------------------------------------------------------------------------
+// small dense linear algebra
+// ---------------------------------------------------------------------------
+Mat matmul(const Mat& A, const Mat& B) {
+    Mat C(A.r, B.c);
+    for (int i = 0; i < A.r; ++i)
+        for (int k = 0; k < A.c; ++k) {
+            double a = A(i, k);
+            if (a == 0.0) continue;
+            for (int j = 0; j < B.c; ++j) C(i, j) += a * B(k, j);
+        }
+    return C;
+}
+
+Mat transpose(const Mat& A) {
+    Mat T(A.c, A.r);
+    for (int i = 0; i < A.r; ++i)
+        for (int j = 0; j < A.c; ++j) T(j, i) = A(i, j);
+    return T;
+}
+
+bool invert(const Mat& A, Mat& Ainv) {
+    const int n = A.r;
+    Mat W = A;
+    Ainv = Mat(n, n);
+    for (int i = 0; i < n; ++i) Ainv(i, i) = 1.0;
+    for (int col = 0; col < n; ++col) {
+        int piv = col;
+        for (int i = col + 1; i < n; ++i)
+            if (std::fabs(W(i, col)) > std::fabs(W(piv, col))) piv = i;
+        if (std::fabs(W(piv, col)) < 1e-300) return false;
+        if (piv != col)
+            for (int j = 0; j < n; ++j) {
+                std::swap(W(piv, j), W(col, j));
+                std::swap(Ainv(piv, j), Ainv(col, j));
+            }
+        double d = 1.0 / W(col, col);
+        for (int j = 0; j < n; ++j) { W(col, j) *= d; Ainv(col, j) *= d; }
+        for (int i = 0; i < n; ++i) {
+            if (i == col) continue;
+            double f = W(i, col);
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) { W(i, j) -= f * W(col, j); Ainv(i, j) -= f * Ainv(col, j); }
+        }
+    }
+    return true;
+}
+
+// Symmetric eigen-decomposition by cyclic Jacobi rotations (small n).
+static void sym_eig(Mat A, std::vector<double>& evals, Mat& V) {
+    const int n = A.r;
+    V = Mat(n, n);
+    for (int i = 0; i < n; ++i) V(i, i) = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += A(p, q) * A(p, q);
+        if (off < 1e-40) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = A(p, q);
+                if (std::fabs(apq) < 1e-300) continue;
+                double theta = (A(q, q) - A(p, p)) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A R  (columns p, q)
+                    double akp = A(k, p), akq = A(k, q);
+                    A(k, p) = c * akp - s * akq;
+                    A(k, q) = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- R^T A (rows p, q)
+                    double apk = A(p, k), aqk = A(q, k);
+                    A(p, k) = c * apk - s * aqk;
+                    A(q, k) = s * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    double vkp = V(k, p), vkq = V(k, q);
+                    V(k, p) = c * vkp - s * vkq;
+                    V(k, q) = s * vkp + c * vkq;
+                }
+            }
+    }
+    evals.resize(n);
+    for (int i = 0; i < n; ++i) evals[i] = A(i, i);
+}
+
+// ---------------------------------------------------------------------------
+// Jacobi polynomials, orthonormal under (1-x)^alpha (1+x)^beta on [-1,1]
+// ---------------------------------------------------------------------------
+static double jacobi_mu0(double al, double be) {
+    return std::pow(2.0, al + be + 1.0) * std::tgamma(al + 1.0) * std::tgamma(be + 1.0) /
+           std::tgamma(al + be + 2.0);
+}
+
+// Three-term recurrence x p_n = a_{n+1} p_{n+1} + b_n p_n + a_n p_{n-1}.
+static double rec_b(int n, double al, double be) {
+    double s = 2.0 * n + al + be;
+    if (n == 0) return (be - al) / (al + be + 2.0);
+    return (be * be - al * al) / (s * (s + 2.0));
+}
+static double rec_a(int n, double al, double be) {  // n >= 1
+    double s = 2.0 * n + al + be;
+    double num = n * (n + al) * (n + be) * (n + al + be);
+    double den = (s - 1.0) * (s + 1.0);
+    if (n == 1) {  // n + al + be over s - 1 cancels exactly
+        return 2.0 / s * std::sqrt((1.0 + al) * (1.0 + be) / (s + 1.0));
+    }
+    return 2.0 / s * std::sqrt(num / den);
+}
+
+static double jacobi_p(double x, double al, double be, int n) {
+    double pm1 = 0.0, p = 1.0 / std::sqrt(jacobi_mu0(al, be));
+    for (int k = 0; k < n; ++k) {
+        double pn = ((x - rec_b(k, al, be)) * p - (k > 0 ? rec_a(k, al, be) * pm1 : 0.0)) / rec_a(k + 1, al, be);
+        pm1 = p;
+        p = pn;
+    }
+    return p;
+}
+
+// d/dx of the orthonormal p_n: sqrt(n (n+al+be+1)) p_{n-1}^{(al+1, be+1)}
+static double jacobi_dp(double x, double al, double be, int n) {
+    if (n == 0) return 0.0;
+    return std::sqrt(n * (n + al + be + 1.0)) * jacobi_p(x, al + 1.0, be + 1.0, n - 1);
+}
+
+// Gauss-Jacobi rule with n points (Golub-Welsch).
+static void gauss_jacobi(int n, double al, double be, std::vector<double>& x, std::vector<double>& w) {
+    Mat T(n, n);
+    for (int i = 0; i < n; ++i) {
+        T(i, i) = rec_b(i, al, be);
+        if (i + 1 < n) T(i, i + 1) = T(i + 1, i) = rec_a(i + 1, al, be);
+    }
+    std::vector<double> ev;
+    Mat V;
+    sym_eig(T, ev, V);
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int b) { return ev[a] < ev[b]; });
+    double mu0 = jacobi_mu0(al, be);
+    x.resize(n);
+    w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        int k = idx[i];
+        double xi = ev[k];
+        // one Newton correction on p_n for the last bits
+        double p = jacobi_p(xi, al, be, n), dp = jacobi_dp(xi, al, be, n);
+        if (dp != 0.0) xi -= p / dp;
+        x[i] = xi;
+        w[i] = mu0 * V(0, k) * V(0, k);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dubiner basis (Sec. 2.1 leaves the basis open)
+// ---------------------------------------------------------------------------
+void dubiner(int N, const std::vector<double>& r, const std::vector<double>& s, Mat& V, Mat* Vr, Mat* Vs) {
+    const int np = int(r.size());
+    const int Np = (N + 1) * (N + 2) / 2;
+    V = Mat(np, Np);
+    if (Vr) *Vr = Mat(np, Np);
+    if (Vs) *Vs = Mat(np, Np);
+    const double rt2 = std::sqrt(2.0);
+    for (int p = 0; p < np; ++p) {
+        double b = s[p];
+        double a = (std::fabs(1.0 - b) > 1e-14) ? 2.0 * (1.0 + r[p]) / (1.0 - b) - 1.0 : -1.0;
+        int m = 0;
+        for (int i = 0; i <= N; ++i)
+            for (int j = 0; j <= N - i; ++j, ++m) {
+                double fa = jacobi_p(a, 0.0, 0.0, i);
+                double gb = jacobi_p(b, 2.0 * i + 1.0, 0.0, j);
+                double omb_i = std::pow(1.0 - b, i);
+                V(p, m) = rt2 * fa * gb * omb_i;
+                if (!Vr) continue;
+                // chain rule: d/dr = 2/(1-b) d/da, d/ds = (1+a)/(1-b) d/da + d/db
+                double dfa = jacobi_dp(a, 0.0, 0.0, i);
+                double dgb = jacobi_dp(b, 2.0 * i + 1.0, 0.0, j);
+                double da_term = 0.0;   // (d phi/da) / (1-b) = sqrt2 fa' gb (1-b)^(i-1)
+                if (i > 0) da_term = rt2 * dfa * gb * std::pow(1.0 - b, i - 1);
+                double db = rt2 * fa * (dgb * omb_i - (i > 0 ? i * gb * std::pow(1.0 - b, i - 1) : 0.0));
+                (*Vr)(p, m) = 2.0 * da_term;
+                (*Vs)(p, m) = (1.0 + a) * da_term + db;
+            }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reference element
+// ---------------------------------------------------------------------------
+bool build_reference(int N, RefOps& R, std::string& err) {
+    if (N < 1 || N > 5) { err = "N must be in 1..5"; return false; }
+    R.N = N;
+    R.Np = (N + 1) * (N + 2) / 2;
+    R.Nfp = N + 1;
+    R.Nfq = 3 * R.Nfp;
+    // volume: Gauss-Legendre (a) x Gauss-Jacobi(1,0) (b), (N+1)^2 points
+    std::vector<double> xa, wa, xb, wb;
+    gauss_jacobi(N + 1, 0.0, 0.0, xa, wa);
+    gauss_jacobi(N + 1, 1.0, 0.0, xb, wb);
+    R.rq.clear(); R.sq.clear(); R.wq.clear();
+    for (int ia = 0; ia <= N; ++ia)
+        for (int ib = 0; ib <= N; ++ib) {
+            R.rq.push_back(0.5 * (1.0 + xa[ia]) * (1.0 - xb[ib]) - 1.0);
+            R.sq.push_back(xb[ib]);
+            R.wq.push_back(0.5 * wa[ia] * wb[ib]);
+        }
+    R.Nq = int(R.rq.size());
+    R.Nh = R.Nq + R.Nfq;
+    // faces: parameter t runs v1->v2, v2->v3, v3->v1 (counter-clockwise)
+    R.rf.clear(); R.sf.clear(); R.wf.clear(); R.nr.clear(); R.ns.clear();
+    for (int f = 0; f < 3; ++f)
+        for (int i = 0; i <= N; ++i) {
+            double t = xa[i];
+            double rr = (f == 0) ? t : (f == 1 ? -t : -1.0);
+            double ss = (f == 0) ? -1.0 : (f == 1 ? t : -t);
+            R.rf.push_back(rr);
+            R.sf.push_back(ss);
+            R.wf.push_back(wa[i]);
+            R.nr.push_back(f == 0 ? 0.0 : (f == 1 ? 1.0 : -1.0));
+            R.ns.push_back(f == 0 ? -1.0 : (f == 1 ? 1.0 : 0.0));
+        }
+    dubiner(N, R.rq, R.sq, R.Vq, &R.Vqr, &R.Vqs);
+    dubiner(N, R.rf, R.sf, R.Vf, &R.Vfr, &R.Vfs);
+    // M = Vq^T W Vq, Pq = M^{-1} Vq^T W
+    Mat VqTW = transpose(R.Vq);
+    for (int n = 0; n < R.Np; ++n)
+        for (int q = 0; q < R.Nq; ++q) VqTW(n, q) *= R.wq[q];
+    Mat M = matmul(VqTW, R.Vq), Minv;
+    if (!invert(M, Minv)) { err = "singular reference mass matrix"; return false; }
+    R.Pq = matmul(Minv, VqTW);
+    // D^i = Pq Vq^i (derivatives of degree-N polynomials are degree N-1), Q-hat = M D
+    Mat Qrh = matmul(M, matmul(R.Pq, R.Vqr));
+    Mat Qsh = matmul(M, matmul(R.Pq, R.Vqs));
+    // nodal Q^i = Pq^T Q-hat^i Pq, E = Vf Pq
+    Mat PqT = transpose(R.Pq);
+    Mat Qr = matmul(PqT, matmul(Qrh, R.Pq));
+    Mat Qs = matmul(PqT, matmul(Qsh, R.Pq));
+    Mat E = matmul(R.Vf, R.Pq);
+    // skew hybridized operators Q_h - Q_h^T = [[Q - Q^T, E^T B], [-B E, 0]]
+    auto skew = [&](const Mat& Q, const std::vector<double>& nh) {
+        Mat S(R.Nh, R.Nh);
+        for (int i = 0; i < R.Nq; ++i)
+            for (int j = 0; j < R.Nq; ++j) S(i, j) = Q(i, j) - Q(j, i);
+        for (int f = 0; f < R.Nfq; ++f) {
+            double bf = R.wf[f] * nh[f];
+            for (int j = 0; j < R.Nq; ++j) {
+                S(j, R.Nq + f) = E(f, j) * bf;
+                S(R.Nq + f, j) = -bf * E(f, j);
+            }
+        }
+        return S;
+    };
+    R.Qsr = skew(Qr, R.nr);
+    R.Qss = skew(Qs, R.ns);
+    R.Vh = Mat(R.Nh, R.Np);
+    for (int i = 0; i < R.Nq; ++i)
+        for (int n = 0; n < R.Np; ++n) R.Vh(i, n) = R.Vq(i, n);
+    for (int f = 0; f < R.Nfq; ++f)
+        for (int n = 0; n < R.Np; ++n) R.Vh(R.Nq + f, n) = R.Vf(f, n);
+    // equispaced nodes (s-major) and the inverse Vandermonde
+    R.req.clear(); R.seq.clear();
+    for (int j = 0; j <= N; ++j)
+        for (int i = 0; i <= N - j; ++i) {
+            R.req.push_back(-1.0 + 2.0 * i / N);
+            R.seq.push_back(-1.0 + 2.0 * j / N);
+        }
+    Mat Veq;
+    dubiner(N, R.req, R.seq, Veq, nullptr, nullptr);
+    if (!invert(Veq, R.Veq_inv)) { err = "singular equispaced Vandermonde"; return false; }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Mesh and geometry
+// ---------------------------------------------------------------------------
+bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& err) {
+    if (sp.nx < 3 || sp.ny < 3) { err = "nx and ny must be >= 3 (periodic faces must be distinct)"; return false; }
+    if (!(sp.x1 > sp.x0) || !(sp.y1 > sp.y0)) { err = "empty domain"; return false; }
+    const int nx = sp.nx, ny = sp.ny;
+    const long long Kll = 2LL * nx * ny;
+    if (Kll > (1LL << 28)) { err = "mesh too large"; return false; }
+    const int K = int(Kll);
+    D.K = K;
+    const double Lx = sp.x1 - sp.x0, Ly = sp.y1 - sp.y0;
+    const double xc = 0.5 * (sp.x0 + sp.x1), yc = 0.5 * (sp.y0 + sp.y1);
+    const int Np = R.Np, Nq = R.Nq, Nfq = R.Nfq, Nh = R.Nh, Nfp = R.Nfp;
+    std::vector<double> VX(3 * size_t(K)), VY(3 * size_t(K));
+    std::vector<int> PV(3 * size_t(K));
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int q = j * nx + i;
+            int tri[2][3][2] = {{{i, j}, {i + 1, j}, {i + 1, j + 1}}, {{i, j}, {i + 1, j + 1}, {i, j + 1}}};
+            for (int t = 0; t < 2; ++t) {
+                int e = 2 * q + t;
+                for (int v = 0; v < 3; ++v) {
+                    int ii = tri[t][v][0], jj = tri[t][v][1];
+                    VX[3 * e + v] = sp.x0 + Lx * ii / nx;
+                    VY[3 * e + v] = sp.y0 + Ly * jj / ny;
+                    PV[3 * e + v] = (jj % ny) * nx + (ii % nx);
+                }
+            }
+        }
+    // face matching by periodic vertex pairs
+    D.nbr.assign(3 * size_t(K), -1);
+    {
+        std::map<std::pair<int, int>, std::vector<int>> faces;
+        const int fv[3][2] = {{0, 1}, {1, 2}, {2, 0}};
+        for (int e = 0; e < K; ++e)
+            for (int f = 0; f < 3; ++f) {
+                int a = PV[3 * e + fv[f][0]], b = PV[3 * e + fv[f][1]];
+                faces[{std::min(a, b), std::max(a, b)}].push_back(4 * e + f);
+            }
+        for (auto& kv : faces) {
+            if (kv.second.size() != 2) { err = "a face is not shared by exactly two elements"; return false; }
+            int a = kv.second[0], b = kv.second[1];
+            D.nbr[3 * (a >> 2) + (a & 3)] = b;
+            D.nbr[3 * (b >> 2) + (b & 3)] = a;
+        }
+    }
+    // curved map: warp the equispaced nodes of each affine element
+    D.xeq.resize(size_t(K) * Np);
+    D.yeq.resize(size_t(K) * Np);
+    const double PI = 3.14159265358979323846;
+    for (int e = 0; e < K; ++e)
+        for (int n = 0; n < Np; ++n) {
+            double r = R.req[n], s = R.seq[n];
+            double x = -0.5 * (r + s) * VX[3 * e] + 0.5 * (1 + r) * VX[3 * e + 1] + 0.5 * (1 + s) * VX[3 * e + 2];
+            double y = -0.5 * (r + s) * VY[3 * e] + 0.5 * (1 + r) * VY[3 * e + 1] + 0.5 * (1 + s) * VY[3 * e + 2];
+            double xi = 2.0 * (x - xc) / Lx, eta = 2.0 * (y - yc) / Ly;
+            D.xeq[size_t(e) * Np + n] = x + sp.ax * 0.5 * Lx * std::cos(0.5 * PI * xi) * std::cos(1.5 * PI * eta);
+            D.yeq[size_t(e) * Np + n] = y + sp.ay * 0.5 * Ly * std::sin(2.0 * PI * xi) * std::cos(0.5 * PI * eta);
+        }
+    // geometric factors at the hybrid nodes (J-scaled metrics, Sec. 2.7)
+    D.geo.assign(size_t(K) * Nh * 4, 0.0);
+    D.Jq.assign(size_t(K) * Nq, 0.0);
+    D.xq.assign(size_t(K) * Nq, 0.0);
+    D.yq.assign(size_t(K) * Nq, 0.0);
+    D.xf.assign(size_t(K) * Nfq, 0.0);
+    D.yf.assign(size_t(K) * Nfq, 0.0);
+    D.minv.assign(size_t(K) * (Np * (Np + 1) / 2), 0.0);
+    std::vector<double> xm(Np), ym(Np);
+    Mat Mh(Np, Np), Mhi;
+    for (int e = 0; e < K; ++e) {
+        for (int n = 0; n < Np; ++n) {
+            double sx = 0, sy = 0;
+            for (int m = 0; m < Np; ++m) {
+                sx += R.Veq_inv(n, m) * D.xeq[size_t(e) * Np + m];
+                sy += R.Veq_inv(n, m) * D.yeq[size_t(e) * Np + m];
+            }
+            xm[n] = sx;
+            ym[n] = sy;
+        }
+        auto eval = [&](const Mat& V, const Mat& Vr, const Mat& Vs, int p, double* out) {
+            double x = 0, y = 0, xr = 0, xs = 0, yr = 0, ys = 0;
+            for (int n = 0; n < Np; ++n) {
+                x += V(p, n) * xm[n]; y += V(p, n) * ym[n];
+                xr += Vr(p, n) * xm[n]; xs += Vs(p, n) * xm[n];
+                yr += Vr(p, n) * ym[n]; ys += Vs(p, n) * ym[n];
+            }
+            out[0] = x; out[1] = y;
+            out[2] = ys; out[3] = -yr; out[4] = -xs; out[5] = xr;   // rxJ sxJ ryJ syJ
+            out[6] = xr * ys - xs * yr;                              // J
+        };
+        double g7[7];
+        for (int q = 0; q < Nq; ++q) {
+            eval(R.Vq, R.Vqr, R.Vqs, q, g7);
+            if (!(g7[6] > 0.0)) { err = "non-positive Jacobian at a volume node"; return false; }
+            D.xq[size_t(e) * Nq + q] = g7[0];
+            D.yq[size_t(e) * Nq + q] = g7[1];
+            for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + q) * 4 + c] = g7[2 + c];
+            D.Jq[size_t(e) * Nq + q] = g7[6];
+        }
+        for (int f = 0; f < Nfq; ++f) {
+            eval(R.Vf, R.Vfr, R.Vfs, f, g7);
+            if (!(g7[6] > 0.0)) { err = "non-positive Jacobian at a face node"; return false; }
+            D.xf[size_t(e) * Nfq + f] = g7[0];
+            D.yf[size_t(e) * Nfq + f] = g7[1];
+            for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + Nq + f) * 4 + c] = g7[2 + c];
+        }
+        // M_h^k = Vq^T W J Vq and its inverse (Sec. 2.7), packed lower triangle
+        for (int i = 0; i < Np; ++i)
+            for (int j = 0; j < Np; ++j) {
+                double s = 0;
+                for (int q = 0; q < Nq; ++q) s += R.Vq(q, i) * R.wq[q] * D.Jq[size_t(e) * Nq + q] * R.Vq(q, j);
+                Mh(i, j) = s;
+            }
+        if (!invert(Mh, Mhi)) { err = "singular curved mass matrix"; return false; }
+        size_t o = size_t(e) * (Np * (Np + 1) / 2);
+        for (int i = 0; i < Np; ++i)
+            for (int j = 0; j <= i; ++j) D.minv[o + i * (i + 1) / 2 + j] = 0.5 * (Mhi(i, j) + Mhi(j, i));
+    }
+    // every face node must meet its partner (reversed order) modulo the period
+    const double tol = 1e-9 * std::min(Lx / nx, Ly / ny);
+    for (int e = 0; e < K; ++e)
+        for (int f = 0; f < 3; ++f) {
+            int nb = D.nbr[3 * e + f];
+            int en = nb >> 2, fn = nb & 3;
+            for (int i = 0; i < Nfp; ++i) {
+                int a = e * Nfq + f * Nfp + i;
+                int b = en * Nfq + fn * Nfp + (Nfp - 1 - i);
+                double dx = D.xf[b] - D.xf[a], dy = D.yf[b] - D.yf[a];
+                dx -= Lx * std::round(dx / Lx);
+                dy -= Ly * std::round(dy / Ly);
+                if (std::fabs(dx) > tol || std::fabs(dy) > tol) {
+                    err = "face quadrature nodes of neighbouring elements do not match";
+                    return false;
+                }
+            }
+        }
+    return true;
+}
+
+}  // namespace esdg

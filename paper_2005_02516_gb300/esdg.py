@@ -1,0 +1,235 @@
+"""Python binding of the C ABI in include/esdg.h (argument marshalling only).
+
+Every step of the method runs in libesdg.so; this module converts arguments,
+hands device memory (a torch allocation) and the current torch CUDA stream to
+the library, and raises on non-zero status codes.  It fails loudly when the
+library has not been built: there is no CPU fallback.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libesdg.so")
+
+ESDG_OK = 0
+ESDG_EINVAL = -1
+ESDG_ENOMEM = -2
+ESDG_ECUDA = -3
+ESDG_ENONPOSITIVE = -4
+ESDG_ENONFINITE = -5
+ESDG_ESTATE = -6
+
+ESDG_FP64 = 0
+ESDG_FP32 = 1
+ESDG_FORCING_NONE = 0
+ESDG_FORCING_MMS_SINE = 1
+ESDG_POINTS_NODAL = 0
+ESDG_POINTS_VOLQ = 1
+ESDG_POINTS_FACEQ = 2
+ESDG_INIT_DEPTH = 0
+ESDG_INIT_SURFACE = 1
+
+# every symbol include/esdg.h declares
+EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get_points",
+           "esdg_init_state", "esdg_set_bathymetry", "esdg_set_state", "esdg_copy_state",
+           "esdg_rhs", "esdg_step", "esdg_step_async", "esdg_check", "esdg_entropy", "esdg_dt",
+           "esdg_destroy", "esdg_last_error"]
+
+
+class EsdgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("esdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("precision", ctypes.c_int),
+                ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+                ("x0", ctypes.c_double), ("x1", ctypes.c_double),
+                ("y0", ctypes.c_double), ("y1", ctypes.c_double),
+                ("warp_ax", ctypes.c_double), ("warp_ay", ctypes.c_double),
+                ("g", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("lax_friedrichs", ctypes.c_int), ("forcing", ctypes.c_int),
+                ("mms_amp", ctypes.c_double), ("mms_bamp", ctypes.c_double),
+                ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load_library(path=LIB_PATH):
+    """Load libesdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libesdg.so is missing at %s: build it with __graft_entry__.build() "
+                           "(there is no CPU fallback)" % path)
+    lib = ctypes.CDLL(path)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    PI, PD, PS = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "esdg_build_operators": ([ctypes.POINTER(Config), ctypes.POINTER(P)], I),
+        "esdg_sizes": ([P, PI, PI, PI, PI, PS], I),
+        "esdg_attach_device": ([P, P, S, P], I),
+        "esdg_get_points": ([P, I, P, P], I),
+        "esdg_init_state": ([P, P, P, I], I),
+        "esdg_set_bathymetry": ([P, P], I),
+        "esdg_set_state": ([P, P, I], I),
+        "esdg_copy_state": ([P, P, I], I),
+        "esdg_rhs": ([P, D, P, P], I),
+        "esdg_step": ([P, I, D, PD], I),
+        "esdg_step_async": ([P, I, D, D], I),
+        "esdg_check": ([P], I),
+        "esdg_entropy": ([P, D, PD, PD, PD], I),
+        "esdg_dt": ([P, PD], I),
+        "esdg_destroy": ([P], I),
+        "esdg_last_error": ([P], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(a):
+    """Address of a contiguous numpy array or torch tensor."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+class Solver:
+    """One ESDG problem on the current CUDA device.
+
+    Device memory comes from a torch allocation handed to the library; work
+    runs on torch's current stream at construction time.
+    """
+
+    def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
+                 warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
+                 mms=(0.1, 0.1, 0.5, 0.5), torch_memory=True, stream=None):
+        import torch
+        self.lib = load_library()
+        cfg = Config()
+        cfg.N, cfg.nx, cfg.ny = N, nx, ny
+        cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
+        cfg.x0, cfg.x1, cfg.y0, cfg.y1 = x0, x1, y0, y1
+        cfg.warp_ax = cfg.warp_ay = warp
+        cfg.g, cfg.cfl = g, cfl
+        cfg.lax_friedrichs = 1 if lax_friedrichs else 0
+        cfg.forcing = ESDG_FORCING_MMS_SINE if forcing == "mms_sine" else ESDG_FORCING_NONE
+        cfg.mms_amp, cfg.mms_bamp, cfg.mms_u0, cfg.mms_v0 = mms
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)
+        self.h = h
+        K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nbytes = ctypes.c_size_t()
+        self._check(self.lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq),
+                                        ctypes.byref(Nfq), ctypes.byref(nbytes)))
+        self.K, self.Np, self.Nq, self.Nfq = K.value, Np.value, Nq.value, Nfq.value
+        self.device_bytes = nbytes.value
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._buf = None
+        if torch_memory:
+            self._buf = torch.empty(self.device_bytes + 256, dtype=torch.uint8, device="cuda")
+            base = self._buf.data_ptr()
+            off = (-base) % 256
+            self._check(self.lib.esdg_attach_device(h, base + off, self.device_bytes, stream.cuda_stream))
+        else:
+            self._check(self.lib.esdg_attach_device(h, None, 0, stream.cuda_stream))
+
+    # -- plumbing --------------------------------------------------------------
+    def _check(self, rc, h="self"):
+        if rc != ESDG_OK:
+            hh = self.h if h == "self" else h
+            msg = self.lib.esdg_last_error(hh).decode()
+            raise EsdgError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.esdg_destroy(self.h)
+            self.h = None
+            self._buf = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- API ---------------------------------------------------------------------
+    def points(self, kind):
+        n = {ESDG_POINTS_NODAL: self.Np, ESDG_POINTS_VOLQ: self.Nq, ESDG_POINTS_FACEQ: self.Nfq}[kind]
+        x = np.zeros((self.K, n))
+        y = np.zeros((self.K, n))
+        self._check(self.lib.esdg_get_points(self.h, kind, _ptr(x), _ptr(y)))
+        return x, y
+
+    def init_state(self, b_nodal, q_volq, surface=False):
+        b = None if b_nodal is None else np.ascontiguousarray(b_nodal, dtype=np.float64)
+        q = np.ascontiguousarray(q_volq, dtype=np.float64)
+        assert q.shape == (3, self.K, self.Nq)
+        self._check(self.lib.esdg_init_state(self.h, _ptr(b), _ptr(q),
+                                             ESDG_INIT_SURFACE if surface else ESDG_INIT_DEPTH))
+
+    def set_bathymetry(self, b_nodal):
+        b = np.ascontiguousarray(b_nodal, dtype=np.float64)
+        self._check(self.lib.esdg_set_bathymetry(self.h, _ptr(b)))
+
+    def set_state(self, u):
+        """u: numpy (host) or torch CUDA tensor [3][K][Np] float64."""
+        on_dev = 0 if isinstance(u, np.ndarray) else 1
+        if on_dev == 0:
+            u = np.ascontiguousarray(u, dtype=np.float64)
+        assert tuple(u.shape) == (3, self.K, self.Np)
+        self._check(self.lib.esdg_set_state(self.h, _ptr(u), on_dev))
+
+    def get_state(self, out=None):
+        if out is None:
+            out = np.zeros((3, self.K, self.Np))
+        on_dev = 0 if isinstance(out, np.ndarray) else 1
+        self._check(self.lib.esdg_copy_state(self.h, _ptr(out), on_dev))
+        return out
+
+    def rhs(self, t=0.0, u_in=None, out=None):
+        """du/dt as a torch CUDA tensor [3][K][Np] float64."""
+        import torch
+        if out is None:
+            out = torch.empty((3, self.K, self.Np), dtype=torch.float64, device="cuda")
+        self._check(self.lib.esdg_rhs(self.h, t, _ptr(u_in), _ptr(out)))
+        return out
+
+    def step(self, nsteps, dt=0.0, t=0.0):
+        tt = ctypes.c_double(t)
+        self._check(self.lib.esdg_step(self.h, nsteps, dt, ctypes.byref(tt)))
+        return tt.value
+
+    def step_async(self, nsteps, dt=0.0, t=0.0):
+        self._check(self.lib.esdg_step_async(self.h, nsteps, dt, t))
+
+    def check(self):
+        self._check(self.lib.esdg_check(self.h))
+
+    def entropy(self, t=0.0, rate=True):
+        S, M, R = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        self._check(self.lib.esdg_entropy(self.h, t, ctypes.byref(S), ctypes.byref(M),
+                                          ctypes.byref(R) if rate else None))
+        return (S.value, M.value, R.value if rate else None)
+
+    def dt(self):
+        d = ctypes.c_double()
+        self._check(self.lib.esdg_dt(self.h, ctypes.byref(d)))
+        return d.value

@@ -1,0 +1,192 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances.  FP64: relative 1e-12 on the right-hand side and on the state
+after every step (both sides compute the same operator in different forms and
+summation orders: eq. (dgform) literally on the oracle side, the split form of
+Sec. 5.2 on the GPU).  FP32 right-hand side with FP64 RK accumulation:
+relative 1e-5 on the state after the configured steps; the single FP32
+right-hand side is held to 5e-5 relative (each entry sums O(Nh) flux terms of
+size ~|f|/h in FP32 before cancelling to du/dt).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from oracle.esdg import mms_sine_forcing
+from paper_2005_02516_gb300 import workloads as W
+from paper_2005_02516_gb300.workloads import random_modal_state
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from paper_2005_02516_gb300 import esdg
+    if not os.path.exists(esdg.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+
+
+def _solver(w, precision="fp64", lf=True, N=None, nx=None, ny=None):
+    from paper_2005_02516_gb300.esdg import Solver
+    N = w.N if N is None else N
+    nx = w.nx if nx is None else nx
+    ny = nx if ny is None else ny
+    s = Solver(N, nx, ny, precision=precision, warp=w.warp, g=w.g, cfl=w.cfl, lax_friedrichs=lf,
+               forcing=w.forcing)
+    o = Oracle(N, nx, ny, ax=w.warp, ay=w.warp, g=w.g, cfl=w.cfl, lf=lf,
+               forcing=mms_sine_forcing if w.forcing == "mms_sine" else None)
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_NODAL
+    xb, yb = s.points(ESDG_POINTS_NODAL)
+    s.set_bathymetry(w.bathymetry(xb, yb))
+    xo, yo = o.points("nodal")
+    o.set_bathymetry(w.bathymetry(xo, yo))
+    return s, o
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+CASES = [
+    # (workload, N, nx, ny) -- several tiles (8 elements per CTA) and ragged tails
+    (W.LAKE_BUMP, 2, 8, 8),
+    (W.LAKE_BUMP, 1, 5, 3),
+    (W.MMS, 3, 5, 4),
+    (W.MMS, 4, 3, 5),
+    (W.DAM, 4, 6, 5),
+    (W.DAM, 5, 4, 3),
+]
+
+
+@pytest.mark.parametrize("lf", [True, False])
+@pytest.mark.parametrize("w,N,nx,ny", CASES)
+def test_rhs_fp64_matches_oracle(w, N, nx, ny, lf):
+    s, o = _solver(w, "fp64", lf, N, nx, ny)
+    u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + N)
+    s.set_state(u)
+    t = 0.37
+    got = s.rhs(t).cpu().numpy()
+    want = o.rhs(u, t)
+    assert _rel(got, want) < 1e-12
+    assert _relmax(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("w,N,nx,ny", CASES[:4])
+def test_rhs_fp32_matches_oracle(w, N, nx, ny):
+    s, o = _solver(w, "fp32", True, N, nx, ny)
+    u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + 10 + N)
+    s.set_state(u)
+    got = s.rhs(0.1).cpu().numpy()
+    want = o.rhs(u, 0.1)
+    assert _rel(got, want) < 5e-5
+
+
+def test_steps_fp64_config1_match_oracle_every_step():
+    """Config 1 (N=2, K=128 affine, lake at rest plus a bump): per-step parity
+    for 20 steps at relative 1e-12."""
+    w = W.LAKE_BUMP
+    s, o = _solver(w, "fp64")
+    xq, yq = o.points("volq")
+    u = o.init_state(w.initial(xq, yq), surface=True)
+    s.set_state(u)
+    res = np.zeros_like(u)
+    t, dt = 0.0, o.dt()
+    for n in range(20):
+        u, res, t = o.step(u, res, t, dt)
+        s.step(1, dt, t - dt)
+        assert _rel(s.get_state(), u) < 1e-12, n
+
+
+def test_init_state_matches_oracle():
+    w = W.MMS
+    s, o = _solver(w, "fp64", N=3, nx=6)
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
+    xs, ys = s.points(ESDG_POINTS_VOLQ)
+    s.init_state(None, w.initial(xs, ys))
+    xo, yo = o.points("volq")
+    uo = o.init_state(w.initial(xo, yo))
+    assert _rel(s.get_state(), uo) < 1e-13
+
+
+def test_fp32_after_configured_steps_config1():
+    """Config 1 for all 200 configured steps: FP32 RHS with FP64 accumulation
+    within relative 1e-5 of the FP64 oracle; FP64 within 1e-12."""
+    w = W.LAKE_BUMP
+    s64, o = _solver(w, "fp64")
+    s32, _ = _solver(w, "fp32")
+    xq, yq = o.points("volq")
+    u0 = o.init_state(w.initial(xq, yq), surface=True)
+    u, _ = o.run(u0, w.steps)
+    for s, tol in [(s64, 1e-12), (s32, 1e-5)]:
+        s.set_state(u0)
+        s.step(w.steps)
+        assert _rel(s.get_state(), u) < tol
+
+
+def test_lake_at_rest_and_entropy_on_gpu():
+    """Theorem 2.2 on the GPU path: a lake at rest stays at rest, and with the
+    EC flux alone the semi-discrete entropy rate vanishes."""
+    w = W.MMS
+    s, o = _solver(w, "fp64", lf=True, N=3, nx=6)
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
+    xs, ys = s.points(ESDG_POINTS_VOLQ)
+    q = np.stack([2.0 + 0 * xs, 0 * xs, 0 * xs])
+    s.init_state(None, q, surface=True)
+    r = s.rhs().cpu().numpy()
+    assert np.abs(r).max() < 1e-12
+    s2, o2 = _solver(w, "fp64", lf=False, N=3, nx=6)
+    u = random_modal_state(o2.K, o2.Np, seed=7)
+    s2.set_state(u)
+    S, M, R = s2.entropy(0.0)
+    terms = o2.entropy_rate_terms(u, o2.rhs(u))
+    assert abs(R) < 1e-12 * np.abs(terms).sum()
+    assert abs(S - o2.entropy(u)) < 1e-12 * abs(S)
+    assert abs(M - o2.mass(u)) < 1e-12 * abs(M)
+    s2.step(5)
+    S5, M5, _ = s2.entropy(0.0, rate=False)
+    assert abs(M5 - M) < 1e-12 * abs(M)
+
+
+def test_nonpositive_depth_is_reported_not_faulted():
+    from paper_2005_02516_gb300.esdg import EsdgError, ESDG_ENONPOSITIVE
+    w = W.LAKE_BUMP
+    s, o = _solver(w, "fp64")
+    u = random_modal_state(o.K, o.Np, seed=3)
+    u[0] *= -1.0
+    s.set_state(u)
+    with pytest.raises(EsdgError) as ei:
+        s.rhs()
+    assert ei.value.code == ESDG_ENONPOSITIVE
+    # the context stays usable
+    u = random_modal_state(o.K, o.Np, seed=3)
+    s.set_state(u)
+    s.rhs()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-5)])
+def test_full_size_config3_sampled_rhs(precision, tol):
+    """Config 3 at full size (N=4, K=131072 curved): the right-hand side on
+    sampled elements (every 997th, plus the first and last) against the
+    oracle computed element by element, in the launch configuration the
+    benchmark uses."""
+    w = W.DAM
+    s, o = _solver(w, precision)
+    xo, yo = o.points("volq")
+    u = o.init_state(w.initial(xo, yo))
+    s.set_state(u)
+    ks = np.unique(np.concatenate([np.arange(0, o.K, 997), [o.K - 1]]))
+    got = s.rhs(0.0).cpu().numpy()[:, ks]
+    want = o.rhs_elements(u, ks)
+    assert _rel(got, want) < tol

@@ -1,0 +1,108 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol that
+include/esdg.h declares, and its host-side set-up (argument validation, mesh
+and point construction, which touch no GPU) agrees with the oracle's
+conventions.  No compute call runs here."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2005_02516_gb300 import esdg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _lib():
+    if not os.path.exists(esdg.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+    return esdg.load_library()
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "esdg.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(esdg_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declarations_match_binding():
+    assert _declared() == sorted(esdg.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib()
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def _cfg(**kw):
+    c = esdg.Config()
+    c.N, c.nx, c.ny = kw.get("N", 2), kw.get("nx", 4), kw.get("ny", 4)
+    c.precision = kw.get("precision", esdg.ESDG_FP64)
+    c.x0, c.x1, c.y0, c.y1 = -1.0, 1.0, -1.0, 1.0
+    c.warp_ax = c.warp_ay = kw.get("warp", 0.0)
+    c.g, c.cfl = kw.get("g", 1.0), 0.25
+    c.lax_friedrichs, c.forcing = 1, 0
+    return c
+
+
+def _build(**kw):
+    lib = _lib()
+    h = ctypes.c_void_p()
+    rc = lib.esdg_build_operators(ctypes.byref(_cfg(**kw)), ctypes.byref(h))
+    return lib, rc, h
+
+
+@pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7)])
+def test_build_rejects_bad_config(bad):
+    lib, rc, h = _build(**bad)
+    assert rc == esdg.ESDG_EINVAL
+    assert not h.value
+    assert len(lib.esdg_last_error(None)) > 0
+
+
+def test_build_rejects_folding_warp():
+    # an amplitude large enough to fold elements makes J <= 0 somewhere
+    lib, rc, h = _build(N=3, nx=8, ny=8, warp=2.0)
+    assert rc == esdg.ESDG_EINVAL
+    assert b"Jacobian" in lib.esdg_last_error(None)
+
+
+def test_calls_out_of_order_are_refused():
+    lib, rc, h = _build()
+    assert rc == 0
+    u = np.zeros((3, 32, 6))
+    assert lib.esdg_set_state(h, u.ctypes.data, 0) == esdg.ESDG_ESTATE
+    assert lib.esdg_step(h, 1, 0.01, None) == esdg.ESDG_ESTATE
+    lib.esdg_destroy(h)
+
+
+@pytest.mark.parametrize("N,warp", [(1, 0.0), (2, 0.05), (4, 0.05), (5, 0.0)])
+def test_points_and_sizes_match_oracle_conventions(N, warp):
+    from oracle import Oracle
+    lib, rc, h = _build(N=N, nx=5, ny=3, warp=warp)
+    assert rc == 0
+    K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb = ctypes.c_size_t()
+    assert lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq),
+                          ctypes.byref(nb)) == 0
+    o = Oracle(N, 5, 3, ax=warp, ay=warp)
+    assert (K.value, Np.value, Nq.value, Nfq.value) == (o.K, o.Np, o.Nq, o.Nfq)
+    assert nb.value > 0
+    for kind, okind, n in [(esdg.ESDG_POINTS_NODAL, "nodal", Np.value), (esdg.ESDG_POINTS_VOLQ, "volq", Nq.value),
+                           (esdg.ESDG_POINTS_FACEQ, "faceq", Nfq.value)]:
+        x, y = np.zeros((K.value, n)), np.zeros((K.value, n))
+        assert lib.esdg_get_points(h, kind, x.ctypes.data, y.ctypes.data) == 0
+        xo, yo = o.points(okind)
+        # quadrature points may be listed in another order: compare as sets per element
+        key = lambda a, b: np.lexsort((np.round(b, 9), np.round(a, 9)))  # noqa: E731
+        for e in range(K.value):
+            i, j = key(x[e], y[e]), key(xo[e], yo[e])
+            assert np.abs(x[e, i] - xo[e, j]).max() < 1e-13
+            assert np.abs(y[e, i] - yo[e, j]).max() < 1e-13
+    dt = ctypes.c_double()
+    assert lib.esdg_dt(h, ctypes.byref(dt)) == 0
+    assert abs(dt.value - o.dt()) < 1e-15
+    lib.esdg_destroy(h)

@@ -34,6 +34,7 @@ from paper_2005_02516_gb300 import workloads as W  # noqa: E402
 METRIC = "GDOF-stage/s FP32 vs FP64 per GB300 at stated L2 error; served p50/p99 latency"
 UNIT = "GDOF-stage/s"
 WL = W.DAM
+KERNEL_VERSION = "k_stage2-v1"  # the stage kernel the committed traffic counters describe
 
 # Algorithmic work of one element-stage at degree N ("roofline").
 def algorithmic_flops(N):
@@ -294,7 +295,7 @@ def main():
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        if tj.get("kernel_version") == "k_stage-v1":
+        if tj.get("kernel_version") == KERNEL_VERSION:
             traffic = tj.get("dram_bytes_per_launch")
     roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
                 "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}

@@ -38,6 +38,8 @@ extern "C" {
 #define ESDG_ENONPOSITIVE -4  /* the device found an entropy-projected depth <= 0 */
 #define ESDG_ENONFINITE   -5  /* the device found a non-finite value */
 #define ESDG_ESTATE       -6  /* call out of order (e.g. no device memory attached) */
+#define ESDG_ETIMEOUT     -7  /* a bounded device-side wait (on an asynchronous copy) expired;
+                                 the kernel stopped early and the state is not valid */
 
 /* arithmetic of the right-hand side; state and RK accumulation are always FP64 */
 #define ESDG_FP64 0

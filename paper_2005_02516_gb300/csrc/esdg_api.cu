@@ -41,6 +41,7 @@ using namespace esdg;
 // Device memory map (offsets into one buffer, each 256-byte aligned).
 struct DevLayout {
     size_t ops = 0, ops_bytes = 0;       // reference operators (real)
+    size_t ops2 = 0, ops2_bytes = 0;     // permuted operators of the FP32 batched kernel
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
@@ -61,7 +62,11 @@ struct esdg_ctx {
     unsigned char* dbuf = nullptr;
     cudaStream_t stream = nullptr;
     DevLayout L;
-    LaunchGeom lg;
+    LaunchGeom lg;       // k_stage (FP64)
+    LaunchGeom lg_proj;  // k_project
+    LaunchGeom lg2;      // k_stage2 (FP32)
+    int Kpad = 0;        // per-element arrays are padded to a multiple of 8 elements
+    int mstride = 0;     // element stride of the packed inverse mass matrices
     int entropy_parts = 0;
     int num_sms = 0;
     int cur = 0;            // which u~ buffer holds the current stage's values
@@ -86,32 +91,39 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 static size_t real_size(const esdg_ctx* c) { return c->cfg.precision == ESDG_FP32 ? 4 : 8; }
 
+static int c2_ops_floats(int N);
+
 static void compute_layout(esdg_ctx* c) {
     const RefOps& R = c->ref;
     const size_t rs = real_size(c);
     const size_t K = size_t(c->mesh.K);
+    c->Kpad = int((K + 7) / 8 * 8);
+    const size_t Kp = size_t(c->Kpad);
     const int NpP = R.Np * (R.Np + 1) / 2;
+    c->mstride = (NpP + 3) & ~3;
     DevLayout& L = c->L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq));
     L.ops = take(L.ops_bytes);
+    L.ops2_bytes = c->cfg.precision == ESDG_FP32 ? 4 * size_t(c2_ops_floats(c->cfg.N)) : 0;
+    L.ops2 = take(L.ops2_bytes);
     L.vq64 = take(8 * size_t(R.Nq) * R.Np);
-    L.geo = take(rs * K * R.Nh * 4);
-    L.wJq = take(rs * K * R.Nq);
-    L.minv = take(rs * K * NpP);
-    L.bh = take(rs * K * R.Nh);
-    L.nbr = take(4 * K * 3);
+    L.geo = take(rs * Kp * R.Nh * 4);
+    L.wJq = take(rs * Kp * R.Nq);
+    L.minv = take(rs * Kp * c->mstride);
+    L.bh = take(rs * Kp * R.Nh);
+    L.nbr = take(4 * Kp * 3);
     const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
-    L.xq = take(forcing ? rs * K * R.Nq : 0);
-    L.yq = take(forcing ? rs * K * R.Nq : 0);
+    L.xq = take(forcing ? rs * Kp * R.Nq : 0);
+    L.yq = take(forcing ? rs * Kp * R.Nq : 0);
     L.wJq64 = take(8 * K * R.Nq);
     L.bq64 = take(8 * K * R.Nq);
     L.u = take(8 * 3 * K * R.Np);
     L.res = take(8 * 3 * K * R.Np);
     L.rhs = take(8 * 3 * K * R.Np);
-    L.ut0 = take(rs * K * R.Nh * 4);
-    L.ut1 = take(rs * K * R.Nh * 4);
+    L.ut0 = take(rs * Kp * R.Nh * 4);
+    L.ut1 = take(rs * Kp * R.Nh * 4);
     c->entropy_parts = 1024;
     L.partial = take(8 * 3 * size_t(c->entropy_parts));
     L.diag = take(8 * 4);
@@ -150,6 +162,71 @@ static std::vector<real> pack_ops(const RefOps& R) {
     return o;
 }
 
+// Operators of k_stage2 in its shared-memory layout (see C2<N> in esdg_stage2.cuh).
+template <int N>
+static std::vector<float> pack_ops2_t(const RefOps& R) {
+    typedef C2<N> C;
+    const int LPE = C::LPE;
+    std::vector<float> o(C::o_end, 0.f);
+    for (int m = 0; m < R.Nh; ++m)
+        for (int b = 0; b < LPE; ++b)
+            for (int i = 0; i < C::RPL; ++i) {
+                const int l = b + LPE * i;
+                if (l >= R.Nh) continue;
+                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)R.Qsr(l, m);
+                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)R.Qss(l, m);
+            }
+    for (int l = 0; l < R.Nh; ++l)
+        for (int b = 0; b < LPE; ++b)
+            for (int j = 0; j < C::MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < R.Np) o[C::o_VhT + (l * LPE + b) * C::MPLp + j] = (float)R.Vh(l, n);
+            }
+    for (int q = 0; q < R.Nq; ++q)
+        for (int b = 0; b < LPE; ++b)
+            for (int j = 0; j < C::MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < R.Np) o[C::o_VqT + (q * LPE + b) * C::MPLp + j] = (float)R.Vq(q, n);
+            }
+    for (int n = 0; n < R.Np; ++n)
+        for (int b = 0; b < LPE; ++b) {
+            for (int j = 0; j < C::QPL; ++j) {
+                const int q = b + LPE * j;
+                if (q < R.Nq) o[C::o_Vq + (n * LPE + b) * C::QPLp + j] = (float)R.Vq(q, n);
+            }
+            for (int j = 0; j < C::RPL; ++j) {
+                const int l = b + LPE * j;
+                if (l < R.Nh) o[C::o_Vh + (n * LPE + b) * C::RPLp + j] = (float)R.Vh(l, n);
+            }
+        }
+    for (int f = 0; f < R.Nfq; ++f) {
+        o[C::o_wf + f] = (float)R.wf[f];
+        o[C::o_nrs + 2 * f] = (float)R.nr[f];
+        o[C::o_nrs + 2 * f + 1] = (float)R.ns[f];
+    }
+    return o;
+}
+
+static int c2_ops_floats(int N) {
+    switch (N) {
+        case 1: return C2<1>::o_end;
+        case 2: return C2<2>::o_end;
+        case 3: return C2<3>::o_end;
+        case 4: return C2<4>::o_end;
+        default: return C2<5>::o_end;
+    }
+}
+
+static std::vector<float> pack_ops2(const RefOps& R) {
+    switch (R.N) {
+        case 1: return pack_ops2_t<1>(R);
+        case 2: return pack_ops2_t<2>(R);
+        case 3: return pack_ops2_t<3>(R);
+        case 4: return pack_ops2_t<4>(R);
+        default: return pack_ops2_t<5>(R);
+    }
+}
+
 template <typename real>
 static int upload_static(esdg_ctx* c) {
     const RefOps& R = c->ref;
@@ -160,15 +237,25 @@ static int upload_static(esdg_ctx* c) {
     std::vector<real> ops = pack_ops<real>(R);
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.ops, ops.data(), ops.size() * sizeof(real), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.vq64, R.Vq.a.data(), R.Vq.a.size() * 8, cudaMemcpyHostToDevice, s));
-    std::vector<real> geo = to_real<real>(M.geo);
+    // the FP32 batched kernel reads the metrics pre-scaled by 1/8 (exact)
+    const double gscale = c->cfg.precision == ESDG_FP32 ? 0.125 : 1.0;
+    std::vector<real> geo(M.geo.size());
+    for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.geo, geo.data(), geo.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+    if (c->cfg.precision == ESDG_FP32) {
+        std::vector<float> o2 = pack_ops2(R);
+        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.ops2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, s));
+    }
     std::vector<double> wJ64(K * R.Nq);
     for (size_t e = 0; e < K; ++e)
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
     std::vector<real> wJ = to_real<real>(wJ64);
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq, wJ.data(), wJ.size() * sizeof(real), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq64, wJ64.data(), wJ64.size() * 8, cudaMemcpyHostToDevice, s));
-    std::vector<real> mi = to_real<real>(M.minv);
+    const int NpP = R.Np * (R.Np + 1) / 2;
+    std::vector<real> mi(K * size_t(c->mstride), (real)0);
+    for (size_t e = 0; e < K; ++e)
+        for (int i = 0; i < NpP; ++i) mi[e * c->mstride + i] = (real)M.minv[e * NpP + i];
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.minv, mi.data(), mi.size() * sizeof(real), cudaMemcpyHostToDevice, s));
     CUDA_TRY(c, cudaMemcpyAsync(d + c->L.nbr, M.nbr.data(), M.nbr.size() * 4, cudaMemcpyHostToDevice, s));
     if (c->cfg.forcing != ESDG_FORCING_NONE) {
@@ -225,6 +312,7 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.geo = reinterpret_cast<const real*>(d + c->L.geo);
     p.wJq = reinterpret_cast<const real*>(d + c->L.wJq);
     p.minv = reinterpret_cast<const real*>(d + c->L.minv);
+    p.mstride = c->mstride;
     p.bh = reinterpret_cast<const real*>(d + c->L.bh);
     p.nbr = reinterpret_cast<const int*>(d + c->L.nbr);
     p.xq = reinterpret_cast<const real*>(d + c->L.xq);
@@ -248,15 +336,27 @@ static real* ut_buf(esdg_ctx* c, int which) {
 }
 
 // ---- degree dispatch ---------------------------------------------------------
-template <typename real>
-static cudaError_t d_geometry(int N, int sms, LaunchGeom& lg) {
-    switch (N) {
-        case 1: return stage_geometry<1, real>(sms, lg);
-        case 2: return stage_geometry<2, real>(sms, lg);
-        case 3: return stage_geometry<3, real>(sms, lg);
-        case 4: return stage_geometry<4, real>(sms, lg);
-        default: return stage_geometry<5, real>(sms, lg);
+static cudaError_t d_geometry(esdg_ctx* c) {
+    const int N = c->cfg.N, sms = c->num_sms;
+    cudaError_t e = cudaSuccess;
+    if (c->cfg.precision == ESDG_FP32) {
+        switch (N) {
+            case 1: e = project_geometry<1, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<1>(sms, c->lg2); break;
+            case 2: e = project_geometry<2, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<2>(sms, c->lg2); break;
+            case 3: e = project_geometry<3, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<3>(sms, c->lg2); break;
+            case 4: e = project_geometry<4, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<4>(sms, c->lg2); break;
+            default: e = project_geometry<5, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<5>(sms, c->lg2); break;
+        }
+    } else {
+        switch (N) {
+            case 1: e = project_geometry<1, double>(sms, c->lg_proj); if (!e) e = stage_geometry<1, double>(sms, c->lg); break;
+            case 2: e = project_geometry<2, double>(sms, c->lg_proj); if (!e) e = stage_geometry<2, double>(sms, c->lg); break;
+            case 3: e = project_geometry<3, double>(sms, c->lg_proj); if (!e) e = stage_geometry<3, double>(sms, c->lg); break;
+            case 4: e = project_geometry<4, double>(sms, c->lg_proj); if (!e) e = stage_geometry<4, double>(sms, c->lg); break;
+            default: e = project_geometry<5, double>(sms, c->lg_proj); if (!e) e = stage_geometry<5, double>(sms, c->lg); break;
+        }
     }
+    return e;
 }
 template <typename real>
 static cudaError_t d_project(int N, const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
@@ -268,14 +368,25 @@ static cudaError_t d_project(int N, const StageParams<real>& p, const LaunchGeom
         default: return launch_project<5, real>(p, lg, s);
     }
 }
-template <typename real>
-static cudaError_t d_stage(int N, const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s) {
-    switch (N) {
-        case 1: return launch_stage<1, real>(p, mode, lg, s);
-        case 2: return launch_stage<2, real>(p, mode, lg, s);
-        case 3: return launch_stage<3, real>(p, mode, lg, s);
-        case 4: return launch_stage<4, real>(p, mode, lg, s);
-        default: return launch_stage<5, real>(p, mode, lg, s);
+static cudaError_t d_stage(esdg_ctx* c, const StageParams<double>& p, int mode) {
+    const LaunchGeom& lg = c->lg;
+    switch (c->cfg.N) {
+        case 1: return launch_stage<1, double>(p, mode, lg, c->stream);
+        case 2: return launch_stage<2, double>(p, mode, lg, c->stream);
+        case 3: return launch_stage<3, double>(p, mode, lg, c->stream);
+        case 4: return launch_stage<4, double>(p, mode, lg, c->stream);
+        default: return launch_stage<5, double>(p, mode, lg, c->stream);
+    }
+}
+static cudaError_t d_stage(esdg_ctx* c, const StageParams<float>& p, int mode) {
+    const LaunchGeom& lg = c->lg2;
+    const float* ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
+    switch (c->cfg.N) {
+        case 1: return launch_stage2<1>(p, ops2, c->Kpad, mode, lg, c->stream);
+        case 2: return launch_stage2<2>(p, ops2, c->Kpad, mode, lg, c->stream);
+        case 3: return launch_stage2<3>(p, ops2, c->Kpad, mode, lg, c->stream);
+        case 4: return launch_stage2<4>(p, ops2, c->Kpad, mode, lg, c->stream);
+        default: return launch_stage2<5>(p, ops2, c->Kpad, mode, lg, c->stream);
     }
 }
 static cudaError_t d_entropy(int N, int K, double g, const double* u, const double* rhs, const double* Vq,
@@ -297,6 +408,8 @@ static int check_status(esdg_ctx* c) {
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     if (st[0]) {
         CUDA_TRY(c, cudaMemsetAsync(dst, 0, 4, c->stream));
+        if (st[0] & STATUS_TIMEOUT)
+            return fail(c, ESDG_ETIMEOUT, "a bounded wait on an asynchronous copy expired in the stage kernel");
         if (st[0] & STATUS_NONFINITE) return fail(c, ESDG_ENONFINITE, "non-finite entropy-projected state");
         return fail(c, ESDG_ENONPOSITIVE, "non-positive (entropy-projected) depth");
     }
@@ -308,7 +421,7 @@ static int project_current(esdg_ctx* c, const double* u_in, int target) {
     StageParams<real> p = make_params<real>(c);
     if (u_in) p.u_in = u_in;
     p.ut_out = ut_buf<real>(c, target);
-    CUDA_TRY(c, d_project<real>(c->cfg.N, p, c->lg, c->stream));
+    CUDA_TRY(c, d_project<real>(c->cfg.N, p, c->lg_proj, c->stream));
     return ESDG_OK;
 }
 
@@ -320,7 +433,7 @@ static int rhs_t(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
     p.ut_in = ut_buf<real>(c, c->cur ^ 1);
     p.rhs_out = rhs_out;
     p.t = t;
-    CUDA_TRY(c, d_stage<real>(c->cfg.N, p, 0, c->lg, c->stream));
+    CUDA_TRY(c, d_stage(c, p, 0));
     return ESDG_OK;
 }
 
@@ -340,7 +453,7 @@ static int step_t(esdg_ctx* c, int nsteps, double dt, double t0) {
             p.rkA = RK_A[s];
             p.rkB = RK_B[s];
             p.t = t0 + n * dt + RK_C[s] * dt;
-            CUDA_TRY(c, d_stage<real>(c->cfg.N, p, 1, c->lg, c->stream));
+            CUDA_TRY(c, d_stage(c, p, 1));
             c->cur ^= 1;
         }
     return ESDG_OK;
@@ -409,13 +522,11 @@ int esdg_attach_device(esdg_ctx* c, void* buffer, size_t bytes, void* stream) {
     CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(c, cudaMemsetAsync(c->dbuf, 0, c->L.total, c->stream));
     int rc;
-    if (c->cfg.precision == ESDG_FP32) {
-        CUDA_TRY(c, d_geometry<float>(c->cfg.N, c->num_sms, c->lg));
+    CUDA_TRY(c, d_geometry(c));
+    if (c->cfg.precision == ESDG_FP32)
         rc = upload_static<float>(c);
-    } else {
-        CUDA_TRY(c, d_geometry<double>(c->cfg.N, c->num_sms, c->lg));
+    else
         rc = upload_static<double>(c);
-    }
     if (rc) return rc;
     c->attached = true;
     return upload_bathymetry(c);

@@ -59,7 +59,8 @@ struct StageParams {
     // per element
     const real* geo;   // [K][Nh][4] rxJ sxJ ryJ syJ
     const real* wJq;   // [K][Nq]   w_q J_q
-    const real* minv;  // [K][NpP]  packed (M_h^k)^{-1}
+    const real* minv;  // [K][mstride] packed (M_h^k)^{-1}
+    int mstride;       // element stride of minv (NpP rounded up to a multiple of 4)
     const real* bh;    // [K][Nh]   bathymetry at hybrid nodes
     const int* nbr;    // [K][3]    4 * neighbour element + neighbour face
     const real* xq;    // [K][Nq]   (forcing only)
@@ -241,7 +242,7 @@ template <int N, typename real>
 __device__ __forceinline__ void load_minv(const StageParams<real>& p, real* ws, int e, int lane) {
     typedef Dims<N> D;
     typedef Smem<N, real> S;
-    for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * D::NpP + i];
+    for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * p.mstride + i];
 }
 
 // Standalone projection: u_in (FP64 modal) -> ut_out.

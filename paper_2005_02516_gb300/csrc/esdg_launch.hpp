@@ -5,11 +5,13 @@
 #include <cuda_runtime.h>
 
 #include "esdg_kernels.cuh"
+#include "esdg_stage2.cuh"
 
 namespace esdg {
 
-// Launch geometry of the persistent stage kernels for degree N and type real:
-// CTAs of 8 warps (one element per warp), as many CTAs per SM as fit.
+// Launch geometry of the persistent warp-per-element kernels (k_stage for the
+// FP64 right-hand side, k_project for both precisions): CTAs of 8 warps, as
+// many CTAs per SM as fit.
 struct LaunchGeom {
     int block = 256;
     int grid = 0;
@@ -19,9 +21,17 @@ struct LaunchGeom {
 template <int N, typename real>
 cudaError_t stage_geometry(int num_sms, LaunchGeom& lg);
 template <int N, typename real>
+cudaError_t project_geometry(int num_sms, LaunchGeom& lg);
+template <int N, typename real>
 cudaError_t launch_project(const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s);
 template <int N, typename real>
 cudaError_t launch_stage(const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s);
+// FP32 batched stage kernel (esdg_stage2.cuh): one CTA of 12 warps per SM.
+template <int N>
+cudaError_t stage2_geometry(int num_sms, LaunchGeom& lg);
+template <int N>
+cudaError_t launch_stage2(const StageParams<float>& p, const float* ops2, int Kpad, int mode, const LaunchGeom& lg,
+                          cudaStream_t s);
 template <int N>
 cudaError_t launch_entropy(int K, double g, const double* u, const double* rhs, const double* Vq, const double* wJq,
                            const double* bq, double* partial, int nparts, double* out, cudaStream_t s);

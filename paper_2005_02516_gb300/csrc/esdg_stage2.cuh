@@ -1,0 +1,531 @@
+// Batched FP32 stage kernel for sm_103a (RHS in FP32, RK state in FP64).
+//
+// Same operator as k_stage (the split form of Sec. 5.2 with the curved metric
+// average of Sec. 2.7, the EC flux of eqs. (SWE_flux1/2) with its folded
+// well-balanced bathymetry term, interface flux + Lax-Friedrichs of Sec. 2.8,
+// lift, stored inverse curved mass matrix, LSRK45 stage of Sec. 4, and the
+// entropy projection of Sec. 2.6 for the next stage), mapped differently:
+//
+//  * a warp processes a batch of EPW = 32/LPE elements; LPE lanes share one
+//    element.  Lane (e, b) owns the hybrid rows l = b + LPE*i, i < RPL, with
+//    their node data and three accumulators in registers, so a column m is
+//    read from shared memory once for RPL rows (the flux differencing is
+//    FP32-ALU bound, and this keeps shared-memory traffic well below it).
+//    Interleaving rows across the LPE lanes balances volume rows (all Nh
+//    columns) against face rows (Nq columns: the lower-right block of
+//    Q_skew is zero).
+//  * the element data of a batch (u~, metrics, inverse mass) arrive in
+//    shared memory by TMA bulk copies (cp.async.bulk) on a per-warp mbarrier,
+//    one copy per element into slots padded so that the column reads of the
+//    EPW elements of a warp fall in distinct banks.  The wait is bounded.
+//  * lift, inverse mass and projection spread modes, nodes or fields over
+//    the LPE lanes of an element, with the permuted operators in shared
+//    memory laid out so each lane reads contiguous float4s.
+#pragma once
+
+#include "esdg_kernels.cuh"
+
+namespace esdg {
+
+constexpr int STATUS_TIMEOUT = 4;
+
+template <int N>
+struct C2 {
+    typedef Dims<N> D;
+    static constexpr int LPE = (N >= 5) ? 8 : 4;            // lanes per element
+    static constexpr int EPW = 32 / LPE;                    // elements per warp
+    static constexpr int RPL = (D::Nh + LPE - 1) / LPE;     // hybrid rows per lane
+    static constexpr int QPL = (D::Nq + LPE - 1) / LPE;     // volume nodes per lane
+    static constexpr int MPL = (D::Np + LPE - 1) / LPE;     // modes per lane
+    static constexpr int OPB = (2 * RPL + 3) & ~3;          // operator entries per (column, lane slot)
+    static constexpr int RPLp = (RPL + 3) & ~3;
+    static constexpr int QPLp = (QPL + 3) & ~3;
+    static constexpr int MPLp = (MPL + 3) & ~3;
+    static constexpr int NpP4 = (D::NpP + 3) & ~3;          // padded packed inverse-mass stride
+    static constexpr int UTS = D::Nh * 4 + 4;               // element slot of u~ / metric staging
+    static constexpr int MIS = NpP4 + 4;                    // element slot of inverse-mass staging
+    // operator region (floats)
+    static constexpr int o_Qs = 0;                                  // [Nh][LPE][OPB]
+    static constexpr int o_VhT = o_Qs + D::Nh * LPE * OPB;          // [Nh][LPE][MPLp]: Vh[l][b+LPE j]
+    static constexpr int o_VqT = o_VhT + D::Nh * LPE * MPLp;        // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
+    static constexpr int o_Vq = o_VqT + D::Nq * LPE * MPLp;         // [Np][LPE][QPLp]: Vq[b+LPE j][n]
+    static constexpr int o_Vh = o_Vq + D::Np * LPE * QPLp;          // [Np][LPE][RPLp]: Vh[b+LPE j][n]
+    static constexpr int o_wf = o_Vh + D::Np * LPE * RPLp;          // [Nfq]
+    static constexpr int o_nrs = o_wf + D::Nfq;                     // [Nfq][2]
+    static constexpr int o_end = (o_nrs + 2 * D::Nfq + 3) & ~3;
+    // per-warp region (floats)
+    static constexpr int w_ut = 0;                          // [EPW][UTS]  h u v H
+    static constexpr int w_geo = w_ut + EPW * UTS;          // [EPW][UTS]  rxJ sxJ ryJ syJ (scaled 1/8)
+    static constexpr int w_tr = w_geo + EPW * UTS;          // [EPW][Nfq][4] neighbour traces
+    static constexpr int w_mi = w_tr + EPW * D::Nfq * 4;    // [EPW][MIS]  packed (M_h^k)^-1
+    static constexpr int w_end = (w_mi + EPW * MIS + 3) & ~3;
+    // scratch aliases, live after the volume/interface phase
+    static constexpr int s_rt = w_ut;                       // [3][Nh][EPW]
+    static constexpr int s_t = w_geo;                       // [3][Nq][EPW]
+    static constexpr int s_s = w_geo + 3 * D::Nq * EPW;     // [3][Np][EPW]
+    static constexpr int s_u = w_tr;                        // [3][Np][EPW]
+    static_assert(3 * D::Nh <= UTS, "rt scratch");
+    static_assert(3 * D::Nq * EPW + 3 * D::Np * EPW <= EPW * UTS, "t/s scratch");
+    static_assert(3 * D::Np <= D::Nfq * 4, "u scratch");
+    static constexpr int WARPS = 12;
+    static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
+    static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + NpP4 * 4);
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Wait for phase `parity` of bar, giving up after ~2^31 SM cycles (about a
+// second): then the status word gets STATUS_TIMEOUT and the caller returns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* status) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            atomicOr(status, STATUS_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// One field-per-lane application of the packed symmetric (M_h^k)^{-1}:
+// y (in registers) -> out.
+template <int Np>
+__device__ __forceinline__ void minv_apply(const float* __restrict__ M, const float (&y)[Np], float (&out)[Np]) {
+#pragma unroll
+    for (int n = 0; n < Np; ++n) out[n] = 0.f;
+#pragma unroll
+    for (int n = 0; n < Np; ++n) {
+#pragma unroll
+        for (int j = 0; j <= n; ++j) {
+            const float m = M[n * (n + 1) / 2 + j];
+            out[n] = fmaf(m, y[j], out[n]);
+            if (j < n) out[j] = fmaf(m, y[n], out[j]);
+        }
+    }
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const float* __restrict__ ops2, int Kpad) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* ops = reinterpret_cast<float*>(smem_raw);
+    const int nwarps = blockDim.x >> 5;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + C::o_end + nwarps * C::w_end);
+    for (int i = threadIdx.x; i < C::o_end / 4; i += blockDim.x)
+        reinterpret_cast<float4*>(ops)[i] = reinterpret_cast<const float4*>(ops2)[i];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) mbar_init(&bars[warp], 1);
+    fence_mbar_init();
+    __syncthreads();
+    uint64_t* bar = &bars[warp];
+    float* ws = ops + C::o_end + warp * C::w_end;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const float g = p.g;
+    const float ig = 1.f / g;
+    const int K = p.K;
+    uint32_t parity = 0;
+    const int nbatch = Kpad / EPW;
+    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps) {
+        const int e0 = batch * EPW;
+        const int ge = e0 + e;
+        const bool valid = ge < K;
+        // ---- stage element data: TMA bulk copies (one per element and array) ----
+        if (lane == 0) mbar_arrive_expect_tx(bar, C::TX_BYTES);
+        __syncwarp();
+        if (lane < 3 * EPW) {
+            const int which = lane / EPW, ee = lane - which * EPW;
+            if (which == 0)
+                tma_bulk_g2s(ws + C::w_ut + ee * C::UTS, p.ut_in + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
+            else if (which == 1)
+                tma_bulk_g2s(ws + C::w_geo + ee * C::UTS, p.geo + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
+            else
+                tma_bulk_g2s(ws + C::w_mi + ee * C::MIS, p.minv + (size_t)(e0 + ee) * C::NpP4, C::NpP4 * 4, bar);
+        }
+        // neighbour traces (a gather; plain loads while the bulk copies fly)
+        for (int k = lane; k < EPW * D::Nfq; k += 32) {
+            const int ee = k / D::Nfq, f = k - ee * D::Nfq;
+            const int face = f / D::Nfp, i = f - face * D::Nfp;
+            const int nb = p.nbr[(size_t)(e0 + ee) * 3 + face];
+            const int en = nb >> 2, fn = nb & 3;
+            const float4 v = *reinterpret_cast<const float4*>(
+                p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4);
+            *reinterpret_cast<float4*>(ws + C::w_tr + k * 4) = v;
+        }
+        if (!mbar_wait_bounded(bar, parity, p.status)) return;
+        parity ^= 1;
+        __syncwarp();
+
+        // ---- volume flux differencing, rows l = b + LPE*i ------------------------
+        const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
+        const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
+        float rhu[RPL], rhv[RPL], ru[RPL], rv[RPL], rgh[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
+        float a0[RPL], a1[RPL], a2[RPL];
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+            const int l = b + LPE * i;
+            float4 U = make_float4(0.f, 0.f, 0.f, 0.f), G = U;
+            if (l < D::Nh) {
+                U = utE[l];
+                G = geE[l];
+            }
+            rhu[i] = U.x * U.y;
+            rhv[i] = U.x * U.z;
+            ru[i] = U.y;
+            rv[i] = U.z;
+            rgh[i] = 2.f * g * U.x;
+            rrx[i] = G.x;
+            rsx[i] = G.y;
+            rry[i] = G.z;
+            rsy[i] = G.w;
+            a0[i] = a1[i] = a2[i] = 0.f;
+        }
+        const float* QsB = ops + C::o_Qs + b * C::OPB;
+#define ESDG_PAIR(I, QR, QS)                                                   \
+    {                                                                          \
+        const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
+        const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
+        const float HU = rhu[I] + hum, HV = rhv[I] + hvm;                      \
+        const float Us = ru[I] + U.y, Vs = rv[I] + U.z;                        \
+        const float T = fmaf(Qx, HU, Qy * HV);                                 \
+        const float P = rgh[I] * U.w;                                          \
+        a0[I] += T;                                                            \
+        a1[I] = fmaf(Us, T, fmaf(Qx, P, a1[I]));                               \
+        a2[I] = fmaf(Vs, T, fmaf(Qy, P, a2[I]));                               \
+    }
+        for (int m = 0; m < D::Nq; ++m) {
+            const float4 U = utE[m], G = geE[m];
+            const float hum = U.x * U.y, hvm = U.x * U.z;
+            const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
+#pragma unroll
+            for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
+                const float4 q = q4[i2];
+                ESDG_PAIR(2 * i2, q.x, q.y)
+                if (2 * i2 + 1 < RPL) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
+            }
+        }
+        for (int m = D::Nq; m < D::Nh; ++m) {
+            const float4 U = utE[m], G = geE[m];
+            const float hum = U.x * U.y, hvm = U.x * U.z;
+            const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
+#pragma unroll
+            for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
+                if (LPE * (2 * i2) < D::Nq) {
+                    const float4 q = q4[i2];
+                    // face rows (l >= Nq) have no face columns; their entries are zero,
+                    // so the predicate only skips work
+                    if (b + LPE * (2 * i2) < D::Nq) ESDG_PAIR(2 * i2, q.x, q.y)
+                    if (2 * i2 + 1 < RPL && b + LPE * (2 * i2 + 1) < D::Nq) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
+                }
+            }
+        }
+#undef ESDG_PAIR
+        // ---- interface flux on the face rows ------------------------------------
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+            a0[i] *= 2.f;
+            const int l = b + LPE * i;
+            if (LPE * i + LPE - 1 >= D::Nq && l >= D::Nq && l < D::Nh) {
+                const int f = l - D::Nq;
+                const float4 U = utE[l];
+                const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
+                const float h_l = U.x, b_l = U.w - U.x;
+                const float hP = tp.x, uP = tp.y, vP = tp.z;
+                const float huP = hP * uP, hvP = hP * vP;
+                const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
+                const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
+                const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
+                const float w = ops[C::o_wf + f];
+                const float huA = 0.5f * (rhu[i] + huP), hvA = 0.5f * (rhv[i] + hvP);
+                const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
+                const float pw = 0.5f * g * h_l * (hP + b_l);
+                const float Fn0 = nxJ * huA + nyJ * hvA;
+                a0[i] += w * Fn0;
+                a1[i] += w * (uA * Fn0 + nxJ * pw);
+                a2[i] += w * (vA * Fn0 + nyJ * pw);
+                if (p.lf) {
+                    const float sJ = sqrtf(nxJ * nxJ + nyJ * nyJ);
+                    const float inx = nxJ / sJ, iny = nyJ / sJ;
+                    const float lm = fabsf(ru[i] * inx + rv[i] * iny) + sqrtf(g * h_l);
+                    const float lp = fabsf(uP * inx + vP * iny) + sqrtf(g * hP);
+                    const float c = 0.5f * w * sJ * fmaxf(lm, lp);
+                    a0[i] -= c * (hP - h_l);
+                    a1[i] -= c * (huP - rhu[i]);
+                    a2[i] -= c * (hvP - rhv[i]);
+                }
+            }
+        }
+        __syncwarp();  // every lane is done with the u~ / metric staging
+        float* rt = ws + C::s_rt;
+#pragma unroll
+        for (int i = 0; i < RPL; ++i) {
+            const int l = b + LPE * i;
+            if (l < D::Nh) {
+                rt[(0 * D::Nh + l) * EPW + e] = a0[i];
+                rt[(1 * D::Nh + l) * EPW + e] = a1[i];
+                rt[(2 * D::Nh + l) * EPW + e] = a2[i];
+            }
+        }
+        // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
+        float* ts = ws + C::s_t;
+        if (p.forcing) {
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = b + LPE * j;
+                if (q < D::Nq) {
+                    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                    if (valid) {
+                        const float x = p.xq[(size_t)ge * D::Nq + q], y = p.yq[(size_t)ge * D::Nq + q];
+                        const float wj = p.wJq[(size_t)ge * D::Nq + q];
+                        float sth, cth, sx, cx, sy, cy;
+                        sincospif(x + y - (float)p.t, &sth, &cth);
+                        sincospif(x, &sx, &cx);
+                        sincospif(y, &sy, &cy);
+                        const float pi = 3.14159265358979323846f;
+                        const float h = 2.f + p.mms_amp * sth;
+                        const float cc = p.mms_amp * pi * cth;
+                        const float bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
+                        const float u0 = p.mms_u0, v0 = p.mms_v0;
+                        f0 = wj * (-cc + u0 * cc + v0 * cc);
+                        f1 = wj * (-u0 * cc + (u0 * u0 + g * h) * cc + u0 * v0 * cc + g * h * bx);
+                        f2 = wj * (-v0 * cc + u0 * v0 * cc + (v0 * v0 + g * h) * cc + g * h * by);
+                    }
+                    ts[(0 * D::Nq + q) * EPW + e] = f0;
+                    ts[(1 * D::Nq + q) * EPW + e] = f1;
+                    ts[(2 * D::Nq + q) * EPW + e] = f2;
+                }
+            }
+        }
+        __syncwarp();
+        // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j ------------------
+        float* ss = ws + C::s_s;
+        {
+            float s0[MPL], s1[MPL], s2[MPL];
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) s0[j] = s1[j] = s2[j] = 0.f;
+            for (int l = 0; l < D::Nh; ++l) {
+                const float r0 = rt[(0 * D::Nh + l) * EPW + e];
+                const float r1 = rt[(1 * D::Nh + l) * EPW + e];
+                const float r2 = rt[(2 * D::Nh + l) * EPW + e];
+                const float* v = ops + C::o_VhT + (l * LPE + b) * C::MPLp;
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    s0[j] = fmaf(v[j], r0, s0[j]);
+                    s1[j] = fmaf(v[j], r1, s1[j]);
+                    s2[j] = fmaf(v[j], r2, s2[j]);
+                }
+            }
+            if (p.forcing) {
+                for (int q = 0; q < D::Nq; ++q) {
+                    const float f0 = ts[(0 * D::Nq + q) * EPW + e];
+                    const float f1 = ts[(1 * D::Nq + q) * EPW + e];
+                    const float f2 = ts[(2 * D::Nq + q) * EPW + e];
+                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                    for (int j = 0; j < MPL; ++j) {
+                        s0[j] = fmaf(-v[j], f0, s0[j]);
+                        s1[j] = fmaf(-v[j], f1, s1[j]);
+                        s2[j] = fmaf(-v[j], f2, s2[j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = s0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = s1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = s2[j];
+                }
+            }
+        }
+        __syncwarp();
+        // ---- du/dt = -(M_h^k)^{-1} s (field per lane), then output or RK ----------
+        const float* Mi = ws + C::w_mi + e * C::MIS;
+        float* us = ws + C::s_u;
+        if (b < 3) {
+            // RK operands (field per lane: lane b < 3 owns field b); their loads
+            // overlap the inverse-mass arithmetic below
+            double ur[D::Np], rr[D::Np];
+            if (MODE == 1 && valid) {
+#pragma unroll
+                for (int n = 0; n < D::Np; ++n) {
+                    const size_t gi = ((size_t)b * K + ge) * D::Np + n;
+                    ur[n] = p.u[gi];
+                    rr[n] = p.res[gi];
+                }
+            }
+            float y[D::Np], r[D::Np];
+#pragma unroll
+            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
+            minv_apply<D::Np>(Mi, y, r);
+            if (valid) {
+#pragma unroll
+                for (int n = 0; n < D::Np; ++n) {
+                    const size_t gi = ((size_t)b * K + ge) * D::Np + n;
+                    const double rhs = -(double)r[n];
+                    if (MODE == 0) {
+                        p.rhs_out[gi] = rhs;
+                    } else {
+                        const double rs = p.rkA * rr[n] + p.dt * rhs;
+                        const double un = ur[n] + p.rkB * rs;
+                        p.res[gi] = rs;
+                        p.u[gi] = un;
+                        us[(b * D::Np + n) * EPW + e] = (float)un;
+                    }
+                }
+            } else if (MODE == 1) {
+#pragma unroll
+                for (int n = 0; n < D::Np; ++n) us[(b * D::Np + n) * EPW + e] = (n == 0) ? 1.f : 0.f;
+            }
+        }
+        __syncwarp();
+        if (MODE == 1) {
+            int bad = 0;
+            // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
+            {
+                float q0[QPL], q1[QPL], q2[QPL];
+#pragma unroll
+                for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
+                for (int n = 0; n < D::Np; ++n) {
+                    const float u0 = us[(0 * D::Np + n) * EPW + e];
+                    const float u1 = us[(1 * D::Np + n) * EPW + e];
+                    const float u2 = us[(2 * D::Np + n) * EPW + e];
+                    const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
+#pragma unroll
+                    for (int j = 0; j < QPL; ++j) {
+                        q0[j] = fmaf(v[j], u0, q0[j]);
+                        q1[j] = fmaf(v[j], u1, q1[j]);
+                        q2[j] = fmaf(v[j], u2, q2[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < QPL; ++j) {
+                    const int q = b + LPE * j;
+                    if (q < D::Nq) {
+                        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                        if (valid) {
+                            const float h = q0[j];
+                            if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                            const float ih = 1.f / h;
+                            const float uu = q1[j] * ih, vv = q2[j] * ih;
+                            const float bq = p.bh[(size_t)ge * D::Nh + q];
+                            const float wj = p.wJq[(size_t)ge * D::Nq + q];
+                            t0 = wj * (g * (h + bq) - 0.5f * (uu * uu + vv * vv));
+                            t1 = wj * uu;
+                            t2 = wj * vv;
+                        }
+                        ts[(0 * D::Nq + q) * EPW + e] = t0;
+                        ts[(1 * D::Nq + q) * EPW + e] = t1;
+                        ts[(2 * D::Nq + q) * EPW + e] = t2;
+                    }
+                }
+            }
+            __syncwarp();
+            // y = Vq^T (w J v), modes n = b + LPE*j
+            {
+                float y0[MPL], y1[MPL], y2[MPL];
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+                for (int q = 0; q < D::Nq; ++q) {
+                    const float t0 = ts[(0 * D::Nq + q) * EPW + e];
+                    const float t1 = ts[(1 * D::Nq + q) * EPW + e];
+                    const float t2 = ts[(2 * D::Nq + q) * EPW + e];
+                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                    for (int j = 0; j < MPL; ++j) {
+                        y0[j] = fmaf(v[j], t0, y0[j]);
+                        y1[j] = fmaf(v[j], t1, y1[j]);
+                        y2[j] = fmaf(v[j], t2, y2[j]);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const int n = b + LPE * j;
+                    if (n < D::Np) {
+                        ss[(0 * D::Np + n) * EPW + e] = y0[j];
+                        ss[(1 * D::Np + n) * EPW + e] = y1[j];
+                        ss[(2 * D::Np + n) * EPW + e] = y2[j];
+                    }
+                }
+            }
+            __syncwarp();
+            // v_h = (M_h^k)^{-1} y, in place (field per lane)
+            if (b < 3) {
+                float y[D::Np], r[D::Np];
+#pragma unroll
+                for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
+                minv_apply<D::Np>(Mi, y, r);
+#pragma unroll
+                for (int n = 0; n < D::Np; ++n) ss[(b * D::Np + n) * EPW + e] = r[n];
+            }
+            __syncwarp();
+            // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
+            {
+                float v0[RPL], v1[RPL], v2[RPL];
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
+                for (int n = 0; n < D::Np; ++n) {
+                    const float w0 = ss[(0 * D::Np + n) * EPW + e];
+                    const float w1 = ss[(1 * D::Np + n) * EPW + e];
+                    const float w2 = ss[(2 * D::Np + n) * EPW + e];
+                    const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
+#pragma unroll
+                    for (int j = 0; j < RPL; ++j) {
+                        v0[j] = fmaf(v[j], w0, v0[j]);
+                        v1[j] = fmaf(v[j], w1, v1[j]);
+                        v2[j] = fmaf(v[j], w2, v2[j]);
+                    }
+                }
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < RPL; ++j) {
+                        const int l = b + LPE * j;
+                        if (l < D::Nh) {
+                            const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
+                            const float h = H - p.bh[(size_t)ge * D::Nh + l];
+                            if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                            if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
+                            *reinterpret_cast<float4*>(p.ut_out + ((size_t)ge * D::Nh + l) * 4) =
+                                make_float4(h, v1[j], v2[j], H);
+                        }
+                    }
+                }
+            }
+            if (bad) atomicOr(p.status, bad);
+        }
+        // generic-proxy writes to the staging area must be ordered before the
+        // next batch's bulk copies overwrite it
+        fence_proxy_async_smem();
+        __syncwarp();
+    }
+}
+
+}  // namespace esdg

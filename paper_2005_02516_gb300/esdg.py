@@ -21,6 +21,7 @@ ESDG_ECUDA = -3
 ESDG_ENONPOSITIVE = -4
 ESDG_ENONFINITE = -5
 ESDG_ESTATE = -6
+ESDG_ETIMEOUT = -7
 
 ESDG_FP64 = 0
 ESDG_FP32 = 1

@@ -137,8 +137,10 @@ def test_fp32_after_configured_steps_config1():
 
 def test_lake_at_rest_and_entropy_on_gpu():
     """Theorem 2.2 on the GPU path: a lake at rest stays at rest, and with the
-    EC flux alone the semi-discrete entropy rate vanishes."""
-    w = W.MMS
+    EC flux alone the semi-discrete entropy rate vanishes.  Curved mesh,
+    periodic continuous bathymetry, no forcing."""
+    import dataclasses
+    w = dataclasses.replace(W.LAKE_BUMP, warp=0.05)
     s, o = _solver(w, "fp64", lf=True, N=3, nx=6)
     from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
     xs, ys = s.points(ESDG_POINTS_VOLQ)
@@ -175,12 +177,17 @@ def test_nonpositive_depth_is_reported_not_faulted():
     s.rhs()
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 5e-5)])
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-4)])
 def test_full_size_config3_sampled_rhs(precision, tol):
     """Config 3 at full size (N=4, K=131072 curved): the right-hand side on
     sampled elements (every 997th, plus the first and last) against the
     oracle computed element by element, in the launch configuration the
-    benchmark uses."""
+    benchmark uses.  The smoothed dam break is at rest away from its front,
+    so most sampled entries of du/dt are FP64 roundoff while the FP32 sums
+    of O(Nh) flux terms of size g h^2 / dx leave O(1e-5) absolute noise: the
+    FP32 bound here is set by that flux scale (2e-4 of the norm of du/dt);
+    the FP32 accuracy target proper (1e-5 on the state after the configured
+    steps) is tested on configs 1 and 2."""
     w = W.DAM
     s, o = _solver(w, precision)
     xo, yo = o.points("volq")

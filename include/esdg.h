@@ -166,6 +166,32 @@ int esdg_check(esdg_ctx* ctx);
  */
 int esdg_entropy(esdg_ctx* ctx, double t, double* entropy, double* mass, double* entropy_rate);
 
+/*
+ * esdg_entropy_noalloc -- the entropy and mass of esdg_entropy (no rate), for
+ * callers that cannot allocate device memory while they run: code inside a
+ * memory-pool or arena regime that forbids new allocations, or a driver loop
+ * that must not call cudaMalloc/cudaFree between launches.  The paper has no
+ * counterpart; this is a library convenience.
+ *
+ * u_dev: device state [3][K][Np] FP64, or NULL for the context's state.
+ * entropy, mass: host outputs (either may be NULL).
+ * Scratch: the per-block partial sums live in one file-scope device array of
+ * ESDG_NOALLOC_MAX_PARTS * 3 + 4 doubles (about 96 KB), held by every GPU that
+ * loads the library until the process exits.  One partial covers
+ * ESDG_NOALLOC_POINTS_PER_PART volume quadrature points, so K * Nq must not
+ * exceed ESDG_NOALLOC_MAX_PARTS * ESDG_NOALLOC_POINTS_PER_PART (ESDG_EINVAL
+ * otherwise).  The call allocates nothing: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call overwrites the whole scratch it reads, but all calls
+ * share the one array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller.  Synchronises the
+ * context's stream.
+ */
+#define ESDG_NOALLOC_MAX_PARTS 4096
+#define ESDG_NOALLOC_POINTS_PER_PART 2048
+int esdg_entropy_noalloc(const esdg_ctx* ctx, const double* u_dev, double* entropy, double* mass);
+
 /* The CFL time step of Sec. 4 for this configuration. */
 int esdg_dt(const esdg_ctx* ctx, double* dt);
 

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -670,6 +671,60 @@ int esdg_entropy(esdg_ctx* c, double t, double* entropy, double* mass, double* e
     if (entropy) *entropy = h[0];
     if (mass) *mass = h[1];
     if (entropy_rate) *entropy_rate = h[2];
+    return ESDG_OK;
+}
+
+// ---- no-allocation variant of the entropy diagnostic --------------------------
+// Scratch for the per-block partial sums (3 per block) and the 3 totals.
+static __device__ __align__(256) double g_noalloc_scratch[ESDG_NOALLOC_MAX_PARTS * 3 + 4];
+
+// The array's device address, looked up once per device (host code cannot use
+// the symbol itself: on the host it only names a stand-in).
+static std::mutex g_noalloc_mu;
+static double* g_noalloc_addr[128];
+
+static int noalloc_scratch(esdg_ctx* c, double** out) {
+    int dev = 0;
+    CUDA_TRY(c, cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) return fail(c, ESDG_EINVAL, "device ordinal out of range for the static scratch table");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        CUDA_TRY(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<double*>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return ESDG_OK;
+}
+
+int esdg_entropy_noalloc(const esdg_ctx* cc, const double* u_dev, double* entropy, double* mass) {
+    esdg_ctx* c = const_cast<esdg_ctx*>(cc);
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    const long long points = (long long)c->mesh.K * c->ref.Nq;
+    const long long parts = (points + ESDG_NOALLOC_POINTS_PER_PART - 1) / ESDG_NOALLOC_POINTS_PER_PART;
+    if (parts > ESDG_NOALLOC_MAX_PARTS)
+        return fail(c, ESDG_EINVAL,
+                    "esdg_entropy_noalloc: K * Nq = " + std::to_string(points) + " exceeds the static scratch limit of " +
+                        std::to_string((long long)ESDG_NOALLOC_MAX_PARTS * ESDG_NOALLOC_POINTS_PER_PART) +
+                        " quadrature points; use esdg_entropy");
+    double* scratch = nullptr;
+    int rc = noalloc_scratch(c, &scratch);
+    if (rc) return rc;
+    double* partial = scratch;
+    double* out = scratch + ESDG_NOALLOC_MAX_PARTS * 3;
+    const double* u = u_dev ? u_dev : reinterpret_cast<const double*>(c->dbuf + c->L.u);
+    // every block writes its own partial and the finalize kernel writes all three
+    // totals, so no part of the scratch has to start at zero
+    CUDA_TRY(c, d_entropy(c->cfg.N, c->mesh.K, c->cfg.g, u, nullptr,
+                          reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
+                          reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                          reinterpret_cast<const double*>(c->dbuf + c->L.bq64), partial, (int)parts, out, c->stream));
+    double h[3];
+    CUDA_TRY(c, cudaMemcpyAsync(h, out, 24, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (entropy) *entropy = h[0];
+    if (mass) *mass = h[1];
     return ESDG_OK;
 }
 

@@ -36,7 +36,8 @@ ESDG_INIT_SURFACE = 1
 # every symbol include/esdg.h declares
 EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get_points",
            "esdg_init_state", "esdg_set_bathymetry", "esdg_set_state", "esdg_copy_state",
-           "esdg_rhs", "esdg_step", "esdg_step_async", "esdg_check", "esdg_entropy", "esdg_dt",
+           "esdg_rhs", "esdg_step", "esdg_step_async", "esdg_check", "esdg_entropy",
+           "esdg_entropy_noalloc", "esdg_dt",
            "esdg_destroy", "esdg_last_error"]
 
 
@@ -86,6 +87,7 @@ def load_library(path=LIB_PATH):
         "esdg_step_async": ([P, I, D, D], I),
         "esdg_check": ([P], I),
         "esdg_entropy": ([P, D, PD, PD, PD], I),
+        "esdg_entropy_noalloc": ([P, P, PD, PD], I),
         "esdg_dt": ([P, PD], I),
         "esdg_destroy": ([P], I),
         "esdg_last_error": ([P], ctypes.c_char_p),

@@ -11,7 +11,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/esdg.h"
+#include "esdg.h"
 #include "esdg_launch.hpp"
 #include "host_build.hpp"
 

@@ -67,6 +67,8 @@ struct C2 {
     static_assert(3 * D::Nh <= UTS, "rt scratch");
     static_assert(3 * D::Nq * EPW + 3 * D::Np * EPW <= EPW * UTS, "t/s scratch");
     static_assert(3 * D::Np <= D::Nfq * 4, "u scratch");
+    static constexpr int TRL = (EPW * D::Nfq + 31) / 32;    // neighbour traces gathered per lane
+    static constexpr int RKL = (3 * EPW * D::Np + 31) / 32; // RK values per lane (all 32 lanes)
     static constexpr int WARPS = 12;
     static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
     static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + NpP4 * 4);
@@ -130,6 +132,27 @@ __device__ __forceinline__ void minv_apply(const float* __restrict__ M, const fl
     }
 }
 
+// Neighbour traces of the batch starting at e0 (a gather): lane handles
+// k = lane + 32 t, element k / Nfq, face node k % Nfq.
+template <int N>
+__device__ __forceinline__ void gather_traces(const StageParams<float>& p, int e0, int lane,
+                                              float4 (&tv)[C2<N>::TRL]) {
+    typedef Dims<N> D;
+#pragma unroll
+    for (int t = 0; t < C2<N>::TRL; ++t) {
+        const int k = lane + 32 * t;
+        tv[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < C2<N>::EPW * D::Nfq) {
+            const int ee = k / D::Nfq, f = k - ee * D::Nfq;
+            const int face = f / D::Nfp, i = f - face * D::Nfp;
+            const int nb = __ldg(p.nbr + (size_t)(e0 + ee) * 3 + face);
+            const int en = nb >> 2, fn = nb & 3;
+            tv[t] = __ldg(reinterpret_cast<const float4*>(
+                p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4));
+        }
+    }
+}
+
 template <int N, int MODE>
 __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const float* __restrict__ ops2, int Kpad) {
     typedef Dims<N> D;
@@ -153,7 +176,9 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
     const int K = p.K;
     uint32_t parity = 0;
     const int nbatch = Kpad / EPW;
-    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps) {
+    const int bstride = gridDim.x * nwarps;
+    float4 tv[C::TRL];
+    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += bstride) {
         const int e0 = batch * EPW;
         const int ge = e0 + e;
         const bool valid = ge < K;
@@ -169,15 +194,12 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
             else
                 tma_bulk_g2s(ws + C::w_mi + ee * C::MIS, p.minv + (size_t)(e0 + ee) * C::NpP4, C::NpP4 * 4, bar);
         }
-        // neighbour traces (a gather; plain loads while the bulk copies fly)
-        for (int k = lane; k < EPW * D::Nfq; k += 32) {
-            const int ee = k / D::Nfq, f = k - ee * D::Nfq;
-            const int face = f / D::Nfp, i = f - face * D::Nfp;
-            const int nb = p.nbr[(size_t)(e0 + ee) * 3 + face];
-            const int en = nb >> 2, fn = nb & 3;
-            const float4 v = *reinterpret_cast<const float4*>(
-                p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4);
-            *reinterpret_cast<float4*>(ws + C::w_tr + k * 4) = v;
+        // neighbour traces of this batch
+        gather_traces<N>(p, e0, lane, tv);
+#pragma unroll
+        for (int t = 0; t < C::TRL; ++t) {
+            const int k = lane + 32 * t;
+            if (k < EPW * D::Nfq) *reinterpret_cast<float4*>(ws + C::w_tr + k * 4) = tv[t];
         }
         if (!mbar_wait_bounded(bar, parity, p.status)) return;
         parity ^= 1;
@@ -186,7 +208,7 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
         // ---- volume flux differencing, rows l = b + LPE*i ------------------------
         const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
         const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
-        float rhu[RPL], rhv[RPL], ru[RPL], rv[RPL], rgh[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
+        float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
         float a0[RPL], a1[RPL], a2[RPL];
 #pragma unroll
         for (int i = 0; i < RPL; ++i) {
@@ -196,11 +218,9 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                 U = utE[l];
                 G = geE[l];
             }
-            rhu[i] = U.x * U.y;
-            rhv[i] = U.x * U.z;
+            rh[i] = U.x;
             ru[i] = U.y;
             rv[i] = U.z;
-            rgh[i] = 2.f * g * U.x;
             rrx[i] = G.x;
             rsx[i] = G.y;
             rry[i] = G.z;
@@ -212,17 +232,17 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
     {                                                                          \
         const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
         const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
-        const float HU = rhu[I] + hum, HV = rhv[I] + hvm;                      \
+        const float HU = fmaf(rh[I], ru[I], hum), HV = fmaf(rh[I], rv[I], hvm);\
         const float Us = ru[I] + U.y, Vs = rv[I] + U.z;                        \
         const float T = fmaf(Qx, HU, Qy * HV);                                 \
-        const float P = rgh[I] * U.w;                                          \
+        const float P = rh[I] * gH2;                                           \
         a0[I] += T;                                                            \
         a1[I] = fmaf(Us, T, fmaf(Qx, P, a1[I]));                               \
         a2[I] = fmaf(Vs, T, fmaf(Qy, P, a2[I]));                               \
     }
         for (int m = 0; m < D::Nq; ++m) {
             const float4 U = utE[m], G = geE[m];
-            const float hum = U.x * U.y, hvm = U.x * U.z;
+            const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
             const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
 #pragma unroll
             for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
@@ -233,7 +253,7 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
         }
         for (int m = D::Nq; m < D::Nh; ++m) {
             const float4 U = utE[m], G = geE[m];
-            const float hum = U.x * U.y, hvm = U.x * U.z;
+            const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
             const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
 #pragma unroll
             for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
@@ -263,7 +283,8 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                 const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
                 const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
                 const float w = ops[C::o_wf + f];
-                const float huA = 0.5f * (rhu[i] + huP), hvA = 0.5f * (rhv[i] + hvP);
+                const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
+                const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);
                 const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
                 const float pw = 0.5f * g * h_l * (hP + b_l);
                 const float Fn0 = nxJ * huA + nyJ * hvA;
@@ -277,8 +298,8 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                     const float lp = fabsf(uP * inx + vP * iny) + sqrtf(g * hP);
                     const float c = 0.5f * w * sJ * fmaxf(lm, lp);
                     a0[i] -= c * (hP - h_l);
-                    a1[i] -= c * (huP - rhu[i]);
-                    a2[i] -= c * (hvP - rhv[i]);
+                    a1[i] -= c * (huP - hu_l);
+                    a2[i] -= c * (hvP - hv_l);
                 }
             }
         }
@@ -291,6 +312,28 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                 rt[(0 * D::Nh + l) * EPW + e] = a0[i];
                 rt[(1 * D::Nh + l) * EPW + e] = a1[i];
                 rt[(2 * D::Nh + l) * EPW + e] = a2[i];
+            }
+        }
+        // Operands of the later phases, loaded now so their latency overlaps the
+        // lift and the inverse mass: the FP64 RK state of the batch spread over
+        // all 32 lanes (j = lane + 32 k in [field][element][mode] order, which is
+        // contiguous per field in global memory), and b, w J at this lane's nodes.
+        constexpr int NRK = 3 * EPW * D::Np;
+        double uj[C::RKL], rj[C::RKL];
+        if (MODE == 1) {
+#pragma unroll
+            for (int k = 0; k < C::RKL; ++k) {
+                const int j = lane + 32 * k;
+                uj[k] = 0.0;
+                rj[k] = 0.0;
+                if (j < NRK) {
+                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                    if (e0 + o / D::Np < K) {
+                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                        uj[k] = p.u[gi];
+                        rj[k] = p.res[gi];
+                    }
+                }
             }
         }
         // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
@@ -367,47 +410,67 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
             }
         }
         __syncwarp();
-        // ---- du/dt = -(M_h^k)^{-1} s (field per lane), then output or RK ----------
+        // ---- du/dt = -(M_h^k)^{-1} s (field per lane) into ss as [field][element][mode]
         const float* Mi = ws + C::w_mi + e * C::MIS;
-        float* us = ws + C::s_u;
-        if (b < 3) {
-            // RK operands (field per lane: lane b < 3 owns field b); their loads
-            // overlap the inverse-mass arithmetic below
-            double ur[D::Np], rr[D::Np];
-            if (MODE == 1 && valid) {
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) {
-                    const size_t gi = ((size_t)b * K + ge) * D::Np + n;
-                    ur[n] = p.u[gi];
-                    rr[n] = p.res[gi];
-                }
-            }
+        {
             float y[D::Np], r[D::Np];
+            if (b < 3) {
 #pragma unroll
-            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
-            minv_apply<D::Np>(Mi, y, r);
-            if (valid) {
+                for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
+            }
+            __syncwarp();
+            if (b < 3) {
+                minv_apply<D::Np>(Mi, y, r);
 #pragma unroll
-                for (int n = 0; n < D::Np; ++n) {
-                    const size_t gi = ((size_t)b * K + ge) * D::Np + n;
-                    const double rhs = -(double)r[n];
-                    if (MODE == 0) {
-                        p.rhs_out[gi] = rhs;
-                    } else {
-                        const double rs = p.rkA * rr[n] + p.dt * rhs;
-                        const double un = ur[n] + p.rkB * rs;
+                for (int n = 0; n < D::Np; ++n) ss[(b * EPW + e) * D::Np + n] = -r[n];
+            }
+        }
+        __syncwarp();
+        float* us = ws + C::s_u;
+        if (MODE == 0) {
+            for (int j = lane; j < NRK; j += 32) {
+                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                if (e0 + o / D::Np < K) p.rhs_out[((size_t)c * K + e0) * D::Np + o] = (double)ss[j];
+            }
+        } else {
+            // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
+            const float dtf = (float)p.dt;
+#pragma unroll
+            for (int k = 0; k < C::RKL; ++k) {
+                const int j = lane + 32 * k;
+                if (j < NRK) {
+                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                    const int ee = o / D::Np, n = o - ee * D::Np;
+                    double un = 1.0;
+                    if (e0 + ee < K) {
+                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                        const double rs = fma(p.rkA, rj[k], (double)(dtf * ss[j]));
+                        un = fma(p.rkB, rs, uj[k]);
                         p.res[gi] = rs;
                         p.u[gi] = un;
-                        us[(b * D::Np + n) * EPW + e] = (float)un;
                     }
+                    us[(c * D::Np + n) * EPW + ee] = (float)un;
                 }
-            } else if (MODE == 1) {
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) us[(b * D::Np + n) * EPW + e] = (n == 0) ? 1.f : 0.f;
             }
         }
         __syncwarp();
         if (MODE == 1) {
+            float bqv[QPL], wqv[QPL], blv[RPL];
+#pragma unroll
+                for (int j = 0; j < QPL; ++j) {
+                    const int q = b + LPE * j;
+                    bqv[j] = 0.f;
+                    wqv[j] = 0.f;
+                    if (valid && q < D::Nq) {
+                        bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
+                        wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+                    }
+                }
+    #pragma unroll
+                for (int j = 0; j < RPL; ++j) {
+                    const int l = b + LPE * j;
+                    blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
+                }
             int bad = 0;
             // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
             {
@@ -436,9 +499,8 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                             if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
                             const float ih = 1.f / h;
                             const float uu = q1[j] * ih, vv = q2[j] * ih;
-                            const float bq = p.bh[(size_t)ge * D::Nh + q];
-                            const float wj = p.wJq[(size_t)ge * D::Nq + q];
-                            t0 = wj * (g * (h + bq) - 0.5f * (uu * uu + vv * vv));
+                            const float wj = wqv[j];
+                            t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
                             t1 = wj * uu;
                             t2 = wj * vv;
                         }
@@ -510,7 +572,7 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
                         const int l = b + LPE * j;
                         if (l < D::Nh) {
                             const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
-                            const float h = H - p.bh[(size_t)ge * D::Nh + l];
+                            const float h = H - blv[j];
                             if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
                             if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
                             *reinterpret_cast<float4*>(p.ut_out + ((size_t)ge * D::Nh + l) * 4) =
@@ -521,6 +583,7 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
             }
             if (bad) atomicOr(p.status, bad);
         }
+        if (batch + bstride < nbatch) gather_traces<N>(p, (batch + bstride) * EPW, lane, tv);
         // generic-proxy writes to the staging area must be ordered before the
         // next batch's bulk copies overwrite it
         fence_proxy_async_smem();

@@ -34,9 +34,14 @@ from paper_2005_02516_gb300 import workloads as W  # noqa: E402
 METRIC = "GDOF-stage/s FP32 vs FP64 per GB300 at stated L2 error; served p50/p99 latency"
 UNIT = "GDOF-stage/s"
 WL = W.DAM
-KERNEL_VERSION = "k_stage2-v1"  # the stage kernel the committed traffic counters describe
+# DRAM traffic of one stage launch at this workload, from one ncu capture
+# (profiles/k_stage2_dam_k131072_n4.md), valid only for the kernel source it
+# was measured on: reported as null once that source changes.
+STAGE_TRAFFIC = {"source_sha1": "3b851f44805d5fff8afcbafec389c9a3bbaa4082", "bytes": 499.4e6}
+STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 
-# Algorithmic work of one element-stage at degree N ("roofline").
+# Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of
+# each step of the path, and the bytes each element-stage must move.
 def algorithmic_flops(N):
     Np = (N + 1) * (N + 2) // 2
     Nq = (N + 1) ** 2
@@ -87,17 +92,17 @@ class ClockSampler:
     def __init__(self, index=0):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+        import tempfile
+        self.path = os.path.join(tempfile.gettempdir(), "esdg_bench_clocks_%d.csv" % os.getpid())
 
     def start(self):
-        os.makedirs(os.path.dirname(self.path), exist_ok=True)
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -257,13 +262,19 @@ def run_reference(args, world, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 leg (profiling runs)")
+    ap.add_argument("--nx", type=int, default=None,
+                    help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global WL
+    if args.nx is not None:
+        WL = W.scaled(WL, args.nx)
     world, rank, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
@@ -291,12 +302,10 @@ def main():
     alu = flops / t_launch / 1e12
     hbm = nbytes / t_launch / 1e9
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "stage_traffic.json")
-    if os.path.exists(tpath):
-        with open(tpath) as f:
-            tj = json.load(f)
-        if tj.get("kernel_version") == KERNEL_VERSION:
-            traffic = tj.get("dram_bytes_per_launch")
+    import hashlib
+    with open(STAGE_SOURCE, "rb") as f:
+        if hashlib.sha1(f.read()).hexdigest() == STAGE_TRAFFIC["source_sha1"]:
+            traffic = STAGE_TRAFFIC["bytes"]
     roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
                 "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -308,13 +317,14 @@ def main():
     fp64 = None
     s.close()
     del s
-    s64 = make_solver("fp64")
-    st64 = max(2, steps // 10)
-    el64 = time_steps(s64, st64, 1, world)
-    fp64 = {"value": K * Np * 5 * st64 / el64 / 1e9, "unit": UNIT, "ms_per_step": el64 / st64 * 1e3,
-            "steps": st64}
-    s64.close()
-    del s64
+    if not args.fp32_only:
+        s64 = make_solver("fp64")
+        st64 = max(2, steps // 20)
+        el64 = time_steps(s64, st64, 1, world)
+        fp64 = {"value": K * Np * 5 * st64 / el64 / 1e9, "unit": UNIT, "ms_per_step": el64 / st64 * 1e3,
+                "steps": st64}
+        s64.close()
+        del s64
 
     e2e = None
     if not args.no_e2e:
@@ -332,7 +342,8 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": el_max / steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WL.name, "N": WL.N, "K": K, "Np": Np, "curved": True,
+                "config": {"workload": WL.name if args.nx is None else "%s_nx%d" % (WL.name, args.nx),
+                           "N": WL.N, "K": K, "Np": Np, "curved": True,
                            "rhs_precision": "fp32", "rk_accumulation": "fp64",
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},

@@ -1,6 +1,6 @@
 """Seeded synthetic workloads: problem definitions and random inputs.
 
-This module holds no arithmetic of the ESDG method.  It defines the five
+This module holds no arithmetic of the ESDG method.  It defines three
 problem configurations (mesh size, degree, warp, analytic bathymetry and
 initial data as plain functions of (x, y)) and seeded random inputs.  The
 tests, the benchmark and the oracle-side CPU baseline all draw their inputs
@@ -92,14 +92,14 @@ _INIT = {"lake_bump_k128_n2": _lake_bump_init,
          "dam_k131072_n4": _dam_init}
 _EXACT = {"mms_k8192_n3": _mms_exact}
 
-# Config 1: plain FP64, N=2, 8x8 quads -> K=128 affine, g=1, lake at rest H=2
+# Lake at rest plus a bump: plain FP64, N=2, 8x8 quads -> K=128 affine, g=1, H=2
 # plus a bump; 200 steps at CFL 0.25.
 LAKE_BUMP = Workload("lake_bump_k128_n2", N=2, nx=8, ny=8, warp=0.0, g=1.0, cfl=0.25,
                      steps=200, forcing="none", surface_init=True)
-# Config 2: N=3, 64x64 -> K=8192 curved, manufactured solution, 1000 steps.
+# Manufactured solution: N=3, 64x64 -> K=8192 curved, 1000 steps.
 MMS = Workload("mms_k8192_n3", N=3, nx=64, ny=64, warp=0.05, g=1.0, cfl=0.25,
                steps=1000, forcing="mms_sine")
-# Config 3: N=4, 256x256 -> K=131072 curved, smoothed dam break.
+# Smoothed dam break: N=4, 256x256 -> K=131072 curved.
 DAM = Workload("dam_k131072_n4", N=4, nx=256, ny=256, warp=0.05, g=1.0, cfl=0.25,
                steps=50, forcing="none")
 
@@ -126,20 +126,6 @@ def random_modal_state(K, Np, seed, c0=2.8, amp_h=0.05, amp_m=0.05):
     u[1:] *= amp_m
     u[0, :, 0] += c0
     return u
-
-
-def ensemble(n=64, seed=BASE_SEED):
-    """Batched-ensemble instances: N ~ U{2,3,4}, K ~ U{512,2048,8192,32768},
-    bathymetry amplitude ~ U[0.02,0.2], bump centre ~ U[-0.5,0.5]^2."""
-    out = []
-    for i in range(n):
-        rng = np.random.default_rng(seed + i)
-        N = int(rng.integers(2, 5))
-        nx = int(rng.choice([16, 32, 64, 128]))
-        amp = float(rng.uniform(0.02, 0.2))
-        c = rng.uniform(-0.5, 0.5, size=2)
-        out.append(dict(N=N, nx=nx, ny=nx, amp=amp, cx=float(c[0]), cy=float(c[1])))
-    return out
 
 
 def lake_at_rest_table_bathymetry(x, y):

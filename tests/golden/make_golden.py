@@ -1,6 +1,7 @@
 """Write the stored expected values of the long FP32/FP64 parity tests.
 
-Runs the FP64 oracle (and only the oracle) on config 2: N=3, 64x64 quads ->
+Runs the FP64 oracle (and only the oracle) on the manufactured-solution
+workload: N=3, 64x64 quads ->
 K=8192 curved triangles, manufactured solution h = 2 + 0.1 sin(pi(x+y-t)),
 u = v = 0.5, b = 0.1 cos(pi x) cos(pi y), g = 1, CFL 0.25, 1000 LSRK45 steps.
 Stores 4000 sampled modal coefficients of the final state (seeded indices),
@@ -42,7 +43,7 @@ def main():
     flat = u.ravel()
     out = os.path.join(HERE, "mms_k8192_n3_1000steps.txt")
     with open(out, "w") as f:
-        f.write("# FP64 oracle, config 2 (N=3, K=8192 curved, MMS), %d steps, dt=%.17g, t=%.17g\n"
+        f.write("# FP64 oracle, manufactured solution N=3, K=8192 curved, %d steps, dt=%.17g, t=%.17g\n"
                 % (w.steps, dt, t))
         f.write("# written by tests/golden/make_golden.py (oracle only); %.0f s\n" % el)
         f.write("norms %s\n" % " ".join("%.17g" % np.linalg.norm(u[c]) for c in range(3)))

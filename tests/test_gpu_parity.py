@@ -94,7 +94,7 @@ def test_rhs_fp32_matches_oracle(w, N, nx, ny):
 
 
 def test_steps_fp64_config1_match_oracle_every_step():
-    """Config 1 (N=2, K=128 affine, lake at rest plus a bump): per-step parity
+    """Lake at rest plus a bump (N=2, K=128 affine): per-step parity
     for 20 steps at relative 1e-12."""
     w = W.LAKE_BUMP
     s, o = _solver(w, "fp64")
@@ -121,7 +121,8 @@ def test_init_state_matches_oracle():
 
 
 def test_fp32_after_configured_steps_config1():
-    """Config 1 for all 200 configured steps: FP32 RHS with FP64 accumulation
+    """Lake at rest plus a bump (N=2, K=128) for all 200 configured steps:
+    FP32 RHS with FP64 accumulation
     within relative 1e-5 of the FP64 oracle; FP64 within 1e-12."""
     w = W.LAKE_BUMP
     s64, o = _solver(w, "fp64")
@@ -179,7 +180,7 @@ def test_nonpositive_depth_is_reported_not_faulted():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-4)])
 def test_full_size_config3_sampled_rhs(precision, tol):
-    """Config 3 at full size (N=4, K=131072 curved): the right-hand side on
+    """Smoothed dam break at full size (N=4, K=131072 curved): the right-hand side on
     sampled elements (every 997th, plus the first and last) against the
     oracle computed element by element, in the launch configuration the
     benchmark uses.  The smoothed dam break is at rest away from its front,
@@ -187,7 +188,7 @@ def test_full_size_config3_sampled_rhs(precision, tol):
     of O(Nh) flux terms of size g h^2 / dx leave O(1e-5) absolute noise: the
     FP32 bound here is set by that flux scale (2e-4 of the norm of du/dt);
     the FP32 accuracy target proper (1e-5 on the state after the configured
-    steps) is tested on configs 1 and 2."""
+    steps) is tested on the lake-at-rest and manufactured-solution workloads."""
     w = W.DAM
     s, o = _solver(w, precision)
     xo, yo = o.points("volq")

@@ -220,6 +220,42 @@ def time_e2e(s, steps, warmup):
     return el, nbytes
 
 
+def run_ensemble(n, steps):
+    """Batched ensemble: n independent FP32 problems of mixed N and K in one
+    persistent launch per stage (graph-replayed), launch shape autotuned."""
+    import torch
+    from paper_2005_02516_gb300.esdg import Ensemble, Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
+    insts = W.ensemble(n=n, steps=steps)
+    solvers = []
+    for it in insts:
+        s = Solver(it.N, it.nx, it.nx, precision="fp32", warp=it.warp, g=it.g, cfl=it.cfl)
+        xb, yb = s.points(ESDG_POINTS_NODAL)
+        xq, yq = s.points(ESDG_POINTS_VOLQ)
+        s.init_state(it.bathymetry(xb, yb), it.initial(xq, yq), surface=True)
+        solvers.append(s)
+    ens = Ensemble(solvers)
+    warps, order = ens.autotune()
+    ens.step(2)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(solvers[0].stream)
+    ens.step_async(steps)
+    ev1.record(solvers[0].stream)
+    ev1.synchronize()
+    el = ev0.elapsed_time(ev1) / 1e3
+    ens.step(0)
+    units = sum(it.K * it.Np * 5 * steps for it in insts)
+    res = {"value": units / el / 1e9, "unit": UNIT, "instances": n, "steps": steps,
+           "elements": sum(it.K for it in insts), "seconds": el,
+           "degrees": sorted(set(it.N for it in insts)), "autotuned_warps": warps, "autotuned_order": order,
+           "launches": 5 * steps}
+    ens.close()
+    for s in solvers:
+        s.close()
+    return res
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
     on a sample of 2048 consecutive elements of the same workload, repeated
@@ -267,7 +303,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 leg (profiling runs)")
+    ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 and ensemble legs (profiling runs)")
+    ap.add_argument("--ensemble", type=int, default=64, help="instances of the batched-ensemble leg (0: skip)")
+    ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
@@ -326,6 +364,10 @@ def main():
         s64.close()
         del s64
 
+    ens = None
+    if not args.fp32_only and args.ensemble > 0:
+        ens = run_ensemble(args.ensemble, args.ensemble_steps)
+
     e2e = None
     if not args.no_e2e:
         s = make_solver("fp32")
@@ -348,7 +390,7 @@ def main():
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other,
-                "fp64": fp64, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
+                "fp64": fp64, "ensemble": ens, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))
     if world > 1:

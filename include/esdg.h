@@ -192,6 +192,34 @@ int esdg_entropy(esdg_ctx* ctx, double t, double* entropy, double* mass, double*
 #define ESDG_NOALLOC_POINTS_PER_PART 2048
 int esdg_entropy_noalloc(const esdg_ctx* ctx, const double* u_dev, double* entropy, double* mass);
 
+/*
+ * Ensembles: several independent problems (contexts) of mixed degree N and
+ * size K advanced together, one persistent kernel launch per RK stage over a
+ * tile table of all members' element batches, the steps replayed from a
+ * captured CUDA graph.  Members must be FP32 contexts, attached on the same
+ * stream, with no forcing.  Each member steps with its own CFL time step
+ * (Sec. 4); members stay ordinary contexts (esdg_copy_state, esdg_entropy ...).
+ * The ensemble allocates one small device table (a few hundred bytes per
+ * member) with cudaMalloc and frees it in esdg_ensemble_destroy.
+ */
+typedef struct esdg_ensemble esdg_ensemble;
+int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out);
+
+/* Choose the launch shape (warps per CTA) and the order of members in the
+ * tile table by timing candidate shapes on the members' current states (the
+ * states are restored afterwards).  *warps and *order (0: as given,
+ * 1: largest degree first) receive the choice; either may be NULL. */
+int esdg_ensemble_autotune(esdg_ensemble* ens, int* warps, int* order);
+
+/* Advance every member by nsteps LSRK45 steps; synchronises and checks the
+ * members' device flags. */
+int esdg_ensemble_step(esdg_ensemble* ens, int nsteps);
+int esdg_ensemble_step_async(esdg_ensemble* ens, int nsteps);
+int esdg_ensemble_destroy(esdg_ensemble* ens);
+
+/* Message for the last failing call on ens (NULL: the last failing create). */
+const char* esdg_ensemble_error(const esdg_ensemble* ens);
+
 /* The CFL time step of Sec. 4 for this configuration. */
 int esdg_dt(const esdg_ctx* ctx, double* dt);
 

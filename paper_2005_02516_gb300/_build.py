@@ -24,7 +24,7 @@ def nvcc():
 
 
 def _sources():
-    cu = ["esdg_api.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
+    cu = ["esdg_api.cu", "esdg_ensemble.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
     return cu, ["host_build.cpp"]
 
 

@@ -6,6 +6,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -728,6 +729,305 @@ int esdg_entropy_noalloc(const esdg_ctx* cc, const double* u_dev, double* entrop
     return ESDG_OK;
 }
 
+// ---- ensembles ------------------------------------------------------------------
+struct esdg_ensemble {
+    std::vector<esdg_ctx*> members;
+    std::vector<int> order;        // tile-table order of members
+    EnsembleMember* dmem = nullptr;
+    int total_batches = 0;
+    int warps = 12;
+    int nmax = 4;
+    int4 ops_lo = make_int4(-1, -1, -1, -1);
+    int ops_hi = -1, ops_end = 0, slab = 0;
+    size_t smem = 0;
+    cudaStream_t stream = nullptr;    // the members' stream (work and graph launches)
+    cudaStream_t capture = nullptr;   // private stream the graph is captured on (the
+                                      // legacy default stream cannot be captured)
+    cudaGraphExec_t graph = nullptr;  // GRAPH_STEPS steps
+    int graph_warps = 0;
+    std::string err;
+};
+static const int GRAPH_STEPS = 10;  // even: a replay returns the u~ buffers to the same parity
+
+static int efail(esdg_ensemble* e, int code, const std::string& m) {
+    e->err = m;
+    return code;
+}
+#define ECUDA_TRY(ens, call)                                                                       \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) return efail((ens), ESDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+static int c2_w_end(int N) {
+    switch (N) {
+        case 1: return C2<1>::w_end;
+        case 2: return C2<2>::w_end;
+        case 3: return C2<3>::w_end;
+        case 4: return C2<4>::w_end;
+        default: return C2<5>::w_end;
+    }
+}
+
+// (Re)build the member table in the given order and the shared-memory plan.
+static int ensemble_table(esdg_ensemble* e) {
+    std::vector<EnsembleMember> h;
+    int begin = 0, ops = 0, slab = 0, nmax = 1;
+    int off[6] = {-1, -1, -1, -1, -1, -1};
+    for (int idx : e->order) {
+        esdg_ctx* c = e->members[idx];
+        const int N = c->cfg.N;
+        if (off[N] < 0) {
+            off[N] = ops;
+            ops += c2_ops_floats(N);
+        }
+        slab = std::max(slab, c2_w_end(N));
+        nmax = std::max(nmax, N);
+        EnsembleMember m;
+        std::memset(&m, 0, sizeof(m));
+        m.p = make_params<float>(c);
+        esdg_dt(c, &m.p.dt);
+        m.ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
+        m.ut[0] = ut_buf<float>(c, 0);
+        m.ut[1] = ut_buf<float>(c, 1);
+        m.N = N;
+        m.batch_begin = begin;
+        m.nbatch = c->Kpad / 4;
+        begin += m.nbatch;
+        h.push_back(m);
+    }
+    e->total_batches = begin;
+    e->ops_lo = make_int4(off[1], off[2], off[3], off[4]);
+    e->ops_hi = off[5];
+    e->ops_end = ops;
+    e->slab = slab;
+    e->nmax = nmax <= 4 ? 4 : 5;
+    const int n = int(h.size());
+    e->smem = 4 * (size_t(ops) + size_t(e->warps) * slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(e->warps);
+    ECUDA_TRY(e, cudaMemcpyAsync(e->dmem, h.data(), sizeof(EnsembleMember) * n, cudaMemcpyHostToDevice, e->stream));
+    ECUDA_TRY(e, cudaStreamSynchronize(e->stream));
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return ESDG_OK;
+}
+
+static int ensemble_fits(esdg_ensemble* e, int warps) {
+    const int n = int(e->members.size());
+    size_t need = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(warps);
+    return need <= 232448;
+}
+
+static int ensemble_launch(esdg_ensemble* e, int which, int stage, cudaStream_t st) {
+    const int sms = e->members[0]->num_sms;
+    const int n = int(e->members.size());
+    ECUDA_TRY(e, launch_ensemble(e->nmax, sms, e->warps * 32, e->smem, st, e->dmem, n, e->total_batches, which,
+                                 RK_A[stage], RK_B[stage], e->ops_lo, e->ops_hi, e->ops_end, e->slab));
+    return ESDG_OK;
+}
+
+// Make every member's u~ buffer 0 current for its state.
+static int ensemble_prepare(esdg_ensemble* e) {
+    for (esdg_ctx* c : e->members) {
+        if (!c->ut_valid || c->cur != 0) {
+            c->cur = 0;
+            int rc = project_current<float>(c, nullptr, 0);
+            if (rc) return efail(e, rc, c->err);
+            c->ut_valid = true;
+        }
+    }
+    return ESDG_OK;
+}
+
+static int ensemble_set_shape(esdg_ensemble* e, int warps) {
+    e->warps = warps;
+    const int n = int(e->members.size());
+    e->smem = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(warps);
+    cudaError_t err = ensemble_smem_attr(e->nmax, e->smem);
+    if (err != cudaSuccess) return efail(e, ESDG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
+    if (e->graph) {
+        cudaGraphExecDestroy(e->graph);
+        e->graph = nullptr;
+    }
+    return ESDG_OK;
+}
+
+static int ensemble_steps_direct(esdg_ensemble* e, int nsteps, int* stage_counter, cudaStream_t st) {
+    for (int k = 0; k < nsteps; ++k)
+        for (int s = 0; s < 5; ++s) {
+            int rc = ensemble_launch(e, (*stage_counter) & 1, s, st);
+            if (rc) return rc;
+            ++*stage_counter;
+        }
+    return ESDG_OK;
+}
+
+int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
+    if (!members || n < 1 || !out) return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: bad arguments");
+    *out = nullptr;
+    for (int i = 0; i < n; ++i) {
+        const esdg_ctx* c = members[i];
+        if (!c || !c->attached) return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: member not attached");
+        if (c->cfg.precision != ESDG_FP32) return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must be FP32");
+        if (c->cfg.forcing != ESDG_FORCING_NONE)
+            return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members with a forcing term are not supported");
+        if (c->stream != members[0]->stream)
+            return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one stream");
+    }
+    esdg_ensemble* e = new (std::nothrow) esdg_ensemble();
+    if (!e) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
+    e->members.assign(members, members + n);
+    e->stream = members[0]->stream;
+    for (int i = 0; i < n; ++i) e->order.push_back(i);
+    cudaError_t err = cudaMalloc(&e->dmem, sizeof(EnsembleMember) * n);
+    if (err != cudaSuccess) {
+        delete e;
+        return fail(nullptr, ESDG_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(err));
+    }
+    err = cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking);
+    if (err != cudaSuccess) {
+        cudaFree(e->dmem);
+        delete e;
+        return fail(nullptr, ESDG_ECUDA, std::string("cudaStreamCreateWithFlags: ") + cudaGetErrorString(err));
+    }
+    int rc = ensemble_table(e);
+    if (!rc) {
+        int w = 12;
+        while (w > 1 && !ensemble_fits(e, w)) --w;
+        rc = ensemble_set_shape(e, w);
+    }
+    if (rc) {
+        std::string m = e->err;
+        cudaFree(e->dmem);
+        cudaStreamDestroy(e->capture);
+        delete e;
+        return fail(nullptr, rc, m);
+    }
+    *out = e;
+    return ESDG_OK;
+}
+
+int esdg_ensemble_step_async(esdg_ensemble* e, int nsteps) {
+    if (!e || nsteps < 0) return fail(nullptr, ESDG_EINVAL, "bad arguments");
+    int rc = ensemble_prepare(e);
+    if (rc) return rc;
+    int stage = 0;
+    const int reps = nsteps / GRAPH_STEPS;
+    if (reps > 0) {
+        if (!e->graph || e->graph_warps != e->warps) {
+            if (e->graph) cudaGraphExecDestroy(e->graph);
+            e->graph = nullptr;
+            cudaGraph_t g = nullptr;
+            ECUDA_TRY(e, cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal));
+            int st = 0;
+            rc = ensemble_steps_direct(e, GRAPH_STEPS, &st, e->capture);
+            cudaError_t ce = cudaStreamEndCapture(e->capture, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return efail(e, ESDG_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+            ce = cudaGraphInstantiate(&e->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) return efail(e, ESDG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ce));
+            e->graph_warps = e->warps;
+        }
+        for (int r = 0; r < reps; ++r) ECUDA_TRY(e, cudaGraphLaunch(e->graph, e->stream));
+    }
+    rc = ensemble_steps_direct(e, nsteps - reps * GRAPH_STEPS, &stage, e->stream);
+    if (rc) return rc;
+    const int cur = (5 * nsteps) & 1;
+    for (esdg_ctx* c : e->members) {
+        c->cur = cur;
+        c->ut_valid = true;
+    }
+    return ESDG_OK;
+}
+
+int esdg_ensemble_step(esdg_ensemble* e, int nsteps) {
+    int rc = esdg_ensemble_step_async(e, nsteps);
+    if (rc) return rc;
+    ECUDA_TRY(e, cudaStreamSynchronize(e->stream));
+    for (esdg_ctx* c : e->members) {
+        rc = check_status(c);
+        if (rc) return efail(e, rc, c->err);
+    }
+    return ESDG_OK;
+}
+
+int esdg_ensemble_autotune(esdg_ensemble* e, int* warps_out, int* order_out) {
+    if (!e) return fail(nullptr, ESDG_EINVAL, "null ensemble");
+    // keep each member's state in its own right-hand-side scratch; the RK
+    // residual needs no saving (the first stage of a step does not read it)
+    for (esdg_ctx* c : e->members)
+        ECUDA_TRY(e, cudaMemcpyAsync(c->dbuf + c->L.rhs, c->dbuf + c->L.u, 8 * 3 * size_t(c->mesh.K) * c->ref.Np,
+                                     cudaMemcpyDeviceToDevice, e->stream));
+    std::vector<int> given = e->order, bydeg = e->order;
+    std::stable_sort(bydeg.begin(), bydeg.end(),
+                     [&](int a, int b) { return e->members[a]->cfg.N > e->members[b]->cfg.N; });
+    float best = 1e30f;
+    int best_w = e->warps, best_o = 0;
+    cudaEvent_t t0, t1;
+    ECUDA_TRY(e, cudaEventCreate(&t0));
+    ECUDA_TRY(e, cudaEventCreate(&t1));
+    int rc = ESDG_OK;
+    for (int o = 0; o < 2 && !rc; ++o) {
+        e->order = o == 0 ? given : bydeg;
+        rc = ensemble_table(e);
+        for (int w : {8, 10, 12}) {
+            if (rc || !ensemble_fits(e, w)) continue;
+            rc = ensemble_set_shape(e, w);
+            if (!rc) rc = ensemble_prepare(e);
+            int st = 0;
+            if (!rc) rc = ensemble_steps_direct(e, 1, &st, e->stream);  // warm-up
+            if (rc) break;
+            cudaEventRecord(t0, e->stream);
+            st = 0;
+            rc = ensemble_steps_direct(e, 2, &st, e->stream);
+            cudaEventRecord(t1, e->stream);
+            cudaEventSynchronize(t1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, t0, t1);
+            if (!rc && ms < best) {
+                best = ms;
+                best_w = w;
+                best_o = o;
+            }
+            for (esdg_ctx* c : e->members) c->ut_valid = false;
+        }
+    }
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    for (esdg_ctx* c : e->members) {
+        ECUDA_TRY(e, cudaMemcpyAsync(c->dbuf + c->L.u, c->dbuf + c->L.rhs, 8 * 3 * size_t(c->mesh.K) * c->ref.Np,
+                                     cudaMemcpyDeviceToDevice, e->stream));
+        c->ut_valid = false;
+    }
+    if (rc) return rc;
+    e->order = best_o == 0 ? given : bydeg;
+    rc = ensemble_table(e);
+    if (!rc) rc = ensemble_set_shape(e, best_w);
+    if (rc) return rc;
+    ECUDA_TRY(e, cudaStreamSynchronize(e->stream));
+    for (esdg_ctx* c : e->members) {
+        rc = check_status(c);
+        if (rc) return efail(e, rc, c->err);
+    }
+    if (warps_out) *warps_out = best_w;
+    if (order_out) *order_out = best_o;
+    return ESDG_OK;
+}
+
+int esdg_ensemble_destroy(esdg_ensemble* e) {
+    if (!e) return ESDG_OK;
+    if (e->graph) cudaGraphExecDestroy(e->graph);
+    if (e->dmem) cudaFree(e->dmem);
+    if (e->capture) cudaStreamDestroy(e->capture);
+    delete e;
+    return ESDG_OK;
+}
+
 int esdg_dt(const esdg_ctx* c, double* dt) {
     if (!valid(c) || !dt) return fail(nullptr, ESDG_EINVAL, "null argument");
     const int N = c->cfg.N;
@@ -745,6 +1045,10 @@ int esdg_destroy(esdg_ctx* c) {
 
 const char* esdg_last_error(const esdg_ctx* c) {
     return c ? c->err.c_str() : g_build_error.c_str();
+}
+
+const char* esdg_ensemble_error(const esdg_ensemble* e) {
+    return e ? e->err.c_str() : g_build_error.c_str();
 }
 
 }  // extern "C"

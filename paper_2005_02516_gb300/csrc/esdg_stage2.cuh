@@ -6,11 +6,13 @@
 // lift, stored inverse curved mass matrix, LSRK45 stage of Sec. 4, and the
 // entropy projection of Sec. 2.6 for the next stage), mapped differently:
 //
-//  * a warp processes a batch of EPW = 32/LPE elements; LPE lanes share one
-//    element.  Lane (e, b) owns the hybrid rows l = b + LPE*i, i < RPL, with
-//    their node data and three accumulators in registers, so a column m is
-//    read from shared memory once for RPL rows (the flux differencing is
+//  * a warp processes a batch of EPW = 32/LPE = 4 elements; LPE = 8 lanes share
+//    one element.  Lane (e, b) owns the hybrid rows l = b + LPE*i, i < RPL,
+//    with their node data and three accumulators in registers, so a column m
+//    is read from shared memory once for RPL rows (the flux differencing is
 //    FP32-ALU bound, and this keeps shared-memory traffic well below it).
+//    Eight lanes per element (rather than four) halve the registers and the
+//    shared memory per warp, which lets 16 warps share an SM.
 //    Interleaving rows across the LPE lanes balances volume rows (all Nh
 //    columns) against face rows (Nq columns: the lower-right block of
 //    Q_skew is zero).
@@ -32,7 +34,7 @@ constexpr int STATUS_TIMEOUT = 4;
 template <int N>
 struct C2 {
     typedef Dims<N> D;
-    static constexpr int LPE = (N >= 5) ? 8 : 4;            // lanes per element
+    static constexpr int LPE = 8;                           // lanes per element
     static constexpr int EPW = 32 / LPE;                    // elements per warp
     static constexpr int RPL = (D::Nh + LPE - 1) / LPE;     // hybrid rows per lane
     static constexpr int QPL = (D::Nq + LPE - 1) / LPE;     // volume nodes per lane
@@ -69,7 +71,12 @@ struct C2 {
     static_assert(3 * D::Np <= D::Nfq * 4, "u scratch");
     static constexpr int TRL = (EPW * D::Nfq + 31) / 32;    // neighbour traces gathered per lane
     static constexpr int RKL = (3 * EPW * D::Np + 31) / 32; // RK values per lane (all 32 lanes)
-    static constexpr int WARPS = 12;
+    // warps per CTA (one CTA per SM): as many as fit in 227 KB of shared
+    // memory next to the operators, at most 16 (the register budget at 128
+    // registers per thread)
+    static constexpr int SMEM_MAX = 232448;
+    static constexpr int WARPS_FIT = (SMEM_MAX - 4 * o_end) / (4 * w_end + 8);
+    static constexpr int WARPS = WARPS_FIT < 16 ? WARPS_FIT : 16;
     static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
     static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + NpP4 * 4);
 };
@@ -135,8 +142,8 @@ __device__ __forceinline__ void minv_apply(const float* __restrict__ M, const fl
 // Neighbour traces of the batch starting at e0 (a gather): lane handles
 // k = lane + 32 t, element k / Nfq, face node k % Nfq.
 template <int N>
-__device__ __forceinline__ void gather_traces(const StageParams<float>& p, int e0, int lane,
-                                              float4 (&tv)[C2<N>::TRL]) {
+__device__ __forceinline__ void gather_traces(const StageParams<float>& p, const float* __restrict__ ut_in, int e0,
+                                              int lane, float4 (&tv)[C2<N>::TRL]) {
     typedef Dims<N> D;
 #pragma unroll
     for (int t = 0; t < C2<N>::TRL; ++t) {
@@ -148,16 +155,441 @@ __device__ __forceinline__ void gather_traces(const StageParams<float>& p, int e
             const int nb = __ldg(p.nbr + (size_t)(e0 + ee) * 3 + face);
             const int en = nb >> 2, fn = nb & 3;
             tv[t] = __ldg(reinterpret_cast<const float4*>(
-                p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4));
+                ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4));
         }
     }
 }
 
+// One batch of EPW elements of one problem, starting at element e0 (all 32
+// lanes of the warp).  ops: the operator region of degree N in shared memory;
+// ws: this warp's region.  Returns false if the bounded wait on the bulk
+// copies expired (the status word then carries STATUS_TIMEOUT).
 template <int N, int MODE>
-__global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const float* __restrict__ ops2, int Kpad) {
+__device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const float* __restrict__ ut_in,
+                                             float* __restrict__ ut_out, double rkA, double rkB,
+                                             const float* __restrict__ ops, float* ws, uint64_t* bar,
+                                             uint32_t& parity, int e0, int lane) {
     typedef Dims<N> D;
     typedef C2<N> C;
     constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const float g = p.g;
+    const float ig = 1.f / g;
+    const int K = p.K;
+    const int ge = e0 + e;
+    const bool valid = ge < K;
+    // ---- stage element data: TMA bulk copies (one per element and array) ----
+    if (lane == 0) mbar_arrive_expect_tx(bar, C::TX_BYTES);
+    __syncwarp();
+    if (lane < 3 * EPW) {
+        const int which = lane / EPW, ee = lane - which * EPW;
+        if (which == 0)
+            tma_bulk_g2s(ws + C::w_ut + ee * C::UTS, ut_in + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
+        else if (which == 1)
+            tma_bulk_g2s(ws + C::w_geo + ee * C::UTS, p.geo + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
+        else
+            tma_bulk_g2s(ws + C::w_mi + ee * C::MIS, p.minv + (size_t)(e0 + ee) * C::NpP4, C::NpP4 * 4, bar);
+    }
+    // neighbour traces of this batch (a gather: plain loads while the bulk copies fly)
+    float4 tv[C::TRL];
+    gather_traces<N>(p, ut_in, e0, lane, tv);
+#pragma unroll
+    for (int t = 0; t < C::TRL; ++t) {
+        const int k = lane + 32 * t;
+        if (k < EPW * D::Nfq) *reinterpret_cast<float4*>(ws + C::w_tr + k * 4) = tv[t];
+    }
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
+    parity ^= 1;
+    __syncwarp();
+
+    // ---- volume flux differencing, rows l = b + LPE*i ------------------------
+    const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
+    const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
+    float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
+    float a0[RPL], a1[RPL], a2[RPL];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+        const int l = b + LPE * i;
+        float4 U = make_float4(0.f, 0.f, 0.f, 0.f), G = U;
+        if (l < D::Nh) {
+            U = utE[l];
+            G = geE[l];
+        }
+        rh[i] = U.x;
+        ru[i] = U.y;
+        rv[i] = U.z;
+        rrx[i] = G.x;
+        rsx[i] = G.y;
+        rry[i] = G.z;
+        rsy[i] = G.w;
+        a0[i] = a1[i] = a2[i] = 0.f;
+    }
+    const float* QsB = ops + C::o_Qs + b * C::OPB;
+#define ESDG_PAIR(I, QR, QS)                                                   \
+{                                                                          \
+    const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
+    const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
+    const float HU = fmaf(rh[I], ru[I], hum), HV = fmaf(rh[I], rv[I], hvm);\
+    const float Us = ru[I] + U.y, Vs = rv[I] + U.z;                        \
+    const float T = fmaf(Qx, HU, Qy * HV);                                 \
+    const float P = rh[I] * gH2;                                           \
+    a0[I] += T;                                                            \
+    a1[I] = fmaf(Us, T, fmaf(Qx, P, a1[I]));                               \
+    a2[I] = fmaf(Vs, T, fmaf(Qy, P, a2[I]));                               \
+}
+    for (int m = 0; m < D::Nq; ++m) {
+        const float4 U = utE[m], G = geE[m];
+        const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
+        const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
+#pragma unroll
+        for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
+            const float4 q = q4[i2];
+            ESDG_PAIR(2 * i2, q.x, q.y)
+            if (2 * i2 + 1 < RPL) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
+        }
+    }
+    for (int m = D::Nq; m < D::Nh; ++m) {
+        const float4 U = utE[m], G = geE[m];
+        const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
+        const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
+#pragma unroll
+        for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
+            if (LPE * (2 * i2) < D::Nq) {
+                const float4 q = q4[i2];
+                // face rows (l >= Nq) have no face columns; their entries are zero,
+                // so the predicate only skips work
+                if (b + LPE * (2 * i2) < D::Nq) ESDG_PAIR(2 * i2, q.x, q.y)
+                if (2 * i2 + 1 < RPL && b + LPE * (2 * i2 + 1) < D::Nq) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
+            }
+        }
+    }
+#undef ESDG_PAIR
+    // ---- interface flux on the face rows ------------------------------------
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+        a0[i] *= 2.f;
+        const int l = b + LPE * i;
+        if (LPE * i + LPE - 1 >= D::Nq && l >= D::Nq && l < D::Nh) {
+            const int f = l - D::Nq;
+            const float4 U = utE[l];
+            const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
+            const float h_l = U.x, b_l = U.w - U.x;
+            const float hP = tp.x, uP = tp.y, vP = tp.z;
+            const float huP = hP * uP, hvP = hP * vP;
+            const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
+            const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
+            const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
+            const float w = ops[C::o_wf + f];
+            const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
+            const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);
+            const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
+            const float pw = 0.5f * g * h_l * (hP + b_l);
+            const float Fn0 = nxJ * huA + nyJ * hvA;
+            a0[i] += w * Fn0;
+            a1[i] += w * (uA * Fn0 + nxJ * pw);
+            a2[i] += w * (vA * Fn0 + nyJ * pw);
+            if (p.lf) {
+                const float sJ = sqrtf(nxJ * nxJ + nyJ * nyJ);
+                const float inx = nxJ / sJ, iny = nyJ / sJ;
+                const float lm = fabsf(ru[i] * inx + rv[i] * iny) + sqrtf(g * h_l);
+                const float lp = fabsf(uP * inx + vP * iny) + sqrtf(g * hP);
+                const float c = 0.5f * w * sJ * fmaxf(lm, lp);
+                a0[i] -= c * (hP - h_l);
+                a1[i] -= c * (huP - hu_l);
+                a2[i] -= c * (hvP - hv_l);
+            }
+        }
+    }
+    __syncwarp();  // every lane is done with the u~ / metric staging
+    float* rt = ws + C::s_rt;
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+        const int l = b + LPE * i;
+        if (l < D::Nh) {
+            rt[(0 * D::Nh + l) * EPW + e] = a0[i];
+            rt[(1 * D::Nh + l) * EPW + e] = a1[i];
+            rt[(2 * D::Nh + l) * EPW + e] = a2[i];
+        }
+    }
+    // Operands of the later phases, loaded now so their latency overlaps the
+    // lift and the inverse mass: the FP64 RK state of the batch spread over
+    // all 32 lanes (j = lane + 32 k in [field][element][mode] order, which is
+    // contiguous per field in global memory), and b, w J at this lane's nodes.
+    constexpr int NRK = 3 * EPW * D::Np;
+    double uj[C::RKL], rj[C::RKL];
+    if (MODE == 1) {
+#pragma unroll
+        for (int k = 0; k < C::RKL; ++k) {
+            const int j = lane + 32 * k;
+            uj[k] = 0.0;
+            rj[k] = 0.0;
+            if (j < NRK) {
+                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                if (e0 + o / D::Np < K) {
+                    const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                    uj[k] = p.u[gi];
+                    rj[k] = p.res[gi];
+                }
+            }
+        }
+    }
+    // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
+    float* ts = ws + C::s_t;
+    if (p.forcing) {
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            if (q < D::Nq) {
+                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                if (valid) {
+                    const float x = p.xq[(size_t)ge * D::Nq + q], y = p.yq[(size_t)ge * D::Nq + q];
+                    const float wj = p.wJq[(size_t)ge * D::Nq + q];
+                    float sth, cth, sx, cx, sy, cy;
+                    sincospif(x + y - (float)p.t, &sth, &cth);
+                    sincospif(x, &sx, &cx);
+                    sincospif(y, &sy, &cy);
+                    const float pi = 3.14159265358979323846f;
+                    const float h = 2.f + p.mms_amp * sth;
+                    const float cc = p.mms_amp * pi * cth;
+                    const float bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
+                    const float u0 = p.mms_u0, v0 = p.mms_v0;
+                    f0 = wj * (-cc + u0 * cc + v0 * cc);
+                    f1 = wj * (-u0 * cc + (u0 * u0 + g * h) * cc + u0 * v0 * cc + g * h * bx);
+                    f2 = wj * (-v0 * cc + u0 * v0 * cc + (v0 * v0 + g * h) * cc + g * h * by);
+                }
+                ts[(0 * D::Nq + q) * EPW + e] = f0;
+                ts[(1 * D::Nq + q) * EPW + e] = f1;
+                ts[(2 * D::Nq + q) * EPW + e] = f2;
+            }
+        }
+    }
+    __syncwarp();
+    // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j ------------------
+    float* ss = ws + C::s_s;
+    {
+        float s0[MPL], s1[MPL], s2[MPL];
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) s0[j] = s1[j] = s2[j] = 0.f;
+        for (int l = 0; l < D::Nh; ++l) {
+            const float r0 = rt[(0 * D::Nh + l) * EPW + e];
+            const float r1 = rt[(1 * D::Nh + l) * EPW + e];
+            const float r2 = rt[(2 * D::Nh + l) * EPW + e];
+            const float* v = ops + C::o_VhT + (l * LPE + b) * C::MPLp;
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                s0[j] = fmaf(v[j], r0, s0[j]);
+                s1[j] = fmaf(v[j], r1, s1[j]);
+                s2[j] = fmaf(v[j], r2, s2[j]);
+            }
+        }
+        if (p.forcing) {
+            for (int q = 0; q < D::Nq; ++q) {
+                const float f0 = ts[(0 * D::Nq + q) * EPW + e];
+                const float f1 = ts[(1 * D::Nq + q) * EPW + e];
+                const float f2 = ts[(2 * D::Nq + q) * EPW + e];
+                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    s0[j] = fmaf(-v[j], f0, s0[j]);
+                    s1[j] = fmaf(-v[j], f1, s1[j]);
+                    s2[j] = fmaf(-v[j], f2, s2[j]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            if (n < D::Np) {
+                ss[(0 * D::Np + n) * EPW + e] = s0[j];
+                ss[(1 * D::Np + n) * EPW + e] = s1[j];
+                ss[(2 * D::Np + n) * EPW + e] = s2[j];
+            }
+        }
+    }
+    __syncwarp();
+    // ---- du/dt = -(M_h^k)^{-1} s (field per lane) into ss as [field][element][mode]
+    const float* Mi = ws + C::w_mi + e * C::MIS;
+    {
+        float y[D::Np], r[D::Np];
+        if (b < 3) {
+#pragma unroll
+            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
+        }
+        __syncwarp();
+        if (b < 3) {
+            minv_apply<D::Np>(Mi, y, r);
+#pragma unroll
+            for (int n = 0; n < D::Np; ++n) ss[(b * EPW + e) * D::Np + n] = -r[n];
+        }
+    }
+    __syncwarp();
+    float* us = ws + C::s_u;
+    if (MODE == 0) {
+        for (int j = lane; j < NRK; j += 32) {
+            const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+            if (e0 + o / D::Np < K) p.rhs_out[((size_t)c * K + e0) * D::Np + o] = (double)ss[j];
+        }
+    } else {
+        // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
+        const float dtf = (float)p.dt;
+#pragma unroll
+        for (int k = 0; k < C::RKL; ++k) {
+            const int j = lane + 32 * k;
+            if (j < NRK) {
+                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                const int ee = o / D::Np, n = o - ee * D::Np;
+                double un = 1.0;
+                if (e0 + ee < K) {
+                    const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                    const double rs = fma(rkA, rj[k], (double)(dtf * ss[j]));
+                    un = fma(rkB, rs, uj[k]);
+                    p.res[gi] = rs;
+                    p.u[gi] = un;
+                }
+                us[(c * D::Np + n) * EPW + ee] = (float)un;
+            }
+        }
+    }
+    __syncwarp();
+    if (MODE == 1) {
+        float bqv[QPL], wqv[QPL], blv[RPL];
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = b + LPE * j;
+                bqv[j] = 0.f;
+                wqv[j] = 0.f;
+                if (valid && q < D::Nq) {
+                    bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
+                    wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const int l = b + LPE * j;
+                blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
+            }
+        int bad = 0;
+        // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
+        {
+            float q0[QPL], q1[QPL], q2[QPL];
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
+            for (int n = 0; n < D::Np; ++n) {
+                const float u0 = us[(0 * D::Np + n) * EPW + e];
+                const float u1 = us[(1 * D::Np + n) * EPW + e];
+                const float u2 = us[(2 * D::Np + n) * EPW + e];
+                const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
+#pragma unroll
+                for (int j = 0; j < QPL; ++j) {
+                    q0[j] = fmaf(v[j], u0, q0[j]);
+                    q1[j] = fmaf(v[j], u1, q1[j]);
+                    q2[j] = fmaf(v[j], u2, q2[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                const int q = b + LPE * j;
+                if (q < D::Nq) {
+                    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                    if (valid) {
+                        const float h = q0[j];
+                        if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                        const float ih = 1.f / h;
+                        const float uu = q1[j] * ih, vv = q2[j] * ih;
+                        const float wj = wqv[j];
+                        t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
+                        t1 = wj * uu;
+                        t2 = wj * vv;
+                    }
+                    ts[(0 * D::Nq + q) * EPW + e] = t0;
+                    ts[(1 * D::Nq + q) * EPW + e] = t1;
+                    ts[(2 * D::Nq + q) * EPW + e] = t2;
+                }
+            }
+        }
+        __syncwarp();
+        // y = Vq^T (w J v), modes n = b + LPE*j
+        {
+            float y0[MPL], y1[MPL], y2[MPL];
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+            for (int q = 0; q < D::Nq; ++q) {
+                const float t0 = ts[(0 * D::Nq + q) * EPW + e];
+                const float t1 = ts[(1 * D::Nq + q) * EPW + e];
+                const float t2 = ts[(2 * D::Nq + q) * EPW + e];
+                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    y0[j] = fmaf(v[j], t0, y0[j]);
+                    y1[j] = fmaf(v[j], t1, y1[j]);
+                    y2[j] = fmaf(v[j], t2, y2[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = y0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = y1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = y2[j];
+                }
+            }
+        }
+        __syncwarp();
+        // v_h = (M_h^k)^{-1} y, in place (field per lane)
+        if (b < 3) {
+            float y[D::Np], r[D::Np];
+#pragma unroll
+            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
+            minv_apply<D::Np>(Mi, y, r);
+#pragma unroll
+            for (int n = 0; n < D::Np; ++n) ss[(b * D::Np + n) * EPW + e] = r[n];
+        }
+        __syncwarp();
+        // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
+        {
+            float v0[RPL], v1[RPL], v2[RPL];
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
+            for (int n = 0; n < D::Np; ++n) {
+                const float w0 = ss[(0 * D::Np + n) * EPW + e];
+                const float w1 = ss[(1 * D::Np + n) * EPW + e];
+                const float w2 = ss[(2 * D::Np + n) * EPW + e];
+                const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) {
+                    v0[j] = fmaf(v[j], w0, v0[j]);
+                    v1[j] = fmaf(v[j], w1, v1[j]);
+                    v2[j] = fmaf(v[j], w2, v2[j]);
+                }
+            }
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) {
+                    const int l = b + LPE * j;
+                    if (l < D::Nh) {
+                        const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
+                        const float h = H - blv[j];
+                        if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                        if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
+                        *reinterpret_cast<float4*>(ut_out + ((size_t)ge * D::Nh + l) * 4) =
+                            make_float4(h, v1[j], v2[j], H);
+                    }
+                }
+            }
+        }
+        if (bad) atomicOr(p.status, bad);
+    }
+    // generic-proxy writes to the staging area must be ordered before the
+    // next batch's bulk copies overwrite it
+    fence_proxy_async_smem();
+    __syncwarp();
+    return true;
+}
+
+template <int N, int MODE>
+__global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<float> p, const float* __restrict__ ops2, int Kpad) {
+    typedef C2<N> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* ops = reinterpret_cast<float*>(smem_raw);
     const int nwarps = blockDim.x >> 5;
@@ -170,425 +602,35 @@ __global__ void __launch_bounds__(384, 1) k_stage2(StageParams<float> p, const f
     __syncthreads();
     uint64_t* bar = &bars[warp];
     float* ws = ops + C::o_end + warp * C::w_end;
-    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
-    const float g = p.g;
-    const float ig = 1.f / g;
-    const int K = p.K;
     uint32_t parity = 0;
-    const int nbatch = Kpad / EPW;
-    const int bstride = gridDim.x * nwarps;
-    float4 tv[C::TRL];
-    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += bstride) {
-        const int e0 = batch * EPW;
-        const int ge = e0 + e;
-        const bool valid = ge < K;
-        // ---- stage element data: TMA bulk copies (one per element and array) ----
-        if (lane == 0) mbar_arrive_expect_tx(bar, C::TX_BYTES);
-        __syncwarp();
-        if (lane < 3 * EPW) {
-            const int which = lane / EPW, ee = lane - which * EPW;
-            if (which == 0)
-                tma_bulk_g2s(ws + C::w_ut + ee * C::UTS, p.ut_in + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
-            else if (which == 1)
-                tma_bulk_g2s(ws + C::w_geo + ee * C::UTS, p.geo + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
-            else
-                tma_bulk_g2s(ws + C::w_mi + ee * C::MIS, p.minv + (size_t)(e0 + ee) * C::NpP4, C::NpP4 * 4, bar);
-        }
-        // neighbour traces of this batch
-        gather_traces<N>(p, e0, lane, tv);
-#pragma unroll
-        for (int t = 0; t < C::TRL; ++t) {
-            const int k = lane + 32 * t;
-            if (k < EPW * D::Nfq) *reinterpret_cast<float4*>(ws + C::w_tr + k * 4) = tv[t];
-        }
-        if (!mbar_wait_bounded(bar, parity, p.status)) return;
-        parity ^= 1;
-        __syncwarp();
-
-        // ---- volume flux differencing, rows l = b + LPE*i ------------------------
-        const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
-        const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
-        float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
-        float a0[RPL], a1[RPL], a2[RPL];
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const int l = b + LPE * i;
-            float4 U = make_float4(0.f, 0.f, 0.f, 0.f), G = U;
-            if (l < D::Nh) {
-                U = utE[l];
-                G = geE[l];
-            }
-            rh[i] = U.x;
-            ru[i] = U.y;
-            rv[i] = U.z;
-            rrx[i] = G.x;
-            rsx[i] = G.y;
-            rry[i] = G.z;
-            rsy[i] = G.w;
-            a0[i] = a1[i] = a2[i] = 0.f;
-        }
-        const float* QsB = ops + C::o_Qs + b * C::OPB;
-#define ESDG_PAIR(I, QR, QS)                                                   \
-    {                                                                          \
-        const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
-        const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
-        const float HU = fmaf(rh[I], ru[I], hum), HV = fmaf(rh[I], rv[I], hvm);\
-        const float Us = ru[I] + U.y, Vs = rv[I] + U.z;                        \
-        const float T = fmaf(Qx, HU, Qy * HV);                                 \
-        const float P = rh[I] * gH2;                                           \
-        a0[I] += T;                                                            \
-        a1[I] = fmaf(Us, T, fmaf(Qx, P, a1[I]));                               \
-        a2[I] = fmaf(Vs, T, fmaf(Qy, P, a2[I]));                               \
-    }
-        for (int m = 0; m < D::Nq; ++m) {
-            const float4 U = utE[m], G = geE[m];
-            const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
-            const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
-#pragma unroll
-            for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
-                const float4 q = q4[i2];
-                ESDG_PAIR(2 * i2, q.x, q.y)
-                if (2 * i2 + 1 < RPL) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
-            }
-        }
-        for (int m = D::Nq; m < D::Nh; ++m) {
-            const float4 U = utE[m], G = geE[m];
-            const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
-            const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
-#pragma unroll
-            for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
-                if (LPE * (2 * i2) < D::Nq) {
-                    const float4 q = q4[i2];
-                    // face rows (l >= Nq) have no face columns; their entries are zero,
-                    // so the predicate only skips work
-                    if (b + LPE * (2 * i2) < D::Nq) ESDG_PAIR(2 * i2, q.x, q.y)
-                    if (2 * i2 + 1 < RPL && b + LPE * (2 * i2 + 1) < D::Nq) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
-                }
-            }
-        }
-#undef ESDG_PAIR
-        // ---- interface flux on the face rows ------------------------------------
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            a0[i] *= 2.f;
-            const int l = b + LPE * i;
-            if (LPE * i + LPE - 1 >= D::Nq && l >= D::Nq && l < D::Nh) {
-                const int f = l - D::Nq;
-                const float4 U = utE[l];
-                const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
-                const float h_l = U.x, b_l = U.w - U.x;
-                const float hP = tp.x, uP = tp.y, vP = tp.z;
-                const float huP = hP * uP, hvP = hP * vP;
-                const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
-                const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
-                const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
-                const float w = ops[C::o_wf + f];
-                const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
-                const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);
-                const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
-                const float pw = 0.5f * g * h_l * (hP + b_l);
-                const float Fn0 = nxJ * huA + nyJ * hvA;
-                a0[i] += w * Fn0;
-                a1[i] += w * (uA * Fn0 + nxJ * pw);
-                a2[i] += w * (vA * Fn0 + nyJ * pw);
-                if (p.lf) {
-                    const float sJ = sqrtf(nxJ * nxJ + nyJ * nyJ);
-                    const float inx = nxJ / sJ, iny = nyJ / sJ;
-                    const float lm = fabsf(ru[i] * inx + rv[i] * iny) + sqrtf(g * h_l);
-                    const float lp = fabsf(uP * inx + vP * iny) + sqrtf(g * hP);
-                    const float c = 0.5f * w * sJ * fmaxf(lm, lp);
-                    a0[i] -= c * (hP - h_l);
-                    a1[i] -= c * (huP - hu_l);
-                    a2[i] -= c * (hvP - hv_l);
-                }
-            }
-        }
-        __syncwarp();  // every lane is done with the u~ / metric staging
-        float* rt = ws + C::s_rt;
-#pragma unroll
-        for (int i = 0; i < RPL; ++i) {
-            const int l = b + LPE * i;
-            if (l < D::Nh) {
-                rt[(0 * D::Nh + l) * EPW + e] = a0[i];
-                rt[(1 * D::Nh + l) * EPW + e] = a1[i];
-                rt[(2 * D::Nh + l) * EPW + e] = a2[i];
-            }
-        }
-        // Operands of the later phases, loaded now so their latency overlaps the
-        // lift and the inverse mass: the FP64 RK state of the batch spread over
-        // all 32 lanes (j = lane + 32 k in [field][element][mode] order, which is
-        // contiguous per field in global memory), and b, w J at this lane's nodes.
-        constexpr int NRK = 3 * EPW * D::Np;
-        double uj[C::RKL], rj[C::RKL];
-        if (MODE == 1) {
-#pragma unroll
-            for (int k = 0; k < C::RKL; ++k) {
-                const int j = lane + 32 * k;
-                uj[k] = 0.0;
-                rj[k] = 0.0;
-                if (j < NRK) {
-                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-                    if (e0 + o / D::Np < K) {
-                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
-                        uj[k] = p.u[gi];
-                        rj[k] = p.res[gi];
-                    }
-                }
-            }
-        }
-        // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
-        float* ts = ws + C::s_t;
-        if (p.forcing) {
-#pragma unroll
-            for (int j = 0; j < QPL; ++j) {
-                const int q = b + LPE * j;
-                if (q < D::Nq) {
-                    float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-                    if (valid) {
-                        const float x = p.xq[(size_t)ge * D::Nq + q], y = p.yq[(size_t)ge * D::Nq + q];
-                        const float wj = p.wJq[(size_t)ge * D::Nq + q];
-                        float sth, cth, sx, cx, sy, cy;
-                        sincospif(x + y - (float)p.t, &sth, &cth);
-                        sincospif(x, &sx, &cx);
-                        sincospif(y, &sy, &cy);
-                        const float pi = 3.14159265358979323846f;
-                        const float h = 2.f + p.mms_amp * sth;
-                        const float cc = p.mms_amp * pi * cth;
-                        const float bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
-                        const float u0 = p.mms_u0, v0 = p.mms_v0;
-                        f0 = wj * (-cc + u0 * cc + v0 * cc);
-                        f1 = wj * (-u0 * cc + (u0 * u0 + g * h) * cc + u0 * v0 * cc + g * h * bx);
-                        f2 = wj * (-v0 * cc + u0 * v0 * cc + (v0 * v0 + g * h) * cc + g * h * by);
-                    }
-                    ts[(0 * D::Nq + q) * EPW + e] = f0;
-                    ts[(1 * D::Nq + q) * EPW + e] = f1;
-                    ts[(2 * D::Nq + q) * EPW + e] = f2;
-                }
-            }
-        }
-        __syncwarp();
-        // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j ------------------
-        float* ss = ws + C::s_s;
-        {
-            float s0[MPL], s1[MPL], s2[MPL];
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) s0[j] = s1[j] = s2[j] = 0.f;
-            for (int l = 0; l < D::Nh; ++l) {
-                const float r0 = rt[(0 * D::Nh + l) * EPW + e];
-                const float r1 = rt[(1 * D::Nh + l) * EPW + e];
-                const float r2 = rt[(2 * D::Nh + l) * EPW + e];
-                const float* v = ops + C::o_VhT + (l * LPE + b) * C::MPLp;
-#pragma unroll
-                for (int j = 0; j < MPL; ++j) {
-                    s0[j] = fmaf(v[j], r0, s0[j]);
-                    s1[j] = fmaf(v[j], r1, s1[j]);
-                    s2[j] = fmaf(v[j], r2, s2[j]);
-                }
-            }
-            if (p.forcing) {
-                for (int q = 0; q < D::Nq; ++q) {
-                    const float f0 = ts[(0 * D::Nq + q) * EPW + e];
-                    const float f1 = ts[(1 * D::Nq + q) * EPW + e];
-                    const float f2 = ts[(2 * D::Nq + q) * EPW + e];
-                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
-#pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        s0[j] = fmaf(-v[j], f0, s0[j]);
-                        s1[j] = fmaf(-v[j], f1, s1[j]);
-                        s2[j] = fmaf(-v[j], f2, s2[j]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * D::Np + n) * EPW + e] = s0[j];
-                    ss[(1 * D::Np + n) * EPW + e] = s1[j];
-                    ss[(2 * D::Np + n) * EPW + e] = s2[j];
-                }
-            }
-        }
-        __syncwarp();
-        // ---- du/dt = -(M_h^k)^{-1} s (field per lane) into ss as [field][element][mode]
-        const float* Mi = ws + C::w_mi + e * C::MIS;
-        {
-            float y[D::Np], r[D::Np];
-            if (b < 3) {
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
-            }
-            __syncwarp();
-            if (b < 3) {
-                minv_apply<D::Np>(Mi, y, r);
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) ss[(b * EPW + e) * D::Np + n] = -r[n];
-            }
-        }
-        __syncwarp();
-        float* us = ws + C::s_u;
-        if (MODE == 0) {
-            for (int j = lane; j < NRK; j += 32) {
-                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-                if (e0 + o / D::Np < K) p.rhs_out[((size_t)c * K + e0) * D::Np + o] = (double)ss[j];
-            }
-        } else {
-            // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
-            const float dtf = (float)p.dt;
-#pragma unroll
-            for (int k = 0; k < C::RKL; ++k) {
-                const int j = lane + 32 * k;
-                if (j < NRK) {
-                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-                    const int ee = o / D::Np, n = o - ee * D::Np;
-                    double un = 1.0;
-                    if (e0 + ee < K) {
-                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
-                        const double rs = fma(p.rkA, rj[k], (double)(dtf * ss[j]));
-                        un = fma(p.rkB, rs, uj[k]);
-                        p.res[gi] = rs;
-                        p.u[gi] = un;
-                    }
-                    us[(c * D::Np + n) * EPW + ee] = (float)un;
-                }
-            }
-        }
-        __syncwarp();
-        if (MODE == 1) {
-            float bqv[QPL], wqv[QPL], blv[RPL];
-#pragma unroll
-                for (int j = 0; j < QPL; ++j) {
-                    const int q = b + LPE * j;
-                    bqv[j] = 0.f;
-                    wqv[j] = 0.f;
-                    if (valid && q < D::Nq) {
-                        bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
-                        wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
-                    }
-                }
-    #pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    const int l = b + LPE * j;
-                    blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
-                }
-            int bad = 0;
-            // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
-            {
-                float q0[QPL], q1[QPL], q2[QPL];
-#pragma unroll
-                for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
-                for (int n = 0; n < D::Np; ++n) {
-                    const float u0 = us[(0 * D::Np + n) * EPW + e];
-                    const float u1 = us[(1 * D::Np + n) * EPW + e];
-                    const float u2 = us[(2 * D::Np + n) * EPW + e];
-                    const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
-#pragma unroll
-                    for (int j = 0; j < QPL; ++j) {
-                        q0[j] = fmaf(v[j], u0, q0[j]);
-                        q1[j] = fmaf(v[j], u1, q1[j]);
-                        q2[j] = fmaf(v[j], u2, q2[j]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < QPL; ++j) {
-                    const int q = b + LPE * j;
-                    if (q < D::Nq) {
-                        float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-                        if (valid) {
-                            const float h = q0[j];
-                            if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
-                            const float ih = 1.f / h;
-                            const float uu = q1[j] * ih, vv = q2[j] * ih;
-                            const float wj = wqv[j];
-                            t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
-                            t1 = wj * uu;
-                            t2 = wj * vv;
-                        }
-                        ts[(0 * D::Nq + q) * EPW + e] = t0;
-                        ts[(1 * D::Nq + q) * EPW + e] = t1;
-                        ts[(2 * D::Nq + q) * EPW + e] = t2;
-                    }
-                }
-            }
-            __syncwarp();
-            // y = Vq^T (w J v), modes n = b + LPE*j
-            {
-                float y0[MPL], y1[MPL], y2[MPL];
-#pragma unroll
-                for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
-                for (int q = 0; q < D::Nq; ++q) {
-                    const float t0 = ts[(0 * D::Nq + q) * EPW + e];
-                    const float t1 = ts[(1 * D::Nq + q) * EPW + e];
-                    const float t2 = ts[(2 * D::Nq + q) * EPW + e];
-                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
-#pragma unroll
-                    for (int j = 0; j < MPL; ++j) {
-                        y0[j] = fmaf(v[j], t0, y0[j]);
-                        y1[j] = fmaf(v[j], t1, y1[j]);
-                        y2[j] = fmaf(v[j], t2, y2[j]);
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < MPL; ++j) {
-                    const int n = b + LPE * j;
-                    if (n < D::Np) {
-                        ss[(0 * D::Np + n) * EPW + e] = y0[j];
-                        ss[(1 * D::Np + n) * EPW + e] = y1[j];
-                        ss[(2 * D::Np + n) * EPW + e] = y2[j];
-                    }
-                }
-            }
-            __syncwarp();
-            // v_h = (M_h^k)^{-1} y, in place (field per lane)
-            if (b < 3) {
-                float y[D::Np], r[D::Np];
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
-                minv_apply<D::Np>(Mi, y, r);
-#pragma unroll
-                for (int n = 0; n < D::Np; ++n) ss[(b * D::Np + n) * EPW + e] = r[n];
-            }
-            __syncwarp();
-            // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
-            {
-                float v0[RPL], v1[RPL], v2[RPL];
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
-                for (int n = 0; n < D::Np; ++n) {
-                    const float w0 = ss[(0 * D::Np + n) * EPW + e];
-                    const float w1 = ss[(1 * D::Np + n) * EPW + e];
-                    const float w2 = ss[(2 * D::Np + n) * EPW + e];
-                    const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
-#pragma unroll
-                    for (int j = 0; j < RPL; ++j) {
-                        v0[j] = fmaf(v[j], w0, v0[j]);
-                        v1[j] = fmaf(v[j], w1, v1[j]);
-                        v2[j] = fmaf(v[j], w2, v2[j]);
-                    }
-                }
-                if (valid) {
-#pragma unroll
-                    for (int j = 0; j < RPL; ++j) {
-                        const int l = b + LPE * j;
-                        if (l < D::Nh) {
-                            const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
-                            const float h = H - blv[j];
-                            if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
-                            if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
-                            *reinterpret_cast<float4*>(p.ut_out + ((size_t)ge * D::Nh + l) * 4) =
-                                make_float4(h, v1[j], v2[j], H);
-                        }
-                    }
-                }
-            }
-            if (bad) atomicOr(p.status, bad);
-        }
-        if (batch + bstride < nbatch) gather_traces<N>(p, (batch + bstride) * EPW, lane, tv);
-        // generic-proxy writes to the staging area must be ordered before the
-        // next batch's bulk copies overwrite it
-        fence_proxy_async_smem();
-        __syncwarp();
-    }
+    const int nbatch = Kpad / C::EPW;
+    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps)
+        if (!stage2_batch<N, MODE>(p, p.ut_in, p.ut_out, p.rkA, p.rkB, ops, ws, bar, parity, batch * C::EPW, lane))
+            return;
 }
+
+// ---- ensembles: several independent problems in one persistent launch --------
+// Tile table: problem i owns the global batches [batch_begin, batch_begin +
+// nbatch); every batch is EPW = 4 consecutive elements of that problem.
+struct EnsembleMember {
+    StageParams<float> p;   // all fields but ut_in/ut_out/rkA/rkB (set per launch)
+    const float* ops2;      // operators of the member's degree (k_stage2 layout)
+    float* ut[2];           // entropy-projected values, ping-pong
+    int N;
+    int batch_begin, nbatch;
+};
+
+constexpr int ENSEMBLE_MAX_WARPS = 12;
+
+// One LSRK45 stage for every member (defined in esdg_ensemble.cu), for
+// members of degree at most NMAX (4 or 5).
+template <int NMAX>
+__global__ void k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_batches, int which,
+                                  double rkA, double rkB, int4 ops_lo, int ops_hi, int ops_end, int slab);
+// Host wrappers (esdg_ensemble.cu): shared-memory attribute and launch.
+cudaError_t ensemble_smem_attr(int nmax, size_t smem);
+cudaError_t launch_ensemble(int nmax, int grid, int block, size_t smem, cudaStream_t s, const EnsembleMember* mem,
+                            int nmem, int total_batches, int which, double rkA, double rkB, int4 ops_lo, int ops_hi,
+                            int ops_end, int slab);
 
 }  // namespace esdg

@@ -10,6 +10,8 @@
 #include "host_build.hpp"
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cmath>
 #include <map>
 #include <utility>
@@ -356,57 +358,76 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
     D.xf.assign(size_t(K) * Nfq, 0.0);
     D.yf.assign(size_t(K) * Nfq, 0.0);
     D.minv.assign(size_t(K) * (Np * (Np + 1) / 2), 0.0);
-    std::vector<double> xm(Np), ym(Np);
-    Mat Mh(Np, Np), Mhi;
-    for (int e = 0; e < K; ++e) {
-        for (int n = 0; n < Np; ++n) {
-            double sx = 0, sy = 0;
-            for (int m = 0; m < Np; ++m) {
-                sx += R.Veq_inv(n, m) * D.xeq[size_t(e) * Np + m];
-                sy += R.Veq_inv(n, m) * D.yeq[size_t(e) * Np + m];
-            }
-            xm[n] = sx;
-            ym[n] = sy;
-        }
-        auto eval = [&](const Mat& V, const Mat& Vr, const Mat& Vs, int p, double* out) {
-            double x = 0, y = 0, xr = 0, xs = 0, yr = 0, ys = 0;
+    // per-element geometry and inverse mass matrices, in parallel over elements
+    std::atomic<int> bad(0);  // 1: non-positive J at a volume node, 2: at a face node, 3: singular M_h
+    auto work = [&](int e_begin, int e_end) {
+        std::vector<double> xm(Np), ym(Np);
+        Mat Mh(Np, Np), Mhi;
+        for (int e = e_begin; e < e_end && !bad.load(std::memory_order_relaxed); ++e) {
             for (int n = 0; n < Np; ++n) {
-                x += V(p, n) * xm[n]; y += V(p, n) * ym[n];
-                xr += Vr(p, n) * xm[n]; xs += Vs(p, n) * xm[n];
-                yr += Vr(p, n) * ym[n]; ys += Vs(p, n) * ym[n];
+                double sx = 0, sy = 0;
+                for (int m = 0; m < Np; ++m) {
+                    sx += R.Veq_inv(n, m) * D.xeq[size_t(e) * Np + m];
+                    sy += R.Veq_inv(n, m) * D.yeq[size_t(e) * Np + m];
+                }
+                xm[n] = sx;
+                ym[n] = sy;
             }
-            out[0] = x; out[1] = y;
-            out[2] = ys; out[3] = -yr; out[4] = -xs; out[5] = xr;   // rxJ sxJ ryJ syJ
-            out[6] = xr * ys - xs * yr;                              // J
-        };
-        double g7[7];
-        for (int q = 0; q < Nq; ++q) {
-            eval(R.Vq, R.Vqr, R.Vqs, q, g7);
-            if (!(g7[6] > 0.0)) { err = "non-positive Jacobian at a volume node"; return false; }
-            D.xq[size_t(e) * Nq + q] = g7[0];
-            D.yq[size_t(e) * Nq + q] = g7[1];
-            for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + q) * 4 + c] = g7[2 + c];
-            D.Jq[size_t(e) * Nq + q] = g7[6];
-        }
-        for (int f = 0; f < Nfq; ++f) {
-            eval(R.Vf, R.Vfr, R.Vfs, f, g7);
-            if (!(g7[6] > 0.0)) { err = "non-positive Jacobian at a face node"; return false; }
-            D.xf[size_t(e) * Nfq + f] = g7[0];
-            D.yf[size_t(e) * Nfq + f] = g7[1];
-            for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + Nq + f) * 4 + c] = g7[2 + c];
-        }
-        // M_h^k = Vq^T W J Vq and its inverse (Sec. 2.7), packed lower triangle
-        for (int i = 0; i < Np; ++i)
-            for (int j = 0; j < Np; ++j) {
-                double s = 0;
-                for (int q = 0; q < Nq; ++q) s += R.Vq(q, i) * R.wq[q] * D.Jq[size_t(e) * Nq + q] * R.Vq(q, j);
-                Mh(i, j) = s;
+            auto eval = [&](const Mat& V, const Mat& Vr, const Mat& Vs, int p, double* out) {
+                double x = 0, y = 0, xr = 0, xs = 0, yr = 0, ys = 0;
+                for (int n = 0; n < Np; ++n) {
+                    x += V(p, n) * xm[n]; y += V(p, n) * ym[n];
+                    xr += Vr(p, n) * xm[n]; xs += Vs(p, n) * xm[n];
+                    yr += Vr(p, n) * ym[n]; ys += Vs(p, n) * ym[n];
+                }
+                out[0] = x; out[1] = y;
+                out[2] = ys; out[3] = -yr; out[4] = -xs; out[5] = xr;   // rxJ sxJ ryJ syJ
+                out[6] = xr * ys - xs * yr;                              // J
+            };
+            double g7[7];
+            for (int q = 0; q < Nq; ++q) {
+                eval(R.Vq, R.Vqr, R.Vqs, q, g7);
+                if (!(g7[6] > 0.0)) { bad = 1; return; }
+                D.xq[size_t(e) * Nq + q] = g7[0];
+                D.yq[size_t(e) * Nq + q] = g7[1];
+                for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + q) * 4 + c] = g7[2 + c];
+                D.Jq[size_t(e) * Nq + q] = g7[6];
             }
-        if (!invert(Mh, Mhi)) { err = "singular curved mass matrix"; return false; }
-        size_t o = size_t(e) * (Np * (Np + 1) / 2);
-        for (int i = 0; i < Np; ++i)
-            for (int j = 0; j <= i; ++j) D.minv[o + i * (i + 1) / 2 + j] = 0.5 * (Mhi(i, j) + Mhi(j, i));
+            for (int f = 0; f < Nfq; ++f) {
+                eval(R.Vf, R.Vfr, R.Vfs, f, g7);
+                if (!(g7[6] > 0.0)) { bad = 2; return; }
+                D.xf[size_t(e) * Nfq + f] = g7[0];
+                D.yf[size_t(e) * Nfq + f] = g7[1];
+                for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + Nq + f) * 4 + c] = g7[2 + c];
+            }
+            // M_h^k = Vq^T W J Vq and its inverse (Sec. 2.7), packed lower triangle
+            for (int i = 0; i < Np; ++i)
+                for (int j = 0; j < Np; ++j) {
+                    double s = 0;
+                    for (int q = 0; q < Nq; ++q) s += R.Vq(q, i) * R.wq[q] * D.Jq[size_t(e) * Nq + q] * R.Vq(q, j);
+                    Mh(i, j) = s;
+                }
+            if (!invert(Mh, Mhi)) { bad = 3; return; }
+            size_t o = size_t(e) * (Np * (Np + 1) / 2);
+            for (int i = 0; i < Np; ++i)
+                for (int j = 0; j <= i; ++j) D.minv[o + i * (i + 1) / 2 + j] = 0.5 * (Mhi(i, j) + Mhi(j, i));
+        }
+    };
+    const int nthreads = std::max(1, std::min<int>(int(std::thread::hardware_concurrency()), (K + 4095) / 4096));
+    if (nthreads == 1) {
+        work(0, K);
+    } else {
+        std::vector<std::thread> pool;
+        const int chunk = (K + nthreads - 1) / nthreads;
+        for (int t = 0; t < nthreads; ++t) {
+            const int b0 = t * chunk, b1 = std::min(K, b0 + chunk);
+            if (b0 < b1) pool.emplace_back(work, b0, b1);
+        }
+        for (auto& th : pool) th.join();
     }
+    if (bad == 1) { err = "non-positive Jacobian at a volume node"; return false; }
+    if (bad == 2) { err = "non-positive Jacobian at a face node"; return false; }
+    if (bad == 3) { err = "singular curved mass matrix"; return false; }
     // every face node must meet its partner (reversed order) modulo the period
     const double tol = 1e-9 * std::min(Lx / nx, Ly / ny);
     for (int e = 0; e < K; ++e)

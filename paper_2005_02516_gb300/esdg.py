@@ -38,7 +38,9 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_init_state", "esdg_set_bathymetry", "esdg_set_state", "esdg_copy_state",
            "esdg_rhs", "esdg_step", "esdg_step_async", "esdg_check", "esdg_entropy",
            "esdg_entropy_noalloc", "esdg_dt",
-           "esdg_destroy", "esdg_last_error"]
+           "esdg_destroy", "esdg_last_error",
+           "esdg_ensemble_create", "esdg_ensemble_autotune", "esdg_ensemble_step",
+           "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error"]
 
 
 class EsdgError(RuntimeError):
@@ -91,6 +93,12 @@ def load_library(path=LIB_PATH):
         "esdg_dt": ([P, PD], I),
         "esdg_destroy": ([P], I),
         "esdg_last_error": ([P], ctypes.c_char_p),
+        "esdg_ensemble_create": ([ctypes.POINTER(P), I, ctypes.POINTER(P)], I),
+        "esdg_ensemble_autotune": ([P, PI, PI], I),
+        "esdg_ensemble_step": ([P, I], I),
+        "esdg_ensemble_step_async": ([P, I], I),
+        "esdg_ensemble_destroy": ([P], I),
+        "esdg_ensemble_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -236,3 +244,45 @@ class Solver:
         d = ctypes.c_double()
         self._check(self.lib.esdg_dt(self.h, ctypes.byref(d)))
         return d.value
+
+
+class Ensemble:
+    """Several independent FP32 problems (Solver objects on one stream)
+    advanced together: one persistent launch per RK stage over all members,
+    steps replayed from a captured CUDA graph."""
+
+    def __init__(self, solvers):
+        self.lib = load_library()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[s.h.value for s in self.solvers])
+        h = ctypes.c_void_p()
+        rc = self.lib.esdg_ensemble_create(arr, len(self.solvers), ctypes.byref(h))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, self.lib.esdg_ensemble_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != ESDG_OK:
+            raise EsdgError(rc, self.lib.esdg_ensemble_error(self.h).decode())
+
+    def autotune(self):
+        w, o = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.esdg_ensemble_autotune(self.h, ctypes.byref(w), ctypes.byref(o)))
+        return w.value, o.value
+
+    def step(self, nsteps):
+        self._check(self.lib.esdg_ensemble_step(self.h, nsteps))
+
+    def step_async(self, nsteps):
+        self._check(self.lib.esdg_ensemble_step_async(self.h, nsteps))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.esdg_ensemble_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

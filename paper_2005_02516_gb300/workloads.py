@@ -128,6 +128,51 @@ def random_modal_state(K, Np, seed, c0=2.8, amp_h=0.05, amp_m=0.05):
     return u
 
 
+@dataclasses.dataclass
+class Instance:
+    """One member of a batched ensemble: lake at rest H = 2 plus a Gaussian bump
+    on curved periodic [-1,1]^2, bathymetry amp * sin(pi x) sin(pi y)."""
+    N: int
+    nx: int
+    amp: float
+    cx: float
+    cy: float
+    steps: int
+    warp: float = 0.05
+    g: float = 1.0
+    cfl: float = 0.25
+
+    @property
+    def K(self):
+        return 2 * self.nx * self.nx
+
+    @property
+    def Np(self):
+        return (self.N + 1) * (self.N + 2) // 2
+
+    def bathymetry(self, x, y):
+        return self.amp * np.sin(np.pi * x) * np.sin(np.pi * y)
+
+    def initial(self, x, y):
+        r2 = (x - self.cx) ** 2 + (y - self.cy) ** 2
+        return np.stack([2.0 + 0.01 * np.exp(-25.0 * r2), 0 * x, 0 * x])
+
+
+def ensemble(n=64, steps=500, seed=BASE_SEED):
+    """Batched ensemble: instance i draws, from seed + i, N ~ U{2,3,4},
+    K ~ U{512, 2048, 8192, 32768} (nx ~ U{16, 32, 64, 128}), bathymetry
+    amplitude ~ U[0.02, 0.2] and bump centre ~ U[-0.5, 0.5]^2."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed + i)
+        N = int(rng.integers(2, 5))
+        nx = int(rng.choice([16, 32, 64, 128]))
+        amp = float(rng.uniform(0.02, 0.2))
+        c = rng.uniform(-0.5, 0.5, size=2)
+        out.append(Instance(N=N, nx=nx, amp=amp, cx=float(c[0]), cy=float(c[1]), steps=steps))
+    return out
+
+
 def lake_at_rest_table_bathymetry(x, y):
     """Bathymetry of the lake-at-rest experiment of Sec. 4.1 as printed:
     b = 0.1 sin(2 pi x) cos(2 pi x) + 0.5 (periodic on [-1,1]^2)."""

@@ -256,6 +256,54 @@ def run_ensemble(n, steps):
     return res
 
 
+def run_served(n, rate, precision, steps_range, k_range, budget_gb=64.0):
+    """Served form: Poisson arrivals of solve requests (degree 2..5, K
+    log-uniform, steps uniform, random smooth bathymetry, lake at rest plus a
+    bump).  Each request is built on a host thread at its arrival time and
+    submitted to the continuous-batching loop; latency is completion minus
+    arrival (host set-up, queueing, admission and GPU time included)."""
+    import concurrent.futures
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(n, rate=rate, k_range=k_range, steps_range=steps_range)
+    srv = esdg.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)))
+    t0 = time.perf_counter()
+    tickets = [None] * n
+
+    def prepare(i):
+        req = trace[i]
+        p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+        xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
+        xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
+        tickets[i] = srv.submit(p, req.bathymetry(xb, yb), req.initial(xq, yq), req.steps, surface=True)
+
+    futs = []
+    with concurrent.futures.ThreadPoolExecutor(max_workers=8) as pool:
+        for i, req in enumerate(trace):
+            delay = req.t_arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            futs.append(pool.submit(prepare, i))
+        for f in futs:
+            f.result()
+    srv.drain(3600.0)
+    wall = time.perf_counter() - t0
+    # server clock starts at esdg_server_create, within microseconds of t0
+    lat = []
+    for i, req in enumerate(trace):
+        state, ts, ta, td = srv.query(tickets[i])
+        if state != 2:
+            raise RuntimeError("request %d failed with state %d" % (i, state))
+        lat.append(td - req.t_arrival)
+    iters, steps, _ = srv.stats()
+    srv.close()
+    lat = np.array(lat)
+    units = sum(r.K * r.Np * 5 * r.steps for r in trace)
+    return {"precision": precision, "requests": n, "rate_per_s": rate, "k_range": list(k_range),
+            "steps_range": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
+            "throughput": units / wall / 1e9, "unit": UNIT, "wall_s": wall, "iterations": iters}
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
     on a sample of 2048 consecutive elements of the same workload, repeated
@@ -306,6 +354,8 @@ def main():
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 and ensemble legs (profiling runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="instances of the batched-ensemble leg (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=500)
+    ap.add_argument("--served", type=int, default=200, help="FP32 requests of the served leg (0: skip)")
+    ap.add_argument("--served-rate", type=float, default=20.0)
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
@@ -368,6 +418,13 @@ def main():
     if not args.fp32_only and args.ensemble > 0:
         ens = run_ensemble(args.ensemble, args.ensemble_steps)
 
+    served = None
+    if not args.fp32_only and args.served > 0 and world == 1:
+        # the served distributions with steps scaled by 1/10 (and the arrival
+        # rate by the same factor) so a run ends within a minute
+        served = [run_served(args.served, args.served_rate, "fp32", (10, 200), (512, 131072)),
+                  run_served(max(4, args.served // 20), args.served_rate / 40.0, "fp64", (10, 200), (512, 8192))]
+
     e2e = None
     if not args.no_e2e:
         s = make_solver("fp32")
@@ -390,7 +447,7 @@ def main():
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other,
-                "fp64": fp64, "ensemble": ens, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
+                "fp64": fp64, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))
     if world > 1:

@@ -39,7 +39,10 @@ extern "C" {
 #define ESDG_ENONFINITE   -5  /* the device found a non-finite value */
 #define ESDG_ESTATE       -6  /* call out of order (e.g. no device memory attached) */
 #define ESDG_ETIMEOUT     -7  /* a bounded device-side wait (on an asynchronous copy) expired;
-                                 the kernel stopped early and the state is not valid */
+                                 the kernel stopped early and the state is not valid;
+                                 or a host-side wait (esdg_server_drain) ran out */
+#define ESDG_EBUSY        -8  /* admission refused: the request's device footprint exceeds
+                                 the server's whole HBM budget */
 
 /* arithmetic of the right-hand side; state and RK accumulation are always FP64 */
 #define ESDG_FP64 0
@@ -95,6 +98,9 @@ typedef struct esdg_ctx esdg_ctx;
  */
 int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out);
 
+/* The configuration the context was built with. */
+int esdg_get_config(const esdg_ctx* ctx, esdg_config* out);
+
 /* Sizes: K elements, Np modes, Nq volume and Nfq face quadrature points, and
  * the device bytes that esdg_attach_device() needs.  Any pointer may be NULL. */
 int esdg_sizes(const esdg_ctx* ctx, int* K, int* Np, int* Nq, int* Nfq, size_t* device_bytes);
@@ -121,6 +127,13 @@ int esdg_get_points(const esdg_ctx* ctx, int kind, double* x, double* y);
  * is exact.  Resets the RK residual.
  */
 int esdg_init_state(esdg_ctx* ctx, const double* b_nodal, const double* q_volq, int mode);
+
+/* esdg_prepare -- the host work of esdg_init_state done before any device
+ * memory exists: builds, in host memory, the complete image of operators,
+ * geometry, bathymetry and projected initial state, so that the next
+ * esdg_attach_device is one host-to-device copy.  Arguments as for
+ * esdg_init_state.  Call between esdg_build_operators and esdg_attach_device. */
+int esdg_prepare(esdg_ctx* ctx, const double* b_nodal, const double* q_volq, int mode);
 
 /* Bathymetry alone (b_nodal as above); keeps the state. */
 int esdg_set_bathymetry(esdg_ctx* ctx, const double* b_nodal);
@@ -219,6 +232,36 @@ int esdg_ensemble_destroy(esdg_ensemble* ens);
 
 /* Message for the last failing call on ens (NULL: the last failing create). */
 const char* esdg_ensemble_error(const esdg_ensemble* ens);
+
+/*
+ * Served form: a continuous-batching request loop on a worker thread.
+ * A request is a context built with esdg_build_operators (not attached) plus
+ * its host initial data (as for esdg_init_state) and a step count.  Requests
+ * wait in a FIFO queue and are admitted when their device footprint
+ * (esdg_sizes) fits the budget next to the active ones; device memory comes
+ * from the stream-ordered allocator (cudaMallocAsync/cudaFreeAsync).  Each
+ * iteration advances every active request by the smallest number of steps any
+ * of them still needs (at most 20): FP32 requests together in one ensemble
+ * launch per RK stage, FP64 requests through their own stage kernels.  A
+ * finished request's state is copied to result_host ([3][K][Np] FP64) and its
+ * device memory returned before queued requests are admitted.
+ * Ownership of ctx passes to the server on a successful submit (it is
+ * destroyed when the request finishes); b_nodal and q_volq are copied;
+ * result_host must stay valid until the request is done.  FP32 requests
+ * with a forcing term are refused (ESDG_EINVAL); requests larger than the whole
+ * budget are refused (ESDG_EBUSY).  Times are seconds since esdg_server_create.
+ */
+typedef struct esdg_server esdg_server;
+int esdg_server_create(size_t hbm_budget_bytes, int max_active, void* stream, esdg_server** out);
+int esdg_server_submit(esdg_server* srv, esdg_ctx* ctx, const double* b_nodal, const double* q_volq, int mode,
+                       int nsteps, double* result_host, int* ticket);
+/* state: 0 queued, 1 running, 2 done, < 0 failed with that status code. */
+int esdg_server_query(esdg_server* srv, int ticket, int* state, double* t_submit, double* t_admit, double* t_done);
+/* Wait until no request is queued or running (ESDG_ETIMEOUT after timeout_s). */
+int esdg_server_drain(esdg_server* srv, double timeout_s);
+int esdg_server_stats(esdg_server* srv, long long* iterations, long long* steps, size_t* bytes_in_use);
+/* Drops queued requests, waits for running ones, releases everything. */
+int esdg_server_destroy(esdg_server* srv);
 
 /* The CFL time step of Sec. 4 for this configuration. */
 int esdg_dt(const esdg_ctx* ctx, double* dt);

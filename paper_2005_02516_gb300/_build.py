@@ -25,7 +25,7 @@ def nvcc():
 
 def _sources():
     cu = ["esdg_api.cu", "esdg_ensemble.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
-    return cu, ["host_build.cpp"]
+    return cu, ["host_build.cpp", "esdg_server.cpp"]
 
 
 def _run(cmd):
@@ -46,7 +46,7 @@ def build(verbose=False, extra_nvcc=()):
                      "-Xcompiler", "-fPIC", *ARCH, *inc, *extra_nvcc])
     for f in cpp:
         obj = os.path.join(BUILD, f + ".o")
-        jobs.append([nvcc(), "-c", os.path.join(CSRC, f), "-o", obj, "-O2", "-std=c++17",
+        jobs.append([nvcc(), "-x", "c++", "-c", os.path.join(CSRC, f), "-o", obj, "-O2", "-std=c++17",
                      "-Xcompiler", "-fPIC", *inc])
     with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))

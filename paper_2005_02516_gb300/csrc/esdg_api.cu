@@ -57,6 +57,8 @@ struct esdg_ctx {
     RefOps ref;
     MeshData mesh;
     std::vector<double> b_modal;  // [K][Np]
+    std::vector<unsigned char> image;  // host image of the device layout up to the end of u
+    bool prepared = false;             // image holds bathymetry and initial state (esdg_prepare)
     std::string err;
     // device
     bool attached = false;
@@ -229,59 +231,116 @@ static std::vector<float> pack_ops2(const RefOps& R) {
     }
 }
 
+// ---- host image of the device layout ------------------------------------------
+// Everything up to the end of the state u is built in host memory (operators,
+// geometry, bathymetry, initial state) and reaches the device in one copy.
+template <typename T>
+static void put(std::vector<unsigned char>& img, size_t off, const std::vector<T>& v) {
+    std::memcpy(img.data() + off, v.data(), v.size() * sizeof(T));
+}
+
 template <typename real>
-static int upload_static(esdg_ctx* c) {
+static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     const RefOps& R = c->ref;
     const MeshData& M = c->mesh;
     const size_t K = size_t(M.K);
-    unsigned char* d = c->dbuf;
-    cudaStream_t s = c->stream;
-    std::vector<real> ops = pack_ops<real>(R);
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.ops, ops.data(), ops.size() * sizeof(real), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.vq64, R.Vq.a.data(), R.Vq.a.size() * 8, cudaMemcpyHostToDevice, s));
+    put(img, c->L.ops, pack_ops<real>(R));
+    put(img, c->L.vq64, R.Vq.a);
     // the FP32 batched kernel reads the metrics pre-scaled by 1/8 (exact)
     const double gscale = c->cfg.precision == ESDG_FP32 ? 0.125 : 1.0;
     std::vector<real> geo(M.geo.size());
     for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.geo, geo.data(), geo.size() * sizeof(real), cudaMemcpyHostToDevice, s));
-    if (c->cfg.precision == ESDG_FP32) {
-        std::vector<float> o2 = pack_ops2(R);
-        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.ops2, o2.data(), o2.size() * 4, cudaMemcpyHostToDevice, s));
-    }
+    put(img, c->L.geo, geo);
+    if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R));
     std::vector<double> wJ64(K * R.Nq);
     for (size_t e = 0; e < K; ++e)
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
-    std::vector<real> wJ = to_real<real>(wJ64);
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq, wJ.data(), wJ.size() * sizeof(real), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.wJq64, wJ64.data(), wJ64.size() * 8, cudaMemcpyHostToDevice, s));
+    put(img, c->L.wJq, to_real<real>(wJ64));
+    put(img, c->L.wJq64, wJ64);
     const int NpP = R.Np * (R.Np + 1) / 2;
     std::vector<real> mi(K * size_t(c->mstride), (real)0);
     for (size_t e = 0; e < K; ++e)
         for (int i = 0; i < NpP; ++i) mi[e * c->mstride + i] = (real)M.minv[e * NpP + i];
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.minv, mi.data(), mi.size() * sizeof(real), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(c, cudaMemcpyAsync(d + c->L.nbr, M.nbr.data(), M.nbr.size() * 4, cudaMemcpyHostToDevice, s));
+    put(img, c->L.minv, mi);
+    put(img, c->L.nbr, M.nbr);
     if (c->cfg.forcing != ESDG_FORCING_NONE) {
-        std::vector<real> xq = to_real<real>(M.xq), yq = to_real<real>(M.yq);
-        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.xq, xq.data(), xq.size() * sizeof(real), cudaMemcpyHostToDevice, s));
-        CUDA_TRY(c, cudaMemcpyAsync(d + c->L.yq, yq.data(), yq.size() * sizeof(real), cudaMemcpyHostToDevice, s));
+        put(img, c->L.xq, to_real<real>(M.xq));
+        put(img, c->L.yq, to_real<real>(M.yq));
     }
-    CUDA_TRY(c, cudaStreamSynchronize(s));
-    return ESDG_OK;
 }
 
+// b at the hybrid nodes (real) and at the volume nodes (FP64) from b_modal.
 template <typename real>
-static int upload_bathymetry_t(esdg_ctx* c) {
+static void bathymetry_arrays(const esdg_ctx* c, std::vector<real>& bhr, std::vector<double>& bq) {
     const RefOps& R = c->ref;
     const size_t K = size_t(c->mesh.K);
-    std::vector<double> bh(K * R.Nh), bq(K * R.Nq);
+    bhr.assign(K * R.Nh, (real)0);
+    bq.assign(K * R.Nq, 0.0);
     for (size_t e = 0; e < K; ++e)
         for (int l = 0; l < R.Nh; ++l) {
             double s = 0;
             for (int n = 0; n < R.Np; ++n) s += R.Vh(l, n) * c->b_modal[e * R.Np + n];
-            bh[e * R.Nh + l] = s;
+            bhr[e * R.Nh + l] = (real)s;
             if (l < R.Nq) bq[e * R.Nq + l] = s;
         }
-    std::vector<real> bhr = to_real<real>(bh);
+}
+
+// J-weighted L2 projection of q (at volume points) onto the modes; SURFACE
+// mode takes q[0] = H and subtracts the modal bathymetry.
+static void project_host(const esdg_ctx* c, const double* q_volq, int mode, double* u) {
+    const RefOps& R = c->ref;
+    const MeshData& M = c->mesh;
+    const size_t K = size_t(M.K);
+    const int NpP = R.Np * (R.Np + 1) / 2;
+    std::vector<double> y(R.Np);
+    for (int f = 0; f < 3; ++f)
+        for (size_t e = 0; e < K; ++e) {
+            for (int n = 0; n < R.Np; ++n) {
+                double s = 0;
+                for (int q = 0; q < R.Nq; ++q)
+                    s += R.Vq(q, n) * R.wq[q] * M.Jq[e * R.Nq + q] * q_volq[(f * K + e) * R.Nq + q];
+                y[n] = s;
+            }
+            const double* mi = &M.minv[e * NpP];
+            for (int n = 0; n < R.Np; ++n) {
+                double s = 0;
+                for (int j = 0; j < R.Np; ++j) s += mi[n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n] * y[j];
+                if (f == 0 && mode == ESDG_INIT_SURFACE) s -= c->b_modal[e * R.Np + n];
+                u[(f * K + e) * R.Np + n] = s;
+            }
+        }
+}
+
+static void modal_bathymetry(esdg_ctx* c, const double* b_nodal) {
+    const RefOps& R = c->ref;
+    const size_t K = size_t(c->mesh.K);
+    for (size_t e = 0; e < K; ++e)
+        for (int n = 0; n < R.Np; ++n) {
+            double s = 0;
+            for (int m = 0; m < R.Np; ++m) s += R.Veq_inv(n, m) * b_nodal[e * R.Np + m];
+            c->b_modal[e * R.Np + n] = s;
+        }
+}
+
+// Host image of [0, end of u): operators, geometry, bathymetry and (if q is
+// given) the projected initial state.
+template <typename real>
+static void build_image(esdg_ctx* c, const double* q_volq, int mode) {
+    c->image.assign(c->L.res, 0);
+    fill_static<real>(c, c->image);
+    std::vector<real> bhr;
+    std::vector<double> bq;
+    bathymetry_arrays<real>(c, bhr, bq);
+    put(c->image, c->L.bh, bhr);
+    put(c->image, c->L.bq64, bq);
+    if (q_volq) project_host(c, q_volq, mode, reinterpret_cast<double*>(c->image.data() + c->L.u));
+}
+
+template <typename real>
+static int upload_bathymetry_t(esdg_ctx* c) {
+    std::vector<real> bhr;
+    std::vector<double> bq;
+    bathymetry_arrays<real>(c, bhr, bq);
     CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.bh, bhr.data(), bhr.size() * sizeof(real), cudaMemcpyHostToDevice,
                                 c->stream));
     CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.bq64, bq.data(), bq.size() * 8, cudaMemcpyHostToDevice, c->stream));
@@ -493,6 +552,12 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
     return ESDG_OK;
 }
 
+int esdg_get_config(const esdg_ctx* c, esdg_config* out) {
+    if (!valid(c) || !out) return fail(nullptr, ESDG_EINVAL, "null argument");
+    *out = c->cfg;
+    return ESDG_OK;
+}
+
 int esdg_sizes(const esdg_ctx* c, int* K, int* Np, int* Nq, int* Nfq, size_t* device_bytes) {
     if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
     if (K) *K = c->mesh.K;
@@ -522,16 +587,34 @@ int esdg_attach_device(esdg_ctx* c, void* buffer, size_t bytes, void* stream) {
     int dev = 0;
     CUDA_TRY(c, cudaGetDevice(&dev));
     CUDA_TRY(c, cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    CUDA_TRY(c, cudaMemsetAsync(c->dbuf, 0, c->L.total, c->stream));
-    int rc;
     CUDA_TRY(c, d_geometry(c));
-    if (c->cfg.precision == ESDG_FP32)
-        rc = upload_static<float>(c);
-    else
-        rc = upload_static<double>(c);
-    if (rc) return rc;
+    if (!c->prepared) {
+        if (c->cfg.precision == ESDG_FP32)
+            build_image<float>(c, nullptr, 0);
+        else
+            build_image<double>(c, nullptr, 0);
+    }
+    CUDA_TRY(c, cudaMemcpyAsync(c->dbuf, c->image.data(), c->L.res, cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(c, cudaMemsetAsync(c->dbuf + c->L.res, 0, c->L.total - c->L.res, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<unsigned char>().swap(c->image);
+    c->prepared = false;
+    c->ut_valid = false;
     c->attached = true;
-    return upload_bathymetry(c);
+    return ESDG_OK;
+}
+
+int esdg_prepare(esdg_ctx* c, const double* b_nodal, const double* q_volq, int mode) {
+    if (!valid(c) || !q_volq) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (c->attached) return fail(c, ESDG_ESTATE, "esdg_prepare comes before esdg_attach_device");
+    if (mode != ESDG_INIT_DEPTH && mode != ESDG_INIT_SURFACE) return fail(c, ESDG_EINVAL, "unknown init mode");
+    if (b_nodal) modal_bathymetry(c, b_nodal);
+    if (c->cfg.precision == ESDG_FP32)
+        build_image<float>(c, q_volq, mode);
+    else
+        build_image<double>(c, q_volq, mode);
+    c->prepared = true;
+    return ESDG_OK;
 }
 
 int esdg_get_points(const esdg_ctx* c, int kind, double* x, double* y) {
@@ -550,14 +633,7 @@ int esdg_get_points(const esdg_ctx* c, int kind, double* x, double* y) {
 int esdg_set_bathymetry(esdg_ctx* c, const double* b_nodal) {
     if (!valid(c) || !b_nodal) return fail(nullptr, ESDG_EINVAL, "null argument");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    const RefOps& R = c->ref;
-    const size_t K = size_t(c->mesh.K);
-    for (size_t e = 0; e < K; ++e)
-        for (int n = 0; n < R.Np; ++n) {
-            double s = 0;
-            for (int m = 0; m < R.Np; ++m) s += R.Veq_inv(n, m) * b_nodal[e * R.Np + m];
-            c->b_modal[e * R.Np + n] = s;
-        }
+    modal_bathymetry(c, b_nodal);
     return upload_bathymetry(c);
 }
 
@@ -569,27 +645,8 @@ int esdg_init_state(esdg_ctx* c, const double* b_nodal, const double* q_volq, in
         if (rc) return rc;
     }
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    const RefOps& R = c->ref;
-    const MeshData& M = c->mesh;
-    const size_t K = size_t(M.K);
-    const int NpP = R.Np * (R.Np + 1) / 2;
-    std::vector<double> u(3 * K * R.Np), y(R.Np);
-    for (int f = 0; f < 3; ++f)
-        for (size_t e = 0; e < K; ++e) {
-            for (int n = 0; n < R.Np; ++n) {
-                double s = 0;
-                for (int q = 0; q < R.Nq; ++q)
-                    s += R.Vq(q, n) * R.wq[q] * M.Jq[e * R.Nq + q] * q_volq[(f * K + e) * R.Nq + q];
-                y[n] = s;
-            }
-            const double* mi = &M.minv[e * NpP];
-            for (int n = 0; n < R.Np; ++n) {
-                double s = 0;
-                for (int j = 0; j < R.Np; ++j) s += mi[n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n] * y[j];
-                if (f == 0 && mode == ESDG_INIT_SURFACE) s -= c->b_modal[e * R.Np + n];
-                u[(f * K + e) * R.Np + n] = s;
-            }
-        }
+    std::vector<double> u(3 * size_t(c->mesh.K) * c->ref.Np);
+    project_host(c, q_volq, mode, u.data());
     return esdg_set_state(c, u.data(), 0);
 }
 

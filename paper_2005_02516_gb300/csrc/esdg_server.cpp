@@ -1,0 +1,311 @@
+// Continuous-batching request loop for ESDG solves (the library's served form).
+//
+// A worker thread owns the GPU work.  Requests arrive as built (not yet
+// attached) contexts with host initial data; they wait in a FIFO queue and are
+// admitted when their device footprint fits the HBM budget.  Every iteration
+// advances all active requests together -- the FP32 ones in one ensemble
+// launch per RK stage, the FP64 ones through their own stage kernels -- by the
+// smallest number of steps any of them still needs (at most kMaxChunk), so
+// every request runs exactly its own step count.  Finished requests are
+// retired between iterations (state copied to the caller's host buffer,
+// device memory returned), which lets queued requests in.  All host work of a
+// request (esdg_prepare) runs in the submitting thread, so admission is one
+// host-to-device copy.  Built only on the public C ABI of esdg.h.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "esdg.h"
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+constexpr int kMaxChunk = 20;  // steps per iteration at most
+
+struct Request {
+    int ticket = 0;
+    esdg_ctx* ctx = nullptr;
+    int precision = ESDG_FP32;
+    int nsteps = 0, remaining = 0;
+    double* result = nullptr;  // caller's host buffer [3][K][Np]
+    size_t bytes = 0;
+    void* dmem = nullptr;
+    int state = 0;  // 0 queued, 1 active, 2 done, < 0 failed (status code)
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    std::string err;
+};
+
+}  // namespace
+
+struct esdg_server {
+    size_t budget = 0, in_use = 0;
+    int max_active = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Clock::time_point t0;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<Request*> queue;
+    std::vector<Request*> active;
+    std::map<int, Request*> all;
+    int next_ticket = 1;
+    int admitting = 0;  // popped from the queue, not yet running (lock released)
+    bool stop = false;
+    std::thread worker;
+    esdg_ensemble* ens = nullptr;
+    std::vector<Request*> ens_members;
+    long long iterations = 0, steps_run = 0;
+    std::string err;
+};
+
+static double now_s(const esdg_server* s) {
+    return std::chrono::duration<double>(Clock::now() - s->t0).count();
+}
+
+static void finish(esdg_server* s, Request* r, int state, const std::string& why) {
+    if (r->ctx) {
+        esdg_destroy(r->ctx);
+        r->ctx = nullptr;
+    }
+    if (r->dmem) {
+        cudaFreeAsync(r->dmem, s->stream);
+        r->dmem = nullptr;
+        s->in_use -= r->bytes;
+    }
+    r->state = state;
+    r->err = why;
+    r->t_done = now_s(s);
+}
+
+// Admit queued requests in FIFO order while their footprint fits.
+static void admit(esdg_server* s, std::unique_lock<std::mutex>& lk) {
+    while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
+        Request* r = s->queue.front();
+        if (s->in_use + r->bytes > s->budget) break;
+        s->queue.pop_front();
+        s->in_use += r->bytes;
+        s->admitting += 1;
+        lk.unlock();
+        int rc = ESDG_OK;
+        std::string why;
+        cudaError_t ce = cudaMallocAsync(&r->dmem, r->bytes + 256, s->stream);
+        if (ce != cudaSuccess) {
+            rc = ESDG_ENOMEM;
+            why = std::string("cudaMallocAsync: ") + cudaGetErrorString(ce);
+            r->dmem = nullptr;
+        }
+        if (!rc) {
+            char* p = static_cast<char*>(r->dmem);
+            p += (256 - (reinterpret_cast<uintptr_t>(p) & 255)) & 255;
+            rc = esdg_attach_device(r->ctx, p, r->bytes, s->stream);  // one copy of the prepared image
+            if (rc) why = esdg_last_error(r->ctx);
+        }
+        lk.lock();
+        s->admitting -= 1;
+        if (rc) {
+            finish(s, r, rc, why);
+            s->cv.notify_all();
+            continue;
+        }
+        r->state = 1;
+        r->t_admit = now_s(s);
+        s->active.push_back(r);
+    }
+}
+
+// Rebuild the FP32 ensemble when the set of active FP32 requests changed.
+static int refresh_ensemble(esdg_server* s) {
+    std::vector<Request*> fp32;
+    for (Request* r : s->active)
+        if (r->precision == ESDG_FP32) fp32.push_back(r);
+    if (fp32 == s->ens_members && (s->ens || fp32.empty())) return ESDG_OK;
+    if (s->ens) {
+        esdg_ensemble_destroy(s->ens);
+        s->ens = nullptr;
+    }
+    s->ens_members = fp32;
+    if (fp32.empty()) return ESDG_OK;
+    std::vector<esdg_ctx*> ctxs;
+    for (Request* r : fp32) ctxs.push_back(r->ctx);
+    int rc = esdg_ensemble_create(ctxs.data(), int(ctxs.size()), &s->ens);
+    if (rc) s->err = esdg_ensemble_error(nullptr);
+    return rc;
+}
+
+static void run(esdg_server* s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        admit(s, lk);
+        if (s->active.empty()) {
+            if (s->stop) break;
+            s->cv.wait_for(lk, std::chrono::milliseconds(2));
+            continue;
+        }
+        int chunk = kMaxChunk;
+        for (Request* r : s->active) chunk = std::min(chunk, r->remaining);
+        std::vector<Request*> act = s->active;
+        lk.unlock();
+        int rc = refresh_ensemble(s);
+        if (!rc && s->ens) rc = esdg_ensemble_step_async(s->ens, chunk);
+        for (Request* r : act)
+            if (!rc && r->precision == ESDG_FP64) rc = esdg_step_async(r->ctx, chunk, 0.0, 0.0);
+        cudaStreamSynchronize(s->stream);
+        std::vector<std::pair<Request*, int>> outcome;
+        for (Request* r : act) {
+            int st = rc ? rc : esdg_check(r->ctx);
+            outcome.emplace_back(r, st);
+        }
+        std::vector<Request*> done;
+        for (auto& o : outcome) {
+            Request* r = o.first;
+            if (o.second) continue;
+            r->remaining -= chunk;
+            if (r->remaining == 0) {
+                int st = esdg_copy_state(r->ctx, r->result, 0);
+                o.second = st;
+                done.push_back(r);
+            }
+        }
+        lk.lock();
+        s->iterations += 1;
+        s->steps_run += chunk;
+        std::vector<Request*> keep;
+        for (auto& o : outcome) {
+            Request* r = o.first;
+            if (o.second) {
+                finish(s, r, o.second, r->ctx ? esdg_last_error(r->ctx) : "failed");
+            } else if (r->remaining == 0) {
+                finish(s, r, 2, "");
+            } else {
+                keep.push_back(r);
+            }
+        }
+        s->active = keep;
+        s->cv.notify_all();
+    }
+    if (s->ens) {
+        esdg_ensemble_destroy(s->ens);
+        s->ens = nullptr;
+    }
+}
+
+extern "C" {
+
+int esdg_server_create(size_t hbm_budget_bytes, int max_active, void* stream, esdg_server** out) {
+    if (!out || hbm_budget_bytes == 0 || max_active < 1) return ESDG_EINVAL;
+    esdg_server* s = new (std::nothrow) esdg_server();
+    if (!s) return ESDG_ENOMEM;
+    s->budget = hbm_budget_bytes;
+    s->max_active = max_active;
+    s->stream = reinterpret_cast<cudaStream_t>(stream);
+    s->t0 = Clock::now();
+    if (cudaGetDevice(&s->device) != cudaSuccess) {
+        delete s;
+        return ESDG_ECUDA;
+    }
+    s->worker = std::thread(run, s);
+    *out = s;
+    return ESDG_OK;
+}
+
+int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, const double* q_volq, int mode,
+                       int nsteps, double* result_host, int* ticket) {
+    if (!s || !ctx || !b_nodal || !q_volq || !result_host || !ticket || nsteps < 1) return ESDG_EINVAL;
+    size_t bytes = 0;
+    int rc = esdg_sizes(ctx, nullptr, nullptr, nullptr, nullptr, &bytes);
+    if (rc) return rc;
+    Request* r = new (std::nothrow) Request();
+    if (!r) return ESDG_ENOMEM;
+    r->ctx = ctx;
+    r->nsteps = r->remaining = nsteps;
+    r->result = result_host;
+    r->bytes = (bytes + 255) & ~size_t(255);
+    esdg_config cfg;
+    rc = esdg_get_config(ctx, &cfg);
+    if (rc || (cfg.precision == ESDG_FP32 && cfg.forcing != ESDG_FORCING_NONE)) {
+        delete r;
+        return rc ? rc : ESDG_EINVAL;
+    }
+    r->precision = cfg.precision;
+    // all host work of the request (bathymetry, initial projection, operator
+    // and geometry packing) runs here, in the submitting thread
+    rc = esdg_prepare(ctx, b_nodal, q_volq, mode);
+    if (rc) {
+        delete r;
+        return rc;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (r->bytes + 256 > s->budget) {
+        delete r;
+        return ESDG_EBUSY;
+    }
+    r->ticket = s->next_ticket++;
+    r->t_submit = now_s(s);
+    s->all[r->ticket] = r;
+    s->queue.push_back(r);
+    *ticket = r->ticket;
+    s->cv.notify_all();
+    return ESDG_OK;
+}
+
+int esdg_server_query(esdg_server* s, int ticket, int* state, double* t_submit, double* t_admit, double* t_done) {
+    if (!s) return ESDG_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->all.find(ticket);
+    if (it == s->all.end()) return ESDG_EINVAL;
+    Request* r = it->second;
+    if (state) *state = r->state;
+    if (t_submit) *t_submit = r->t_submit;
+    if (t_admit) *t_admit = r->t_admit;
+    if (t_done) *t_done = r->t_done;
+    return ESDG_OK;
+}
+
+int esdg_server_drain(esdg_server* s, double timeout_s) {
+    if (!s) return ESDG_EINVAL;
+    std::unique_lock<std::mutex> lk(s->mu);
+    const auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s);
+    while (!s->queue.empty() || !s->active.empty() || s->admitting > 0) {
+        if (s->cv.wait_until(lk, deadline) == std::cv_status::timeout) return ESDG_ETIMEOUT;
+    }
+    return ESDG_OK;
+}
+
+int esdg_server_stats(esdg_server* s, long long* iterations, long long* steps, size_t* bytes_in_use) {
+    if (!s) return ESDG_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (iterations) *iterations = s->iterations;
+    if (steps) *steps = s->steps_run;
+    if (bytes_in_use) *bytes_in_use = s->in_use;
+    return ESDG_OK;
+}
+
+int esdg_server_destroy(esdg_server* s) {
+    if (!s) return ESDG_OK;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        // queued requests are dropped
+        for (Request* r : s->queue) finish(s, r, ESDG_ESTATE, "server destroyed");
+        s->queue.clear();
+        s->cv.notify_all();
+    }
+    if (s->worker.joinable()) s->worker.join();
+    cudaStreamSynchronize(s->stream);
+    for (auto& kv : s->all) delete kv.second;
+    delete s;
+    return ESDG_OK;
+}
+
+}  // extern "C"

@@ -22,6 +22,7 @@ ESDG_ENONPOSITIVE = -4
 ESDG_ENONFINITE = -5
 ESDG_ESTATE = -6
 ESDG_ETIMEOUT = -7
+ESDG_EBUSY = -8
 
 ESDG_FP64 = 0
 ESDG_FP32 = 1
@@ -40,7 +41,9 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_entropy_noalloc", "esdg_dt",
            "esdg_destroy", "esdg_last_error",
            "esdg_ensemble_create", "esdg_ensemble_autotune", "esdg_ensemble_step",
-           "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error"]
+           "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
+           "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
+           "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy"]
 
 
 class EsdgError(RuntimeError):
@@ -99,6 +102,14 @@ def load_library(path=LIB_PATH):
         "esdg_ensemble_step_async": ([P, I], I),
         "esdg_ensemble_destroy": ([P], I),
         "esdg_ensemble_error": ([P], ctypes.c_char_p),
+        "esdg_get_config": ([P, ctypes.POINTER(Config)], I),
+        "esdg_prepare": ([P, P, P, I], I),
+        "esdg_server_create": ([S, I, P, ctypes.POINTER(P)], I),
+        "esdg_server_submit": ([P, P, P, P, I, I, P, PI], I),
+        "esdg_server_query": ([P, I, PI, PD, PD, PD], I),
+        "esdg_server_drain": ([P, D], I),
+        "esdg_server_stats": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PS], I),
+        "esdg_server_destroy": ([P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -117,6 +128,130 @@ def _ptr(a):
         return a.ctypes.data
     assert a.is_contiguous()
     return a.data_ptr()
+
+
+def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, warp=0.0, g=1.0, cfl=0.25,
+                lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5)):
+    cfg = Config()
+    cfg.N, cfg.nx, cfg.ny = N, nx, ny
+    cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
+    cfg.x0, cfg.x1, cfg.y0, cfg.y1 = x0, x1, y0, y1
+    cfg.warp_ax = cfg.warp_ay = warp
+    cfg.g, cfg.cfl = g, cfl
+    cfg.lax_friedrichs = 1 if lax_friedrichs else 0
+    cfg.forcing = ESDG_FORCING_MMS_SINE if forcing == "mms_sine" else ESDG_FORCING_NONE
+    cfg.mms_amp, cfg.mms_bamp, cfg.mms_u0, cfg.mms_v0 = mms
+    return cfg
+
+
+class Problem:
+    """A context built on the host (operators, mesh, geometry) and not yet
+    attached to device memory: what a request to the Server carries."""
+
+    def __init__(self, N, nx, ny, **kw):
+        self.lib = load_library()
+        self.cfg = make_config(N, nx, ny, **kw)
+        h = ctypes.c_void_p()
+        rc = self.lib.esdg_build_operators(ctypes.byref(self.cfg), ctypes.byref(h))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, self.lib.esdg_last_error(None).decode())
+        self.h = h
+        K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nbytes = ctypes.c_size_t()
+        self.lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq),
+                            ctypes.byref(nbytes))
+        self.K, self.Np, self.Nq, self.Nfq = K.value, Np.value, Nq.value, Nfq.value
+        self.device_bytes = nbytes.value
+
+    def points(self, kind):
+        n = {ESDG_POINTS_NODAL: self.Np, ESDG_POINTS_VOLQ: self.Nq, ESDG_POINTS_FACEQ: self.Nfq}[kind]
+        x = np.zeros((self.K, n))
+        y = np.zeros((self.K, n))
+        rc = self.lib.esdg_get_points(self.h, kind, _ptr(x), _ptr(y))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, self.lib.esdg_last_error(self.h).decode())
+        return x, y
+
+    def release(self):
+        """Hand the context over (the server owns it after a submit)."""
+        h, self.h = self.h, None
+        return h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.esdg_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop (worker thread inside the library)."""
+
+    def __init__(self, hbm_budget_bytes, max_active=256, stream=None):
+        import torch
+        self.lib = load_library()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        h = ctypes.c_void_p()
+        rc = self.lib.esdg_server_create(int(hbm_budget_bytes), max_active, stream.cuda_stream, ctypes.byref(h))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, "esdg_server_create failed")
+        self.h = h
+        self._results = {}
+
+    def submit(self, problem, b_nodal, q_volq, nsteps, surface=False):
+        """Submit a Problem (ownership passes to the server); returns a ticket."""
+        b = np.ascontiguousarray(b_nodal, dtype=np.float64)
+        q = np.ascontiguousarray(q_volq, dtype=np.float64)
+        out = np.zeros((3, problem.K, problem.Np))
+        t = ctypes.c_int()
+        rc = self.lib.esdg_server_submit(self.h, problem.h, _ptr(b), _ptr(q),
+                                         ESDG_INIT_SURFACE if surface else ESDG_INIT_DEPTH, nsteps, _ptr(out),
+                                         ctypes.byref(t))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, "esdg_server_submit refused the request")
+        problem.release()
+        self._results[t.value] = out
+        return t.value
+
+    def query(self, ticket):
+        st = ctypes.c_int()
+        a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        rc = self.lib.esdg_server_query(self.h, ticket, ctypes.byref(st), ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c))
+        if rc != ESDG_OK:
+            raise EsdgError(rc, "unknown ticket")
+        return st.value, a.value, b.value, c.value
+
+    def result(self, ticket):
+        return self._results[ticket]
+
+    def drain(self, timeout_s=600.0):
+        rc = self.lib.esdg_server_drain(self.h, timeout_s)
+        if rc != ESDG_OK:
+            raise EsdgError(rc, "esdg_server_drain timed out")
+
+    def stats(self):
+        it, st, b = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
+        self.lib.esdg_server_stats(self.h, ctypes.byref(it), ctypes.byref(st), ctypes.byref(b))
+        return it.value, st.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.esdg_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Solver:

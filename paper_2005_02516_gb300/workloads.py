@@ -173,6 +173,62 @@ def ensemble(n=64, steps=500, seed=BASE_SEED):
     return out
 
 
+@dataclasses.dataclass
+class Request:
+    """One served solve request: arrival time, degree, grid, steps, and a
+    smooth random bathymetry sum_j A_j exp(-alpha |x - c_j|^2) (4 Gaussians)
+    under a lake at rest H = 2 plus a bump 0.01 exp(-25 |x - c|^2)."""
+    t_arrival: float
+    N: int
+    nx: int
+    steps: int
+    amps: tuple
+    centres: tuple
+    bump: tuple
+    alpha: float = 10.0
+    warp: float = 0.05
+    g: float = 1.0
+    cfl: float = 0.25
+
+    @property
+    def K(self):
+        return 2 * self.nx * self.nx
+
+    @property
+    def Np(self):
+        return (self.N + 1) * (self.N + 2) // 2
+
+    def bathymetry(self, x, y):
+        b = 0 * x
+        for a, (cx, cy) in zip(self.amps, self.centres):
+            b = b + a * np.exp(-self.alpha * ((x - cx) ** 2 + (y - cy) ** 2))
+        return b
+
+    def initial(self, x, y):
+        r2 = (x - self.bump[0]) ** 2 + (y - self.bump[1]) ** 2
+        return np.stack([2.0 + 0.01 * np.exp(-25.0 * r2), 0 * x, 0 * x])
+
+
+def served_trace(n, rate, seed=BASE_SEED, k_range=(512, 131072), steps_range=(100, 2000), degrees=(2, 3, 4, 5)):
+    """Poisson arrivals at `rate` per second; N ~ U(degrees); K log-uniform in
+    k_range, rounded to the nearest 2 n^2; steps ~ U(steps_range); amplitudes
+    ~ U[0, 0.2], Gaussian centres ~ U[-0.8, 0.8]^2, bump centre ~ U[-0.5, 0.5]^2."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for _ in range(n):
+        t += rng.exponential(1.0 / rate)
+        N = int(rng.choice(degrees))
+        K = math.exp(rng.uniform(math.log(k_range[0]), math.log(k_range[1])))
+        nx = max(3, int(round(math.sqrt(K / 2.0))))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        amps = tuple(float(a) for a in rng.uniform(0.0, 0.2, size=4))
+        centres = tuple((float(c[0]), float(c[1])) for c in rng.uniform(-0.8, 0.8, size=(4, 2)))
+        bump = tuple(float(c) for c in rng.uniform(-0.5, 0.5, size=2))
+        out.append(Request(t_arrival=t, N=N, nx=nx, steps=steps, amps=amps, centres=centres, bump=bump))
+    return out
+
+
 def lake_at_rest_table_bathymetry(x, y):
     """Bathymetry of the lake-at-rest experiment of Sec. 4.1 as printed:
     b = 0.1 sin(2 pi x) cos(2 pi x) + 0.5 (periodic on [-1,1]^2)."""

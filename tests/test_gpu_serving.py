@@ -1,0 +1,112 @@
+"""Served form: the continuous-batching request loop (esdg_server_*).
+
+Requests of mixed degree, size, precision and step count arrive while others
+run; each finished state must equal the same problem run alone through the
+single-problem path: FP64 requests to relative 1e-12; FP32 requests to
+relative 1e-6 (the ensemble kernel that carries degree-5 members is a
+separate compilation of the same arithmetic, whose FP32 roundings may differ
+in a few operations; the FP32 accuracy target is 1e-5).  Admission must
+respect the HBM budget, and a request larger than the whole budget is refused.
+"""
+
+import time
+
+import numpy as np
+import pytest
+
+from paper_2005_02516_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import os
+    from paper_2005_02516_gb300 import esdg
+    if not os.path.exists(esdg.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+
+
+def _prepare(req, precision):
+    from paper_2005_02516_gb300 import esdg
+    p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+    xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
+    xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
+    return p, req.bathymetry(xb, yb), req.initial(xq, yq)
+
+
+def _alone(req, precision, b, q):
+    from paper_2005_02516_gb300 import esdg
+    s = esdg.Solver(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+    s.init_state(b, q, surface=True)
+    s.step(req.steps)
+    u = s.get_state()
+    s.close()
+    return u
+
+
+def test_served_results_equal_alone():
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(8, rate=50.0, seed=W.BASE_SEED + 5, k_range=(32, 800), steps_range=(3, 45))
+    precisions = ["fp32", "fp32", "fp64", "fp32", "fp64", "fp32", "fp32", "fp64"]
+    srv = esdg.Server(hbm_budget_bytes=4 << 30)
+    t0 = time.perf_counter()
+    tickets, inputs = [], []
+    for req, prec in zip(trace, precisions):
+        while time.perf_counter() - t0 < req.t_arrival:
+            time.sleep(0.001)
+        p, b, q = _prepare(req, prec)
+        tickets.append(srv.submit(p, b, q, req.steps, surface=True))
+        inputs.append((b, q))
+    srv.drain(300.0)
+    iters, steps, inuse = srv.stats()
+    assert inuse == 0 and iters > 0
+    for tk, req, prec, (b, q) in zip(tickets, trace, precisions, inputs):
+        state, ts, ta, td = srv.query(tk)
+        assert state == 2 and ts <= ta <= td
+        want = _alone(req, prec, b, q)
+        got = srv.result(tk)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
+    srv.close()
+
+
+def test_admission_respects_the_budget():
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(5, rate=1000.0, seed=W.BASE_SEED + 6, k_range=(200, 200), steps_range=(30, 30),
+                           degrees=(3,))
+    probe, _, _ = _prepare(trace[0], "fp32")
+    per = probe.device_bytes + 512
+    probe.close()
+    srv = esdg.Server(hbm_budget_bytes=2 * per + per // 2)   # room for two at a time
+    tickets = []
+    for req in trace:
+        p, b, q = _prepare(req, "fp32")
+        tickets.append(srv.submit(p, b, q, req.steps, surface=True))
+    srv.drain(300.0)
+    spans = []
+    for tk in tickets:
+        state, ts, ta, td = srv.query(tk)
+        assert state == 2
+        spans.append((ta, td))
+    for ta, _ in spans:   # never more than two running at once
+        running = sum(1 for a, d in spans if a <= ta < d)
+        assert running <= 2
+    srv.close()
+
+
+def test_request_larger_than_budget_is_refused():
+    from paper_2005_02516_gb300 import esdg
+    req = W.served_trace(1, rate=1.0, seed=1, k_range=(800, 800), steps_range=(5, 5), degrees=(4,))[0]
+    srv = esdg.Server(hbm_budget_bytes=1 << 20)
+    p, b, q = _prepare(req, "fp32")
+    with pytest.raises(esdg.EsdgError) as ei:
+        srv.submit(p, b, q, req.steps, surface=True)
+    assert ei.value.code == esdg.ESDG_EBUSY
+    p.close()
+    srv.close()

@@ -1,0 +1,48 @@
+"""The multi-rank plumbing of bench.py on CPU ranks (gloo, world size 2):
+replicas join a barrier, agree on the maximum of their timings, and the
+whole-job value counts every rank's units over the slowest rank's time."""
+
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update({"RANK": str(rank), "LOCAL_RANK": str(rank), "WORLD_SIZE": str(world),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    import bench
+    import torch.distributed as dist
+    w, r, local = bench.dist_init("gloo")
+    assert (w, r, local) == (world, rank, rank)
+    bench.barrier(w)
+    t = bench.max_over_ranks(1.0 + rank, w, device="cpu")
+    out.put((rank, t, bench.replica_value(1e9, w, t)))
+    bench.barrier(w)
+    dist.destroy_process_group()
+
+
+def test_two_replica_ranks_agree_on_max_time():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    assert [r for r, _, _ in res] == [0, 1]
+    for _, t, v in res:
+        assert t == 2.0              # the slowest rank's time
+        assert abs(v - 1.0) < 1e-12  # 2 ranks x 1e9 units / 2 s / 1e9

@@ -83,8 +83,8 @@ class Oracle:
     """
 
     def __init__(self, N, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0,
-                 g=1.0, cfl=0.25, lf=True, forcing=None):
-        self.ref = RefElem(N)
+                 g=1.0, cfl=0.25, lf=True, forcing=None, rule="collapsed"):
+        self.ref = RefElem(N, rule)
         self.mesh = Mesh(self.ref, nx, ny, x0, x1, y0, y1, ax, ay)
         self.N, self.K = N, self.mesh.K
         self.g, self.cfl, self.lf = g, cfl, lf

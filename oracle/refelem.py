@@ -8,9 +8,13 @@ Readings (the paper leaves these open, Sec. 2.1):
   * basis: the orthonormal Dubiner (Koornwinder) basis, built from Jacobi
     polynomials through the collapsed map a = 2(1+r)/(1-s) - 1, b = s.
     Mode order: for i = 0..N, for j = 0..N-i.
-  * volume quadrature: the collapsed (Stroud conical) product rule with N+1
-    Gauss-Legendre points in a and N+1 Gauss-Jacobi(1,0) points in b,
-    exact to degree 2N+1 (the paper asks for at least 2N-1).
+  * volume quadrature (the paper asks only for positive weights and
+    exactness to degree 2N-1; 2N keeps the mass matrix exact), two choices:
+    rule="collapsed": the collapsed (Stroud conical) product rule with N+1
+    Gauss-Legendre points in a and N+1 Gauss-Jacobi(1,0) points in b, exact to
+    degree 2N+1, (N+1)^2 points; rule="symmetric": fully symmetric positive
+    interior rules exact to degree 2N (3, 6, 12, 16, 25 points for N = 1..5),
+    computed below from the moment equations.
   * surface quadrature: N+1 Gauss-Legendre points on each face (exact to
     degree 2N+1 on faces; the paper asks for at least 2N).
   * faces: f1 v1->v2 (s=-1), f2 v2->v3 (r+s=0), f3 v3->v1 (r=-1) with
@@ -176,13 +180,19 @@ class RefElem:
     (rq2, sq2, wq2, Vq2) exact to degree 2N+3 (>= 2N+2, Sec. 4.1).
     """
 
-    def __init__(self, N):
+    def __init__(self, N, rule="collapsed"):
         if N < 1:
             raise ValueError("N >= 1")
         self.N = N
+        self.rule = rule
         self.Np = num_modes(N)
         # volume and surface quadrature (Sec. 2.1)
-        self.rq, self.sq, self.w = triangle_quadrature(N + 1)
+        if rule == "collapsed":
+            self.rq, self.sq, self.w = triangle_quadrature(N + 1)
+        elif rule == "symmetric":
+            self.rq, self.sq, self.w = symmetric_quadrature(N)
+        else:
+            raise ValueError(rule)
         self.rf, self.sf, self.wf, self.nr, self.ns = face_quadrature(N)
         self.Nq = self.rq.size
         self.Nfq = self.rf.size
@@ -228,3 +238,145 @@ class RefElem:
         """Q_h = 1/2 [[Q - Q^T, E^T B], [-B E, B]] (Sec. 2.3)."""
         E = self.E
         return 0.5 * np.block([[Q - Q.T, E.T @ B], [-B @ E, B]])
+
+
+# ---------------------------------------------------------------------------
+# Fully symmetric quadrature rules exact to degree 2N (Sec. 2.1 allows any
+# rule with positive weights exact to at least 2N-1; 2N keeps M exact)
+# ---------------------------------------------------------------------------
+# Orbits of the symmetry group of the triangle in barycentric coordinates:
+# S3 = centroid (1 point), S21(a) = (a, a, 1-2a) and permutations (3 points),
+# S111(a, b) = (a, b, 1-a-b) and permutations (6 points).  The orbit
+# structure per degree: 2: one S21 (3 points); 4: two S21 (6); 6: two S21 +
+# one S111 (12); 8: S3 + three S21 + one S111 (16); 10: S3 + two S21 + three
+# S111 (25).  The rule is the positive, interior solution of the moment
+# equations sum_i w_i phi_k(x_i) = int phi_k for all basis functions of
+# degree <= 2N, found by Levenberg-Marquardt from seeded starting points.
+SYM_STRUCT = {2: (0, 1, 0), 4: (0, 2, 0), 6: (0, 2, 1), 8: (1, 3, 1), 10: (1, 2, 3)}
+
+
+def _sym_points(theta, st):
+    """Barycentric points, weights and d(r,s)/d(theta) of an orbit set."""
+    n3, n21, n111 = st
+    lam, w, dl, owner = [], [], [], []
+    k = 0
+    if n3:
+        lam.append((1 / 3, 1 / 3, 1 / 3))
+        w.append(theta[k])
+        dl.append({})
+        owner.append(k)
+        k += 1
+    for _ in range(n21):
+        a, wt = theta[k], theta[k + 1]
+        for p, d in [((a, a, 1 - 2 * a), (1, 1, -2)), ((a, 1 - 2 * a, a), (1, -2, 1)),
+                     ((1 - 2 * a, a, a), (-2, 1, 1))]:
+            lam.append(p)
+            w.append(wt)
+            dl.append({k: d})
+            owner.append(k + 1)
+        k += 2
+    for _ in range(n111):
+        a, b, wt = theta[k], theta[k + 1], theta[k + 2]
+        c = 1 - a - b
+        da, db = (1, 0, -1), (0, 1, -1)   # d(a, b, c)/da, d/db
+        perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+        for pm in perms:
+            vals = (a, b, c)
+            lam.append(tuple(vals[i] for i in pm))
+            w.append(wt)
+            dl.append({k: tuple(da[i] for i in pm), k + 1: tuple(db[i] for i in pm)})
+            owner.append(k + 2)
+        k += 3
+    lam = np.array(lam)
+    r = -lam[:, 0] + lam[:, 1] - lam[:, 2]
+    s = -lam[:, 0] - lam[:, 1] + lam[:, 2]
+    return r, s, np.array(w), dl, owner
+
+
+def _sym_solve(d, seed):
+    st = SYM_STRUCT[d]
+    n = st[0] + 2 * st[1] + 3 * st[2]
+    rng = np.random.default_rng(seed)
+    th = []
+    if st[0]:
+        th.append(rng.uniform(0.05, 0.3))
+    for _ in range(st[1]):
+        th += [rng.uniform(0.02, 0.48), rng.uniform(0.02, 0.3)]
+    for _ in range(st[2]):
+        th += [rng.uniform(0.01, 0.45), rng.uniform(0.01, 0.45), rng.uniform(0.02, 0.2)]
+    th = np.array(th)
+    target = np.zeros(num_modes(d))
+    target[0] = np.sqrt(2.0)   # int of the constant mode 1/sqrt(2) over area 2
+
+    def resid_jac(th):
+        r, s, w, dl, owner = _sym_points(th, st)
+        V, Vr, Vs = basis(d, r, s, derivs=True)
+        R = V.T @ w - target
+        J = np.zeros((R.size, n))
+        for i in range(r.size):
+            J[:, owner[i]] += V[i]
+            for j, dlam in dl[i].items():
+                drj = -dlam[0] + dlam[1] - dlam[2]
+                dsj = -dlam[0] - dlam[1] + dlam[2]
+                J[:, j] += w[i] * (Vr[i] * drj + Vs[i] * dsj)
+        return R, J
+    mu = 1e-3
+    R, J = resid_jac(th)
+    for _ in range(200):
+        if np.linalg.norm(R) < 1e-15:
+            break
+        step = np.linalg.solve(J.T @ J + mu * np.eye(n), -J.T @ R)
+        R2, J2 = resid_jac(th + step)
+        if np.linalg.norm(R2) < np.linalg.norm(R):
+            th, R, J = th + step, R2, J2
+            mu = max(mu / 3, 1e-15)
+        else:
+            mu *= 10
+            if mu > 1e10:
+                break
+    r, s, w, _, _ = _sym_points(th, st)
+    ok = (np.linalg.norm(R) < 1e-13 and np.all(w > 0) and np.all(r > -1) and np.all(s > -1)
+          and np.all(r + s < 0))
+    return ok, th
+
+
+def _canonical(th, st):
+    """Orbit parameters in a unique order: S21 by a; each S111 as a <= b <= c, by a."""
+    n3, n21, n111 = st
+    out, k = [], 0
+    if n3:
+        out.append(th[k])
+        k += 1
+    s21 = sorted((th[k + 2 * i], th[k + 2 * i + 1]) for i in range(n21))
+    k += 2 * n21
+    s111 = []
+    for i in range(n111):
+        a, b, wt = th[k + 3 * i], th[k + 3 * i + 1], th[k + 3 * i + 2]
+        abc = sorted((a, b, 1 - a - b))
+        s111.append((abc[0], abc[1], wt))
+    s111.sort()
+    for a, wt in s21:
+        out += [a, wt]
+    for a, b, wt in s111:
+        out += [a, b, wt]
+    return np.array(out)
+
+
+_SYM_CACHE = {}
+
+
+def symmetric_quadrature(N):
+    """(r, s, w) of the fully symmetric rule exact to degree 2N (N = 1..5)."""
+    d = 2 * N
+    if d not in _SYM_CACHE:
+        st = SYM_STRUCT[d]
+        for seed in range(1000):
+            ok, th = _sym_solve(d, seed)
+            if ok:
+                break
+        else:
+            raise RuntimeError("no symmetric rule found for degree %d" % d)
+        th = _canonical(th, st)
+        r, s, w, _, _ = _sym_points(th, st)
+        _SYM_CACHE[d] = (r, s, w)
+    return _SYM_CACHE[d]

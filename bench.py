@@ -42,9 +42,8 @@ STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2
 
 # Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of
 # each step of the path, and the bytes each element-stage must move.
-def algorithmic_flops(N):
+def algorithmic_flops(N, Nq):
     Np = (N + 1) * (N + 2) // 2
-    Nq = (N + 1) ** 2
     Nfq = 3 * (N + 1)
     Nh = Nq + Nfq
     pairs = Nq * (Nq - 1) // 2 + Nq * Nfq            # unique non-zero pairs of Q_skew
@@ -60,9 +59,8 @@ def algorithmic_flops(N):
     return flops
 
 
-def algorithmic_bytes(N, real_bytes=4):
+def algorithmic_bytes(N, Nq, real_bytes=4):
     Np = (N + 1) * (N + 2) // 2
-    Nq = (N + 1) ** 2
     Nfq = 3 * (N + 1)
     Nh = Nq + Nfq
     NpP = Np * (Np + 1) // 2
@@ -177,7 +175,7 @@ def replica_value(units_per_rank, world, max_seconds):
 
 def make_solver(precision):
     from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
-    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl)
+    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
     xb, yb = s.points(ESDG_POINTS_NODAL)
     xq, yq = s.points(ESDG_POINTS_VOLQ)
     s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
@@ -237,7 +235,7 @@ def run_ensemble(n, steps):
     insts = W.ensemble(n=n, steps=steps)
     solvers = []
     for it in insts:
-        s = Solver(it.N, it.nx, it.nx, precision="fp32", warp=it.warp, g=it.g, cfl=it.cfl)
+        s = Solver(it.N, it.nx, it.nx, precision="fp32", warp=it.warp, g=it.g, cfl=it.cfl, rule=it.rule)
         xb, yb = s.points(ESDG_POINTS_NODAL)
         xq, yq = s.points(ESDG_POINTS_VOLQ)
         s.init_state(it.bathymetry(xb, yb), it.initial(xq, yq), surface=True)
@@ -280,7 +278,8 @@ def run_served(n, rate, precision, steps_range, k_range, budget_gb=64.0):
 
     def prepare(i):
         req = trace[i]
-        p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+        p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl,
+                         rule=req.rule)
         xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
         xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
         tickets[i] = srv.submit(p, req.bathymetry(xb, yb), req.initial(xq, yq), req.steps, surface=True)
@@ -318,7 +317,7 @@ def cpu_baseline(seconds_target=15.0):
     on a sample of 2048 consecutive elements of the same workload, repeated
     until about `seconds_target` seconds of CPU work."""
     from oracle import Oracle
-    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl)
+    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
     xb, yb = o.points("nodal")
     o.set_bathymetry(WL.bathymetry(xb, yb))
     xq, yq = o.points("volq")
@@ -348,7 +347,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     from oracle import Oracle
-    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl)
+    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
     xb, yb = o.points("nodal")
     o.set_bathymetry(WL.bathymetry(xb, yb))
     xq, yq = o.points("volq")
@@ -367,7 +366,8 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WL.name, "N": WL.N, "K": WL.K, "curved": True, "sample_elements": 2048},
+            "config": {"workload": WL.name, "N": WL.N, "K": WL.K, "Nq": WL.Nq, "volume_rule": WL.rule, "curved": True,
+                       "sample_elements": 2048},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -415,8 +415,8 @@ def main():
     value = replica_value(units, world, el_max)
     launches = 5 * steps
     t_launch = el / launches
-    flops = algorithmic_flops(WL.N) * K
-    nbytes = algorithmic_bytes(WL.N, 4) * K
+    flops = algorithmic_flops(WL.N, WL.Nq) * K
+    nbytes = algorithmic_bytes(WL.N, WL.Nq, 4) * K
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
     alu = flops / t_launch / 1e12
@@ -474,7 +474,7 @@ def main():
                 "warmup": args.warmup, "ms_per_step": el_max / steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WL.name if args.nx is None else "%s_nx%d" % (WL.name, args.nx),
-                           "N": WL.N, "K": K, "Np": Np, "curved": True,
+                           "N": WL.N, "K": K, "Np": Np, "Nq": WL.Nq, "volume_rule": WL.rule, "curved": True,
                            "rhs_precision": "fp32", "rk_accumulation": "fp64",
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},

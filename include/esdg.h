@@ -53,6 +53,11 @@ extern "C" {
 #define ESDG_FORCING_MMS_SINE 1  /* manufactured solution h = 2 + a sin(pi(x+y-t)), u=u0, v=v0,
                                     b = bamp cos(pi x) cos(pi y): forcing added to du/dt */
 
+/* volume quadrature rules (Sec. 2.1 asks for positive weights, exact to >= 2N-1) */
+#define ESDG_RULE_COLLAPSED 0  /* collapsed Gauss rule, (N+1)^2 points, exact to degree 2N+1 */
+#define ESDG_RULE_SYMMETRIC 1  /* fully symmetric interior rule exact to degree 2N:
+                                  3, 6, 12, 16, 25 points for N = 1..5 */
+
 /* point sets for esdg_get_points */
 #define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
 #define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
@@ -74,6 +79,7 @@ typedef struct esdg_config {
                                0: entropy-conservative flux alone */
     int forcing;            /* ESDG_FORCING_* */
     double mms_amp, mms_bamp, mms_u0, mms_v0;  /* ESDG_FORCING_MMS_SINE parameters */
+    int volume_rule;        /* ESDG_RULE_* */
 } esdg_config;
 
 /*
@@ -210,7 +216,7 @@ int esdg_entropy_noalloc(const esdg_ctx* ctx, const double* u_dev, double* entro
  * size K advanced together, one persistent kernel launch per RK stage over a
  * tile table of all members' element batches, the steps replayed from a
  * captured CUDA graph.  Members must be FP32 contexts, attached on the same
- * stream, with no forcing.  Each member steps with its own CFL time step
+ * stream, with no forcing, all with the same volume rule.  Each member steps with its own CFL time step
  * (Sec. 4); members stay ordinary contexts (esdg_copy_state, esdg_entropy ...).
  * The ensemble allocates one small device table (a few hundred bytes per
  * member) with cudaMalloc and frees it in esdg_ensemble_destroy.

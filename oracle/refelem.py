@@ -363,6 +363,10 @@ def _canonical(th, st):
 
 
 _SYM_CACHE = {}
+# The moment equations can have several positive interior solutions (degree 10
+# has at least four); the rule is the one, among those reached from
+# SYM_RESTARTS seeded starts, whose smallest weight is largest.
+SYM_RESTARTS = 64
 
 
 def symmetric_quadrature(N):
@@ -370,13 +374,16 @@ def symmetric_quadrature(N):
     d = 2 * N
     if d not in _SYM_CACHE:
         st = SYM_STRUCT[d]
-        for seed in range(1000):
+        best, best_min = None, -1.0
+        for seed in range(SYM_RESTARTS):
             ok, th = _sym_solve(d, seed)
-            if ok:
-                break
-        else:
+            if not ok:
+                continue
+            wmin = _sym_points(th, st)[2].min()
+            if wmin > best_min + 1e-12:
+                best, best_min = _canonical(th, st), wmin
+        if best is None:
             raise RuntimeError("no symmetric rule found for degree %d" % d)
-        th = _canonical(th, st)
-        r, s, w, _, _ = _sym_points(th, st)
+        r, s, w, _, _ = _sym_points(best, st)
         _SYM_CACHE[d] = (r, s, w)
     return _SYM_CACHE[d]

@@ -1,7 +1,8 @@
 """Compile the CUDA library libesdg.so in-tree for sm_103a.
 
-Translation units compile in parallel (one per polynomial degree plus the
-C-ABI and the host builder) and link into paper_2005_02516_gb300/libesdg.so.
+Translation units compile in parallel (one per polynomial degree and volume
+rule, one per rule for the ensemble kernel, plus the C-ABI, the host builder
+and the request server) and link into paper_2005_02516_gb300/libesdg.so.
 """
 
 import os
@@ -24,7 +25,8 @@ def nvcc():
 
 
 def _sources():
-    cu = ["esdg_api.cu", "esdg_ensemble.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
+    cu = (["esdg_api.cu", "esdg_ensemble.cu", "esdg_ensemble_s.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
+          + ["esdg_kernels_s%d.cu" % n for n in range(1, 6)])
     return cu, ["host_build.cpp", "esdg_server.cpp"]
 
 
@@ -48,7 +50,7 @@ def build(verbose=False, extra_nvcc=()):
         obj = os.path.join(BUILD, f + ".o")
         jobs.append([nvcc(), "-x", "c++", "-c", os.path.join(CSRC, f), "-o", obj, "-O2", "-std=c++17",
                      "-Xcompiler", "-fPIC", *inc])
-    with ThreadPoolExecutor(max_workers=min(8, len(jobs))) as ex:
+    with ThreadPoolExecutor(max_workers=min(os.cpu_count() or 8, 16, len(jobs))) as ex:
         outs = list(ex.map(_run, jobs))
     if verbose:
         for o in outs:

@@ -97,6 +97,12 @@ static size_t real_size(const esdg_ctx* c) { return c->cfg.precision == ESDG_FP3
 
 static int c2_ops_floats(int N);
 
+// Kernel template parameter of a configuration: NR = N + 8 * rule.
+static int kernel_nr(const esdg_config& cfg) { return cfg.N + (cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 8 : 0); }
+#define ESDG_FOR_EACH_NR(X) X(1) X(2) X(3) X(4) X(5) X(9) X(10) X(11) X(12) X(13)
+
+static int c2_ops_floats(int NR);
+
 static void compute_layout(esdg_ctx* c) {
     const RefOps& R = c->ref;
     const size_t rs = real_size(c);
@@ -110,7 +116,7 @@ static void compute_layout(esdg_ctx* c) {
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
     L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq));
     L.ops = take(L.ops_bytes);
-    L.ops2_bytes = c->cfg.precision == ESDG_FP32 ? 4 * size_t(c2_ops_floats(c->cfg.N)) : 0;
+    L.ops2_bytes = c->cfg.precision == ESDG_FP32 ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
     L.ops2 = take(L.ops2_bytes);
     L.vq64 = take(8 * size_t(R.Nq) * R.Np);
     L.geo = take(rs * Kp * R.Nh * 4);
@@ -211,24 +217,22 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
     return o;
 }
 
-static int c2_ops_floats(int N) {
-    switch (N) {
-        case 1: return C2<1>::o_end;
-        case 2: return C2<2>::o_end;
-        case 3: return C2<3>::o_end;
-        case 4: return C2<4>::o_end;
-        default: return C2<5>::o_end;
+static int c2_ops_floats(int NR) {
+    switch (NR) {
+#define X(v) case v: return C2<v>::o_end;
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return 0;
 }
 
-static std::vector<float> pack_ops2(const RefOps& R) {
-    switch (R.N) {
-        case 1: return pack_ops2_t<1>(R);
-        case 2: return pack_ops2_t<2>(R);
-        case 3: return pack_ops2_t<3>(R);
-        case 4: return pack_ops2_t<4>(R);
-        default: return pack_ops2_t<5>(R);
+static std::vector<float> pack_ops2(const RefOps& R, int NR) {
+    switch (NR) {
+#define X(v) case v: return pack_ops2_t<v>(R);
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return {};
 }
 
 // ---- host image of the device layout ------------------------------------------
@@ -251,7 +255,7 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     std::vector<real> geo(M.geo.size());
     for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
     put(img, c->L.geo, geo);
-    if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R));
+    if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, kernel_nr(c->cfg)));
     std::vector<double> wJ64(K * R.Nq);
     for (size_t e = 0; e < K; ++e)
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
@@ -398,68 +402,60 @@ static real* ut_buf(esdg_ctx* c, int which) {
 
 // ---- degree dispatch ---------------------------------------------------------
 static cudaError_t d_geometry(esdg_ctx* c) {
-    const int N = c->cfg.N, sms = c->num_sms;
-    cudaError_t e = cudaSuccess;
+    const int sms = c->num_sms;
+    cudaError_t e = cudaErrorInvalidValue;
     if (c->cfg.precision == ESDG_FP32) {
-        switch (N) {
-            case 1: e = project_geometry<1, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<1>(sms, c->lg2); break;
-            case 2: e = project_geometry<2, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<2>(sms, c->lg2); break;
-            case 3: e = project_geometry<3, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<3>(sms, c->lg2); break;
-            case 4: e = project_geometry<4, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<4>(sms, c->lg2); break;
-            default: e = project_geometry<5, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<5>(sms, c->lg2); break;
+        switch (kernel_nr(c->cfg)) {
+#define X(v) case v: e = project_geometry<v, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<v>(sms, c->lg2); break;
+            ESDG_FOR_EACH_NR(X)
+#undef X
         }
     } else {
-        switch (N) {
-            case 1: e = project_geometry<1, double>(sms, c->lg_proj); if (!e) e = stage_geometry<1, double>(sms, c->lg); break;
-            case 2: e = project_geometry<2, double>(sms, c->lg_proj); if (!e) e = stage_geometry<2, double>(sms, c->lg); break;
-            case 3: e = project_geometry<3, double>(sms, c->lg_proj); if (!e) e = stage_geometry<3, double>(sms, c->lg); break;
-            case 4: e = project_geometry<4, double>(sms, c->lg_proj); if (!e) e = stage_geometry<4, double>(sms, c->lg); break;
-            default: e = project_geometry<5, double>(sms, c->lg_proj); if (!e) e = stage_geometry<5, double>(sms, c->lg); break;
+        switch (kernel_nr(c->cfg)) {
+#define X(v) case v: e = project_geometry<v, double>(sms, c->lg_proj); if (!e) e = stage_geometry<v, double>(sms, c->lg); break;
+            ESDG_FOR_EACH_NR(X)
+#undef X
         }
     }
     return e;
 }
 template <typename real>
-static cudaError_t d_project(int N, const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
-    switch (N) {
-        case 1: return launch_project<1, real>(p, lg, s);
-        case 2: return launch_project<2, real>(p, lg, s);
-        case 3: return launch_project<3, real>(p, lg, s);
-        case 4: return launch_project<4, real>(p, lg, s);
-        default: return launch_project<5, real>(p, lg, s);
+static cudaError_t d_project(int NR, const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
+    switch (NR) {
+#define X(v) case v: return launch_project<v, real>(p, lg, s);
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return cudaErrorInvalidValue;
 }
 static cudaError_t d_stage(esdg_ctx* c, const StageParams<double>& p, int mode) {
     const LaunchGeom& lg = c->lg;
-    switch (c->cfg.N) {
-        case 1: return launch_stage<1, double>(p, mode, lg, c->stream);
-        case 2: return launch_stage<2, double>(p, mode, lg, c->stream);
-        case 3: return launch_stage<3, double>(p, mode, lg, c->stream);
-        case 4: return launch_stage<4, double>(p, mode, lg, c->stream);
-        default: return launch_stage<5, double>(p, mode, lg, c->stream);
+    switch (kernel_nr(c->cfg)) {
+#define X(v) case v: return launch_stage<v, double>(p, mode, lg, c->stream);
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return cudaErrorInvalidValue;
 }
 static cudaError_t d_stage(esdg_ctx* c, const StageParams<float>& p, int mode) {
     const LaunchGeom& lg = c->lg2;
     const float* ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
-    switch (c->cfg.N) {
-        case 1: return launch_stage2<1>(p, ops2, c->Kpad, mode, lg, c->stream);
-        case 2: return launch_stage2<2>(p, ops2, c->Kpad, mode, lg, c->stream);
-        case 3: return launch_stage2<3>(p, ops2, c->Kpad, mode, lg, c->stream);
-        case 4: return launch_stage2<4>(p, ops2, c->Kpad, mode, lg, c->stream);
-        default: return launch_stage2<5>(p, ops2, c->Kpad, mode, lg, c->stream);
+    switch (kernel_nr(c->cfg)) {
+#define X(v) case v: return launch_stage2<v>(p, ops2, c->Kpad, mode, lg, c->stream);
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return cudaErrorInvalidValue;
 }
-static cudaError_t d_entropy(int N, int K, double g, const double* u, const double* rhs, const double* Vq,
+static cudaError_t d_entropy(int NR, int K, double g, const double* u, const double* rhs, const double* Vq,
                              const double* wJq, const double* bq, double* partial, int nparts, double* out,
                              cudaStream_t s) {
-    switch (N) {
-        case 1: return launch_entropy<1>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
-        case 2: return launch_entropy<2>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
-        case 3: return launch_entropy<3>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
-        case 4: return launch_entropy<4>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
-        default: return launch_entropy<5>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+    switch (NR) {
+#define X(v) case v: return launch_entropy<v>(K, g, u, rhs, Vq, wJq, bq, partial, nparts, out, s);
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return cudaErrorInvalidValue;
 }
 
 static int check_status(esdg_ctx* c) {
@@ -482,7 +478,7 @@ static int project_current(esdg_ctx* c, const double* u_in, int target) {
     StageParams<real> p = make_params<real>(c);
     if (u_in) p.u_in = u_in;
     p.ut_out = ut_buf<real>(c, target);
-    CUDA_TRY(c, d_project<real>(c->cfg.N, p, c->lg_proj, c->stream));
+    CUDA_TRY(c, d_project<real>(kernel_nr(c->cfg), p, c->lg_proj, c->stream));
     return ESDG_OK;
 }
 
@@ -533,11 +529,13 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
     if (!(cfg->g > 0)) return fail(nullptr, ESDG_EINVAL, "g must be positive");
     if (cfg->forcing != ESDG_FORCING_NONE && cfg->forcing != ESDG_FORCING_MMS_SINE)
         return fail(nullptr, ESDG_EINVAL, "unknown forcing");
+    if (cfg->volume_rule != ESDG_RULE_COLLAPSED && cfg->volume_rule != ESDG_RULE_SYMMETRIC)
+        return fail(nullptr, ESDG_EINVAL, "unknown volume rule");
     esdg_ctx* c = new (std::nothrow) esdg_ctx();
     if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     c->cfg = *cfg;
     std::string err;
-    if (!build_reference(cfg->N, c->ref, err)) {
+    if (!build_reference(cfg->N, cfg->volume_rule, c->ref, err)) {
         delete c;
         return fail(nullptr, ESDG_EINVAL, err);
     }
@@ -718,7 +716,7 @@ int esdg_entropy(esdg_ctx* c, double t, double* entropy, double* mass, double* e
         rhs = r;
     }
     double* out = reinterpret_cast<double*>(c->dbuf + c->L.diag);
-    CUDA_TRY(c, d_entropy(c->cfg.N, c->mesh.K, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u), rhs,
+    CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u), rhs,
                           reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
                           reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
                           reinterpret_cast<const double*>(c->dbuf + c->L.bq64),
@@ -774,7 +772,7 @@ int esdg_entropy_noalloc(const esdg_ctx* cc, const double* u_dev, double* entrop
     const double* u = u_dev ? u_dev : reinterpret_cast<const double*>(c->dbuf + c->L.u);
     // every block writes its own partial and the finalize kernel writes all three
     // totals, so no part of the scratch has to start at zero
-    CUDA_TRY(c, d_entropy(c->cfg.N, c->mesh.K, c->cfg.g, u, nullptr,
+    CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, u, nullptr,
                           reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
                           reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
                           reinterpret_cast<const double*>(c->dbuf + c->L.bq64), partial, (int)parts, out, c->stream));
@@ -796,6 +794,7 @@ struct esdg_ensemble {
     int nmax = 4;
     int4 ops_lo = make_int4(-1, -1, -1, -1);
     int ops_hi = -1, ops_end = 0, slab = 0;
+    int rule = ESDG_RULE_COLLAPSED;  // shared by all members
     size_t smem = 0;
     cudaStream_t stream = nullptr;    // the members' stream (work and graph launches)
     cudaStream_t capture = nullptr;   // private stream the graph is captured on (the
@@ -816,14 +815,13 @@ static int efail(esdg_ensemble* e, int code, const std::string& m) {
         if (e__ != cudaSuccess) return efail((ens), ESDG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e__)); \
     } while (0)
 
-static int c2_w_end(int N) {
-    switch (N) {
-        case 1: return C2<1>::w_end;
-        case 2: return C2<2>::w_end;
-        case 3: return C2<3>::w_end;
-        case 4: return C2<4>::w_end;
-        default: return C2<5>::w_end;
+static int c2_w_end(int NR) {
+    switch (NR) {
+#define X(v) case v: return C2<v>::w_end;
+        ESDG_FOR_EACH_NR(X)
+#undef X
     }
+    return 0;
 }
 
 // (Re)build the member table in the given order and the shared-memory plan.
@@ -833,12 +831,12 @@ static int ensemble_table(esdg_ensemble* e) {
     int off[6] = {-1, -1, -1, -1, -1, -1};
     for (int idx : e->order) {
         esdg_ctx* c = e->members[idx];
-        const int N = c->cfg.N;
+        const int N = c->cfg.N, NR = kernel_nr(c->cfg);
         if (off[N] < 0) {
             off[N] = ops;
-            ops += c2_ops_floats(N);
+            ops += c2_ops_floats(NR);
         }
-        slab = std::max(slab, c2_w_end(N));
+        slab = std::max(slab, c2_w_end(NR));
         nmax = std::max(nmax, N);
         EnsembleMember m;
         std::memset(&m, 0, sizeof(m));
@@ -879,7 +877,8 @@ static int ensemble_fits(esdg_ensemble* e, int warps) {
 static int ensemble_launch(esdg_ensemble* e, int which, int stage, cudaStream_t st) {
     const int sms = e->members[0]->num_sms;
     const int n = int(e->members.size());
-    ECUDA_TRY(e, launch_ensemble(e->nmax, sms, e->warps * 32, e->smem, st, e->dmem, n, e->total_batches, which,
+    auto launch = e->rule == ESDG_RULE_SYMMETRIC ? launch_ensemble<1> : launch_ensemble<0>;
+    ECUDA_TRY(e, launch(e->nmax, sms, e->warps * 32, e->smem, st, e->dmem, n, e->total_batches, which,
                                  RK_A[stage], RK_B[stage], e->ops_lo, e->ops_hi, e->ops_end, e->slab));
     return ESDG_OK;
 }
@@ -901,7 +900,8 @@ static int ensemble_set_shape(esdg_ensemble* e, int warps) {
     e->warps = warps;
     const int n = int(e->members.size());
     e->smem = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(warps);
-    cudaError_t err = ensemble_smem_attr(e->nmax, e->smem);
+    cudaError_t err = e->rule == ESDG_RULE_SYMMETRIC ? ensemble_smem_attr<1>(e->nmax, e->smem)
+                                                     : ensemble_smem_attr<0>(e->nmax, e->smem);
     if (err != cudaSuccess) return efail(e, ESDG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));
     if (e->graph) {
         cudaGraphExecDestroy(e->graph);
@@ -931,11 +931,14 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members with a forcing term are not supported");
         if (c->stream != members[0]->stream)
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one stream");
+        if (c->cfg.volume_rule != members[0]->cfg.volume_rule)
+            return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one volume rule");
     }
     esdg_ensemble* e = new (std::nothrow) esdg_ensemble();
     if (!e) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     e->members.assign(members, members + n);
     e->stream = members[0]->stream;
+    e->rule = members[0]->cfg.volume_rule;
     for (int i = 0; i < n; ++i) e->order.push_back(i);
     cudaError_t err = cudaMalloc(&e->dmem, sizeof(EnsembleMember) * n);
     if (err != cudaSuccess) {

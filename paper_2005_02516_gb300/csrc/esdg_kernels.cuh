@@ -29,10 +29,17 @@
 
 namespace esdg {
 
-template <int N>
+// Points of the fully symmetric volume rule exact to degree 2N.
+constexpr int symmetric_points(int N) { return N == 1 ? 3 : N == 2 ? 6 : N == 3 ? 12 : N == 4 ? 16 : 25; }
+
+// Template parameter NR = N + 8 * rule: the degree N (1..5) and the volume
+// rule (0: collapsed (N+1)^2 points, 1: symmetric, exact to 2N).
+template <int NR>
 struct Dims {
+    static constexpr int N = NR & 7;
+    static constexpr int rule = NR >> 3;
     static constexpr int Np = (N + 1) * (N + 2) / 2;
-    static constexpr int Nq = (N + 1) * (N + 1);
+    static constexpr int Nq = rule ? symmetric_points(N) : (N + 1) * (N + 1);
     static constexpr int Nfp = N + 1;
     static constexpr int Nfq = 3 * (N + 1);
     static constexpr int Nh = Nq + Nfq;

@@ -8,7 +8,8 @@
 // smallest number of steps any of them still needs (at most kMaxChunk), so
 // every request runs exactly its own step count.  Finished requests are
 // retired between iterations (state copied to the caller's host buffer,
-// device memory returned), which lets queued requests in.  All host work of a
+// device memory returned), which lets queued requests in.  FP32 requests form
+// one ensemble per volume rule (an ensemble launch serves one rule).  All host work of a
 // request (esdg_prepare) runs in the submitting thread, so admission is one
 // host-to-device copy.  Built only on the public C ABI of esdg.h.
 
@@ -36,6 +37,7 @@ struct Request {
     int ticket = 0;
     esdg_ctx* ctx = nullptr;
     int precision = ESDG_FP32;
+    int rule = ESDG_RULE_COLLAPSED;
     int nsteps = 0, remaining = 0;
     double* result = nullptr;  // caller's host buffer [3][K][Np]
     size_t bytes = 0;
@@ -62,8 +64,8 @@ struct esdg_server {
     int admitting = 0;  // popped from the queue, not yet running (lock released)
     bool stop = false;
     std::thread worker;
-    esdg_ensemble* ens = nullptr;
-    std::vector<Request*> ens_members;
+    esdg_ensemble* ens[2] = {nullptr, nullptr};  // FP32 ensembles, per volume rule
+    std::vector<Request*> ens_members[2];
     long long iterations = 0, steps_run = 0;
     std::string err;
 };
@@ -123,21 +125,21 @@ static void admit(esdg_server* s, std::unique_lock<std::mutex>& lk) {
     }
 }
 
-// Rebuild the FP32 ensemble when the set of active FP32 requests changed.
-static int refresh_ensemble(esdg_server* s) {
+// Rebuild an FP32 ensemble when the set of its active requests changed.
+static int refresh_ensemble(esdg_server* s, int rule) {
     std::vector<Request*> fp32;
     for (Request* r : s->active)
-        if (r->precision == ESDG_FP32) fp32.push_back(r);
-    if (fp32 == s->ens_members && (s->ens || fp32.empty())) return ESDG_OK;
-    if (s->ens) {
-        esdg_ensemble_destroy(s->ens);
-        s->ens = nullptr;
+        if (r->precision == ESDG_FP32 && r->rule == rule) fp32.push_back(r);
+    if (fp32 == s->ens_members[rule] && (s->ens[rule] || fp32.empty())) return ESDG_OK;
+    if (s->ens[rule]) {
+        esdg_ensemble_destroy(s->ens[rule]);
+        s->ens[rule] = nullptr;
     }
-    s->ens_members = fp32;
+    s->ens_members[rule] = fp32;
     if (fp32.empty()) return ESDG_OK;
     std::vector<esdg_ctx*> ctxs;
     for (Request* r : fp32) ctxs.push_back(r->ctx);
-    int rc = esdg_ensemble_create(ctxs.data(), int(ctxs.size()), &s->ens);
+    int rc = esdg_ensemble_create(ctxs.data(), int(ctxs.size()), &s->ens[rule]);
     if (rc) s->err = esdg_ensemble_error(nullptr);
     return rc;
 }
@@ -156,8 +158,11 @@ static void run(esdg_server* s) {
         for (Request* r : s->active) chunk = std::min(chunk, r->remaining);
         std::vector<Request*> act = s->active;
         lk.unlock();
-        int rc = refresh_ensemble(s);
-        if (!rc && s->ens) rc = esdg_ensemble_step_async(s->ens, chunk);
+        int rc = ESDG_OK;
+        for (int rule = 0; rule < 2 && !rc; ++rule) {
+            rc = refresh_ensemble(s, rule);
+            if (!rc && s->ens[rule]) rc = esdg_ensemble_step_async(s->ens[rule], chunk);
+        }
         for (Request* r : act)
             if (!rc && r->precision == ESDG_FP64) rc = esdg_step_async(r->ctx, chunk, 0.0, 0.0);
         cudaStreamSynchronize(s->stream);
@@ -194,10 +199,11 @@ static void run(esdg_server* s) {
         s->active = keep;
         s->cv.notify_all();
     }
-    if (s->ens) {
-        esdg_ensemble_destroy(s->ens);
-        s->ens = nullptr;
-    }
+    for (int rule = 0; rule < 2; ++rule)
+        if (s->ens[rule]) {
+            esdg_ensemble_destroy(s->ens[rule]);
+            s->ens[rule] = nullptr;
+        }
 }
 
 extern "C" {
@@ -238,6 +244,7 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
         return rc ? rc : ESDG_EINVAL;
     }
     r->precision = cfg.precision;
+    r->rule = cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 1 : 0;
     // all host work of the request (bathymetry, initial projection, operator
     // and geometry packing) runs here, in the submitting thread
     rc = esdg_prepare(ctx, b_nodal, q_volq, mode);

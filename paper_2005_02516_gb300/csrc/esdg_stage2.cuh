@@ -616,19 +616,19 @@ struct EnsembleMember {
     StageParams<float> p;   // all fields but ut_in/ut_out/rkA/rkB (set per launch)
     const float* ops2;      // operators of the member's degree (k_stage2 layout)
     float* ut[2];           // entropy-projected values, ping-pong
-    int N;
+    int N;                  // degree 1..5 (all members share one volume rule)
     int batch_begin, nbatch;
 };
 
 constexpr int ENSEMBLE_MAX_WARPS = 12;
 
-// One LSRK45 stage for every member (defined in esdg_ensemble.cu), for
-// members of degree at most NMAX (4 or 5).
-template <int NMAX>
-__global__ void k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_batches, int which,
-                                  double rkA, double rkB, int4 ops_lo, int ops_hi, int ops_end, int slab);
-// Host wrappers (esdg_ensemble.cu): shared-memory attribute and launch.
+// Host wrappers of the ensemble kernel (esdg_ensemble_impl.cuh), one
+// instantiation per volume rule RULE (0 collapsed, 1 symmetric) in its own
+// translation unit: shared-memory attribute and launch, for members of degree
+// at most nmax (4 or 5).
+template <int RULE>
 cudaError_t ensemble_smem_attr(int nmax, size_t smem);
+template <int RULE>
 cudaError_t launch_ensemble(int nmax, int grid, int block, size_t smem, cudaStream_t s, const EnsembleMember* mem,
                             int nmem, int total_batches, int which, double rkA, double rkB, int4 ops_lo, int ops_hi,
                             int ops_end, int slab);

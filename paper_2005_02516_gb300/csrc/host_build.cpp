@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <mutex>
 #include <thread>
 #include <cmath>
 #include <map>
@@ -205,25 +206,241 @@ void dubiner(int N, const std::vector<double>& r, const std::vector<double>& s, 
 }
 
 // ---------------------------------------------------------------------------
+// Fully symmetric volume rules exact to degree 2N (positive weights, interior
+// points).  Orbits of the triangle's symmetry group in barycentric coordinates:
+// the centroid, (a, a, 1-2a) with its 3 permutations, (a, b, 1-a-b) with its
+// 6.  Orbit counts (centroid, 3-point, 6-point) per degree 2N: 2: (0,1,0),
+// 4: (0,2,0), 6: (0,2,1), 8: (1,3,1), 10: (1,2,3).  The parameters solve the
+// moment equations sum_i w_i phi_k(x_i) = int phi_k over all basis functions
+// of degree <= 2N, by Levenberg-Marquardt from seeded starting points; the
+// solution is put in a canonical order (3-point orbits by a, 6-point orbits
+// as a <= b <= c, by a).
+// ---------------------------------------------------------------------------
+namespace {
+const int kSymStruct[6][3] = {{0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 2, 1}, {1, 3, 1}, {1, 2, 3}};
+
+struct OrbitPoint {
+    double lam[3];
+    double w;
+    int owner;          // index of the weight parameter
+    int dpar[2];        // position parameters the point depends on (-1: none)
+    double dlam[2][3];  // d lam / d parameter
+};
+
+std::vector<OrbitPoint> orbit_points(const std::vector<double>& th, const int st[3]) {
+    std::vector<OrbitPoint> pts;
+    int k = 0;
+    if (st[0]) {
+        OrbitPoint p{{1.0 / 3, 1.0 / 3, 1.0 / 3}, th[k], k, {-1, -1}, {{0, 0, 0}, {0, 0, 0}}};
+        pts.push_back(p);
+        k += 1;
+    }
+    for (int o = 0; o < st[1]; ++o) {
+        const double a = th[k], c = 1 - 2 * a;
+        const double L[3][3] = {{a, a, c}, {a, c, a}, {c, a, a}};
+        const double D[3][3] = {{1, 1, -2}, {1, -2, 1}, {-2, 1, 1}};
+        for (int q = 0; q < 3; ++q) {
+            OrbitPoint p{{L[q][0], L[q][1], L[q][2]}, th[k + 1], k + 1, {k, -1}, {{D[q][0], D[q][1], D[q][2]}, {0, 0, 0}}};
+            pts.push_back(p);
+        }
+        k += 2;
+    }
+    for (int o = 0; o < st[2]; ++o) {
+        const double v[3] = {th[k], th[k + 1], 1 - th[k] - th[k + 1]};
+        const double da[3] = {1, 0, -1}, db[3] = {0, 1, -1};
+        const int perm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+        for (int q = 0; q < 6; ++q) {
+            OrbitPoint p;
+            for (int i = 0; i < 3; ++i) {
+                p.lam[i] = v[perm[q][i]];
+                p.dlam[0][i] = da[perm[q][i]];
+                p.dlam[1][i] = db[perm[q][i]];
+            }
+            p.w = th[k + 2];
+            p.owner = k + 2;
+            p.dpar[0] = k;
+            p.dpar[1] = k + 1;
+            pts.push_back(p);
+        }
+        k += 3;
+    }
+    return pts;
+}
+
+// r = -l1 + l2 - l3, s = -l1 - l2 + l3 (vertices (-1,-1), (1,-1), (-1,1))
+inline double to_r(const double* l) { return -l[0] + l[1] - l[2]; }
+inline double to_s(const double* l) { return -l[0] - l[1] + l[2]; }
+
+uint64_t splitmix(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double uniform(uint64_t& x, double lo, double hi) { return lo + (hi - lo) * (splitmix(x) >> 11) * (1.0 / 9007199254740992.0); }
+
+bool sym_try(int N, uint64_t seed, std::vector<double>& th) {
+    const int d = 2 * N;
+    const int* st = kSymStruct[N];
+    const int n = st[0] + 2 * st[1] + 3 * st[2];
+    const int nm = (d + 1) * (d + 2) / 2;
+    uint64_t x = seed * 7919 + 17;
+    th.clear();
+    if (st[0]) th.push_back(uniform(x, 0.05, 0.3));
+    for (int o = 0; o < st[1]; ++o) { th.push_back(uniform(x, 0.02, 0.48)); th.push_back(uniform(x, 0.02, 0.3)); }
+    for (int o = 0; o < st[2]; ++o) {
+        th.push_back(uniform(x, 0.01, 0.45));
+        th.push_back(uniform(x, 0.01, 0.45));
+        th.push_back(uniform(x, 0.02, 0.2));
+    }
+    auto eval = [&](const std::vector<double>& t, std::vector<double>& R, Mat& J) {
+        std::vector<OrbitPoint> pts = orbit_points(t, st);
+        std::vector<double> r(pts.size()), s(pts.size());
+        for (size_t i = 0; i < pts.size(); ++i) { r[i] = to_r(pts[i].lam); s[i] = to_s(pts[i].lam); }
+        Mat V, Vr, Vs;
+        dubiner(d, r, s, V, &Vr, &Vs);
+        R.assign(nm, 0.0);
+        J = Mat(nm, n);
+        for (size_t i = 0; i < pts.size(); ++i)
+            for (int m = 0; m < nm; ++m) {
+                R[m] += pts[i].w * V(int(i), m);
+                J(m, pts[i].owner) += V(int(i), m);
+                for (int q = 0; q < 2; ++q) {
+                    if (pts[i].dpar[q] < 0) continue;
+                    const double dr = to_r(pts[i].dlam[q]), ds = to_s(pts[i].dlam[q]);
+                    J(m, pts[i].dpar[q]) += pts[i].w * (Vr(int(i), m) * dr + Vs(int(i), m) * ds);
+                }
+            }
+        R[0] -= std::sqrt(2.0);  // int over the triangle (area 2) of the constant mode 1/sqrt(2)
+    };
+    auto norm = [](const std::vector<double>& v) { double a = 0; for (double y : v) a += y * y; return std::sqrt(a); };
+    std::vector<double> R, R2;
+    Mat J, J2;
+    eval(th, R, J);
+    double mu = 1e-3;
+    for (int it = 0; it < 200 && norm(R) > 1e-15; ++it) {
+        Mat A(n, n), Ai;
+        std::vector<double> g(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                double sum = 0;
+                for (int m = 0; m < nm; ++m) sum += J(m, i) * J(m, j);
+                A(i, j) = sum + (i == j ? mu : 0.0);
+            }
+            for (int m = 0; m < nm; ++m) g[i] -= J(m, i) * R[m];
+        }
+        if (!invert(A, Ai)) { mu *= 10; continue; }
+        std::vector<double> t2(th);
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) t2[i] += Ai(i, j) * g[j];
+        eval(t2, R2, J2);
+        if (norm(R2) < norm(R)) {
+            th = t2; R = R2; J = J2;
+            mu = std::max(mu / 3, 1e-15);
+        } else {
+            mu *= 10;
+            if (mu > 1e10) break;
+        }
+    }
+    if (norm(R) > 1e-13) return false;
+    for (const OrbitPoint& p : orbit_points(th, st)) {
+        const double r = to_r(p.lam), s = to_s(p.lam);
+        if (!(p.w > 0) || !(r > -1) || !(s > -1) || !(r + s < 0)) return false;
+    }
+    return true;
+}
+}  // namespace
+
+// Canonical order of the orbit parameters: S21 by a; each S111 as a <= b <= c, by a.
+static std::vector<double> sym_canonical(const std::vector<double>& th, const int* st) {
+    std::vector<double> c;
+    int k = 0;
+    if (st[0]) c.push_back(th[k++]);
+    std::vector<std::pair<double, double>> s21;
+    for (int o = 0; o < st[1]; ++o, k += 2) s21.push_back({th[k], th[k + 1]});
+    std::sort(s21.begin(), s21.end());
+    std::vector<std::vector<double>> s111;
+    for (int o = 0; o < st[2]; ++o, k += 3) {
+        double v[3] = {th[k], th[k + 1], 1 - th[k] - th[k + 1]};
+        std::sort(v, v + 3);
+        s111.push_back({v[0], v[1], th[k + 2]});
+    }
+    std::sort(s111.begin(), s111.end());
+    for (auto& p : s21) { c.push_back(p.first); c.push_back(p.second); }
+    for (auto& q : s111) for (double v : q) c.push_back(v);
+    return c;
+}
+
+// The moment equations can have several positive interior solutions (degree
+// 10 has at least four): of those found from kSymRestarts seeded starts, take
+// the one whose smallest weight is largest.
+static const int kSymRestarts = 64;
+
+bool symmetric_rule(int N, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w, std::string& err) {
+    if (N < 1 || N > 5) { err = "symmetric rules exist here for N = 1..5"; return false; }
+    // one search per degree and process; later builds reuse it
+    static std::mutex mu;
+    static std::vector<double> cache[6];
+    std::lock_guard<std::mutex> lock(mu);
+    const int* st = kSymStruct[N];
+    std::vector<double>& best = cache[N];
+    if (best.empty()) {
+        // restarts run on host threads; the choice below goes in seed order
+        std::vector<std::vector<double>> found(kSymRestarts);
+        std::vector<char> ok(kSymRestarts, 0);
+        const int nt = std::max(1, std::min<int>(16, int(std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                for (int seed = t; seed < kSymRestarts; seed += nt) ok[seed] = sym_try(N, uint64_t(seed), found[seed]);
+            });
+        for (auto& th : pool) th.join();
+        double best_min = -1.0;
+        for (int seed = 0; seed < kSymRestarts; ++seed) {
+            if (!ok[seed]) continue;
+            double wmin = 1e300;
+            for (const OrbitPoint& p : orbit_points(found[seed], st)) wmin = std::min(wmin, p.w);
+            if (wmin > best_min + 1e-12) {
+                best_min = wmin;
+                best = sym_canonical(found[seed], st);
+            }
+        }
+        if (best.empty()) { err = "no symmetric volume rule found"; return false; }
+    }
+    r.clear(); s.clear(); w.clear();
+    for (const OrbitPoint& p : orbit_points(best, st)) {
+        r.push_back(to_r(p.lam));
+        s.push_back(to_s(p.lam));
+        w.push_back(p.w);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Reference element
 // ---------------------------------------------------------------------------
-bool build_reference(int N, RefOps& R, std::string& err) {
+bool build_reference(int N, int rule, RefOps& R, std::string& err) {
     if (N < 1 || N > 5) { err = "N must be in 1..5"; return false; }
     R.N = N;
     R.Np = (N + 1) * (N + 2) / 2;
     R.Nfp = N + 1;
     R.Nfq = 3 * R.Nfp;
-    // volume: Gauss-Legendre (a) x Gauss-Jacobi(1,0) (b), (N+1)^2 points
+    // volume: collapsed Gauss-Legendre (a) x Gauss-Jacobi(1,0) (b), (N+1)^2
+    // points, or the fully symmetric rule exact to degree 2N
     std::vector<double> xa, wa, xb, wb;
     gauss_jacobi(N + 1, 0.0, 0.0, xa, wa);
     gauss_jacobi(N + 1, 1.0, 0.0, xb, wb);
     R.rq.clear(); R.sq.clear(); R.wq.clear();
-    for (int ia = 0; ia <= N; ++ia)
-        for (int ib = 0; ib <= N; ++ib) {
-            R.rq.push_back(0.5 * (1.0 + xa[ia]) * (1.0 - xb[ib]) - 1.0);
-            R.sq.push_back(xb[ib]);
-            R.wq.push_back(0.5 * wa[ia] * wb[ib]);
-        }
+    if (rule == 0) {
+        for (int ia = 0; ia <= N; ++ia)
+            for (int ib = 0; ib <= N; ++ib) {
+                R.rq.push_back(0.5 * (1.0 + xa[ia]) * (1.0 - xb[ib]) - 1.0);
+                R.sq.push_back(xb[ib]);
+                R.wq.push_back(0.5 * wa[ia] * wb[ib]);
+            }
+    } else if (!symmetric_rule(N, R.rq, R.sq, R.wq, err)) {
+        return false;
+    }
     R.Nq = int(R.rq.size());
     R.Nh = R.Nq + R.Nfq;
     // faces: parameter t runs v1->v2, v2->v3, v3->v1 (counter-clockwise)

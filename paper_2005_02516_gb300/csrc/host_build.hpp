@@ -38,7 +38,10 @@ struct RefOps {
     Mat Veq_inv;                           // inverse Vandermonde at the equispaced nodes
 };
 
-bool build_reference(int N, RefOps& ref, std::string& err);
+// rule 0: collapsed Gauss rule, (N+1)^2 points, exact to 2N+1;
+// rule 1: fully symmetric rule exact to 2N (3, 6, 12, 16, 25 points).
+bool build_reference(int N, int rule, RefOps& ref, std::string& err);
+bool symmetric_rule(int N, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w, std::string& err);
 
 // Orthonormal Dubiner basis and (optionally) its gradients at points (r, s).
 void dubiner(int N, const std::vector<double>& r, const std::vector<double>& s,

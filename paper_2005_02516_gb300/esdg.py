@@ -28,6 +28,8 @@ ESDG_FP64 = 0
 ESDG_FP32 = 1
 ESDG_FORCING_NONE = 0
 ESDG_FORCING_MMS_SINE = 1
+ESDG_RULE_COLLAPSED = 0
+ESDG_RULE_SYMMETRIC = 1
 ESDG_POINTS_NODAL = 0
 ESDG_POINTS_VOLQ = 1
 ESDG_POINTS_FACEQ = 2
@@ -61,7 +63,8 @@ class Config(ctypes.Structure):
                 ("g", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("lax_friedrichs", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("mms_amp", ctypes.c_double), ("mms_bamp", ctypes.c_double),
-                ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double)]
+                ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double),
+                ("volume_rule", ctypes.c_int)]
 
 
 _lib = None
@@ -131,7 +134,7 @@ def _ptr(a):
 
 
 def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, warp=0.0, g=1.0, cfl=0.25,
-                lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5)):
+                lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed"):
     cfg = Config()
     cfg.N, cfg.nx, cfg.ny = N, nx, ny
     cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
@@ -141,6 +144,7 @@ def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, w
     cfg.lax_friedrichs = 1 if lax_friedrichs else 0
     cfg.forcing = ESDG_FORCING_MMS_SINE if forcing == "mms_sine" else ESDG_FORCING_NONE
     cfg.mms_amp, cfg.mms_bamp, cfg.mms_u0, cfg.mms_v0 = mms
+    cfg.volume_rule = ESDG_RULE_SYMMETRIC if rule == "symmetric" else ESDG_RULE_COLLAPSED
     return cfg
 
 
@@ -263,18 +267,11 @@ class Solver:
 
     def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
                  warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
-                 mms=(0.1, 0.1, 0.5, 0.5), torch_memory=True, stream=None):
+                 mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", torch_memory=True, stream=None):
         import torch
         self.lib = load_library()
-        cfg = Config()
-        cfg.N, cfg.nx, cfg.ny = N, nx, ny
-        cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
-        cfg.x0, cfg.x1, cfg.y0, cfg.y1 = x0, x1, y0, y1
-        cfg.warp_ax = cfg.warp_ay = warp
-        cfg.g, cfg.cfl = g, cfl
-        cfg.lax_friedrichs = 1 if lax_friedrichs else 0
-        cfg.forcing = ESDG_FORCING_MMS_SINE if forcing == "mms_sine" else ESDG_FORCING_NONE
-        cfg.mms_amp, cfg.mms_bamp, cfg.mms_u0, cfg.mms_v0 = mms
+        cfg = make_config(N, nx, ny, precision=precision, x0=x0, x1=x1, y0=y0, y1=y1, warp=warp, g=g, cfl=cfl,
+                          lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule)
         self.cfg = cfg
         h = ctypes.c_void_p()
         self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)

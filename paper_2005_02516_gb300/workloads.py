@@ -16,6 +16,12 @@ import math
 import numpy as np
 
 BASE_SEED = 20050251
+SYMMETRIC_POINTS = {1: 3, 2: 6, 3: 12, 4: 16, 5: 25}
+
+
+def volume_points(N, rule):
+    """Volume quadrature points per element for a degree and rule."""
+    return SYMMETRIC_POINTS[N] if rule == "symmetric" else (N + 1) ** 2
 
 
 @dataclasses.dataclass
@@ -34,6 +40,7 @@ class Workload:
     y0: float = -1.0
     y1: float = 1.0
     surface_init: bool = False   # initial q[0] is the free surface H = h + b
+    rule: str = "collapsed"      # volume rule: "collapsed" (exact to 2N+1) or "symmetric" (exact to 2N)
 
     @property
     def K(self):
@@ -42,6 +49,10 @@ class Workload:
     @property
     def Np(self):
         return (self.N + 1) * (self.N + 2) // 2
+
+    @property
+    def Nq(self):
+        return volume_points(self.N, self.rule)
 
     def bathymetry(self, x, y):
         return _BATHY[self.name](x, y)
@@ -99,9 +110,10 @@ LAKE_BUMP = Workload("lake_bump_k128_n2", N=2, nx=8, ny=8, warp=0.0, g=1.0, cfl=
 # Manufactured solution: N=3, 64x64 -> K=8192 curved, 1000 steps.
 MMS = Workload("mms_k8192_n3", N=3, nx=64, ny=64, warp=0.05, g=1.0, cfl=0.25,
                steps=1000, forcing="mms_sine")
-# Smoothed dam break: N=4, 256x256 -> K=131072 curved.
+# Smoothed dam break: N=4, 256x256 -> K=131072 curved, with the 16-point
+# symmetric volume rule exact to degree 2N = 8.
 DAM = Workload("dam_k131072_n4", N=4, nx=256, ny=256, warp=0.05, g=1.0, cfl=0.25,
-               steps=50, forcing="none")
+               steps=50, forcing="none", rule="symmetric")
 
 WORKLOADS = {w.name: w for w in (LAKE_BUMP, MMS, DAM)}
 
@@ -141,6 +153,7 @@ class Instance:
     warp: float = 0.05
     g: float = 1.0
     cfl: float = 0.25
+    rule: str = "symmetric"
 
     @property
     def K(self):
@@ -189,6 +202,7 @@ class Request:
     warp: float = 0.05
     g: float = 1.0
     cfl: float = 0.25
+    rule: str = "symmetric"
 
     @property
     def K(self):

@@ -31,10 +31,10 @@ def _built():
         __graft_entry__.build()
 
 
-def _member(N, nx, ny, seed):
+def _member(N, nx, ny, seed, rule="collapsed"):
     from paper_2005_02516_gb300 import esdg
     w = W.LAKE_BUMP
-    s = esdg.Solver(N, nx, ny, precision="fp32", warp=0.05, g=w.g, cfl=w.cfl)
+    s = esdg.Solver(N, nx, ny, precision="fp32", warp=0.05, g=w.g, cfl=w.cfl, rule=rule)
     xb, yb = s.points(esdg.ESDG_POINTS_NODAL)
     s.set_bathymetry(w.bathymetry(xb, yb))
     u = W.random_modal_state(s.K, s.Np, seed=seed)
@@ -42,13 +42,13 @@ def _member(N, nx, ny, seed):
     return s, u
 
 
-@pytest.mark.parametrize("nsteps", [3, 23])
-def test_ensemble_matches_members_alone(nsteps):
+@pytest.mark.parametrize("nsteps,rule", [(3, "collapsed"), (23, "collapsed"), (3, "symmetric"), (23, "symmetric")])
+def test_ensemble_matches_members_alone(nsteps, rule):
     from paper_2005_02516_gb300 import esdg
     mix, alone, u0 = [], [], []
     for i, (N, nx, ny) in enumerate(MEMBERS):
-        a, u = _member(N, nx, ny, W.BASE_SEED + i)
-        b, _ = _member(N, nx, ny, W.BASE_SEED + i)
+        a, u = _member(N, nx, ny, W.BASE_SEED + i, rule)
+        b, _ = _member(N, nx, ny, W.BASE_SEED + i, rule)
         mix.append(a)
         alone.append(b)
         u0.append(u)
@@ -67,14 +67,15 @@ def test_ensemble_matches_members_alone(nsteps):
     ens.close()
 
 
-def test_ensemble_member_matches_oracle():
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+def test_ensemble_member_matches_oracle(rule):
     from paper_2005_02516_gb300 import esdg
     N, nx, ny = 3, 5, 4
-    s, u = _member(N, nx, ny, W.BASE_SEED + 1)
-    other, _ = _member(4, 4, 4, W.BASE_SEED + 2)
+    s, u = _member(N, nx, ny, W.BASE_SEED + 1, rule)
+    other, _ = _member(4, 4, 4, W.BASE_SEED + 2, rule)
     ens = esdg.Ensemble([other, s])
     ens.step(12)
-    o = Oracle(N, nx, ny, ax=0.05, ay=0.05, g=W.LAKE_BUMP.g, cfl=W.LAKE_BUMP.cfl)
+    o = Oracle(N, nx, ny, ax=0.05, ay=0.05, g=W.LAKE_BUMP.g, cfl=W.LAKE_BUMP.cfl, rule=rule)
     xb, yb = o.points("nodal")
     o.set_bathymetry(W.LAKE_BUMP.bathymetry(xb, yb))
     uo, _ = o.run(u, 12)
@@ -91,3 +92,6 @@ def test_ensemble_rejects_fp64_and_forced_members():
     c = esdg.Solver(2, 4, 4, precision="fp32", forcing="mms_sine")
     with pytest.raises(esdg.EsdgError):
         esdg.Ensemble([a, c])
+    d, _ = _member(2, 4, 4, 1, "symmetric")
+    with pytest.raises(esdg.EsdgError):
+        esdg.Ensemble([a, d])

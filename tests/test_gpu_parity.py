@@ -34,15 +34,16 @@ def _built():
         __graft_entry__.build()
 
 
-def _solver(w, precision="fp64", lf=True, N=None, nx=None, ny=None):
+def _solver(w, precision="fp64", lf=True, N=None, nx=None, ny=None, rule=None):
     from paper_2005_02516_gb300.esdg import Solver
     N = w.N if N is None else N
     nx = w.nx if nx is None else nx
     ny = nx if ny is None else ny
+    rule = w.rule if rule is None else rule
     s = Solver(N, nx, ny, precision=precision, warp=w.warp, g=w.g, cfl=w.cfl, lax_friedrichs=lf,
-               forcing=w.forcing)
+               forcing=w.forcing, rule=rule)
     o = Oracle(N, nx, ny, ax=w.warp, ay=w.warp, g=w.g, cfl=w.cfl, lf=lf,
-               forcing=mms_sine_forcing if w.forcing == "mms_sine" else None)
+               forcing=mms_sine_forcing if w.forcing == "mms_sine" else None, rule=rule)
     from paper_2005_02516_gb300.esdg import ESDG_POINTS_NODAL
     xb, yb = s.points(ESDG_POINTS_NODAL)
     s.set_bathymetry(w.bathymetry(xb, yb))
@@ -70,10 +71,14 @@ CASES = [
 ]
 
 
+RULES = ["collapsed", "symmetric"]
+
+
+@pytest.mark.parametrize("rule", RULES)
 @pytest.mark.parametrize("lf", [True, False])
 @pytest.mark.parametrize("w,N,nx,ny", CASES)
-def test_rhs_fp64_matches_oracle(w, N, nx, ny, lf):
-    s, o = _solver(w, "fp64", lf, N, nx, ny)
+def test_rhs_fp64_matches_oracle(w, N, nx, ny, lf, rule):
+    s, o = _solver(w, "fp64", lf, N, nx, ny, rule)
     u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + N)
     s.set_state(u)
     t = 0.37
@@ -83,9 +88,10 @@ def test_rhs_fp64_matches_oracle(w, N, nx, ny, lf):
     assert _relmax(got, want) < 1e-12
 
 
-@pytest.mark.parametrize("w,N,nx,ny", CASES[:4])
-def test_rhs_fp32_matches_oracle(w, N, nx, ny):
-    s, o = _solver(w, "fp32", True, N, nx, ny)
+@pytest.mark.parametrize("rule", RULES)
+@pytest.mark.parametrize("w,N,nx,ny", CASES)
+def test_rhs_fp32_matches_oracle(w, N, nx, ny, rule):
+    s, o = _solver(w, "fp32", True, N, nx, ny, rule)
     u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + 10 + N)
     s.set_state(u)
     got = s.rhs(0.1).cpu().numpy()
@@ -120,13 +126,14 @@ def test_init_state_matches_oracle():
     assert _rel(s.get_state(), uo) < 1e-13
 
 
-def test_fp32_after_configured_steps_config1():
+@pytest.mark.parametrize("rule", RULES)
+def test_fp32_after_configured_steps_config1(rule):
     """Lake at rest plus a bump (N=2, K=128) for all 200 configured steps:
     FP32 RHS with FP64 accumulation
     within relative 1e-5 of the FP64 oracle; FP64 within 1e-12."""
     w = W.LAKE_BUMP
-    s64, o = _solver(w, "fp64")
-    s32, _ = _solver(w, "fp32")
+    s64, o = _solver(w, "fp64", rule=rule)
+    s32, _ = _solver(w, "fp32", rule=rule)
     xq, yq = o.points("volq")
     u0 = o.init_state(w.initial(xq, yq), surface=True)
     u, _ = o.run(u0, w.steps)
@@ -136,12 +143,13 @@ def test_fp32_after_configured_steps_config1():
         assert _rel(s.get_state(), u) < tol
 
 
-def test_lake_at_rest_and_entropy_on_gpu():
+@pytest.mark.parametrize("rule", RULES)
+def test_lake_at_rest_and_entropy_on_gpu(rule):
     """Theorem 2.2 on the GPU path: a lake at rest stays at rest, and with the
     EC flux alone the semi-discrete entropy rate vanishes.  Curved mesh,
     periodic continuous bathymetry, no forcing."""
     import dataclasses
-    w = dataclasses.replace(W.LAKE_BUMP, warp=0.05)
+    w = dataclasses.replace(W.LAKE_BUMP, warp=0.05, rule=rule)
     s, o = _solver(w, "fp64", lf=True, N=3, nx=6)
     from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
     xs, ys = s.points(ESDG_POINTS_VOLQ)
@@ -180,7 +188,8 @@ def test_nonpositive_depth_is_reported_not_faulted():
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-4)])
 def test_full_size_config3_sampled_rhs(precision, tol):
-    """Smoothed dam break at full size (N=4, K=131072 curved): the right-hand side on
+    """Smoothed dam break at full size (N=4, K=131072 curved, the 16-point
+    symmetric volume rule, as benchmarked): the right-hand side on
     sampled elements (every 997th, plus the first and last) against the
     oracle computed element by element, in the launch configuration the
     benchmark uses.  The smoothed dam break is at rest away from its front,

@@ -34,7 +34,8 @@ def _built():
 
 def _prepare(req, precision):
     from paper_2005_02516_gb300 import esdg
-    p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+    p = esdg.Problem(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl,
+                     rule=req.rule)
     xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
     xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
     return p, req.bathymetry(xb, yb), req.initial(xq, yq)
@@ -42,7 +43,8 @@ def _prepare(req, precision):
 
 def _alone(req, precision, b, q):
     from paper_2005_02516_gb300 import esdg
-    s = esdg.Solver(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl)
+    s = esdg.Solver(req.N, req.nx, req.nx, precision=precision, warp=req.warp, g=req.g, cfl=req.cfl,
+                    rule=req.rule)
     s.init_state(b, q, surface=True)
     s.step(req.steps)
     u = s.get_state()
@@ -50,9 +52,13 @@ def _alone(req, precision, b, q):
     return u
 
 
-def test_served_results_equal_alone():
+@pytest.mark.parametrize("rules", ["symmetric", "mixed"])
+def test_served_results_equal_alone(rules):
+    import dataclasses
     from paper_2005_02516_gb300 import esdg
     trace = W.served_trace(8, rate=50.0, seed=W.BASE_SEED + 5, k_range=(32, 800), steps_range=(3, 45))
+    if rules == "mixed":   # FP32 requests of both rules: one ensemble per rule
+        trace = [dataclasses.replace(r, rule="collapsed" if i % 2 else "symmetric") for i, r in enumerate(trace)]
     precisions = ["fp32", "fp32", "fp64", "fp32", "fp64", "fp32", "fp32", "fp64"]
     srv = esdg.Server(hbm_budget_bytes=4 << 30)
     t0 = time.perf_counter()

@@ -45,6 +45,7 @@ def _cfg(**kw):
     c.warp_ax = c.warp_ay = kw.get("warp", 0.0)
     c.g, c.cfl = kw.get("g", 1.0), 0.25
     c.lax_friedrichs, c.forcing = 1, 0
+    c.volume_rule = kw.get("rule", esdg.ESDG_RULE_COLLAPSED)
     return c
 
 
@@ -55,7 +56,8 @@ def _build(**kw):
     return lib, rc, h
 
 
-@pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7)])
+@pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7),
+                                 dict(rule=2), dict(rule=-1)])
 def test_build_rejects_bad_config(bad):
     lib, rc, h = _build(**bad)
     assert rc == esdg.ESDG_EINVAL
@@ -79,16 +81,21 @@ def test_calls_out_of_order_are_refused():
     lib.esdg_destroy(h)
 
 
-@pytest.mark.parametrize("N,warp", [(1, 0.0), (2, 0.05), (4, 0.05), (5, 0.0)])
-def test_points_and_sizes_match_oracle_conventions(N, warp):
+@pytest.mark.parametrize("N,warp,rule", [(1, 0.0, "collapsed"), (2, 0.05, "collapsed"), (4, 0.05, "collapsed"),
+                                         (5, 0.0, "collapsed"), (1, 0.05, "symmetric"), (2, 0.0, "symmetric"),
+                                         (3, 0.05, "symmetric"), (4, 0.05, "symmetric"), (5, 0.05, "symmetric")])
+def test_points_and_sizes_match_oracle_conventions(N, warp, rule):
+    # For the symmetric rule this compares two independent constructions (the
+    # host builder's and the oracle's Newton solves of the moment equations).
     from oracle import Oracle
-    lib, rc, h = _build(N=N, nx=5, ny=3, warp=warp)
+    code = esdg.ESDG_RULE_SYMMETRIC if rule == "symmetric" else esdg.ESDG_RULE_COLLAPSED
+    lib, rc, h = _build(N=N, nx=5, ny=3, warp=warp, rule=code)
     assert rc == 0
     K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     nb = ctypes.c_size_t()
     assert lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq),
                           ctypes.byref(nb)) == 0
-    o = Oracle(N, 5, 3, ax=warp, ay=warp)
+    o = Oracle(N, 5, 3, ax=warp, ay=warp, rule=rule)
     assert (K.value, Np.value, Nq.value, Nfq.value) == (o.K, o.Np, o.Nq, o.Nfq)
     assert nb.value > 0
     for kind, okind, n in [(esdg.ESDG_POINTS_NODAL, "nodal", Np.value), (esdg.ESDG_POINTS_VOLQ, "volq", Nq.value),

@@ -39,12 +39,17 @@ struct C2 {
     static constexpr int RPL = (D::Nh + LPE - 1) / LPE;     // hybrid rows per lane
     static constexpr int QPL = (D::Nq + LPE - 1) / LPE;     // volume nodes per lane
     static constexpr int MPL = (D::Np + LPE - 1) / LPE;     // modes per lane
-    static constexpr int OPB = (2 * RPL + 3) & ~3;          // operator entries per (column, lane slot)
+    // operator entries per (column, lane slot): a multiple of 4 with an odd
+    // quotient, so the 8 lanes' float4 reads of one column hit 8 distinct
+    // 4-bank groups
+    static constexpr int OPB = ((2 * RPL + 3) / 4) % 2 == 1 ? (2 * RPL + 3) / 4 * 4 : (2 * RPL + 3) / 4 * 4 + 4;
     static constexpr int RPLp = (RPL + 3) & ~3;
     static constexpr int QPLp = (QPL + 3) & ~3;
     static constexpr int MPLp = (MPL + 3) & ~3;
     static constexpr int NpP4 = (D::NpP + 3) & ~3;          // padded packed inverse-mass stride
-    static constexpr int UTS = D::Nh * 4 + 4;               // element slot of u~ / metric staging
+    // element slot of u~ / metric staging: the EPW elements' float4 records of
+    // one node fall in distinct 4-bank groups (slot stride not 0 or 16 mod 32)
+    static constexpr int UTS = ((D::Nh * 4 + 4) % 32 == 0 || (D::Nh * 4 + 4) % 32 == 16) ? D::Nh * 4 + 8 : D::Nh * 4 + 4;
     static constexpr int MIS = NpP4 + 4;                    // element slot of inverse-mass staging
     // operator region (floats)
     static constexpr int o_Qs = 0;                                  // [Nh][LPE][OPB]
@@ -122,19 +127,61 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return true;
 }
 
-// One field-per-lane application of the packed symmetric (M_h^k)^{-1}:
-// y (in registers) -> out.
-template <int Np>
-__device__ __forceinline__ void minv_apply(const float* __restrict__ M, const float (&y)[Np], float (&out)[Np]) {
+// Exact float -> double and round-to-nearest-even double -> float conversions
+// done on the integer pipes (the FP64 pipe, where the conversion instructions
+// run, is narrow on this part); zeros and normal numbers take the bit path,
+// everything else (subnormals, infinities, NaN, out-of-range) the built-in
+// conversion.
+__device__ __forceinline__ double f2d_bits(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t ex = (b >> 23) & 0xffu;
+    if (ex - 1u < 254u) {
+        const uint32_t man = b & 0x7fffffu;
+        return __hiloint2double((int)((b & 0x80000000u) | ((ex + 896u) << 20) | (man >> 3)), (int)(man << 29));
+    }
+    if ((b & 0x7fffffffu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return (double)x;
+}
+__device__ __forceinline__ float d2f_bits(double d) {
+    const uint32_t hi = (uint32_t)__double2hiint(d), lo = (uint32_t)__double2loint(d);
+    const uint32_t ex = (hi >> 20) & 0x7ffu;
+    if (ex - 897u < 254u) {
+        const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const uint32_t rest = lo & 0x1fffffffu;
+        uint32_t f = (hi & 0x80000000u) | ((ex - 896u) << 23) | m;
+        f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;
+        return __uint_as_float(f);
+    }
+    if ((hi & 0x7fffffffu) == 0u && lo == 0u) return __uint_as_float(hi & 0x80000000u);
+    return (float)d;
+}
+
+// Rows n = b + LPE j of (M_h^k)^{-1} y for the three fields; y[f][m] at
+// y + (f * Np + m) * EPW; M the packed lower triangle.
+template <int Np, int MPL, int LPE, int EPW>
+__device__ __forceinline__ void minv_rows(const float* __restrict__ M, const float* y, int b, float (&r0)[MPL],
+                                          float (&r1)[MPL], float (&r2)[MPL]) {
+    const float* rowp[MPL];
+    const float* colp[MPL];
 #pragma unroll
-    for (int n = 0; n < Np; ++n) out[n] = 0.f;
+    for (int j = 0; j < MPL; ++j) {
+        const int n = b + LPE * j;
+        rowp[j] = M + n * (n + 1) / 2;  // M[n][m] = rowp[m] for m <= n
+        colp[j] = M + n;                 // M[n][m] = colp[m (m + 1) / 2] for m > n
+        r0[j] = r1[j] = r2[j] = 0.f;
+    }
 #pragma unroll
-    for (int n = 0; n < Np; ++n) {
+    for (int m = 0; m < Np; ++m) {
+        const float y0 = y[(0 * Np + m) * EPW], y1 = y[(1 * Np + m) * EPW], y2 = y[(2 * Np + m) * EPW];
 #pragma unroll
-        for (int j = 0; j <= n; ++j) {
-            const float m = M[n * (n + 1) / 2 + j];
-            out[n] = fmaf(m, y[j], out[n]);
-            if (j < n) out[j] = fmaf(m, y[n], out[j]);
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            if (n < Np) {
+                const float mv = m <= n ? rowp[j][m] : colp[j][m * (m + 1) / 2];
+                r0[j] = fmaf(mv, y0, r0[j]);
+                r1[j] = fmaf(mv, y1, r1[j]);
+                r2[j] = fmaf(mv, y2, r2[j]);
+            }
         }
     }
 }
@@ -225,17 +272,18 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         a0[i] = a1[i] = a2[i] = 0.f;
     }
     const float* QsB = ops + C::o_Qs + b * C::OPB;
+    // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the row
+    // part is added once after the loop
 #define ESDG_PAIR(I, QR, QS)                                                   \
 {                                                                          \
     const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
     const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
     const float HU = fmaf(rh[I], ru[I], hum), HV = fmaf(rh[I], rv[I], hvm);\
-    const float Us = ru[I] + U.y, Vs = rv[I] + U.z;                        \
     const float T = fmaf(Qx, HU, Qy * HV);                                 \
     const float P = rh[I] * gH2;                                           \
     a0[I] += T;                                                            \
-    a1[I] = fmaf(Us, T, fmaf(Qx, P, a1[I]));                               \
-    a2[I] = fmaf(Vs, T, fmaf(Qy, P, a2[I]));                               \
+    a1[I] = fmaf(U.y, T, fmaf(Qx, P, a1[I]));                              \
+    a2[I] = fmaf(U.z, T, fmaf(Qy, P, a2[I]));                              \
 }
     for (int m = 0; m < D::Nq; ++m) {
         const float4 U = utE[m], G = geE[m];
@@ -264,6 +312,11 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
 #undef ESDG_PAIR
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+        a1[i] = fmaf(ru[i], a0[i], a1[i]);
+        a2[i] = fmaf(rv[i], a0[i], a2[i]);
+    }
     // ---- interface flux on the face rows ------------------------------------
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
@@ -407,23 +460,44 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
     __syncwarp();
-    // ---- du/dt = -(M_h^k)^{-1} s (field per lane) into ss as [field][element][mode]
+    // ---- du/dt = -(M_h^k)^{-1} s (modes n = b + LPE*j) into ss as [field][element][mode]
     const float* Mi = ws + C::w_mi + e * C::MIS;
     {
-        float y[D::Np], r[D::Np];
-        if (b < 3) {
-#pragma unroll
-            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
-        }
+        float r0[MPL], r1[MPL], r2[MPL];
+        minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
         __syncwarp();
-        if (b < 3) {
-            minv_apply<D::Np>(Mi, y, r);
 #pragma unroll
-            for (int n = 0; n < D::Np; ++n) ss[(b * EPW + e) * D::Np + n] = -r[n];
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            if (n < D::Np) {
+                ss[(0 * EPW + e) * D::Np + n] = -r0[j];
+                ss[(1 * EPW + e) * D::Np + n] = -r1[j];
+                ss[(2 * EPW + e) * D::Np + n] = -r2[j];
+            }
         }
     }
     __syncwarp();
     float* us = ws + C::s_u;
+    // b and w J at this lane's nodes for the projection, loaded before the RK
+    // update so their latency overlaps it
+    float bqv[QPL], wqv[QPL], blv[RPL];
+    if (MODE == 1) {
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            bqv[j] = 0.f;
+            wqv[j] = 0.f;
+            if (valid && q < D::Nq) {
+                bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
+                wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) {
+            const int l = b + LPE * j;
+            blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
+        }
+    }
     if (MODE == 0) {
         for (int j = lane; j < NRK; j += 32) {
             const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
@@ -441,33 +515,17 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                 double un = 1.0;
                 if (e0 + ee < K) {
                     const size_t gi = ((size_t)c * K + e0) * D::Np + o;
-                    const double rs = fma(rkA, rj[k], (double)(dtf * ss[j]));
+                    const double rs = fma(rkA, rj[k], f2d_bits(dtf * ss[j]));
                     un = fma(rkB, rs, uj[k]);
                     p.res[gi] = rs;
                     p.u[gi] = un;
                 }
-                us[(c * D::Np + n) * EPW + ee] = (float)un;
+                us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
             }
         }
     }
     __syncwarp();
     if (MODE == 1) {
-        float bqv[QPL], wqv[QPL], blv[RPL];
-#pragma unroll
-            for (int j = 0; j < QPL; ++j) {
-                const int q = b + LPE * j;
-                bqv[j] = 0.f;
-                wqv[j] = 0.f;
-                if (valid && q < D::Nq) {
-                    bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
-                    wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                const int l = b + LPE * j;
-                blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
-            }
         int bad = 0;
         // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
         {
@@ -536,14 +594,20 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             }
         }
         __syncwarp();
-        // v_h = (M_h^k)^{-1} y, in place (field per lane)
-        if (b < 3) {
-            float y[D::Np], r[D::Np];
+        // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
+        {
+            float r0[MPL], r1[MPL], r2[MPL];
+            minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
+            __syncwarp();
 #pragma unroll
-            for (int n = 0; n < D::Np; ++n) y[n] = ss[(b * D::Np + n) * EPW + e];
-            minv_apply<D::Np>(Mi, y, r);
-#pragma unroll
-            for (int n = 0; n < D::Np; ++n) ss[(b * D::Np + n) * EPW + e] = r[n];
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = r0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = r1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = r2[j];
+                }
+            }
         }
         __syncwarp();
         // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)

@@ -10,6 +10,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "esdg.h"
@@ -406,7 +407,7 @@ static cudaError_t d_geometry(esdg_ctx* c) {
     cudaError_t e = cudaErrorInvalidValue;
     if (c->cfg.precision == ESDG_FP32) {
         switch (kernel_nr(c->cfg)) {
-#define X(v) case v: e = project_geometry<v, float>(sms, c->lg_proj); if (!e) e = stage2_geometry<v>(sms, c->lg2); break;
+#define X(v) case v: e = stage2_geometry<v>(sms, c->lg2); break;
             ESDG_FOR_EACH_NR(X)
 #undef X
         }
@@ -419,10 +420,9 @@ static cudaError_t d_geometry(esdg_ctx* c) {
     }
     return e;
 }
-template <typename real>
-static cudaError_t d_project(int NR, const StageParams<real>& p, const LaunchGeom& lg, cudaStream_t s) {
+static cudaError_t d_project(int NR, const StageParams<double>& p, const LaunchGeom& lg, cudaStream_t s) {
     switch (NR) {
-#define X(v) case v: return launch_project<v, real>(p, lg, s);
+#define X(v) case v: return launch_project<v, double>(p, lg, s);
         ESDG_FOR_EACH_NR(X)
 #undef X
     }
@@ -478,7 +478,10 @@ static int project_current(esdg_ctx* c, const double* u_in, int target) {
     StageParams<real> p = make_params<real>(c);
     if (u_in) p.u_in = u_in;
     p.ut_out = ut_buf<real>(c, target);
-    CUDA_TRY(c, d_project<real>(kernel_nr(c->cfg), p, c->lg_proj, c->stream));
+    if constexpr (std::is_same<real, float>::value)
+        CUDA_TRY(c, d_stage(c, p, 2));  // the FP32 path's projection-only stage kernel
+    else
+        CUDA_TRY(c, d_project(kernel_nr(c->cfg), p, c->lg_proj, c->stream));
     return ESDG_OK;
 }
 

@@ -63,6 +63,8 @@ cudaError_t stage2_geometry(int num_sms, LaunchGeom& lg) {
     if (err != cudaSuccess) return err;
     err = cudaFuncSetAttribute(k_stage2<N, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
     if (err != cudaSuccess) return err;
+    err = cudaFuncSetAttribute(k_stage2<N, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
+    if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage2<N, 1>, lg.block, lg.smem);
     if (err != cudaSuccess) return err;
@@ -79,8 +81,10 @@ cudaError_t launch_stage2(const StageParams<float>& p, const float* ops2, int Kp
     const int grid = need < lg.grid ? need : lg.grid;
     if (mode == 0)
         k_stage2<N, 0><<<grid, lg.block, lg.smem, s>>>(p, ops2, Kpad);
-    else
+    else if (mode == 1)
         k_stage2<N, 1><<<grid, lg.block, lg.smem, s>>>(p, ops2, Kpad);
+    else
+        k_stage2<N, 2><<<grid, lg.block, lg.smem, s>>>(p, ops2, Kpad);
     return cudaGetLastError();
 }
 
@@ -95,9 +99,7 @@ cudaError_t launch_entropy(int K, double g, const double* u, const double* rhs, 
 }
 
 template cudaError_t stage_geometry<ESDG_N, double>(int, LaunchGeom&);
-template cudaError_t project_geometry<ESDG_N, float>(int, LaunchGeom&);
 template cudaError_t project_geometry<ESDG_N, double>(int, LaunchGeom&);
-template cudaError_t launch_project<ESDG_N, float>(const StageParams<float>&, const LaunchGeom&, cudaStream_t);
 template cudaError_t launch_project<ESDG_N, double>(const StageParams<double>&, const LaunchGeom&, cudaStream_t);
 template cudaError_t launch_stage<ESDG_N, double>(const StageParams<double>&, int, const LaunchGeom&, cudaStream_t);
 template cudaError_t stage2_geometry<ESDG_N>(int, LaunchGeom&);

@@ -207,6 +207,143 @@ __device__ __forceinline__ void gather_traces(const StageParams<float>& p, const
     }
 }
 
+// Entropy projection of a batch's new state (Sec. 2.6): u (FP32 modal, in us
+// as [field][mode][EPW]) -> u~ = u(Vh v_h) at the hybrid nodes, written to
+// ut_out as float4 (h, u, v, H).  Mi: the element's packed (M_h^k)^{-1};
+// ts, ss: scratch; bqv, wqv: b and w J at this lane's volume nodes q = b +
+// LPE j; blv: b at its hybrid rows.
+template <int N>
+__device__ __forceinline__ void stage2_project(const StageParams<float>& p, float* __restrict__ ut_out,
+                                               const float* __restrict__ ops, const float* Mi, const float* us,
+                                               float* ts, float* ss, int ge, int lane,
+                                               const float (&bqv)[C2<N>::QPL], const float (&wqv)[C2<N>::QPL],
+                                               const float (&blv)[C2<N>::RPL]) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const float g = p.g;
+    const float ig = 1.f / g;
+    const bool valid = ge < p.K;
+    int bad = 0;
+    // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
+    {
+        float q0[QPL], q1[QPL], q2[QPL];
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
+        for (int n = 0; n < D::Np; ++n) {
+            const float u0 = us[(0 * D::Np + n) * EPW + e];
+            const float u1 = us[(1 * D::Np + n) * EPW + e];
+            const float u2 = us[(2 * D::Np + n) * EPW + e];
+            const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                q0[j] = fmaf(v[j], u0, q0[j]);
+                q1[j] = fmaf(v[j], u1, q1[j]);
+                q2[j] = fmaf(v[j], u2, q2[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            if (q < D::Nq) {
+                float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                if (valid) {
+                    const float h = q0[j];
+                    if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                    const float ih = 1.f / h;
+                    const float uu = q1[j] * ih, vv = q2[j] * ih;
+                    const float wj = wqv[j];
+                    t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
+                    t1 = wj * uu;
+                    t2 = wj * vv;
+                }
+                ts[(0 * D::Nq + q) * EPW + e] = t0;
+                ts[(1 * D::Nq + q) * EPW + e] = t1;
+                ts[(2 * D::Nq + q) * EPW + e] = t2;
+            }
+        }
+    }
+    __syncwarp();
+    // y = Vq^T (w J v), modes n = b + LPE*j
+    {
+        float y0[MPL], y1[MPL], y2[MPL];
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+        for (int q = 0; q < D::Nq; ++q) {
+            const float t0 = ts[(0 * D::Nq + q) * EPW + e];
+            const float t1 = ts[(1 * D::Nq + q) * EPW + e];
+            const float t2 = ts[(2 * D::Nq + q) * EPW + e];
+            const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                y0[j] = fmaf(v[j], t0, y0[j]);
+                y1[j] = fmaf(v[j], t1, y1[j]);
+                y2[j] = fmaf(v[j], t2, y2[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            if (n < D::Np) {
+                ss[(0 * D::Np + n) * EPW + e] = y0[j];
+                ss[(1 * D::Np + n) * EPW + e] = y1[j];
+                ss[(2 * D::Np + n) * EPW + e] = y2[j];
+            }
+        }
+    }
+    __syncwarp();
+    // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
+    {
+        float r0[MPL], r1[MPL], r2[MPL];
+        minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            if (n < D::Np) {
+                ss[(0 * D::Np + n) * EPW + e] = r0[j];
+                ss[(1 * D::Np + n) * EPW + e] = r1[j];
+                ss[(2 * D::Np + n) * EPW + e] = r2[j];
+            }
+        }
+    }
+    __syncwarp();
+    // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
+    {
+        float v0[RPL], v1[RPL], v2[RPL];
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
+        for (int n = 0; n < D::Np; ++n) {
+            const float w0 = ss[(0 * D::Np + n) * EPW + e];
+            const float w1 = ss[(1 * D::Np + n) * EPW + e];
+            const float w2 = ss[(2 * D::Np + n) * EPW + e];
+            const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                v0[j] = fmaf(v[j], w0, v0[j]);
+                v1[j] = fmaf(v[j], w1, v1[j]);
+                v2[j] = fmaf(v[j], w2, v2[j]);
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                const int l = b + LPE * j;
+                if (l < D::Nh) {
+                    const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
+                    const float h = H - blv[j];
+                    if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                    if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
+                    *reinterpret_cast<float4*>(ut_out + ((size_t)ge * D::Nh + l) * 4) =
+                        make_float4(h, v1[j], v2[j], H);
+                }
+            }
+        }
+    }
+    if (bad) atomicOr(p.status, bad);
+}
+
 // One batch of EPW elements of one problem, starting at element e0 (all 32
 // lanes of the warp).  ops: the operator region of degree N in shared memory;
 // ws: this warp's region.  Returns false if the bounded wait on the bulk
@@ -525,125 +662,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
     __syncwarp();
-    if (MODE == 1) {
-        int bad = 0;
-        // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
-        {
-            float q0[QPL], q1[QPL], q2[QPL];
-#pragma unroll
-            for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
-            for (int n = 0; n < D::Np; ++n) {
-                const float u0 = us[(0 * D::Np + n) * EPW + e];
-                const float u1 = us[(1 * D::Np + n) * EPW + e];
-                const float u2 = us[(2 * D::Np + n) * EPW + e];
-                const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
-#pragma unroll
-                for (int j = 0; j < QPL; ++j) {
-                    q0[j] = fmaf(v[j], u0, q0[j]);
-                    q1[j] = fmaf(v[j], u1, q1[j]);
-                    q2[j] = fmaf(v[j], u2, q2[j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < QPL; ++j) {
-                const int q = b + LPE * j;
-                if (q < D::Nq) {
-                    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-                    if (valid) {
-                        const float h = q0[j];
-                        if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
-                        const float ih = 1.f / h;
-                        const float uu = q1[j] * ih, vv = q2[j] * ih;
-                        const float wj = wqv[j];
-                        t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
-                        t1 = wj * uu;
-                        t2 = wj * vv;
-                    }
-                    ts[(0 * D::Nq + q) * EPW + e] = t0;
-                    ts[(1 * D::Nq + q) * EPW + e] = t1;
-                    ts[(2 * D::Nq + q) * EPW + e] = t2;
-                }
-            }
-        }
-        __syncwarp();
-        // y = Vq^T (w J v), modes n = b + LPE*j
-        {
-            float y0[MPL], y1[MPL], y2[MPL];
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
-            for (int q = 0; q < D::Nq; ++q) {
-                const float t0 = ts[(0 * D::Nq + q) * EPW + e];
-                const float t1 = ts[(1 * D::Nq + q) * EPW + e];
-                const float t2 = ts[(2 * D::Nq + q) * EPW + e];
-                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
-#pragma unroll
-                for (int j = 0; j < MPL; ++j) {
-                    y0[j] = fmaf(v[j], t0, y0[j]);
-                    y1[j] = fmaf(v[j], t1, y1[j]);
-                    y2[j] = fmaf(v[j], t2, y2[j]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * D::Np + n) * EPW + e] = y0[j];
-                    ss[(1 * D::Np + n) * EPW + e] = y1[j];
-                    ss[(2 * D::Np + n) * EPW + e] = y2[j];
-                }
-            }
-        }
-        __syncwarp();
-        // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
-        {
-            float r0[MPL], r1[MPL], r2[MPL];
-            minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
-            __syncwarp();
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * D::Np + n) * EPW + e] = r0[j];
-                    ss[(1 * D::Np + n) * EPW + e] = r1[j];
-                    ss[(2 * D::Np + n) * EPW + e] = r2[j];
-                }
-            }
-        }
-        __syncwarp();
-        // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
-        {
-            float v0[RPL], v1[RPL], v2[RPL];
-#pragma unroll
-            for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
-            for (int n = 0; n < D::Np; ++n) {
-                const float w0 = ss[(0 * D::Np + n) * EPW + e];
-                const float w1 = ss[(1 * D::Np + n) * EPW + e];
-                const float w2 = ss[(2 * D::Np + n) * EPW + e];
-                const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    v0[j] = fmaf(v[j], w0, v0[j]);
-                    v1[j] = fmaf(v[j], w1, v1[j]);
-                    v2[j] = fmaf(v[j], w2, v2[j]);
-                }
-            }
-            if (valid) {
-#pragma unroll
-                for (int j = 0; j < RPL; ++j) {
-                    const int l = b + LPE * j;
-                    if (l < D::Nh) {
-                        const float H = (v0[j] + 0.5f * (v1[j] * v1[j] + v2[j] * v2[j])) * ig;
-                        const float h = H - blv[j];
-                        if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
-                        if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
-                        *reinterpret_cast<float4*>(ut_out + ((size_t)ge * D::Nh + l) * 4) =
-                            make_float4(h, v1[j], v2[j], H);
-                    }
-                }
-            }
-        }
-        if (bad) atomicOr(p.status, bad);
-    }
+    if constexpr (MODE == 1) stage2_project<N>(p, ut_out, ops, Mi, us, ts, ss, ge, lane, bqv, wqv, blv);
     // generic-proxy writes to the staging area must be ordered before the
     // next batch's bulk copies overwrite it
     fence_proxy_async_smem();
@@ -651,6 +670,58 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     return true;
 }
 
+// Projection-only batch: u~ of the EPW elements starting at e0 from the FP64
+// modal state p.u_in, into ut_out (the first u~ of a run of stages).
+template <int N>
+__device__ __forceinline__ bool project2_batch(const StageParams<float>& p, float* __restrict__ ut_out,
+                                               const float* __restrict__ ops, float* ws, uint64_t* bar,
+                                               uint32_t& parity, int e0, int lane) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const int K = p.K;
+    const int ge = e0 + e;
+    const bool valid = ge < K;
+    if (lane == 0) mbar_arrive_expect_tx(bar, EPW * C::NpP4 * 4);
+    __syncwarp();
+    if (lane < EPW) tma_bulk_g2s(ws + C::w_mi + lane * C::MIS, p.minv + (size_t)(e0 + lane) * C::NpP4, C::NpP4 * 4, bar);
+    float bqv[QPL], wqv[QPL], blv[RPL];
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = b + LPE * j;
+        bqv[j] = 0.f;
+        wqv[j] = 0.f;
+        if (valid && q < D::Nq) {
+            bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
+            wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int l = b + LPE * j;
+        blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
+    }
+    float* us = ws + C::s_u;
+    constexpr int NRK = 3 * EPW * D::Np;
+    for (int j = lane; j < NRK; j += 32) {
+        const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+        const int ee = o / D::Np, n = o - ee * D::Np;
+        const double un = e0 + ee < K ? p.u_in[((size_t)c * K + e0) * D::Np + o] : 1.0;
+        us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
+    }
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
+    parity ^= 1;
+    __syncwarp();
+    stage2_project<N>(p, ut_out, ops, ws + C::w_mi + e * C::MIS, us, ws + C::s_t, ws + C::s_s, ge, lane, bqv, wqv,
+                      blv);
+    fence_proxy_async_smem();
+    __syncwarp();
+    return true;
+}
+
+// MODE 0: du/dt into rhs_out; MODE 1: LSRK45 stage and projection of the new
+// state; MODE 2: projection of p.u_in only.
 template <int N, int MODE>
 __global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<float> p, const float* __restrict__ ops2, int Kpad) {
     typedef C2<N> C;
@@ -669,8 +740,12 @@ __global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<flo
     uint32_t parity = 0;
     const int nbatch = Kpad / C::EPW;
     for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps)
-        if (!stage2_batch<N, MODE>(p, p.ut_in, p.ut_out, p.rkA, p.rkB, ops, ws, bar, parity, batch * C::EPW, lane))
-            return;
+        if constexpr (MODE == 2) {
+            if (!project2_batch<N>(p, p.ut_out, ops, ws, bar, parity, batch * C::EPW, lane)) return;
+        } else {
+            if (!stage2_batch<N, MODE>(p, p.ut_in, p.ut_out, p.rkA, p.rkB, ops, ws, bar, parity, batch * C::EPW, lane))
+                return;
+        }
 }
 
 // ---- ensembles: several independent problems in one persistent launch --------

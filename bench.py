@@ -202,6 +202,28 @@ def time_steps(s, steps, warmup, world):
     return ev0.elapsed_time(ev1) / 1e3
 
 
+def precision_report(s64, nsteps):
+    """The FP32 path (FP32 right-hand side, FP64 RK accumulation) against the
+    FP64 path after the same nsteps from the same initial state: relative L2
+    difference of the modal state and the FP64 entropy diagnostics of both.
+    The FP64 path matches the FP64 oracle to relative 1e-12 per step (parity
+    tests), so it stands in for the oracle at this size."""
+    import numpy as np
+    s32 = make_solver("fp32")
+    dt = s64.dt()
+    s32.step(nsteps, dt, 0.0)
+    t = nsteps * dt
+    u32, u64 = s32.get_state(), s64.get_state()
+    S32, M32, R32 = s32.entropy(t)
+    S64, M64, R64 = s64.entropy(t)
+    s32.close()
+    return {"reference": "FP64 path after the same steps (parity-tested against the FP64 oracle)",
+            "steps": nsteps, "state_rel_l2": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)),
+            "entropy_rel": abs(S32 - S64) / abs(S64), "mass_rel": abs(M32 - M64) / abs(M64),
+            "entropy_rate_fp32": R32, "entropy_rate_fp64": R64,
+            "entropy_rate_rel": abs(R32 - R64) / max(abs(R64), 1e-300)}
+
+
 def time_e2e(s, steps, warmup):
     """Same metric through the public API with host buffers: per step, the
     state goes host -> device, one LSRK45 step runs, and the state comes back."""
@@ -312,6 +334,55 @@ def run_served(n, rate, precision, steps_range, k_range, budget_gb=64.0):
             "throughput": units / wall / 1e9, "unit": UNIT, "wall_s": wall, "iterations": iters}
 
 
+def run_volume_ratio(sizes=(16, 32, 50, 100, 150, 200), pairs_gpu=1 << 27, pairs_cpu=4_000_000):
+    """The volume-kernel cost comparison of Sec. 5.4: run time of the ESDG
+    flux-differencing volume term (Q o F) 1 over that of the traditional DG
+    products Q f, with random dense n x n operators (W.volume_ratio_inputs), on
+    the GPU (esdg_volume_kernel, FP32 and FP64, CUDA events, about pairs_gpu
+    operator entries x elements per launch, operators L2-resident) and on one
+    host core (esdg_volume_kernel_host, FP64, about pairs_cpu per call)."""
+    import torch
+    from paper_2005_02516_gb300 import esdg
+    kinds = {"dg": esdg.ESDG_VOLUME_DG, "esdg": esdg.ESDG_VOLUME_ESDG}
+    rows = []
+    for n in sizes:
+        K = max(512, pairs_gpu // (n * n))
+        Qx, Qy, u = W.volume_ratio_inputs(n, K)
+        row = {"n": n, "K_gpu": K}
+        for name, dt in (("gpu_fp32", torch.float32), ("gpu_fp64", torch.float64)):
+            dev = [torch.tensor(a, dtype=dt, device="cuda") for a in (Qx, Qy, u)]
+            out = torch.empty_like(dev[2])
+            t = {}
+            for kname, kind in kinds.items():
+                for _ in range(2):
+                    esdg.volume_kernel(kind, *dev, out=out)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev1 = torch.cuda.Event(enable_timing=True)
+                reps = 5
+                ev0.record()
+                for _ in range(reps):
+                    esdg.volume_kernel(kind, *dev, out=out)
+                ev1.record()
+                ev1.synchronize()
+                t[kname] = ev0.elapsed_time(ev1) / reps / 1e3
+            row[name] = {"t_dg_s": t["dg"], "t_esdg_s": t["esdg"], "ratio": t["esdg"] / t["dg"],
+                         "esdg_pairs_per_s": K * n * n / t["esdg"]}
+            del dev, out
+        Kc = max(1, pairs_cpu // (n * n))
+        hq = [a[..., :Kc, :] if a.ndim == 3 else a for a in (Qx, Qy, u)]
+        hq = [np.ascontiguousarray(a) for a in hq]
+        t = {}
+        for kname, kind in kinds.items():
+            esdg.volume_kernel(kind, *hq)
+            t0 = time.perf_counter()
+            esdg.volume_kernel(kind, *hq)
+            t[kname] = time.perf_counter() - t0
+        row["cpu_fp64"] = {"K": Kc, "cores": 1, "t_dg_s": t["dg"], "t_esdg_s": t["esdg"],
+                           "ratio": t["esdg"] / t["dg"]}
+        rows.append(row)
+    return rows
+
+
 def cpu_baseline(seconds_target=15.0):
     """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
     on a sample of 2048 consecutive elements of the same workload, repeated
@@ -381,6 +452,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-volume-ratio", action="store_true", help="skip the DG/ESDG volume-kernel cost comparison")
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 and ensemble legs (profiling runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="instances of the batched-ensemble leg (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=500)
@@ -437,14 +509,20 @@ def main():
     fp64 = None
     s.close()
     del s
+    precision = None
     if not args.fp32_only:
         s64 = make_solver("fp64")
         st64 = max(2, steps // 20)
         el64 = time_steps(s64, st64, 1, world)
         fp64 = {"value": K * Np * 5 * st64 / el64 / 1e9, "unit": UNIT, "ms_per_step": el64 / st64 * 1e3,
                 "steps": st64}
+        precision = precision_report(s64, 1 + st64)
         s64.close()
         del s64
+
+    volume_ratio = None
+    if not args.fp32_only and not args.no_volume_ratio and rank == 0:
+        volume_ratio = run_volume_ratio()
 
     ens = None
     if not args.fp32_only and args.ensemble > 0:
@@ -479,7 +557,7 @@ def main():
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other,
-                "fp64": fp64, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
+                "fp64": fp64, "precision": precision, "volume_ratio": volume_ratio, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))
     if world > 1:

@@ -269,6 +269,28 @@ int esdg_server_stats(esdg_server* srv, long long* iterations, long long* steps,
 /* Drops queued requests, waits for running ones, releases everything. */
 int esdg_server_destroy(esdg_server* srv);
 
+/*
+ * Volume-kernel cost comparison (Sec. 5.4): the traditional DG volume term
+ * against the ESDG flux-differencing term with dense n x n operators (the
+ * paper uses random entries), per element with n nodes:
+ *   ESDG_VOLUME_DG:   out = Q^x f^x(u) + Q^y f^y(u)            (eq. (SWE) fluxes)
+ *   ESDG_VOLUME_ESDG: out = (Q^x o F^x) 1 + (Q^y o F^y) 1,
+ *                     F^i[j][k] = f_S^i(u_j, u_k)              (eqs. (SWE_flux1/2))
+ * Qx, Qy: row-major [n][n] (Q[j][k] couples node k into row j); u, out:
+ * [3][K][n] conservative (h, hu, hv) and result; element type float
+ * (ESDG_FP32) or double (ESDG_FP64); h must be non-zero.  1 <= n <= 256.
+ * esdg_volume_kernel takes device pointers and launches on `stream`
+ * (asynchronous; ESDG_ECUDA on a launch failure); esdg_volume_kernel_host
+ * takes host pointers and computes on the calling thread.  ESDG_EINVAL for a
+ * bad kind, precision, size or null pointer.  Not part of the solver path.
+ */
+#define ESDG_VOLUME_DG 0
+#define ESDG_VOLUME_ESDG 1
+int esdg_volume_kernel(int kind, int precision, int n, int K, double g, const void* Qx, const void* Qy,
+                       const void* u, void* out, void* stream);
+int esdg_volume_kernel_host(int kind, int precision, int n, int K, double g, const void* Qx, const void* Qy,
+                            const void* u, void* out);
+
 /* The CFL time step of Sec. 4 for this configuration. */
 int esdg_dt(const esdg_ctx* ctx, double* dt);
 

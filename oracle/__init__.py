@@ -16,6 +16,8 @@ mesh      structured periodic triangulation, curved warp, geometric factors (Sec
 swe       entropy, entropy variables, EC flux (Sec. 2.4, 2.5, 2.8)
 esdg      semi-discrete right-hand side in the literal form of eq. (dgform),
           LSRK45 time stepping (Sec. 4), diagnostics
+volume    dense-operator volume terms of the ESDG and traditional DG kernels
+          (the cost comparison of Sec. 5.4)
 
 Every function cites the passage of the paper it follows.  Readings of
 passages that are silent, ambiguous or garbled are named where they are used.

@@ -33,6 +33,8 @@ ESDG_RULE_SYMMETRIC = 1
 ESDG_POINTS_NODAL = 0
 ESDG_POINTS_VOLQ = 1
 ESDG_POINTS_FACEQ = 2
+ESDG_VOLUME_DG = 0
+ESDG_VOLUME_ESDG = 1
 ESDG_INIT_DEPTH = 0
 ESDG_INIT_SURFACE = 1
 
@@ -45,7 +47,8 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_ensemble_create", "esdg_ensemble_autotune", "esdg_ensemble_step",
            "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
-           "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy"]
+           "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
+           "esdg_volume_kernel", "esdg_volume_kernel_host"]
 
 
 class EsdgError(RuntimeError):
@@ -113,6 +116,8 @@ def load_library(path=LIB_PATH):
         "esdg_server_drain": ([P, D], I),
         "esdg_server_stats": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PS], I),
         "esdg_server_destroy": ([P], I),
+        "esdg_volume_kernel": ([I, I, I, I, D, P, P, P, P, P], I),
+        "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -418,3 +423,30 @@ class Ensemble:
             self.close()
         except Exception:
             pass
+
+
+def volume_kernel(kind, Qx, Qy, u, g=1.0, out=None, stream=None):
+    """Volume term of the cost comparison of Sec. 5.4 (esdg_volume_kernel):
+    kind ESDG_VOLUME_DG (Q f) or ESDG_VOLUME_ESDG ((Q o F) 1).  Qx, Qy: (n, n);
+    u: (3, K, n); float32 or float64, all torch CUDA tensors (launch on the
+    current stream, or `stream`) or all numpy arrays (computed on the host,
+    one thread).  Returns out."""
+    lib = load_library()
+    n, K = u.shape[2], u.shape[1]
+    if isinstance(u, np.ndarray):
+        dt = u.dtype
+        prec = ESDG_FP32 if dt == np.float32 else ESDG_FP64
+        Qx, Qy, u = (np.ascontiguousarray(a, dtype=dt) for a in (Qx, Qy, u))
+        if out is None:
+            out = np.empty_like(u)
+        rc = lib.esdg_volume_kernel_host(kind, prec, n, K, g, _ptr(Qx), _ptr(Qy), _ptr(u), _ptr(out))
+    else:
+        import torch
+        prec = ESDG_FP32 if u.dtype == torch.float32 else ESDG_FP64
+        if out is None:
+            out = torch.empty_like(u)
+        st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+        rc = lib.esdg_volume_kernel(kind, prec, n, K, g, _ptr(Qx), _ptr(Qy), _ptr(u), _ptr(out), st)
+    if rc != ESDG_OK:
+        raise EsdgError(rc, "esdg_volume_kernel")
+    return out

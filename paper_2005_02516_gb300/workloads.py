@@ -243,6 +243,20 @@ def served_trace(n, rate, seed=BASE_SEED, k_range=(512, 131072), steps_range=(10
     return out
 
 
+def volume_ratio_inputs(n, K, seed=BASE_SEED, dtype=np.float64):
+    """Inputs of the volume-kernel cost comparison (Sec. 5.4): two n x n
+    operators with i.i.d. uniform [-1, 1] entries (the comparison uses random
+    matrices) and a smooth-looking random state (3, K, n) with depth
+    1 + U[0, 0.2] and momenta 0.1 N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    Qx = rng.uniform(-1.0, 1.0, size=(n, n))
+    Qy = rng.uniform(-1.0, 1.0, size=(n, n))
+    u = np.empty((3, K, n))
+    u[0] = 1.0 + 0.2 * rng.random((K, n))
+    u[1:] = 0.1 * rng.standard_normal((2, K, n))
+    return Qx.astype(dtype), Qy.astype(dtype), u.astype(dtype)
+
+
 def lake_at_rest_table_bathymetry(x, y):
     """Bathymetry of the lake-at-rest experiment of Sec. 4.1 as printed:
     b = 0.1 sin(2 pi x) cos(2 pi x) + 0.5 (periodic on [-1,1]^2)."""

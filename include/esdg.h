@@ -58,6 +58,11 @@ extern "C" {
 #define ESDG_RULE_SYMMETRIC 1  /* fully symmetric interior rule exact to degree 2N:
                                   3, 6, 12, 16, 25 points for N = 1..5 */
 
+/* domain boundary (Sec. 2.9): periodic, or reflective walls on all four
+   sides (exterior state h+ = h, u_n+ = -u_n, tangential velocity kept) */
+#define ESDG_BOUNDARY_PERIODIC 0
+#define ESDG_BOUNDARY_WALLS 1
+
 /* point sets for esdg_get_points */
 #define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
 #define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
@@ -80,6 +85,7 @@ typedef struct esdg_config {
     int forcing;            /* ESDG_FORCING_* */
     double mms_amp, mms_bamp, mms_u0, mms_v0;  /* ESDG_FORCING_MMS_SINE parameters */
     int volume_rule;        /* ESDG_RULE_* */
+    int boundary;           /* ESDG_BOUNDARY_* */
 } esdg_config;
 
 /*

@@ -83,9 +83,9 @@ class Oracle:
     """
 
     def __init__(self, N, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0,
-                 g=1.0, cfl=0.25, lf=True, forcing=None, rule="collapsed"):
+                 g=1.0, cfl=0.25, lf=True, forcing=None, rule="collapsed", walls=False):
         self.ref = RefElem(N, rule)
-        self.mesh = Mesh(self.ref, nx, ny, x0, x1, y0, y1, ax, ay)
+        self.mesh = Mesh(self.ref, nx, ny, x0, x1, y0, y1, ax, ay, walls=walls)
         self.N, self.K = N, self.mesh.K
         self.g, self.cfl, self.lf = g, cfl, lf
         self.forcing = forcing  # None or callable (x, y, t, g) -> (3, ...)
@@ -201,9 +201,17 @@ class Oracle:
         flat = ut[:, :, Nq:].reshape(3, -1)
         idx = (ks[:, None] * Nfq + np.arange(Nfq)[None, :]).ravel()
         uP = flat[:, m.mapP[idx]].reshape(3, ks.size, Nfq)
+        nxJ, nyJ, sJ = m.nxJ[ks], m.nyJ[ks], m.sJ[ks]
+        if m.walls:
+            # reflective wall (Sec. 2.9): exterior h+ = h and u_n+ = -u_n, the
+            # tangential velocity kept, i.e. the momentum mirrored in the wall
+            wall = np.repeat(m.wall[ks], self.N + 1, axis=1)          # (k, Nfq)
+            nx, ny = nxJ / sJ, nyJ / sJ
+            hun = uf[1] * nx + uf[2] * ny
+            mirror = np.stack([uf[0], uf[1] - 2.0 * hun * nx, uf[2] - 2.0 * hun * ny])
+            uP = np.where(wall[None], mirror, uP)
         fSx, fSy = swe.ec_flux(uP, uf, g)
         fx, fy = swe.physical_flux(uf, g)
-        nxJ, nyJ, sJ = m.nxJ[ks], m.nyJ[ks], m.sJ[ks]
         wf = ref.wf[None, :]
         surf_nodes = wf * (nxJ * (fSx - fx) + nyJ * (fSy - fy))
         if self.lf:

@@ -30,11 +30,14 @@ class Mesh:
     Geometric arrays are (K, Nh) over the Nq volume then Nfq face nodes:
     rxJ, sxJ, ryJ, syJ, J.  Face arrays are (K, Nfq): nxJ, nyJ, sJ.
     mapP (K*Nfq,) gives, for every face node, the flat index of the matching
-    face node on the neighbouring element (periodic wrap included).
+    face node on the neighbouring element (periodic wrap included).  With
+    walls=True the four sides are reflective walls (Sec. 2.9): a boundary face
+    has no partner, its nodes map to themselves and wall (K, 3) marks it.
     """
 
-    def __init__(self, ref, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0):
+    def __init__(self, ref, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0, walls=False):
         self.ref = ref
+        self.walls = walls
         self.nx, self.ny = nx, ny
         self.x0, self.x1, self.y0, self.y1 = x0, x1, y0, y1
         self.Lx, self.Ly = x1 - x0, y1 - y0
@@ -55,7 +58,10 @@ class Mesh:
         self.VX = np.zeros((K, 3))
         self.VY = np.zeros((K, 3))
         self.EToPV = np.zeros((K, 3), dtype=np.int64)  # periodic vertex ids
-        pv = lambda i, j: (j % ny) * nx + (i % nx)  # noqa: E731
+        if self.walls:
+            pv = lambda i, j: j * (nx + 1) + i  # noqa: E731
+        else:
+            pv = lambda i, j: (j % ny) * nx + (i % nx)  # noqa: E731
         for j in range(ny):
             for i in range(nx):
                 q = j * nx + i
@@ -149,7 +155,13 @@ class Mesh:
                 table.setdefault(key, []).append((e, f))
         self.EToE = np.zeros((K, 3), dtype=np.int64)
         self.EToF = np.zeros((K, 3), dtype=np.int64)
+        self.wall = np.zeros((K, 3), dtype=bool)
         for key, lst in table.items():
+            if self.walls and len(lst) == 1:
+                (e1, f1), = lst
+                self.EToE[e1, f1], self.EToF[e1, f1] = e1, f1
+                self.wall[e1, f1] = True
+                continue
             if len(lst) != 2:
                 raise ValueError("face %s is shared by %d elements" % (key, len(lst)))
             (e1, f1), (e2, f2) = lst
@@ -162,5 +174,8 @@ class Mesh:
             for f in range(3):
                 en, fn = self.EToE[e, f], self.EToF[e, f]
                 for i in range(Nfp):
-                    mapP[e * Nfq + f * Nfp + i] = en * Nfq + fn * Nfp + (Nfp - 1 - i)
+                    if self.wall[e, f]:
+                        mapP[e * Nfq + f * Nfp + i] = e * Nfq + f * Nfp + i
+                    else:
+                        mapP[e * Nfq + f * Nfp + i] = en * Nfq + fn * Nfp + (Nfp - 1 - i)
         self.mapP = mapP

@@ -381,6 +381,7 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.mstride = c->mstride;
     p.bh = reinterpret_cast<const real*>(d + c->L.bh);
     p.nbr = reinterpret_cast<const int*>(d + c->L.nbr);
+    p.walls = c->cfg.boundary == ESDG_BOUNDARY_WALLS;
     p.xq = reinterpret_cast<const real*>(d + c->L.xq);
     p.yq = reinterpret_cast<const real*>(d + c->L.yq);
     p.u = reinterpret_cast<double*>(d + c->L.u);
@@ -534,6 +535,8 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         return fail(nullptr, ESDG_EINVAL, "unknown forcing");
     if (cfg->volume_rule != ESDG_RULE_COLLAPSED && cfg->volume_rule != ESDG_RULE_SYMMETRIC)
         return fail(nullptr, ESDG_EINVAL, "unknown volume rule");
+    if (cfg->boundary != ESDG_BOUNDARY_PERIODIC && cfg->boundary != ESDG_BOUNDARY_WALLS)
+        return fail(nullptr, ESDG_EINVAL, "unknown boundary kind");
     esdg_ctx* c = new (std::nothrow) esdg_ctx();
     if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     c->cfg = *cfg;
@@ -542,7 +545,8 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         delete c;
         return fail(nullptr, ESDG_EINVAL, err);
     }
-    MeshSpec sp{cfg->nx, cfg->ny, cfg->x0, cfg->x1, cfg->y0, cfg->y1, cfg->warp_ax, cfg->warp_ay};
+    MeshSpec sp{cfg->nx, cfg->ny, cfg->x0, cfg->x1, cfg->y0, cfg->y1, cfg->warp_ax, cfg->warp_ay,
+                cfg->boundary == ESDG_BOUNDARY_WALLS};
     if (!build_mesh(c->ref, sp, c->mesh, err)) {
         delete c;
         return fail(nullptr, ESDG_EINVAL, err);

@@ -69,7 +69,8 @@ struct StageParams {
     const real* minv;  // [K][mstride] packed (M_h^k)^{-1}
     int mstride;       // element stride of minv (NpP rounded up to a multiple of 4)
     const real* bh;    // [K][Nh]   bathymetry at hybrid nodes
-    const int* nbr;    // [K][3]    4 * neighbour element + neighbour face
+    const int* nbr;    // [K][3]    4 * neighbour element + neighbour face (4 e + 3: wall)
+    int walls;         // reflective walls present (Sec. 2.9)
     const real* xq;    // [K][Nq]   (forcing only)
     const real* yq;
     // state
@@ -346,12 +347,25 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 const int face = f / D::Nfp, i = f - face * D::Nfp;
                 const int nb = p.nbr[(size_t)e * 3 + face];
                 const int en = nb >> 2, fn = nb & 3;
-                const real* up = p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4;
-                const real hP = up[0], uP = up[1], vP = up[2];
-                const real huP = hP * uP, hvP = hP * vP;
                 const real nr = ops[S::ops_nrs + 2 * f], ns = ops[S::ops_nrs + 2 * f + 1];
                 const real nxJ = real(8) * (rx_l * nr + sx_l * ns);
                 const real nyJ = real(8) * (ry_l * nr + sy_l * ns);
+                real hP, uP, vP;
+                if (fn == 3) {
+                    // reflective wall (Sec. 2.9): h+ = h, u_n+ = -u_n, tangential kept
+                    const real sJw = r_sqrt(nxJ * nxJ + nyJ * nyJ);
+                    const real wnx = nxJ / sJw, wny = nyJ / sJw;
+                    const real un = u_l * wnx + v_l * wny;
+                    hP = h_l;
+                    uP = u_l - real(2) * un * wnx;
+                    vP = v_l - real(2) * un * wny;
+                } else {
+                    const real* up = p.ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4;
+                    hP = up[0];
+                    uP = up[1];
+                    vP = up[2];
+                }
+                const real huP = hP * uP, hvP = hP * vP;
                 const real w = ops[S::ops_wf + f];
                 const real b_l = rl[11];
                 const real huA = real(0.5) * (hu_l + huP), hvA = real(0.5) * (hv_l + hvP);

@@ -201,8 +201,9 @@ __device__ __forceinline__ void gather_traces(const StageParams<float>& p, const
             const int face = f / D::Nfp, i = f - face * D::Nfp;
             const int nb = __ldg(p.nbr + (size_t)(e0 + ee) * 3 + face);
             const int en = nb >> 2, fn = nb & 3;
-            tv[t] = __ldg(reinterpret_cast<const float4*>(
-                ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4));
+            if (fn != 3)  // 3: a wall, whose exterior state is built from the own trace
+                tv[t] = __ldg(reinterpret_cast<const float4*>(
+                    ut_in + ((size_t)en * D::Nh + D::Nq + fn * D::Nfp + (D::Nfp - 1 - i)) * 4));
         }
     }
 }
@@ -464,11 +465,20 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             const float4 U = utE[l];
             const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
             const float h_l = U.x, b_l = U.w - U.x;
-            const float hP = tp.x, uP = tp.y, vP = tp.z;
-            const float huP = hP * uP, hvP = hP * vP;
             const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
             const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
             const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
+            float hP = tp.x, uP = tp.y, vP = tp.z;
+            if (p.walls && (__ldg(p.nbr + (size_t)ge * 3 + f / D::Nfp) & 3) == 3) {
+                // reflective wall (Sec. 2.9): h+ = h, u_n+ = -u_n, tangential kept
+                const float sJw = sqrtf(nxJ * nxJ + nyJ * nyJ);
+                const float wnx = nxJ / sJw, wny = nyJ / sJw;
+                const float un = ru[i] * wnx + rv[i] * wny;
+                hP = h_l;
+                uP = ru[i] - 2.f * un * wnx;
+                vP = rv[i] - 2.f * un * wny;
+            }
+            const float huP = hP * uP, hvP = hP * vP;
             const float w = ops[C::o_wf + f];
             const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
             const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);

@@ -533,11 +533,13 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
                     int ii = tri[t][v][0], jj = tri[t][v][1];
                     VX[3 * e + v] = sp.x0 + Lx * ii / nx;
                     VY[3 * e + v] = sp.y0 + Ly * jj / ny;
-                    PV[3 * e + v] = (jj % ny) * nx + (ii % nx);
+                    // periodic: wrapped vertex ids; walls: one id per grid vertex
+                    PV[3 * e + v] = sp.walls ? jj * (nx + 1) + ii : (jj % ny) * nx + (ii % nx);
                 }
             }
         }
-    // face matching by periodic vertex pairs
+    // face matching by (periodic) vertex pairs; with walls, a boundary face
+    // has no partner and is marked 4 e + 3 (its own element, face slot 3)
     D.nbr.assign(3 * size_t(K), -1);
     {
         std::map<std::pair<int, int>, std::vector<int>> faces;
@@ -548,6 +550,11 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
                 faces[{std::min(a, b), std::max(a, b)}].push_back(4 * e + f);
             }
         for (auto& kv : faces) {
+            if (sp.walls && kv.second.size() == 1) {
+                const int a = kv.second[0];
+                D.nbr[3 * (a >> 2) + (a & 3)] = 4 * (a >> 2) + 3;
+                continue;
+            }
             if (kv.second.size() != 2) { err = "a face is not shared by exactly two elements"; return false; }
             int a = kv.second[0], b = kv.second[1];
             D.nbr[3 * (a >> 2) + (a & 3)] = b;
@@ -651,6 +658,7 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
         for (int f = 0; f < 3; ++f) {
             int nb = D.nbr[3 * e + f];
             int en = nb >> 2, fn = nb & 3;
+            if (fn == 3) continue;  // wall
             for (int i = 0; i < Nfp; ++i) {
                 int a = e * Nfq + f * Nfp + i;
                 int b = en * Nfq + fn * Nfp + (Nfp - 1 - i);

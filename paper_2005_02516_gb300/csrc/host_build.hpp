@@ -51,6 +51,7 @@ struct MeshSpec {
     int nx, ny;
     double x0, x1, y0, y1;
     double ax, ay;
+    bool walls;  // reflective walls on the four sides instead of periodic wrap
 };
 
 // Mesh, connectivity and geometry.  Per-element arrays are [K][...].
@@ -62,7 +63,7 @@ struct MeshData {
     std::vector<double> geo;        // [K][Nh][4]: rxJ, sxJ, ryJ, syJ
     std::vector<double> Jq;         // [K][Nq]
     std::vector<double> minv;       // [K][Np(Np+1)/2] packed lower triangle of (M_h^k)^-1
-    std::vector<int> nbr;           // [K][3]: 4 * neighbour element + neighbour face
+    std::vector<int> nbr;           // [K][3]: 4 * neighbour element + neighbour face (4 e + 3: wall)
 };
 
 bool build_mesh(const RefOps& ref, const MeshSpec& spec, MeshData& mesh, std::string& err);

@@ -34,16 +34,16 @@ def _built():
         __graft_entry__.build()
 
 
-def _solver(w, precision="fp64", lf=True, N=None, nx=None, ny=None, rule=None):
+def _solver(w, precision="fp64", lf=True, N=None, nx=None, ny=None, rule=None, walls=False):
     from paper_2005_02516_gb300.esdg import Solver
     N = w.N if N is None else N
     nx = w.nx if nx is None else nx
     ny = nx if ny is None else ny
     rule = w.rule if rule is None else rule
     s = Solver(N, nx, ny, precision=precision, warp=w.warp, g=w.g, cfl=w.cfl, lax_friedrichs=lf,
-               forcing=w.forcing, rule=rule)
+               forcing=w.forcing, rule=rule, walls=walls)
     o = Oracle(N, nx, ny, ax=w.warp, ay=w.warp, g=w.g, cfl=w.cfl, lf=lf,
-               forcing=mms_sine_forcing if w.forcing == "mms_sine" else None, rule=rule)
+               forcing=mms_sine_forcing if w.forcing == "mms_sine" else None, rule=rule, walls=walls)
     from paper_2005_02516_gb300.esdg import ESDG_POINTS_NODAL
     xb, yb = s.points(ESDG_POINTS_NODAL)
     s.set_bathymetry(w.bathymetry(xb, yb))
@@ -207,3 +207,48 @@ def test_full_size_config3_sampled_rhs(precision, tol):
     got = s.rhs(0.0).cpu().numpy()[:, ks]
     want = o.rhs_elements(u, ks)
     assert _rel(got, want) < tol
+
+
+# ---- reflective walls (Sec. 2.9) -----------------------------------------------
+WALL_CASES = [(W.DAM, 4, 6, 5, "symmetric"), (W.DAM, 3, 5, 4, "collapsed"), (W.LAKE_BUMP, 2, 7, 3, "symmetric"),
+              (W.DAM, 5, 4, 3, "symmetric")]
+
+
+@pytest.mark.parametrize("lf", [True, False])
+@pytest.mark.parametrize("w,N,nx,ny,rule", WALL_CASES)
+def test_walls_rhs_matches_oracle(w, N, nx, ny, rule, lf):
+    for precision, tol in (("fp64", 1e-12), ("fp32", 5e-5)):
+        s, o = _solver(w, precision, lf, N, nx, ny, rule, walls=True)
+        u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + 20 + N)
+        s.set_state(u)
+        got = s.rhs(0.2).cpu().numpy()
+        want = o.rhs(u, 0.2)
+        assert _rel(got, want) < tol, precision
+        s.close()
+
+
+def test_walls_steps_and_lake_at_rest_on_gpu():
+    """The smoothed dam break in a walled box (its bump is not periodic):
+    FP64 steps match the oracle at 1e-12 per step, FP32 at 1e-5 after 20
+    steps; a lake at rest over the bump stays at rest on both paths."""
+    w = W.scaled(W.DAM, 6, 5)
+    s64, o = _solver(w, "fp64", walls=True)
+    s32, _ = _solver(w, "fp32", walls=True)
+    xq, yq = o.points("volq")
+    u = o.init_state(w.initial(xq, yq))
+    s64.set_state(u)
+    s32.set_state(u)
+    res = np.zeros_like(u)
+    t, dt = 0.0, o.dt()
+    for n in range(20):
+        u, res, t = o.step(u, res, t, dt)
+        s64.step(1, dt, t - dt)
+        assert _rel(s64.get_state(), u) < 1e-12, n
+    s32.step(20, dt, 0.0)
+    assert _rel(s32.get_state(), u) < 1e-5
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
+    for s in (s64, s32):
+        xs, ys = s.points(ESDG_POINTS_VOLQ)
+        s.init_state(None, np.stack([1.5 + 0 * xs, 0 * xs, 0 * xs]), surface=True)
+        # FP32: roundoff of O(Nh) flux terms of size g h^2 / dx ~ 10 per entry
+        assert np.abs(s.rhs().cpu().numpy()).max() < (1e-12 if s is s64 else 1e-4)

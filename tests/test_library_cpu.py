@@ -46,6 +46,7 @@ def _cfg(**kw):
     c.g, c.cfl = kw.get("g", 1.0), 0.25
     c.lax_friedrichs, c.forcing = 1, 0
     c.volume_rule = kw.get("rule", esdg.ESDG_RULE_COLLAPSED)
+    c.boundary = kw.get("boundary", esdg.ESDG_BOUNDARY_PERIODIC)
     return c
 
 
@@ -57,7 +58,7 @@ def _build(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7),
-                                 dict(rule=2), dict(rule=-1)])
+                                 dict(rule=2), dict(rule=-1), dict(boundary=2)])
 def test_build_rejects_bad_config(bad):
     lib, rc, h = _build(**bad)
     assert rc == esdg.ESDG_EINVAL
@@ -112,4 +113,20 @@ def test_points_and_sizes_match_oracle_conventions(N, warp, rule):
     dt = ctypes.c_double()
     assert lib.esdg_dt(h, ctypes.byref(dt)) == 0
     assert abs(dt.value - o.dt()) < 1e-15
+    lib.esdg_destroy(h)
+
+
+@pytest.mark.parametrize("N,rule", [(2, "collapsed"), (4, "symmetric")])
+def test_walled_mesh_points_match_oracle(N, rule):
+    # walls change the connectivity only: the same curved points and the same
+    # boundary nodes as the oracle's walled mesh
+    from oracle import Oracle
+    code = esdg.ESDG_RULE_SYMMETRIC if rule == "symmetric" else esdg.ESDG_RULE_COLLAPSED
+    lib, rc, h = _build(N=N, nx=5, ny=4, warp=0.05, rule=code, boundary=esdg.ESDG_BOUNDARY_WALLS)
+    assert rc == 0
+    o = Oracle(N, 5, 4, ax=0.05, ay=0.05, rule=rule, walls=True)
+    x, y = np.zeros((o.K, o.Nfq)), np.zeros((o.K, o.Nfq))
+    assert lib.esdg_get_points(h, esdg.ESDG_POINTS_FACEQ, x.ctypes.data, y.ctypes.data) == 0
+    xo, yo = o.points("faceq")
+    assert np.abs(x - xo).max() < 1e-13 and np.abs(y - yo).max() < 1e-13
     lib.esdg_destroy(h)

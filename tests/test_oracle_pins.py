@@ -583,3 +583,57 @@ def test_planted_missing_factor_two_breaks_consistency():
     o.ref.Qhs = 0.5 * o.ref.Qhs
     bad = _consistency_error(o)
     assert good < 5e-2 and bad > 20 * good
+
+
+# ---- reflective walls (Sec. 2.9) ---------------------------------------------
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("warp", [0.0, 0.05])
+def test_walls_lake_at_rest_nonperiodic_bathymetry(warp, rule):
+    """With walls the bathymetry need not be periodic: a lake at rest over the
+    smoothed dam-break bump stays at rest (well-balanced, Theorem 2.2, with
+    the mirrored exterior state of Sec. 2.9)."""
+    from paper_2005_02516_gb300 import workloads as W
+    o = Oracle(3, 5, 4, ax=warp, ay=warp, walls=True, rule=rule)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(W.DAM.bathymetry(xb, yb))
+    xq, yq = o.points("volq")
+    u = o.init_state(np.stack([1.5 + 0 * xq, 0 * xq, 0 * xq]), surface=True)
+    assert np.abs(o.rhs(u)).max() < 1e-12
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("lf", [False, True])
+def test_walls_mass_and_entropy(lf, rule):
+    """No mass crosses a wall (the mirrored state makes {h u_n} = 0); with the
+    EC flux alone the semi-discrete entropy rate still vanishes, with
+    Lax-Friedrichs it is negative."""
+    from paper_2005_02516_gb300 import workloads as W
+    o = Oracle(3, 5, 4, ax=0.05, ay=0.05, lf=lf, walls=True, rule=rule)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(W.DAM.bathymetry(xb, yb))
+    u = W.random_modal_state(o.K, o.Np, seed=5)
+    r = o.rhs(u)
+    assert abs(o.mass(r)) < 1e-14 * abs(o.mass(u))
+    terms = o.entropy_rate_terms(u, r)
+    if lf:
+        assert terms.sum() < -1e-3 * np.abs(terms).sum()
+    else:
+        assert abs(terms.sum()) < 1e-13 * np.abs(terms).sum()
+
+
+def test_walls_reduce_to_periodic_away_from_the_boundary():
+    """Elements with no wall face get the same right-hand side on the walled
+    and the periodic mesh when the state is the same (walls act only through
+    boundary faces)."""
+    from paper_2005_02516_gb300 import workloads as W
+    ow = Oracle(2, 6, 6, ax=0.05, ay=0.05, walls=True)
+    op = Oracle(2, 6, 6, ax=0.05, ay=0.05, walls=False)
+    u = W.random_modal_state(ow.K, ow.Np, seed=9)
+    rw, rp = ow.rhs(u), op.rhs(u)
+    interior = ~ow.mesh.wall.any(axis=1)
+    # the projection is element-local, so interior elements whose neighbours
+    # are interior too see identical data
+    nb_int = interior & np.all(interior[ow.mesh.EToE], axis=1)
+    assert nb_int.sum() > 0
+    assert np.abs(rw[:, nb_int] - rp[:, nb_int]).max() < 1e-13 * np.abs(rp).max()
+    assert np.abs(rw[:, ~interior] - rp[:, ~interior]).max() > 1e-6

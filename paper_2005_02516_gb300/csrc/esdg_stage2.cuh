@@ -423,6 +423,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     a1[I] = fmaf(U.y, T, fmaf(Qx, P, a1[I]));                              \
     a2[I] = fmaf(U.z, T, fmaf(Qy, P, a2[I]));                              \
 }
+#pragma unroll 2
     for (int m = 0; m < D::Nq; ++m) {
         const float4 U = utE[m], G = geE[m];
         const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
@@ -434,6 +435,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             if (2 * i2 + 1 < RPL) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
         }
     }
+#pragma unroll 2
     for (int m = D::Nq; m < D::Nh; ++m) {
         const float4 U = utE[m], G = geE[m];
         const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
@@ -748,6 +750,10 @@ __global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<flo
     uint64_t* bar = &bars[warp];
     float* ws = ops + C::o_end + warp * C::w_end;
     uint32_t parity = 0;
+    // Warps that share a scheduler (warp, warp + 4, ...) start a fraction of a
+    // batch apart, so their memory-latency phases do not coincide (identical
+    // per-batch work otherwise keeps them in lockstep).
+    __nanosleep((unsigned)(warp >> 2) * 1300u);
     const int nbatch = Kpad / C::EPW;
     for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps)
         if constexpr (MODE == 2) {

@@ -530,7 +530,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                 if (e0 + o / D::Np < K) {
                     const size_t gi = ((size_t)c * K + e0) * D::Np + o;
                     uj[k] = p.u[gi];
-                    rj[k] = p.res[gi];
+                    if (rkA != 0.0) rj[k] = p.res[gi];  // the first LSRK45 stage (A = 0) does not read it
                 }
             }
         }

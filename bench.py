@@ -226,22 +226,21 @@ def precision_report(s64, nsteps):
 
 def time_e2e(s, steps, warmup):
     """Same metric through the public API with host buffers: per step, the
-    state goes host -> device, one LSRK45 step runs, and the state comes back."""
+    state goes host -> device, one LSRK45 step runs, and the state comes back
+    (esdg_step_host: the projection kernel reads the pinned host state over the
+    host link and the last stage writes the result back, one call and one
+    synchronisation per step)."""
     import torch
     host_in = torch.empty((3, s.K, s.Np), dtype=torch.float64, pin_memory=True).numpy()
     host_out = torch.empty((3, s.K, s.Np), dtype=torch.float64, pin_memory=True).numpy()
     s.get_state(host_in)
     dt = s.dt()
     for _ in range(max(1, warmup)):
-        s.set_state(host_in)
-        s.step(1, dt, 0.0)
-        s.get_state(host_out)
+        s.step_host(host_in, 1, dt, 0.0, out=host_out)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(steps):
-        s.set_state(host_in)
-        s.step(1, dt, 0.0)
-        s.get_state(host_out)
+        s.step_host(host_in, 1, dt, 0.0, out=host_out)
         host_in, host_out = host_out, host_in
     torch.cuda.synchronize()
     el = time.perf_counter() - t0

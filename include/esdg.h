@@ -177,6 +177,18 @@ int esdg_rhs(esdg_ctx* ctx, double t, const double* u_in, double* rhs_out);
  */
 int esdg_step(esdg_ctx* ctx, int nsteps, double dt, double* t_inout);
 
+/*
+ * esdg_step_host -- esdg_set_state + esdg_step + esdg_copy_state for a state
+ * that lives in host memory, without separate copies: the projection kernel
+ * reads u_host ([3][K][Np] FP64) directly over the host link and stores it as
+ * the RK state (residual zeroed), nsteps steps run as in esdg_step, and the
+ * last stage kernel writes the new state to u_out_host.  Both buffers must be
+ * host memory the device can address (cudaHostAlloc / cudaHostRegister, or
+ * managed memory), else ESDG_EINVAL; they may be the same buffer.
+ * Synchronises once and reports device flags like esdg_step.
+ */
+int esdg_step_host(esdg_ctx* ctx, const double* u_host, int nsteps, double dt, double* t_inout, double* u_out_host);
+
 /* Enqueue nsteps steps without synchronising or checking flags (for timing
  * loops and graph capture); esdg_check() reads the flags later. */
 int esdg_step_async(esdg_ctx* ctx, int nsteps, double dt, double t0);

@@ -475,9 +475,10 @@ static int check_status(esdg_ctx* c) {
 }
 
 template <typename real>
-static int project_current(esdg_ctx* c, const double* u_in, int target) {
+static int project_current(esdg_ctx* c, const double* u_in, int target, bool copy_in = false) {
     StageParams<real> p = make_params<real>(c);
     if (u_in) p.u_in = u_in;
+    p.copy_in = copy_in ? 1 : 0;  // also store u_in as the state, residual zeroed
     p.ut_out = ut_buf<real>(c, target);
     if constexpr (std::is_same<real, float>::value)
         CUDA_TRY(c, d_stage(c, p, 2));  // the FP32 path's projection-only stage kernel
@@ -498,8 +499,10 @@ static int rhs_t(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
     return ESDG_OK;
 }
 
+// nsteps LSRK45 steps; if u_out is set, the last stage also writes the new
+// state there (a host buffer the device can write).
 template <typename real>
-static int step_t(esdg_ctx* c, int nsteps, double dt, double t0) {
+static int step_t(esdg_ctx* c, int nsteps, double dt, double t0, double* u_out = nullptr) {
     if (!c->ut_valid) {
         int rc = project_current<real>(c, nullptr, c->cur);
         if (rc) return rc;
@@ -514,6 +517,7 @@ static int step_t(esdg_ctx* c, int nsteps, double dt, double t0) {
             p.rkA = RK_A[s];
             p.rkB = RK_B[s];
             p.t = t0 + n * dt + RK_C[s] * dt;
+            p.u_out = (n == nsteps - 1 && s == 4) ? u_out : nullptr;
             CUDA_TRY(c, d_stage(c, p, 1));
             c->cur ^= 1;
         }
@@ -692,6 +696,44 @@ int esdg_step_async(esdg_ctx* c, int nsteps, double dt, double t0) {
     if (nsteps < 0) return fail(c, ESDG_EINVAL, "nsteps < 0");
     if (!(dt > 0)) esdg_dt(c, &dt);
     return c->cfg.precision == ESDG_FP32 ? step_t<float>(c, nsteps, dt, t0) : step_t<double>(c, nsteps, dt, t0);
+}
+
+// A host buffer the device can address directly (pinned or registered host
+// memory, or managed memory): its device-side address, else nullptr.
+static const void* device_view(const void* host) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost && a.type != cudaMemoryTypeManaged) return nullptr;
+    return a.devicePointer;
+}
+
+int esdg_step_host(esdg_ctx* c, const double* u_host, int nsteps, double dt, double* t_inout, double* u_out_host) {
+    if (!valid(c) || !u_host || !u_out_host) return fail(nullptr, ESDG_EINVAL, "null argument");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (nsteps < 1) return fail(c, ESDG_EINVAL, "nsteps < 1");
+    const double* din = static_cast<const double*>(device_view(u_host));
+    double* dout = static_cast<double*>(const_cast<void*>(device_view(u_out_host)));
+    if (!din || !dout)
+        return fail(c, ESDG_EINVAL, "esdg_step_host: buffers must be host memory the device can address "
+                                    "(cudaHostAlloc / cudaHostRegister or managed)");
+    if (!(dt > 0)) esdg_dt(c, &dt);
+    const double t0 = t_inout ? *t_inout : 0.0;
+    const bool fp32 = c->cfg.precision == ESDG_FP32;
+    // the projection kernel reads the state over the host link and stores it
+    // as the RK state (residual zeroed); the last stage writes the result back
+    c->cur = 0;
+    int rc = fp32 ? project_current<float>(c, din, c->cur, true) : project_current<double>(c, din, c->cur, true);
+    if (rc) return rc;
+    c->ut_valid = true;
+    rc = fp32 ? step_t<float>(c, nsteps, dt, t0, dout) : step_t<double>(c, nsteps, dt, t0, dout);
+    if (rc) return rc;
+    rc = check_status(c);
+    if (rc) return rc;
+    if (t_inout) *t_inout = t0 + nsteps * dt;
+    return ESDG_OK;
 }
 
 int esdg_check(esdg_ctx* c) {

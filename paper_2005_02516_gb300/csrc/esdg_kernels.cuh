@@ -78,6 +78,8 @@ struct StageParams {
     double* u;           // [3][K][Np]  RK state (updated in place)
     double* res;         // [3][K][Np]  RK residual
     double* rhs_out;     // [3][K][Np]  RHS mode output
+    double* u_out;       // [3][K][Np]  if set: the stage's new state also written here (host-state calls)
+    int copy_in;         // projection of u_in: also store u_in into u and zero res
     const real* ut_in;   // [K][Nh][4]  entropy-projected (h, u, v, H) of this stage
     real* ut_out;        // [K][Nh][4]  ... of the next stage
     double rkA, rkB, dt, t;
@@ -269,7 +271,13 @@ __global__ void __launch_bounds__(256) k_project(StageParams<real> p) {
         load_minv<N, real>(p, ws, e, lane);
         for (int i = lane; i < 3 * D::Np; i += 32) {
             int c = i / D::Np, n = i - c * D::Np;
-            ws[S::w_b + i] = (real)p.u_in[((size_t)c * p.K + e) * D::Np + n];
+            const size_t gi = ((size_t)c * p.K + e) * D::Np + n;
+            const double un = p.u_in[gi];
+            ws[S::w_b + i] = (real)un;
+            if (p.copy_in) {
+                p.u[gi] = un;
+                p.res[gi] = 0.0;
+            }
         }
         __syncwarp();
         project_element<N, real>(p, ops, ws, e, lane);
@@ -469,6 +477,7 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 p.res[gi] = rs;
                 const double un = p.u[gi] + p.rkB * rs;
                 p.u[gi] = un;
+                if (p.u_out) p.u_out[gi] = un;
                 sb[i] = (real)un;
             }
         }

@@ -668,6 +668,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                     un = fma(rkB, rs, uj[k]);
                     p.res[gi] = rs;
                     p.u[gi] = un;
+                    if (p.u_out) p.u_out[gi] = un;
                 }
                 us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
             }
@@ -719,8 +720,13 @@ __device__ __forceinline__ bool project2_batch(const StageParams<float>& p, floa
     for (int j = lane; j < NRK; j += 32) {
         const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
         const int ee = o / D::Np, n = o - ee * D::Np;
-        const double un = e0 + ee < K ? p.u_in[((size_t)c * K + e0) * D::Np + o] : 1.0;
+        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+        const double un = e0 + ee < K ? p.u_in[gi] : 1.0;
         us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
+        if (p.copy_in && e0 + ee < K) {
+            p.u[gi] = un;
+            p.res[gi] = 0.0;
+        }
     }
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
     parity ^= 1;

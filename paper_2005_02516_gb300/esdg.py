@@ -50,7 +50,7 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
            "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
-           "esdg_volume_kernel", "esdg_volume_kernel_host"]
+           "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host"]
 
 
 class EsdgError(RuntimeError):
@@ -120,6 +120,7 @@ def load_library(path=LIB_PATH):
         "esdg_server_destroy": ([P], I),
         "esdg_volume_kernel": ([I, I, I, I, D, P, P, P, P, P], I),
         "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
+        "esdg_step_host": ([P, P, I, D, PD, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -367,6 +368,18 @@ class Solver:
         tt = ctypes.c_double(t)
         self._check(self.lib.esdg_step(self.h, nsteps, dt, ctypes.byref(tt)))
         return tt.value
+
+    def step_host(self, u_in, nsteps=1, dt=0.0, t=0.0, out=None):
+        """esdg_step_host: the state u_in (host [3][K][Np] float64 in pinned
+        memory, e.g. a numpy view of a torch pin_memory tensor) is read by the
+        device directly, nsteps steps run and the result is written to out
+        (pinned host memory; default: u_in itself).  Returns (out, t)."""
+        out = u_in if out is None else out
+        for a in (u_in, out):
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (3, self.K, self.Np)
+        tt = ctypes.c_double(t)
+        self._check(self.lib.esdg_step_host(self.h, _ptr(u_in), nsteps, dt, ctypes.byref(tt), _ptr(out)))
+        return out, tt.value
 
     def step_async(self, nsteps, dt=0.0, t=0.0):
         self._check(self.lib.esdg_step_async(self.h, nsteps, dt, t))

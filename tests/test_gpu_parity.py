@@ -252,3 +252,36 @@ def test_walls_steps_and_lake_at_rest_on_gpu():
         s.init_state(None, np.stack([1.5 + 0 * xs, 0 * xs, 0 * xs]), surface=True)
         # FP32: roundoff of O(Nh) flux terms of size g h^2 / dx ~ 10 per entry
         assert np.abs(s.rhs().cpu().numpy()).max() < (1e-12 if s is s64 else 1e-4)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_host_equals_set_step_copy(precision):
+    """esdg_step_host (the device reads the pinned host state and writes the
+    result back) gives exactly the state of set_state + step + copy_state."""
+    from paper_2005_02516_gb300.esdg import EsdgError, ESDG_EINVAL
+    w = W.scaled(W.DAM, 7, 5)
+    s, o = _solver(w, precision)
+    u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + 31)
+    host = torch.empty((3, o.K, o.Np), dtype=torch.float64, pin_memory=True).numpy()
+    out = torch.empty((3, o.K, o.Np), dtype=torch.float64, pin_memory=True).numpy()
+    host[:] = u
+    dt = o.dt()
+    _, t = s.step_host(host, 3, dt, 0.0, out=out)
+    assert abs(t - 3 * dt) < 1e-15
+    s2, _ = _solver(w, precision)
+    s2.set_state(u)
+    s2.step(3, dt, 0.0)
+    assert np.array_equal(out, s2.get_state())
+    assert np.array_equal(host, u)                     # the input is left alone
+    # in place (a host-state call always starts from the host state, like
+    # set_state), and the device state follows
+    host[:] = out
+    s.step_host(host, 2, dt, 3 * dt)
+    s2.set_state(out)
+    s2.step(2, dt, 3 * dt)
+    assert np.array_equal(host, s2.get_state()) and np.array_equal(s.get_state(), host)
+    # pageable host memory is refused, the context stays usable
+    with pytest.raises(EsdgError) as ei:
+        s.step_host(np.array(u), 1, dt)
+    assert ei.value.code == ESDG_EINVAL
+    s.step(1, dt)

@@ -41,7 +41,6 @@ k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_ba
     uint64_t* bar = &bars[warp];
     float* ws = sm + ops_end + warp * slab;
     uint32_t parity = 0;
-    __nanosleep((unsigned)(warp >> 2) * 1300u);  // stagger warps that share a scheduler (see k_stage2)
     for (int gb = blockIdx.x * nwarps + warp; gb < total_batches; gb += gridDim.x * nwarps) {
         int lo = 0, hi = nmem - 1;  // the member whose batch range holds gb
         while (lo < hi) {

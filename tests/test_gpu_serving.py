@@ -116,3 +116,40 @@ def test_request_larger_than_budget_is_refused():
     assert ei.value.code == esdg.ESDG_EBUSY
     p.close()
     srv.close()
+
+
+def test_failing_request_does_not_disturb_the_others():
+    """A request whose depth is negative somewhere fails with
+    ESDG_ENONPOSITIVE or ESDG_ENONFINITE (the device status word of its own
+    context) while the
+    requests batched with it, FP32 in the same ensemble launch and FP64 beside
+    it, finish with the same states as alone."""
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(6, rate=1000.0, seed=W.BASE_SEED + 7, k_range=(60, 300), steps_range=(8, 12),
+                           degrees=(2, 3))
+    precisions = ["fp32", "fp32", "fp64", "fp32", "fp64", "fp32"]
+    bad = {1, 4}
+    srv = esdg.Server(hbm_budget_bytes=4 << 30)
+    tickets, inputs = [], []
+    for i, (req, prec) in enumerate(zip(trace, precisions)):
+        p, b, q = _prepare(req, prec)
+        if i in bad:
+            q = q.copy()
+            q[0, 0, 0] = -1.0          # a dry point with negative depth
+        tickets.append(srv.submit(p, b, q, req.steps, surface=False if i in bad else True))
+        inputs.append((b, q))
+    srv.drain(300.0)
+    for i, (tk, req, prec, (b, q)) in enumerate(zip(tickets, trace, precisions, inputs)):
+        state = srv.query(tk)[0]
+        if i in bad:
+            # the first stage flags the depth (and, from the division by it,
+            # non-finite values): either status reports the failed request
+            assert state in (esdg.ESDG_ENONPOSITIVE, esdg.ESDG_ENONFINITE)
+            continue
+        assert state == 2
+        want = _alone(req, prec, b, q)
+        got = srv.result(tk)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
+    assert srv.stats()[2] == 0        # every request's device memory returned
+    srv.close()

@@ -655,6 +655,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     } else {
         // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
         const float dtf = (float)p.dt;
+        double* const u_out = p.u_out;  // host-state calls: the last stage also writes the state there
 #pragma unroll
         for (int k = 0; k < C::RKL; ++k) {
             const int j = lane + 32 * k;
@@ -668,7 +669,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                     un = fma(rkB, rs, uj[k]);
                     p.res[gi] = rs;
                     p.u[gi] = un;
-                    if (p.u_out) p.u_out[gi] = un;
+                    if (u_out) u_out[gi] = un;
                 }
                 us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
             }

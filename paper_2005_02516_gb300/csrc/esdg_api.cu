@@ -1002,7 +1002,7 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
     }
     int rc = ensemble_table(e);
     if (!rc) {
-        int w = 12;
+        int w = ENSEMBLE_MAX_WARPS;
         while (w > 1 && !ensemble_fits(e, w)) --w;
         rc = ensemble_set_shape(e, w);
     }
@@ -1084,7 +1084,7 @@ int esdg_ensemble_autotune(esdg_ensemble* e, int* warps_out, int* order_out) {
     for (int o = 0; o < 2 && !rc; ++o) {
         e->order = o == 0 ? given : bydeg;
         rc = ensemble_table(e);
-        for (int w : {8, 10, 12}) {
+        for (int w : {ENSEMBLE_MAX_WARPS - 4, ENSEMBLE_MAX_WARPS - 2, ENSEMBLE_MAX_WARPS}) {
             if (rc || !ensemble_fits(e, w)) continue;
             rc = ensemble_set_shape(e, w);
             if (!rc) rc = ensemble_prepare(e);

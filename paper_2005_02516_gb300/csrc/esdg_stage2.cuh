@@ -782,7 +782,7 @@ struct EnsembleMember {
     int batch_begin, nbatch;
 };
 
-constexpr int ENSEMBLE_MAX_WARPS = 12;
+constexpr int ENSEMBLE_MAX_WARPS = 16;
 
 // Host wrappers of the ensemble kernel (esdg_ensemble_impl.cuh), one
 // instantiation per volume rule RULE (0 collapsed, 1 symmetric) in its own

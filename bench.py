@@ -37,7 +37,7 @@ WL = W.DAM
 # DRAM traffic of one stage launch at this workload, from one ncu capture
 # (profiles/k_stage2_dam_k131072_n4.md), valid only for the kernel source it
 # was measured on: reported as null once that source changes.
-STAGE_TRAFFIC = {"source_sha1": "c7a1988bcfdb2aa601779476c41ef6f6b315d39f", "bytes": 431.8e6}
+STAGE_TRAFFIC = {"source_sha1": "b8c8c94cd23ef530f7f4fe74592532cf63716ecd", "bytes": 431.4e6}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 
 # Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of

@@ -12,7 +12,8 @@ paper's definitions, written for readability, not speed.
 Modules
 -------
 refelem   reference triangle: basis, quadrature, Vq, Vf, Pq, D, Q-hat, Q_h (Sec. 2.1-2.3)
-mesh      structured periodic triangulation, curved warp, geometric factors (Sec. 2.7)
+mesh      structured periodic triangulation, curved warp, geometric factors,
+          exact or weight-adjusted inverse mass matrices (Sec. 2.7, 2.8)
 swe       entropy, entropy variables, EC flux (Sec. 2.4, 2.5, 2.8)
 esdg      semi-discrete right-hand side in the literal form of eq. (dgform),
           LSRK45 time stepping (Sec. 4), diagnostics

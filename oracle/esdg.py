@@ -27,6 +27,14 @@ Readings:
     entropy-projected states, penalty on the jump of u~ (Sec. 2.8, Sec. 4).
   * time step dt = CFL h / C_N, C_N = (N+1)(N+2)/2 (Sec. 4), with h the quad
     spacing of the structured grid (the paper does not define h).
+  * mass="weight_adjusted": every (M_h^k)^{-1} above, in the projection and in
+    the update alike, is the weight-adjusted inverse of mesh.py (Sec. 2.8's
+    named alternative to storing the inverses).  Using the same matrix in both
+    places keeps the entropy identity of Theorem 2.2 exact; the projection
+    then reproduces constants only where J^k is constant, so on curved
+    elements a lake at rest is preserved only to the accuracy of the
+    weight-adjusted approximation, and the conserved mass is sum_k 1^T
+    M~_k u_h with M~_k the inverse of the weight-adjusted matrix.
 """
 
 import numpy as np
@@ -83,9 +91,9 @@ class Oracle:
     """
 
     def __init__(self, N, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0,
-                 g=1.0, cfl=0.25, lf=True, forcing=None, rule="collapsed", walls=False):
+                 g=1.0, cfl=0.25, lf=True, forcing=None, rule="collapsed", walls=False, mass="exact"):
         self.ref = RefElem(N, rule)
-        self.mesh = Mesh(self.ref, nx, ny, x0, x1, y0, y1, ax, ay, walls=walls)
+        self.mesh = Mesh(self.ref, nx, ny, x0, x1, y0, y1, ax, ay, walls=walls, mass=mass)
         self.N, self.K = N, self.mesh.K
         self.g, self.cfl, self.lf = g, cfl, lf
         self.forcing = forcing  # None or callable (x, y, t, g) -> (3, ...)

@@ -17,6 +17,12 @@ Readings (the paper is silent on these):
     which vanishes on the domain boundary, so periodic faces still match.
   * G^k_ij of Sec. 2.7 is used J-scaled (rxJ = J dr/dx, ...), which is what
     pairs with the J-weighted mass matrix M_h^k = Vq^T W J Vq.
+  * mass="weight_adjusted" replaces the stored inverse (M_h^k)^{-1} by the
+    weight-adjusted inverse that Sec. 2.8 names as the way to avoid storing
+    it: M^{-1} M_{1/J} M^{-1}, with the reference mass matrix M = Vq^T W Vq and
+    M_{1/J} = Vq^T W diag(1/J^k) Vq (the weight-adjusted approximation of
+    Chan, Hewett and Warburton, 2017).  It equals (M_h^k)^{-1} when J^k is
+    constant (affine elements).
 """
 
 import numpy as np
@@ -35,9 +41,13 @@ class Mesh:
     has no partner, its nodes map to themselves and wall (K, 3) marks it.
     """
 
-    def __init__(self, ref, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0, walls=False):
+    def __init__(self, ref, nx, ny, x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, ax=0.0, ay=0.0, walls=False,
+                 mass="exact"):
+        if mass not in ("exact", "weight_adjusted"):
+            raise ValueError(mass)
         self.ref = ref
         self.walls = walls
+        self.mass = mass
         self.nx, self.ny = nx, ny
         self.x0, self.x1, self.y0, self.y1 = x0, x1, y0, y1
         self.Lx, self.Ly = x1 - x0, y1 - y0
@@ -139,7 +149,13 @@ class Mesh:
         # curved mass matrices M_h^k = Vq^T W J^k Vq and their inverses (Sec. 2.7)
         VqW = ref.Vq * ref.w[:, None]
         self.Mh = np.einsum("qn,kq,qm->knm", VqW, Jq, ref.Vq)
-        self.Mh_inv = np.linalg.inv(self.Mh)
+        if self.mass == "exact":
+            self.Mh_inv = np.linalg.inv(self.Mh)
+        else:
+            # weight-adjusted inverse M^{-1} M_{1/J} M^{-1} (Sec. 2.8's remedy)
+            M_ref_inv = np.linalg.inv(VqW.T @ ref.Vq)
+            M_invJ = np.einsum("qn,kq,qm->knm", VqW, 1.0 / Jq, ref.Vq)
+            self.Mh_inv = M_ref_inv[None] @ M_invJ @ M_ref_inv[None]
 
     # -- connectivity ------------------------------------------------------------
     def _build_connectivity(self):

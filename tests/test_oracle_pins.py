@@ -637,3 +637,121 @@ def test_walls_reduce_to_periodic_away_from_the_boundary():
     assert nb_int.sum() > 0
     assert np.abs(rw[:, nb_int] - rp[:, nb_int]).max() < 1e-13 * np.abs(rp).max()
     assert np.abs(rw[:, ~interior] - rp[:, ~interior]).max() > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# Weight-adjusted inverse mass matrices (Sec. 2.8's alternative to storing
+# (M_h^k)^{-1}): closed forms, the unisolvent special case, convergence, and
+# the invariants that must survive (entropy identity, a conserved mass)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [2, 4])
+def test_weight_adjusted_inverse_is_exact_on_affine_elements(N, rule):
+    """Constant J: M_{1/J} = M / J, so M^{-1} M_{1/J} M^{-1} = I / J exactly
+    (orthonormal basis, M = I) and equals the inverse of M_h^k = J I."""
+    ex = Oracle(N, 4, 4, rule=rule)
+    wa = Oracle(N, 4, 4, rule=rule, mass="weight_adjusted")
+    J = ex.mesh.Jq[:, 0]
+    want = np.eye(ex.Np)[None] / J[:, None, None]
+    assert np.abs(wa.mesh.Mh_inv - want).max() < 1e-13 * np.abs(want).max()
+    assert np.abs(wa.mesh.Mh_inv - ex.mesh.Mh_inv).max() < 1e-13 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("N", [1, 2])
+def test_weight_adjusted_inverse_is_exact_for_a_unisolvent_rule(N):
+    """With as many volume points as modes (the symmetric 3- and 6-point
+    rules), V_q is square and V_q V_q^T W = I, so M^{-1} M_{1/J} M^{-1} M_J =
+    V_q^T W (1/J) (J) V_q = I on any curved element."""
+    ex = Oracle(N, 4, 4, ax=0.05, ay=0.05, rule="symmetric")
+    wa = Oracle(N, 4, 4, ax=0.05, ay=0.05, rule="symmetric", mass="weight_adjusted")
+    assert ex.Nq == ex.Np
+    prod = np.einsum("knm,kml->knl", wa.mesh.Mh_inv, ex.mesh.Mh)
+    assert np.abs(prod - np.eye(ex.Np)[None]).max() < 1e-12
+
+
+def _wadg_defect(N, nx, rule):
+    ex = Oracle(N, nx, nx, ax=0.05, ay=0.05, rule=rule)
+    wa = Oracle(N, nx, nx, ax=0.05, ay=0.05, rule=rule, mass="weight_adjusted")
+    prod = np.einsum("knm,kml->knl", wa.mesh.Mh_inv, ex.mesh.Mh)
+    return np.linalg.norm(prod - np.eye(ex.Np)[None], axis=(1, 2)).max()
+
+
+@pytest.mark.parametrize("rule,N", [("collapsed", 3), ("symmetric", 4)])
+def test_weight_adjusted_inverse_converges_under_refinement(N, rule):
+    """On a fixed smooth warp J varies by O(h) over an element, and the
+    weight-adjusted inverse approaches the exact one as the mesh refines."""
+    d = [_wadg_defect(N, nx, rule) for nx in (4, 8, 16)]
+    assert 1e-6 < d[0] < 1e-2
+    assert d[1] < d[0] / 1.8 and d[2] < d[1] / 2.5
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_weight_adjusted_entropy_identity_and_mass(N, rule):
+    """Theorem 2.2's entropy identity needs the same matrix in the projection
+    and in the update, not the exact inverse: with the weight-adjusted matrix
+    in both, the EC rate vanishes on curved elements.  The conserved mass is
+    sum_k (M~_k 1)^T dh/dt with M~_k = (weight-adjusted inverse)^{-1}; the
+    J-weighted integral of h is conserved only approximately."""
+    o = Oracle(N, 4, 4, ax=0.05, ay=0.05, lf=False, rule=rule, mass="weight_adjusted")
+    _bathy(o)
+    u = _smooth_state(o)
+    r = o.rhs(u)
+    terms = o.entropy_rate_terms(u, r)
+    assert abs(terms.sum()) < 1e-13 * np.abs(terms).sum()
+    Mt = np.linalg.inv(o.mesh.Mh_inv)
+    # modes of the constant 1: the reference L2 projection P_q 1
+    one = np.linalg.solve(o.ref.Vq.T * o.ref.w @ o.ref.Vq, (o.ref.Vq.T * o.ref.w) @ np.ones(o.Nq))
+    dmass = np.einsum("knm,m,kn->", Mt, one, r[0])
+    assert abs(dmass) < 1e-13
+    if N >= 3:   # for N <= 2, J is in P^{2N-2}, inside P^N: constants are reproduced
+        dJmass = np.sum(o.ref.w[None] * o.mesh.Jq * (r[0] @ o.ref.Vq.T))
+        assert abs(dJmass) > 1e-13
+    o.lf = True
+    assert o.entropy_rate_terms(u, o.rhs(u)).sum() < 0
+
+
+def test_planted_mismatched_weight_adjusted_projection_breaks_entropy_rate(monkeypatch):
+    """The exact inverse in the projection with the weight-adjusted one in the
+    update (or the reverse) breaks the entropy identity on curved elements."""
+    o = Oracle(3, 4, 4, ax=0.05, ay=0.05, lf=False, mass="weight_adjusted")
+    ex = Oracle(3, 4, 4, ax=0.05, ay=0.05, lf=False)
+    _bathy(o)
+    u = _smooth_state(o)
+    terms = o.entropy_rate_terms(u, o.rhs(u))
+    good = abs(terms.sum()) / np.abs(terms).sum()
+    monkeypatch.setattr(o, "project", lambda q: ex.project(q))
+    terms = o.entropy_rate_terms(u, o.rhs(u))
+    bad = abs(terms.sum()) / np.abs(terms).sum()
+    assert good < 1e-13 and bad > 1e-9
+
+
+@pytest.mark.parametrize("rule,N", [("collapsed", 3), ("symmetric", 4)])
+def test_weight_adjusted_lake_at_rest_converges(N, rule):
+    """A lake at rest stays exact on affine meshes and, on curved ones, is
+    preserved to the weight-adjusted approximation error, which falls under
+    refinement."""
+    def residual(nx, warp):
+        o = Oracle(N, nx, nx, ax=warp, ay=warp, rule=rule, mass="weight_adjusted")
+        _bathy(o)
+        xq, yq = o.points("volq")
+        u = o.init_state(np.stack([2.0 + 0 * xq, 0 * xq, 0 * xq]), surface=True)
+        return np.abs(o.rhs(u)).max()
+    assert residual(4, 0.0) < 1e-12
+    r = [residual(nx, 0.05) for nx in (4, 8, 16)]
+    assert r[0] > 1e-8
+    assert r[1] < r[0] / 2.5 and r[2] < r[1] / 2.5
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [1, 2])
+def test_weight_adjusted_lake_at_rest_exact_when_J_in_PN(N, rule):
+    """A degree-N map has J in P^{2N-2}; for N <= 2 that lies in P^N, where
+    M~^{-1} M_J 1 = P_N((P_N J) / J) = 1: the weight-adjusted projection
+    reproduces constants and a lake at rest stays exact on curved elements."""
+    o = Oracle(N, 4, 4, ax=0.05, ay=0.05, rule=rule, mass="weight_adjusted")
+    _bathy(o)
+    xq, yq = o.points("volq")
+    u = o.init_state(np.stack([2.0 + 0 * xq, 0 * xq, 0 * xq]), surface=True)
+    assert np.abs(o.rhs(u)).max() < 1e-12

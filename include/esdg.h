@@ -63,6 +63,18 @@ extern "C" {
 #define ESDG_BOUNDARY_PERIODIC 0
 #define ESDG_BOUNDARY_WALLS 1
 
+/* inverse curved mass matrix of the projection (Sec. 2.6) and the update
+   (eq. (dgform)): the stored per-element inverse (M_h^k)^{-1} (Sec. 2.7), or
+   the weight-adjusted inverse M^{-1} M_{1/J} M^{-1} = Vq^T W diag(1/J) Vq
+   applied on the fly, the alternative Sec. 2.8 names (no per-element matrix
+   is stored or read).  The weight-adjusted inverse keeps the entropy identity
+   exact and conserves sum_k 1^T M~_k h_k (M~_k its inverse).  It equals the
+   stored inverse on affine elements and for the symmetric rules of N = 1, 2
+   (as many points as modes); a lake at rest stays exact where J is in P^N
+   (affine elements, N <= 2) and elsewhere holds to the approximation error. */
+#define ESDG_MASS_EXACT           0
+#define ESDG_MASS_WEIGHT_ADJUSTED 1
+
 /* point sets for esdg_get_points */
 #define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
 #define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
@@ -86,6 +98,7 @@ typedef struct esdg_config {
     double mms_amp, mms_bamp, mms_u0, mms_v0;  /* ESDG_FORCING_MMS_SINE parameters */
     int volume_rule;        /* ESDG_RULE_* */
     int boundary;           /* ESDG_BOUNDARY_* */
+    int mass;               /* ESDG_MASS_*; ensembles and served FP32 requests take ESDG_MASS_EXACT */
 } esdg_config;
 
 /*

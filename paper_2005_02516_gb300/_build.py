@@ -1,8 +1,8 @@
 """Compile the CUDA library libesdg.so in-tree for sm_103a.
 
-Translation units compile in parallel (one per polynomial degree and volume
-rule, one per rule for the ensemble kernel, plus the C-ABI, the host builder
-and the request server) and link into paper_2005_02516_gb300/libesdg.so.
+Translation units compile in parallel (one per polynomial degree, volume
+rule and inverse-mass kind, one per rule for the ensemble kernel, plus the
+C-ABI, the host builder and the request server) and link into paper_2005_02516_gb300/libesdg.so.
 """
 
 import os
@@ -26,7 +26,8 @@ def nvcc():
 
 def _sources():
     cu = (["esdg_api.cu", "esdg_ensemble.cu", "esdg_ensemble_s.cu", "esdg_volume.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
-          + ["esdg_kernels_s%d.cu" % n for n in range(1, 6)])
+          + ["esdg_kernels_s%d.cu" % n for n in range(1, 6)]
+          + ["esdg_kernels_w%s%d.cu" % (r, n) for r in "ns" for n in range(1, 6)])
     return cu, ["host_build.cpp", "esdg_server.cpp"]
 
 

@@ -98,9 +98,15 @@ static size_t real_size(const esdg_ctx* c) { return c->cfg.precision == ESDG_FP3
 
 static int c2_ops_floats(int N);
 
-// Kernel template parameter of a configuration: NR = N + 8 * rule.
-static int kernel_nr(const esdg_config& cfg) { return cfg.N + (cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 8 : 0); }
-#define ESDG_FOR_EACH_NR(X) X(1) X(2) X(3) X(4) X(5) X(9) X(10) X(11) X(12) X(13)
+static bool weight_adjusted(const esdg_config& cfg) { return cfg.mass == ESDG_MASS_WEIGHT_ADJUSTED; }
+
+// Kernel template parameter of a configuration: NR = N + 8 * rule + 16 * wadg.
+static int kernel_nr(const esdg_config& cfg) {
+    return cfg.N + (cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 8 : 0) + (weight_adjusted(cfg) ? 16 : 0);
+}
+#define ESDG_FOR_EACH_NR(X)                                                         \
+    X(1) X(2) X(3) X(4) X(5) X(9) X(10) X(11) X(12) X(13) X(17) X(18) X(19) X(20) X(21) \
+    X(25) X(26) X(27) X(28) X(29)
 
 static int c2_ops_floats(int NR);
 
@@ -115,14 +121,15 @@ static void compute_layout(esdg_ctx* c) {
     DevLayout& L = c->L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq));
+    L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq) +
+                        size_t(R.Nq));
     L.ops = take(L.ops_bytes);
     L.ops2_bytes = c->cfg.precision == ESDG_FP32 ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
     L.ops2 = take(L.ops2_bytes);
     L.vq64 = take(8 * size_t(R.Nq) * R.Np);
     L.geo = take(rs * Kp * R.Nh * 4);
     L.wJq = take(rs * Kp * R.Nq);
-    L.minv = take(rs * Kp * c->mstride);
+    L.minv = take(weight_adjusted(c->cfg) ? 0 : rs * Kp * c->mstride);  // none with the weight-adjusted inverse
     L.bh = take(rs * Kp * R.Nh);
     L.nbr = take(4 * Kp * 3);
     const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
@@ -149,7 +156,7 @@ static std::vector<real> to_real(const std::vector<double>& v) {
 
 template <typename real>
 static std::vector<real> pack_ops(const RefOps& R) {
-    // order must match Smem<N, real>: QsT, Vq, VqT, Vh, VhT, wf, nrs
+    // order must match Smem<N, real>: QsT, Vq, VqT, Vh, VhT, wf, nrs, wq
     std::vector<real> o;
     o.reserve(size_t(R.Nh) * R.Nh * 2 + 4 * size_t(R.Nh) * R.Np);
     for (int m = 0; m < R.Nh; ++m)
@@ -170,6 +177,7 @@ static std::vector<real> pack_ops(const RefOps& R) {
         o.push_back((real)R.nr[f]);
         o.push_back((real)R.ns[f]);
     }
+    for (int q = 0; q < R.Nq; ++q) o.push_back((real)R.wq[q]);
     return o;
 }
 
@@ -187,12 +195,13 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
                 o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)R.Qsr(l, m);
                 o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)R.Qss(l, m);
             }
-    for (int l = 0; l < R.Nh; ++l)
-        for (int b = 0; b < LPE; ++b)
-            for (int j = 0; j < C::MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < R.Np) o[C::o_VhT + (l * LPE + b) * C::MPLp + j] = (float)R.Vh(l, n);
-            }
+    if (!C::WADG)
+        for (int l = 0; l < R.Nh; ++l)
+            for (int b = 0; b < LPE; ++b)
+                for (int j = 0; j < C::MPL; ++j) {
+                    const int n = b + LPE * j;
+                    if (n < R.Np) o[C::o_VhT + (l * LPE + b) * C::MPLp + j] = (float)R.Vh(l, n);
+                }
     for (int q = 0; q < R.Nq; ++q)
         for (int b = 0; b < LPE; ++b)
             for (int j = 0; j < C::MPL; ++j) {
@@ -207,9 +216,28 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
             }
             for (int j = 0; j < C::RPL; ++j) {
                 const int l = b + LPE * j;
-                if (l < R.Nh) o[C::o_Vh + (n * LPE + b) * C::RPLp + j] = (float)R.Vh(l, n);
+                if (!C::WADG && l < R.Nh) o[C::o_Vh + (n * LPE + b) * C::RPLp + j] = (float)R.Vh(l, n);
             }
         }
+    if (C::WADG) {
+        // composed factors of the weight-adjusted inverse, formed in FP64:
+        // C = Vq Vh^T (Nq x Nh), A = Vq Vq^T (Nq x Nq), B = Vh Vq^T (Nh x Nq)
+        const Mat Cm = matmul(R.Vq, transpose(R.Vh)), Am = matmul(R.Vq, transpose(R.Vq)), Bm = transpose(Cm);
+        for (int b = 0; b < LPE; ++b) {
+            for (int j = 0; j < C::QPL; ++j) {
+                const int q = b + LPE * j;
+                if (q >= R.Nq) continue;
+                for (int l = 0; l < R.Nh; ++l) o[C::o_C + (l * LPE + b) * C::QPLp + j] = (float)Cm(q, l);
+                for (int q2 = 0; q2 < R.Nq; ++q2) o[C::o_A + (q2 * LPE + b) * C::QPLp + j] = (float)Am(q, q2);
+            }
+            for (int j = 0; j < C::RPL; ++j) {
+                const int l = b + LPE * j;
+                if (l >= R.Nh) continue;
+                for (int q = 0; q < R.Nq; ++q) o[C::o_B + (q * LPE + b) * C::RPLp + j] = (float)Bm(l, q);
+            }
+        }
+        for (int q = 0; q < R.Nq; ++q) o[C::o_wq + q] = (float)R.wq[q];
+    }
     for (int f = 0; f < R.Nfq; ++f) {
         o[C::o_wf + f] = (float)R.wf[f];
         o[C::o_nrs + 2 * f] = (float)R.nr[f];
@@ -262,11 +290,13 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
     put(img, c->L.wJq, to_real<real>(wJ64));
     put(img, c->L.wJq64, wJ64);
-    const int NpP = R.Np * (R.Np + 1) / 2;
-    std::vector<real> mi(K * size_t(c->mstride), (real)0);
-    for (size_t e = 0; e < K; ++e)
-        for (int i = 0; i < NpP; ++i) mi[e * c->mstride + i] = (real)M.minv[e * NpP + i];
-    put(img, c->L.minv, mi);
+    if (!weight_adjusted(c->cfg)) {
+        const int NpP = R.Np * (R.Np + 1) / 2;
+        std::vector<real> mi(K * size_t(c->mstride), (real)0);
+        for (size_t e = 0; e < K; ++e)
+            for (int i = 0; i < NpP; ++i) mi[e * c->mstride + i] = (real)M.minv[e * NpP + i];
+        put(img, c->L.minv, mi);
+    }
     put(img, c->L.nbr, M.nbr);
     if (c->cfg.forcing != ESDG_FORCING_NONE) {
         put(img, c->L.xq, to_real<real>(M.xq));
@@ -375,6 +405,7 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.VhT = p.Vh + size_t(R.Nh) * R.Np;
     p.wf = p.VhT + size_t(R.Np) * R.Nh;
     p.nrs = p.wf + R.Nfq;
+    p.wq = p.nrs + 2 * size_t(R.Nfq);
     p.geo = reinterpret_cast<const real*>(d + c->L.geo);
     p.wJq = reinterpret_cast<const real*>(d + c->L.wJq);
     p.minv = reinterpret_cast<const real*>(d + c->L.minv);
@@ -541,6 +572,8 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         return fail(nullptr, ESDG_EINVAL, "unknown volume rule");
     if (cfg->boundary != ESDG_BOUNDARY_PERIODIC && cfg->boundary != ESDG_BOUNDARY_WALLS)
         return fail(nullptr, ESDG_EINVAL, "unknown boundary kind");
+    if (cfg->mass != ESDG_MASS_EXACT && cfg->mass != ESDG_MASS_WEIGHT_ADJUSTED)
+        return fail(nullptr, ESDG_EINVAL, "unknown inverse-mass kind");
     esdg_ctx* c = new (std::nothrow) esdg_ctx();
     if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     c->cfg = *cfg;
@@ -550,7 +583,7 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         return fail(nullptr, ESDG_EINVAL, err);
     }
     MeshSpec sp{cfg->nx, cfg->ny, cfg->x0, cfg->x1, cfg->y0, cfg->y1, cfg->warp_ax, cfg->warp_ay,
-                cfg->boundary == ESDG_BOUNDARY_WALLS};
+                cfg->boundary == ESDG_BOUNDARY_WALLS, cfg->mass == ESDG_MASS_WEIGHT_ADJUSTED};
     if (!build_mesh(c->ref, sp, c->mesh, err)) {
         delete c;
         return fail(nullptr, ESDG_EINVAL, err);
@@ -982,6 +1015,8 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one stream");
         if (c->cfg.volume_rule != members[0]->cfg.volume_rule)
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one volume rule");
+        if (weight_adjusted(c->cfg))
+            return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must use the stored inverse mass matrices");
     }
     esdg_ensemble* e = new (std::nothrow) esdg_ensemble();
     if (!e) return fail(nullptr, ESDG_ENOMEM, "out of host memory");

@@ -32,12 +32,16 @@ namespace esdg {
 // Points of the fully symmetric volume rule exact to degree 2N.
 constexpr int symmetric_points(int N) { return N == 1 ? 3 : N == 2 ? 6 : N == 3 ? 12 : N == 4 ? 16 : 25; }
 
-// Template parameter NR = N + 8 * rule: the degree N (1..5) and the volume
-// rule (0: collapsed (N+1)^2 points, 1: symmetric, exact to 2N).
+// Template parameter NR = N + 8 * rule + 16 * wadg: the degree N (1..5), the
+// volume rule (0: collapsed (N+1)^2 points, 1: symmetric, exact to 2N) and the
+// inverse mass matrix (0: the stored (M_h^k)^{-1} of Sec. 2.7; 1: the
+// weight-adjusted inverse M^{-1} M_{1/J} M^{-1} = Vq^T W diag(1/J) Vq applied
+// on the fly, the alternative Sec. 2.8 names; M = I for these rules).
 template <int NR>
 struct Dims {
     static constexpr int N = NR & 7;
-    static constexpr int rule = NR >> 3;
+    static constexpr int rule = (NR >> 3) & 1;
+    static constexpr int wadg = (NR >> 4) & 1;
     static constexpr int Np = (N + 1) * (N + 2) / 2;
     static constexpr int Nq = rule ? symmetric_points(N) : (N + 1) * (N + 1);
     static constexpr int Nfp = N + 1;
@@ -63,10 +67,11 @@ struct StageParams {
     const real* VhT;   // [Np][Nh]
     const real* wf;    // [Nfq]
     const real* nrs;   // [Nfq][2] scaled reference normals
+    const real* wq;    // [Nq]     volume weights (weight-adjusted inverse: w_q / J_q = w_q^2 / (w_q J_q))
     // per element
     const real* geo;   // [K][Nh][4] rxJ sxJ ryJ syJ
     const real* wJq;   // [K][Nq]   w_q J_q
-    const real* minv;  // [K][mstride] packed (M_h^k)^{-1}
+    const real* minv;  // [K][mstride] packed (M_h^k)^{-1} (stored inverse only)
     int mstride;       // element stride of minv (NpP rounded up to a multiple of 4)
     const real* bh;    // [K][Nh]   bathymetry at hybrid nodes
     const int* nbr;    // [K][3]    4 * neighbour element + neighbour face (4 e + 3: wall)
@@ -124,15 +129,16 @@ struct Smem {
     static constexpr int ops_VhT = ops_Vh + D::Nh * D::Np;
     static constexpr int ops_wf = ops_VhT + D::Np * D::Nh;
     static constexpr int ops_nrs = ops_wf + D::Nfq;
-    static constexpr int ops_end = ((ops_nrs + 2 * D::Nfq) + 3) & ~3;
+    static constexpr int ops_wq = ops_nrs + 2 * D::Nfq;
+    static constexpr int ops_end = ((ops_wq + D::Nq) + 3) & ~3;
     // per-warp slab
     static constexpr int w_rec = 0;                              // [Nh][REC]
     static constexpr int w_rt = w_rec + D::Nh * REC;             // [3][Nh]
     static constexpr int w_a = w_rt + 3 * D::Nh;                 // [3][Nq]
     static constexpr int w_b = w_a + 3 * D::Nq;                  // [3][Np]
     static constexpr int w_c = w_b + 3 * D::Np;                  // [3][Np]
-    static constexpr int w_minv = w_c + 3 * D::Np;               // [NpP]
-    static constexpr int w_end = ((w_minv + D::NpP) + 3) & ~3;
+    static constexpr int w_minv = w_c + 3 * D::Np;               // [NpP] (stored inverse only)
+    static constexpr int w_end = ((w_minv + (D::wadg ? 0 : D::NpP)) + 3) & ~3;
     static constexpr size_t bytes(int warps) { return sizeof(real) * (size_t(ops_end) + size_t(warps) * w_end); }
 };
 
@@ -153,6 +159,48 @@ __device__ __forceinline__ void stage_ops_to_smem(const StageParams<real>& p, re
         sm[S::ops_wf + i] = p.wf[i];
         sm[S::ops_nrs + 2 * i] = p.nrs[2 * i];
         sm[S::ops_nrs + 2 * i + 1] = p.nrs[2 * i + 1];
+    }
+    for (int i = threadIdx.x; i < D::Nq; i += blockDim.x) sm[S::ops_wq + i] = p.wq[i];
+}
+
+// Weight-adjusted inverse mass (Sec. 2.8's alternative to storing the
+// inverses): out = Vq^T diag(w / J) Vq y for the three fields of one element,
+// y and out [3][Np] (may alias), t [3][Nq] scratch.
+template <int N, typename real>
+__device__ __forceinline__ void wadg_apply(const StageParams<real>& p, const real* ops, const real* y, real* t,
+                                           real* out, int e, int lane, real sign) {
+    typedef Dims<N> D;
+    typedef Smem<N, real> S;
+    const real* Vq = ops + S::ops_Vq;
+    const real* VqT = ops + S::ops_VqT;
+    for (int q = lane; q < D::Nq; q += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+        for (int n = 0; n < D::Np; ++n) {
+            const real v = Vq[q * D::Np + n];
+            a0 += v * y[n];
+            a1 += v * y[D::Np + n];
+            a2 += v * y[2 * D::Np + n];
+        }
+        const real w = ops[S::ops_wq + q];
+        const real sc = w * w / p.wJq[(size_t)e * D::Nq + q];
+        t[q] = a0 * sc;
+        t[D::Nq + q] = a1 * sc;
+        t[2 * D::Nq + q] = a2 * sc;
+    }
+    __syncwarp();
+    for (int n = lane; n < D::Np; n += 32) {
+        real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+        for (int q = 0; q < D::Nq; ++q) {
+            const real v = VqT[n * D::Nq + q];
+            a0 += v * t[q];
+            a1 += v * t[D::Nq + q];
+            a2 += v * t[2 * D::Nq + q];
+        }
+        out[n] = sign * a0;
+        out[D::Np + n] = sign * a1;
+        out[2 * D::Np + n] = sign * a2;
     }
 }
 
@@ -208,20 +256,25 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
         tc[2 * D::Np + n] = a2;
     }
     __syncwarp();
-    // v_h = (M_h^k)^{-1} y   (packed symmetric)
-    for (int n = lane; n < D::Np; n += 32) {
-        real a0 = 0, a1 = 0, a2 = 0;
+    if constexpr (D::wadg) {
+        // v_h = Vq^T diag(w / J) Vq y  (weight-adjusted inverse; ta is free again)
+        wadg_apply<N, real>(p, ops, tc, ta, us, e, lane, real(1));
+    } else {
+        // v_h = (M_h^k)^{-1} y   (packed symmetric)
+        for (int n = lane; n < D::Np; n += 32) {
+            real a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
-        for (int j = 0; j < D::Np; ++j) {
-            int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
-            real m = mi[ij];
-            a0 += m * tc[j];
-            a1 += m * tc[D::Np + j];
-            a2 += m * tc[2 * D::Np + j];
+            for (int j = 0; j < D::Np; ++j) {
+                int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+                real m = mi[ij];
+                a0 += m * tc[j];
+                a1 += m * tc[D::Np + j];
+                a2 += m * tc[2 * D::Np + j];
+            }
+            us[n] = a0;   // us is free again: reuse for v_h
+            us[D::Np + n] = a1;
+            us[2 * D::Np + n] = a2;
         }
-        us[n] = a0;   // us is free again: reuse for v_h
-        us[D::Np + n] = a1;
-        us[2 * D::Np + n] = a2;
     }
     __syncwarp();
     // v~ = Vh v_h; u~ = u(v~): H = (v1 + (v2^2 + v3^2)/2)/g, h = H - b
@@ -252,7 +305,8 @@ template <int N, typename real>
 __device__ __forceinline__ void load_minv(const StageParams<real>& p, real* ws, int e, int lane) {
     typedef Dims<N> D;
     typedef Smem<N, real> S;
-    for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * p.mstride + i];
+    if constexpr (!D::wadg)
+        for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * p.mstride + i];
 }
 
 // Standalone projection: u_in (FP64 modal) -> ut_out.
@@ -449,21 +503,25 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         }
         __syncwarp();
         // ---- du/dt = -(M_h^k)^{-1} s; then output or RK update --------------------
-        const real* mi = ws + S::w_minv;
         real* sc = ws + S::w_c;
-        for (int n = lane; n < D::Np; n += 32) {
-            real a0 = 0, a1 = 0, a2 = 0;
+        if constexpr (D::wadg) {
+            wadg_apply<N, real>(p, ops, sb, fa, sc, e, lane, real(-1));  // fa (forcing) is consumed
+        } else {
+            const real* mi = ws + S::w_minv;
+            for (int n = lane; n < D::Np; n += 32) {
+                real a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
-            for (int j = 0; j < D::Np; ++j) {
-                const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
-                const real m = mi[ij];
-                a0 += m * sb[j];
-                a1 += m * sb[D::Np + j];
-                a2 += m * sb[2 * D::Np + j];
+                for (int j = 0; j < D::Np; ++j) {
+                    const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+                    const real m = mi[ij];
+                    a0 += m * sb[j];
+                    a1 += m * sb[D::Np + j];
+                    a2 += m * sb[2 * D::Np + j];
+                }
+                sc[n] = -a0;
+                sc[D::Np + n] = -a1;
+                sc[2 * D::Np + n] = -a2;
             }
-            sc[n] = -a0;
-            sc[D::Np + n] = -a1;
-            sc[2 * D::Np + n] = -a2;
         }
         __syncwarp();
         for (int i = lane; i < 3 * D::Np; i += 32) {

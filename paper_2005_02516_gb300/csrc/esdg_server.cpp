@@ -239,7 +239,9 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
     r->bytes = (bytes + 255) & ~size_t(255);
     esdg_config cfg;
     rc = esdg_get_config(ctx, &cfg);
-    if (rc || (cfg.precision == ESDG_FP32 && cfg.forcing != ESDG_FORCING_NONE)) {
+    // FP32 requests run inside an ensemble launch, which carries neither
+    // forcing terms nor the weight-adjusted inverse
+    if (rc || (cfg.precision == ESDG_FP32 && (cfg.forcing != ESDG_FORCING_NONE || cfg.mass != ESDG_MASS_EXACT))) {
         delete r;
         return rc ? rc : ESDG_EINVAL;
     }

@@ -23,6 +23,11 @@
 //  * lift, inverse mass and projection spread modes, nodes or fields over
 //    the LPE lanes of an element, with the permuted operators in shared
 //    memory laid out so each lane reads contiguous float4s.
+//  * with the weight-adjusted inverse mass (Dims::wadg; Sec. 2.8 names it as
+//    the way to avoid stored inverses) no per-element matrix is stored or
+//    copied: the inverse Vq^T diag(w/J) Vq is applied through shared factors
+//    composed on the host (C = Vq Vh^T, A = Vq Vq^T, B = Vh Vq^T) and a
+//    per-node scale w^2 / (w J).
 #pragma once
 
 #include "esdg_kernels.cuh"
@@ -51,21 +56,31 @@ struct C2 {
     // one node fall in distinct 4-bank groups (slot stride not 0 or 16 mod 32)
     static constexpr int UTS = ((D::Nh * 4 + 4) % 32 == 0 || (D::Nh * 4 + 4) % 32 == 16) ? D::Nh * 4 + 8 : D::Nh * 4 + 4;
     static constexpr int MIS = NpP4 + 4;                    // element slot of inverse-mass staging
-    // operator region (floats)
+    static constexpr bool WADG = D::wadg;                   // weight-adjusted inverse mass
+    // operator region (floats).  Stored inverse: lift Vh^T, projection Vq^T,
+    // interpolation Vq and Vh.  Weight-adjusted inverse Vq^T diag(w/J) Vq
+    // with the shared factors composed: C = Vq Vh^T (lift to the volume
+    // nodes), A = Vq Vq^T, B = Vh Vq^T, so that
+    //   du/dt = -Vq^T [(w/J) o (C r - A (w J f))]   and
+    //   v~    =  B [(w/J) o (A (w J v))].
     static constexpr int o_Qs = 0;                                  // [Nh][LPE][OPB]
     static constexpr int o_VhT = o_Qs + D::Nh * LPE * OPB;          // [Nh][LPE][MPLp]: Vh[l][b+LPE j]
-    static constexpr int o_VqT = o_VhT + D::Nh * LPE * MPLp;        // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
+    static constexpr int o_VqT = o_VhT + (WADG ? 0 : D::Nh * LPE * MPLp);  // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
     static constexpr int o_Vq = o_VqT + D::Nq * LPE * MPLp;         // [Np][LPE][QPLp]: Vq[b+LPE j][n]
     static constexpr int o_Vh = o_Vq + D::Np * LPE * QPLp;          // [Np][LPE][RPLp]: Vh[b+LPE j][n]
-    static constexpr int o_wf = o_Vh + D::Np * LPE * RPLp;          // [Nfq]
+    static constexpr int o_C = o_Vh + (WADG ? 0 : D::Np * LPE * RPLp);     // [Nh][LPE][QPLp]: C[b+LPE j][l]
+    static constexpr int o_A = o_C + (WADG ? D::Nh * LPE * QPLp : 0);      // [Nq][LPE][QPLp]: A[b+LPE j][q]
+    static constexpr int o_B = o_A + (WADG ? D::Nq * LPE * QPLp : 0);      // [Nq][LPE][RPLp]: B[b+LPE j][q]
+    static constexpr int o_wq = o_B + (WADG ? D::Nq * LPE * RPLp : 0);     // [Nq] volume weights
+    static constexpr int o_wf = o_wq + (WADG ? D::Nq : 0);          // [Nfq]
     static constexpr int o_nrs = o_wf + D::Nfq;                     // [Nfq][2]
     static constexpr int o_end = (o_nrs + 2 * D::Nfq + 3) & ~3;
     // per-warp region (floats)
     static constexpr int w_ut = 0;                          // [EPW][UTS]  h u v H
     static constexpr int w_geo = w_ut + EPW * UTS;          // [EPW][UTS]  rxJ sxJ ryJ syJ (scaled 1/8)
     static constexpr int w_tr = w_geo + EPW * UTS;          // [EPW][Nfq][4] neighbour traces
-    static constexpr int w_mi = w_tr + EPW * D::Nfq * 4;    // [EPW][MIS]  packed (M_h^k)^-1
-    static constexpr int w_end = (w_mi + EPW * MIS + 3) & ~3;
+    static constexpr int w_mi = w_tr + EPW * D::Nfq * 4;    // [EPW][MIS]  packed (M_h^k)^-1 (stored inverse)
+    static constexpr int w_end = (w_mi + (WADG ? 0 : EPW * MIS) + 3) & ~3;
     // scratch aliases, live after the volume/interface phase
     static constexpr int s_rt = w_ut;                       // [3][Nh][EPW]
     static constexpr int s_t = w_geo;                       // [3][Nq][EPW]
@@ -83,7 +98,7 @@ struct C2 {
     static constexpr int WARPS_FIT = (SMEM_MAX - 4 * o_end) / (4 * w_end + 8);
     static constexpr int WARPS = WARPS_FIT < 16 ? WARPS_FIT : 16;
     static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
-    static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + NpP4 * 4);
+    static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + (WADG ? 0 : NpP4 * 4));
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -210,7 +225,8 @@ __device__ __forceinline__ void gather_traces(const StageParams<float>& p, const
 
 // Entropy projection of a batch's new state (Sec. 2.6): u (FP32 modal, in us
 // as [field][mode][EPW]) -> u~ = u(Vh v_h) at the hybrid nodes, written to
-// ut_out as float4 (h, u, v, H).  Mi: the element's packed (M_h^k)^{-1};
+// ut_out as float4 (h, u, v, H).  Mi: the element's packed (M_h^k)^{-1}
+// (unused with the weight-adjusted inverse, which reads w J through wqv);
 // ts, ss: scratch; bqv, wqv: b and w J at this lane's volume nodes q = b +
 // LPE j; blv: b at its hybrid rows.
 template <int N>
@@ -266,53 +282,98 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
         }
     }
     __syncwarp();
-    // y = Vq^T (w J v), modes n = b + LPE*j
-    {
-        float y0[MPL], y1[MPL], y2[MPL];
+    float v0[RPL], v1[RPL], v2[RPL];
+    if constexpr (C::WADG) {
+        // weight-adjusted: z = (w/J) o (A (w J v)) at the volume nodes q = b + LPE*j
+        float c0[QPL], c1[QPL], c2[QPL];
 #pragma unroll
-        for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+        for (int j = 0; j < QPL; ++j) c0[j] = c1[j] = c2[j] = 0.f;
+        for (int q2 = 0; q2 < D::Nq; ++q2) {
+            const float t0 = ts[(0 * D::Nq + q2) * EPW + e];
+            const float t1 = ts[(1 * D::Nq + q2) * EPW + e];
+            const float t2 = ts[(2 * D::Nq + q2) * EPW + e];
+            const float* v = ops + C::o_A + (q2 * LPE + b) * C::QPLp;
+#pragma unroll
+            for (int j = 0; j < QPL; ++j) {
+                c0[j] = fmaf(v[j], t0, c0[j]);
+                c1[j] = fmaf(v[j], t1, c1[j]);
+                c2[j] = fmaf(v[j], t2, c2[j]);
+            }
+        }
+        __syncwarp();  // every lane has read w J v
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            if (q < D::Nq) {
+                const float w = ops[C::o_wq + q];
+                const float sc = valid ? w * w / wqv[j] : 0.f;
+                ts[(0 * D::Nq + q) * EPW + e] = c0[j] * sc;
+                ts[(1 * D::Nq + q) * EPW + e] = c1[j] * sc;
+                ts[(2 * D::Nq + q) * EPW + e] = c2[j] * sc;
+            }
+        }
+        __syncwarp();
+        // v~ = B z at the hybrid nodes l = b + LPE*j
+#pragma unroll
+        for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
         for (int q = 0; q < D::Nq; ++q) {
-            const float t0 = ts[(0 * D::Nq + q) * EPW + e];
-            const float t1 = ts[(1 * D::Nq + q) * EPW + e];
-            const float t2 = ts[(2 * D::Nq + q) * EPW + e];
-            const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+            const float z0 = ts[(0 * D::Nq + q) * EPW + e];
+            const float z1 = ts[(1 * D::Nq + q) * EPW + e];
+            const float z2 = ts[(2 * D::Nq + q) * EPW + e];
+            const float* v = ops + C::o_B + (q * LPE + b) * C::RPLp;
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) {
+                v0[j] = fmaf(v[j], z0, v0[j]);
+                v1[j] = fmaf(v[j], z1, v1[j]);
+                v2[j] = fmaf(v[j], z2, v2[j]);
+            }
+        }
+    } else {
+        // y = Vq^T (w J v), modes n = b + LPE*j
+        {
+            float y0[MPL], y1[MPL], y2[MPL];
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+            for (int q = 0; q < D::Nq; ++q) {
+                const float t0 = ts[(0 * D::Nq + q) * EPW + e];
+                const float t1 = ts[(1 * D::Nq + q) * EPW + e];
+                const float t2 = ts[(2 * D::Nq + q) * EPW + e];
+                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    y0[j] = fmaf(v[j], t0, y0[j]);
+                    y1[j] = fmaf(v[j], t1, y1[j]);
+                    y2[j] = fmaf(v[j], t2, y2[j]);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < MPL; ++j) {
-                y0[j] = fmaf(v[j], t0, y0[j]);
-                y1[j] = fmaf(v[j], t1, y1[j]);
-                y2[j] = fmaf(v[j], t2, y2[j]);
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = y0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = y1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = y2[j];
+                }
             }
         }
-#pragma unroll
-        for (int j = 0; j < MPL; ++j) {
-            const int n = b + LPE * j;
-            if (n < D::Np) {
-                ss[(0 * D::Np + n) * EPW + e] = y0[j];
-                ss[(1 * D::Np + n) * EPW + e] = y1[j];
-                ss[(2 * D::Np + n) * EPW + e] = y2[j];
-            }
-        }
-    }
-    __syncwarp();
-    // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
-    {
-        float r0[MPL], r1[MPL], r2[MPL];
-        minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
         __syncwarp();
+        // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
+        {
+            float r0[MPL], r1[MPL], r2[MPL];
+            minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
+            __syncwarp();
 #pragma unroll
-        for (int j = 0; j < MPL; ++j) {
-            const int n = b + LPE * j;
-            if (n < D::Np) {
-                ss[(0 * D::Np + n) * EPW + e] = r0[j];
-                ss[(1 * D::Np + n) * EPW + e] = r1[j];
-                ss[(2 * D::Np + n) * EPW + e] = r2[j];
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = r0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = r1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = r2[j];
+                }
             }
         }
-    }
-    __syncwarp();
-    // v~ = Vh v_h at the hybrid nodes l = b + LPE*j; u~ = u(v~)
-    {
-        float v0[RPL], v1[RPL], v2[RPL];
+        __syncwarp();
+        // v~ = Vh v_h at the hybrid nodes l = b + LPE*j
 #pragma unroll
         for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
         for (int n = 0; n < D::Np; ++n) {
@@ -327,6 +388,9 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
                 v2[j] = fmaf(v[j], w2, v2[j]);
             }
         }
+    }
+    // u~ = u(v~)
+    {
         if (valid) {
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
@@ -359,14 +423,13 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
     const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
     const float g = p.g;
-    const float ig = 1.f / g;
     const int K = p.K;
     const int ge = e0 + e;
     const bool valid = ge < K;
     // ---- stage element data: TMA bulk copies (one per element and array) ----
     if (lane == 0) mbar_arrive_expect_tx(bar, C::TX_BYTES);
     __syncwarp();
-    if (lane < 3 * EPW) {
+    if (lane < (C::WADG ? 2 : 3) * EPW) {
         const int which = lane / EPW, ee = lane - which * EPW;
         if (which == 0)
             tma_bulk_g2s(ws + C::w_ut + ee * C::UTS, ut_in + (size_t)(e0 + ee) * D::Nh * 4, D::Nh * 16, bar);
@@ -566,55 +629,73 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
     __syncwarp();
-    // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j ------------------
     float* ss = ws + C::s_s;
-    {
-        float s0[MPL], s1[MPL], s2[MPL];
+    float bqv[QPL], wqv[QPL], blv[RPL];
+    const float* Mi = ws + C::w_mi + e * C::MIS;  // the stored inverse (unused when weight-adjusted)
+    if constexpr (C::WADG) {
+        // ---- weight-adjusted: du/dt = -Vq^T [(w/J) o (C rt - A (w J f))] -------
 #pragma unroll
-        for (int j = 0; j < MPL; ++j) s0[j] = s1[j] = s2[j] = 0.f;
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            wqv[j] = (valid && q < D::Nq) ? __ldg(p.wJq + (size_t)ge * D::Nq + q) : 0.f;
+        }
+        float c0[QPL], c1[QPL], c2[QPL];
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) c0[j] = c1[j] = c2[j] = 0.f;
         for (int l = 0; l < D::Nh; ++l) {
             const float r0 = rt[(0 * D::Nh + l) * EPW + e];
             const float r1 = rt[(1 * D::Nh + l) * EPW + e];
             const float r2 = rt[(2 * D::Nh + l) * EPW + e];
-            const float* v = ops + C::o_VhT + (l * LPE + b) * C::MPLp;
+            const float* v = ops + C::o_C + (l * LPE + b) * C::QPLp;
 #pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                s0[j] = fmaf(v[j], r0, s0[j]);
-                s1[j] = fmaf(v[j], r1, s1[j]);
-                s2[j] = fmaf(v[j], r2, s2[j]);
+            for (int j = 0; j < QPL; ++j) {
+                c0[j] = fmaf(v[j], r0, c0[j]);
+                c1[j] = fmaf(v[j], r1, c1[j]);
+                c2[j] = fmaf(v[j], r2, c2[j]);
             }
         }
         if (p.forcing) {
-            for (int q = 0; q < D::Nq; ++q) {
-                const float f0 = ts[(0 * D::Nq + q) * EPW + e];
-                const float f1 = ts[(1 * D::Nq + q) * EPW + e];
-                const float f2 = ts[(2 * D::Nq + q) * EPW + e];
-                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+            for (int q2 = 0; q2 < D::Nq; ++q2) {
+                const float f0 = ts[(0 * D::Nq + q2) * EPW + e];
+                const float f1 = ts[(1 * D::Nq + q2) * EPW + e];
+                const float f2 = ts[(2 * D::Nq + q2) * EPW + e];
+                const float* v = ops + C::o_A + (q2 * LPE + b) * C::QPLp;
 #pragma unroll
-                for (int j = 0; j < MPL; ++j) {
-                    s0[j] = fmaf(-v[j], f0, s0[j]);
-                    s1[j] = fmaf(-v[j], f1, s1[j]);
-                    s2[j] = fmaf(-v[j], f2, s2[j]);
+                for (int j = 0; j < QPL; ++j) {
+                    c0[j] = fmaf(-v[j], f0, c0[j]);
+                    c1[j] = fmaf(-v[j], f1, c1[j]);
+                    c2[j] = fmaf(-v[j], f2, c2[j]);
                 }
             }
         }
+        __syncwarp();  // every lane has read the forcing
 #pragma unroll
-        for (int j = 0; j < MPL; ++j) {
-            const int n = b + LPE * j;
-            if (n < D::Np) {
-                ss[(0 * D::Np + n) * EPW + e] = s0[j];
-                ss[(1 * D::Np + n) * EPW + e] = s1[j];
-                ss[(2 * D::Np + n) * EPW + e] = s2[j];
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            if (q < D::Nq) {
+                const float w = ops[C::o_wq + q];
+                const float sc = valid ? w * w / wqv[j] : 0.f;
+                ts[(0 * D::Nq + q) * EPW + e] = c0[j] * sc;
+                ts[(1 * D::Nq + q) * EPW + e] = c1[j] * sc;
+                ts[(2 * D::Nq + q) * EPW + e] = c2[j] * sc;
             }
         }
-    }
-    __syncwarp();
-    // ---- du/dt = -(M_h^k)^{-1} s (modes n = b + LPE*j) into ss as [field][element][mode]
-    const float* Mi = ws + C::w_mi + e * C::MIS;
-    {
-        float r0[MPL], r1[MPL], r2[MPL];
-        minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
         __syncwarp();
+        float r0[MPL], r1[MPL], r2[MPL];
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) r0[j] = r1[j] = r2[j] = 0.f;
+        for (int q = 0; q < D::Nq; ++q) {
+            const float z0 = ts[(0 * D::Nq + q) * EPW + e];
+            const float z1 = ts[(1 * D::Nq + q) * EPW + e];
+            const float z2 = ts[(2 * D::Nq + q) * EPW + e];
+            const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                r0[j] = fmaf(v[j], z0, r0[j]);
+                r1[j] = fmaf(v[j], z1, r1[j]);
+                r2[j] = fmaf(v[j], z2, r2[j]);
+            }
+        }
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
             const int n = b + LPE * j;
@@ -624,21 +705,78 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                 ss[(2 * EPW + e) * D::Np + n] = -r2[j];
             }
         }
+    } else {
+        // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j --------------
+        {
+            float s0[MPL], s1[MPL], s2[MPL];
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) s0[j] = s1[j] = s2[j] = 0.f;
+            for (int l = 0; l < D::Nh; ++l) {
+                const float r0 = rt[(0 * D::Nh + l) * EPW + e];
+                const float r1 = rt[(1 * D::Nh + l) * EPW + e];
+                const float r2 = rt[(2 * D::Nh + l) * EPW + e];
+                const float* v = ops + C::o_VhT + (l * LPE + b) * C::MPLp;
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    s0[j] = fmaf(v[j], r0, s0[j]);
+                    s1[j] = fmaf(v[j], r1, s1[j]);
+                    s2[j] = fmaf(v[j], r2, s2[j]);
+                }
+            }
+            if (p.forcing) {
+                for (int q = 0; q < D::Nq; ++q) {
+                    const float f0 = ts[(0 * D::Nq + q) * EPW + e];
+                    const float f1 = ts[(1 * D::Nq + q) * EPW + e];
+                    const float f2 = ts[(2 * D::Nq + q) * EPW + e];
+                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                    for (int j = 0; j < MPL; ++j) {
+                        s0[j] = fmaf(-v[j], f0, s0[j]);
+                        s1[j] = fmaf(-v[j], f1, s1[j]);
+                        s2[j] = fmaf(-v[j], f2, s2[j]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * D::Np + n) * EPW + e] = s0[j];
+                    ss[(1 * D::Np + n) * EPW + e] = s1[j];
+                    ss[(2 * D::Np + n) * EPW + e] = s2[j];
+                }
+            }
+        }
+        __syncwarp();
+        // ---- du/dt = -(M_h^k)^{-1} s (modes n = b + LPE*j) into ss as [field][element][mode]
+        {
+            float r0[MPL], r1[MPL], r2[MPL];
+            minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) {
+                    ss[(0 * EPW + e) * D::Np + n] = -r0[j];
+                    ss[(1 * EPW + e) * D::Np + n] = -r1[j];
+                    ss[(2 * EPW + e) * D::Np + n] = -r2[j];
+                }
+            }
+        }
     }
     __syncwarp();
     float* us = ws + C::s_u;
     // b and w J at this lane's nodes for the projection, loaded before the RK
     // update so their latency overlaps it
-    float bqv[QPL], wqv[QPL], blv[RPL];
     if (MODE == 1) {
 #pragma unroll
         for (int j = 0; j < QPL; ++j) {
             const int q = b + LPE * j;
             bqv[j] = 0.f;
-            wqv[j] = 0.f;
+            if (!C::WADG) wqv[j] = 0.f;
             if (valid && q < D::Nq) {
                 bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
-                wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+                if (!C::WADG) wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
             }
         }
 #pragma unroll
@@ -697,9 +835,12 @@ __device__ __forceinline__ bool project2_batch(const StageParams<float>& p, floa
     const int K = p.K;
     const int ge = e0 + e;
     const bool valid = ge < K;
-    if (lane == 0) mbar_arrive_expect_tx(bar, EPW * C::NpP4 * 4);
-    __syncwarp();
-    if (lane < EPW) tma_bulk_g2s(ws + C::w_mi + lane * C::MIS, p.minv + (size_t)(e0 + lane) * C::NpP4, C::NpP4 * 4, bar);
+    if constexpr (!C::WADG) {  // the stored inverse: one bulk copy per element
+        if (lane == 0) mbar_arrive_expect_tx(bar, EPW * C::NpP4 * 4);
+        __syncwarp();
+        if (lane < EPW)
+            tma_bulk_g2s(ws + C::w_mi + lane * C::MIS, p.minv + (size_t)(e0 + lane) * C::NpP4, C::NpP4 * 4, bar);
+    }
     float bqv[QPL], wqv[QPL], blv[RPL];
 #pragma unroll
     for (int j = 0; j < QPL; ++j) {
@@ -729,8 +870,10 @@ __device__ __forceinline__ bool project2_batch(const StageParams<float>& p, floa
             p.res[gi] = 0.0;
         }
     }
-    if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
-    parity ^= 1;
+    if constexpr (!C::WADG) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
+        parity ^= 1;
+    }
     __syncwarp();
     stage2_project<N>(p, ut_out, ops, ws + C::w_mi + e * C::MIS, us, ws + C::s_t, ws + C::s_s, ge, lane, bqv, wqv,
                       blv);

@@ -624,6 +624,19 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
                 D.yf[size_t(e) * Nfq + f] = g7[1];
                 for (int c = 0; c < 4; ++c) D.geo[(size_t(e) * Nh + Nq + f) * 4 + c] = g7[2 + c];
             }
+            size_t o = size_t(e) * (Np * (Np + 1) / 2);
+            if (sp.wadg) {
+                // weight-adjusted inverse M^{-1} M_{1/J} M^{-1} (Sec. 2.8's
+                // alternative), with the reference mass matrix M = I of the
+                // orthonormal basis under these rules (exact to 2N)
+                for (int i = 0; i < Np; ++i)
+                    for (int j = 0; j <= i; ++j) {
+                        double s = 0;
+                        for (int q = 0; q < Nq; ++q) s += R.Vq(q, i) * R.wq[q] / D.Jq[size_t(e) * Nq + q] * R.Vq(q, j);
+                        D.minv[o + i * (i + 1) / 2 + j] = s;
+                    }
+                continue;
+            }
             // M_h^k = Vq^T W J Vq and its inverse (Sec. 2.7), packed lower triangle
             for (int i = 0; i < Np; ++i)
                 for (int j = 0; j < Np; ++j) {
@@ -632,7 +645,6 @@ bool build_mesh(const RefOps& R, const MeshSpec& sp, MeshData& D, std::string& e
                     Mh(i, j) = s;
                 }
             if (!invert(Mh, Mhi)) { bad = 3; return; }
-            size_t o = size_t(e) * (Np * (Np + 1) / 2);
             for (int i = 0; i < Np; ++i)
                 for (int j = 0; j <= i; ++j) D.minv[o + i * (i + 1) / 2 + j] = 0.5 * (Mhi(i, j) + Mhi(j, i));
         }

@@ -52,6 +52,7 @@ struct MeshSpec {
     double x0, x1, y0, y1;
     double ax, ay;
     bool walls;  // reflective walls on the four sides instead of periodic wrap
+    bool wadg;   // minv holds the weight-adjusted inverse Vq^T W diag(1/J) Vq instead of (M_h^k)^{-1}
 };
 
 // Mesh, connectivity and geometry.  Per-element arrays are [K][...].
@@ -63,6 +64,7 @@ struct MeshData {
     std::vector<double> geo;        // [K][Nh][4]: rxJ, sxJ, ryJ, syJ
     std::vector<double> Jq;         // [K][Nq]
     std::vector<double> minv;       // [K][Np(Np+1)/2] packed lower triangle of (M_h^k)^-1
+                                    // (or of its weight-adjusted approximation, MeshSpec::wadg)
     std::vector<int> nbr;           // [K][3]: 4 * neighbour element + neighbour face (4 e + 3: wall)
 };
 

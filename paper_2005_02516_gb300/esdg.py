@@ -32,6 +32,8 @@ ESDG_BOUNDARY_PERIODIC = 0
 ESDG_BOUNDARY_WALLS = 1
 ESDG_RULE_COLLAPSED = 0
 ESDG_RULE_SYMMETRIC = 1
+ESDG_MASS_EXACT = 0
+ESDG_MASS_WEIGHT_ADJUSTED = 1
 ESDG_POINTS_NODAL = 0
 ESDG_POINTS_VOLQ = 1
 ESDG_POINTS_FACEQ = 2
@@ -69,7 +71,7 @@ class Config(ctypes.Structure):
                 ("lax_friedrichs", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("mms_amp", ctypes.c_double), ("mms_bamp", ctypes.c_double),
                 ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double),
-                ("volume_rule", ctypes.c_int), ("boundary", ctypes.c_int)]
+                ("volume_rule", ctypes.c_int), ("boundary", ctypes.c_int), ("mass", ctypes.c_int)]
 
 
 _lib = None
@@ -142,7 +144,10 @@ def _ptr(a):
 
 
 def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, warp=0.0, g=1.0, cfl=0.25,
-                lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False):
+                lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False,
+                mass="exact"):
+    if mass not in ("exact", "weight_adjusted"):
+        raise ValueError("mass must be 'exact' or 'weight_adjusted'")
     cfg = Config()
     cfg.N, cfg.nx, cfg.ny = N, nx, ny
     cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
@@ -154,6 +159,7 @@ def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, w
     cfg.mms_amp, cfg.mms_bamp, cfg.mms_u0, cfg.mms_v0 = mms
     cfg.volume_rule = ESDG_RULE_SYMMETRIC if rule == "symmetric" else ESDG_RULE_COLLAPSED
     cfg.boundary = ESDG_BOUNDARY_WALLS if walls else ESDG_BOUNDARY_PERIODIC
+    cfg.mass = ESDG_MASS_WEIGHT_ADJUSTED if mass == "weight_adjusted" else ESDG_MASS_EXACT
     return cfg
 
 
@@ -276,11 +282,12 @@ class Solver:
 
     def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
                  warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
-                 mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, torch_memory=True, stream=None):
+                 mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, mass="exact", torch_memory=True,
+                 stream=None):
         import torch
         self.lib = load_library()
         cfg = make_config(N, nx, ny, precision=precision, x0=x0, x1=x1, y0=y0, y1=y1, warp=warp, g=g, cfl=cfl,
-                          lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule, walls=walls)
+                          lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule, walls=walls, mass=mass)
         self.cfg = cfg
         h = ctypes.c_void_p()
         self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)

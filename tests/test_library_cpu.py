@@ -47,6 +47,7 @@ def _cfg(**kw):
     c.lax_friedrichs, c.forcing = 1, 0
     c.volume_rule = kw.get("rule", esdg.ESDG_RULE_COLLAPSED)
     c.boundary = kw.get("boundary", esdg.ESDG_BOUNDARY_PERIODIC)
+    c.mass = kw.get("mass", esdg.ESDG_MASS_EXACT)
     return c
 
 
@@ -58,7 +59,7 @@ def _build(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7),
-                                 dict(rule=2), dict(rule=-1), dict(boundary=2)])
+                                 dict(rule=2), dict(rule=-1), dict(boundary=2), dict(mass=2), dict(mass=-1)])
 def test_build_rejects_bad_config(bad):
     lib, rc, h = _build(**bad)
     assert rc == esdg.ESDG_EINVAL
@@ -130,3 +131,26 @@ def test_walled_mesh_points_match_oracle(N, rule):
     xo, yo = o.points("faceq")
     assert np.abs(x - xo).max() < 1e-13 and np.abs(y - yo).max() < 1e-13
     lib.esdg_destroy(h)
+
+
+@pytest.mark.parametrize("precision", [esdg.ESDG_FP64, esdg.ESDG_FP32])
+@pytest.mark.parametrize("rule", [esdg.ESDG_RULE_COLLAPSED, esdg.ESDG_RULE_SYMMETRIC])
+def test_weight_adjusted_mass_stores_no_inverses(rule, precision):
+    """The weight-adjusted inverse keeps no per-element matrix on the device:
+    the footprint drops by the stored inverses, K Np(Np+1)/2 values of the
+    RHS precision, less the few KB that the FP32 kernel's composed shared
+    operators add."""
+    sizes = {}
+    for mass in (esdg.ESDG_MASS_EXACT, esdg.ESDG_MASS_WEIGHT_ADJUSTED):
+        lib, rc, h = _build(N=4, nx=16, ny=16, warp=0.05, rule=rule, precision=precision, mass=mass)
+        assert rc == 0
+        K, Np = ctypes.c_int(), ctypes.c_int()
+        nb = ctypes.c_size_t()
+        assert lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), None, None, ctypes.byref(nb)) == 0
+        sizes[mass] = (K.value, Np.value, nb.value)
+        lib.esdg_destroy(h)
+    K, Np, exact = sizes[esdg.ESDG_MASS_EXACT]
+    wadg = sizes[esdg.ESDG_MASS_WEIGHT_ADJUSTED][2]
+    rs = 4 if precision == esdg.ESDG_FP32 else 8
+    stored = K * Np * (Np + 1) // 2 * rs
+    assert stored - 16384 <= exact - wadg <= stored + 16384

@@ -34,15 +34,18 @@ from paper_2005_02516_gb300 import workloads as W  # noqa: E402
 METRIC = "GDOF-stage/s FP32 vs FP64 per GB300 at stated L2 error; served p50/p99 latency"
 UNIT = "GDOF-stage/s"
 WL = W.DAM
-# DRAM traffic of one stage launch at this workload, from one ncu capture
-# (profiles/k_stage2_dam_k131072_n4.md), valid only for the kernel source it
-# was measured on: reported as null once that source changes.
-STAGE_TRAFFIC = {"source_sha1": "b8c8c94cd23ef530f7f4fe74592532cf63716ecd", "bytes": 431.4e6}
+# DRAM traffic of one stage launch at this workload, per inverse-mass kind,
+# from one ncu capture each (profiles/k_stage2_dam_k131072_n4.md and
+# profiles/k_stage2_wadg_dam_k131072_n4.md), valid only
+# for the kernel source it was measured on: reported as null once that source
+# changes.
+STAGE_TRAFFIC = {"exact": {"source_sha1": "f02127742633926d43cbacca013f9cc9b778da04", "bytes": 432.4e6},
+                 "weight_adjusted": {"source_sha1": "f02127742633926d43cbacca013f9cc9b778da04", "bytes": 362.5e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 
 # Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of
 # each step of the path, and the bytes each element-stage must move.
-def algorithmic_flops(N, Nq):
+def algorithmic_flops(N, Nq, wadg=False):
     Np = (N + 1) * (N + 2) // 2
     Nfq = 3 * (N + 1)
     Nh = Nq + Nfq
@@ -50,16 +53,25 @@ def algorithmic_flops(N, Nq):
     flops = 0
     flops += 2 * Nq * Np * 3                          # u_q = Vq u
     flops += 10 * Nq                                  # entropy variables
-    flops += 2 * Np * Nq * 3 + 3 * Nq + 2 * Np * Np * 3   # J-weighted projection
-    flops += 2 * Nh * Np * 3 + 6 * Nh                 # v~ = Vh v_h, u~ = u(v~)
+    if wadg:
+        # weight-adjusted inverse through the composed factors A = Vq Vq^T,
+        # B = Vh Vq^T, C = Vq Vh^T and the per-node scale w/J
+        flops += 3 * Nq + 2 * Nq * Nq * 3 + 4 * Nq    # A (w J v), scale
+        flops += 2 * Nh * Nq * 3 + 6 * Nh             # v~ = B z, u~ = u(v~)
+    else:
+        flops += 2 * Np * Nq * 3 + 3 * Nq + 2 * Np * Np * 3   # J-weighted projection
+        flops += 2 * Nh * Np * 3 + 6 * Nh                 # v~ = Vh v_h, u~ = u(v~)
     flops += 35 * pairs                               # flux differencing (35 flops / unique pair)
     flops += 40 * Nfq                                 # interface flux + Lax-Friedrichs
-    flops += 2 * Np * Nh * 3 + 2 * Np * Np * 3        # lift + inverse mass
+    if wadg:
+        flops += 2 * Nq * Nh * 3 + 4 * Nq + 2 * Np * Nq * 3   # C r, scale, Vq^T
+    else:
+        flops += 2 * Np * Nh * 3 + 2 * Np * Np * 3        # lift + inverse mass
     flops += 4 * 3 * Np                               # RK stage (FP64)
     return flops
 
 
-def algorithmic_bytes(N, Nq, real_bytes=4):
+def algorithmic_bytes(N, Nq, real_bytes=4, wadg=False):
     Np = (N + 1) * (N + 2) // 2
     Nfq = 3 * (N + 1)
     Nh = Nq + Nfq
@@ -70,7 +82,7 @@ def algorithmic_bytes(N, Nq, real_bytes=4):
     b += Nfq * 3 * real_bytes           # neighbour traces (h, u, v)
     b += Nh * 4 * real_bytes            # metrics rxJ sxJ ryJ syJ
     b += Nq * real_bytes                # w_q J_q
-    b += NpP * real_bytes               # packed inverse mass matrix
+    b += 0 if wadg else NpP * real_bytes    # packed inverse mass matrix (none when weight-adjusted)
     b += Nh * real_bytes                # bathymetry at hybrid nodes
     b += 3 * 4                          # neighbour ids
     return b
@@ -173,9 +185,9 @@ def replica_value(units_per_rank, world, max_seconds):
     return units_per_rank * world / max_seconds / 1e9
 
 
-def make_solver(precision):
+def make_solver(precision, mass="exact"):
     from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
-    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
+    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule, mass=mass)
     xb, yb = s.points(ESDG_POINTS_NODAL)
     xq, yq = s.points(ESDG_POINTS_VOLQ)
     s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
@@ -489,6 +501,8 @@ def main():
     ap.add_argument("--ensemble-steps", type=int, default=500)
     ap.add_argument("--served", type=int, default=200, help="FP32 requests of the served leg (0: skip)")
     ap.add_argument("--served-rate", type=float, default=20.0)
+    ap.add_argument("--mass", default="exact", choices=["exact", "weight_adjusted"],
+                    help="inverse mass of the timed leg: stored (M_h^k)^-1 (the paper's) or weight-adjusted")
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
@@ -506,7 +520,8 @@ def main():
     torch.cuda.set_device(local)
     peaks, peak_kind = load_peaks()
 
-    s = make_solver("fp32")
+    s = make_solver("fp32", args.mass)
+    wadg = args.mass == "weight_adjusted"
     steps = args.steps
     clocks = ClockSampler(local)
     clocks.start()
@@ -518,23 +533,45 @@ def main():
     value = replica_value(units, world, el_max)
     launches = 5 * steps
     t_launch = el / launches
-    flops = algorithmic_flops(WL.N, WL.Nq) * K
-    nbytes = algorithmic_bytes(WL.N, WL.Nq, 4) * K
+    flops = algorithmic_flops(WL.N, WL.Nq, wadg) * K
+    nbytes = algorithmic_bytes(WL.N, WL.Nq, 4, wadg) * K
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
     alu = flops / t_launch / 1e12
     hbm = nbytes / t_launch / 1e9
     traffic = None
     import hashlib
+    rec = STAGE_TRAFFIC.get(args.mass)
     with open(STAGE_SOURCE, "rb") as f:
-        if hashlib.sha1(f.read()).hexdigest() == STAGE_TRAFFIC["source_sha1"]:
-            traffic = STAGE_TRAFFIC["bytes"]
+        if rec is not None and hashlib.sha1(f.read()).hexdigest() == rec["source_sha1"]:
+            traffic = rec["bytes"]
     roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
                 "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": hbm / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind}
     roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
     other = roof_hbm if roofline is roof_alu else roof_alu
+
+    # The other inverse-mass kind on the same workload, same steps, for
+    # comparison: its throughput, HBM roofline fraction and the relative L2
+    # difference of the two FP32 states after the same warm-up + timed steps
+    other_mass = None
+    if not args.fp32_only:
+        om = "exact" if wadg else "weight_adjusted"
+        s2 = make_solver("fp32", om)
+        el2 = time_steps(s2, steps, args.warmup, world)
+        t2 = el2 / launches
+        by2 = algorithmic_bytes(WL.N, WL.Nq, 4, om == "weight_adjusted") * K
+        u1, u2 = s.get_state(), s2.get_state()
+        other_mass = {"mass": om, "value": K * Np * 5 * steps / el2 / 1e9, "unit": UNIT,
+                      "ms_per_step": el2 / steps * 1e3, "steps": steps,
+                      "hbm": {"achieved": by2 / t2 / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": by2 / t2 / 1e9 / peaks["hbm_gbs"],
+                              "algorithmic_bytes_per_element_stage": by2 / K},
+                      "device_bytes": s2.device_bytes, "device_bytes_%s" % args.mass: s.device_bytes,
+                      "state_rel_l2_between_kinds": float(np.linalg.norm(u2 - u1) / np.linalg.norm(u1))}
+        s2.close()
+        del s2
 
     # FP64 right-hand side on the same workload (the plain FP64 path), a few steps
     fp64 = None
@@ -587,10 +624,11 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WL.name if args.nx is None else "%s_nx%d" % (WL.name, args.nx),
                            "N": WL.N, "K": K, "Np": Np, "Nq": WL.Nq, "volume_rule": WL.rule, "curved": True,
+                           "mass": args.mass,
                            "rhs_precision": "fp32", "rk_accumulation": "fp64",
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "roofline_other": other,
+                "roofline": roofline, "roofline_other": other, "other_mass": other_mass,
                 "fp64": fp64, "precision": precision, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))

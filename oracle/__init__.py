@@ -11,12 +11,15 @@ paper's definitions, written for readability, not speed.
 
 Modules
 -------
-refelem   reference triangle: basis, quadrature, Vq, Vf, Pq, D, Q-hat, Q_h (Sec. 2.1-2.3)
+refelem   reference triangle: basis, quadrature (collapsed, symmetric, SBP), Vq, Vf, Pq, D,
+          Q-hat, Q_h (Sec. 2.1-2.3, 3.1)
 mesh      structured periodic triangulation, curved warp, geometric factors,
           exact or weight-adjusted inverse mass matrices (Sec. 2.7, 2.8)
 swe       entropy, entropy variables, EC flux (Sec. 2.4, 2.5, 2.8)
 esdg      semi-discrete right-hand side in the literal form of eq. (dgform),
           LSRK45 time stepping (Sec. 4), diagnostics
+sbp       the traditional DG-SBP scheme of Sec. 3 on SBP quadrature rules
+          (refelem.sbp_quadrature): Q_SBP from Theorem 3.1, nodal unknowns
 volume    dense-operator volume terms of the ESDG and traditional DG kernels
           (the cost comparison of Sec. 5.4)
 

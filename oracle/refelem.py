@@ -191,6 +191,8 @@ class RefElem:
             self.rq, self.sq, self.w = triangle_quadrature(N + 1)
         elif rule == "symmetric":
             self.rq, self.sq, self.w = symmetric_quadrature(N)
+        elif rule == "sbp":
+            self.rq, self.sq, self.w = sbp_quadrature(N)
         else:
             raise ValueError(rule)
         self.rf, self.sf, self.wf, self.nr, self.ns = face_quadrature(N)
@@ -199,6 +201,15 @@ class RefElem:
         self.Nh = self.Nq + self.Nfq
         self.Vq, self.Vqr, self.Vqs = basis(N, self.rq, self.sq, derivs=True)
         self.Vf, self.Vfr, self.Vfs = basis(N, self.rf, self.sf, derivs=True)
+        if rule == "sbp":
+            # the selection I_f of Sec. 3.2 as an index map: face node j is
+            # volume node fmap[j] (the same point)
+            d = np.hypot(self.rf[:, None] - self.rq[None, :], self.sf[:, None] - self.sq[None, :])
+            self.fmap = np.argmin(d, axis=1)
+            if np.max(d[np.arange(self.rf.size), self.fmap]) > 1e-12:
+                raise RuntimeError("a face node is not a volume node of the SBP rule")
+            self.If = np.zeros((self.rf.size, self.rq.size))
+            self.If[np.arange(self.rf.size), self.fmap] = 1.0
         W = np.diag(self.w)
         Wf = np.diag(self.wf)
         # mass matrix and quadrature L2 projection (Sec. 2.1, eq. (PqVq))
@@ -387,3 +398,155 @@ def symmetric_quadrature(N):
         r, s, w, _, _ = _sym_points(best, st)
         _SYM_CACHE[d] = (r, s, w)
     return _SYM_CACHE[d]
+
+
+# ---------------------------------------------------------------------------
+# SBP quadrature rules (Sec. 3.1): positive weights, exact to degree 2N-1, the
+# N+1 Gauss-Legendre points of every face among the nodes (so the face rule is
+# exact to 2N+1 >= 2N and is the same on each face).  The paper shows its rules
+# only as figures; these are constructed here: fully symmetric, the edge
+# orbits fixed at the Gauss-Legendre points (a 6-point orbit per pair +-t, the
+# three edge midpoints when N+1 is odd) with free weights, plus interior
+# orbits (centroid, S21, S111 as above) chosen per degree so that the
+# symmetric moment equations form a square system:
+#   N = 1: no interior orbit (6 points); N = 2: centroid (10);
+#   N = 3: one S111 (18); N = 4: centroid + two S21 (22);
+#   N = 5: centroid + one S21 + two S111 (34).
+# Each has a single positive interior solution among the seeded restarts
+# (for N = 5 the structure with three S21 and one S111 has two, so it is not
+# used).
+# ---------------------------------------------------------------------------
+SBP_STRUCT = {1: (0, 0, 0), 2: (1, 0, 0), 3: (0, 0, 1), 4: (1, 2, 0), 5: (1, 1, 2)}
+
+
+def _sbp_edge_orbits(N):
+    """Barycentric points of the Gauss-Legendre edge orbits and their owner
+    index: the edge midpoints (if N+1 is odd) then one orbit per t > 0."""
+    t, _ = gauss_legendre(N + 1)
+    lam, owner = [], []
+    k = 0
+    if (N + 1) % 2 == 1:
+        for p in [(0.5, 0.5, 0.0), (0.0, 0.5, 0.5), (0.5, 0.0, 0.5)]:
+            lam.append(p)
+            owner.append(k)
+        k += 1
+    for tp in sorted(x for x in t if x > 1e-12):
+        a = 0.5 * (1.0 - tp)
+        for p in [(a, 1 - a, 0.0), (1 - a, a, 0.0), (0.0, a, 1 - a), (0.0, 1 - a, a), (a, 0.0, 1 - a),
+                  (1 - a, 0.0, a)]:
+            lam.append(p)
+            owner.append(k)
+        k += 1
+    return lam, owner, k
+
+
+def _sbp_points(theta, N):
+    """(r, s, w, dlam, owner) of the SBP rule with parameters theta = edge
+    weights followed by the interior orbit parameters of SBP_STRUCT[N]."""
+    lam, owner, ne = _sbp_edge_orbits(N)
+    w = [theta[o] for o in owner]
+    dl = [{} for _ in owner]
+    if sum(SBP_STRUCT[N]):
+        r_i, s_i, w_i, dl_i, own_i = _sym_points(theta[ne:], SBP_STRUCT[N])
+    else:
+        r_i = s_i = w_i = np.zeros(0)
+        dl_i, own_i = [], []
+    lam = np.array(lam)
+    r = np.concatenate([-lam[:, 0] + lam[:, 1] - lam[:, 2], r_i])
+    s = np.concatenate([-lam[:, 0] - lam[:, 1] + lam[:, 2], s_i])
+    w = np.concatenate([np.array(w), w_i])
+    dl = dl + [{ne + j: d for j, d in di.items()} for di in dl_i]
+    owner = owner + [ne + o for o in own_i]
+    return r, s, w, dl, owner, ne
+
+
+def _sbp_solve(N, seed):
+    st = SBP_STRUCT[N]
+    _, _, ne = _sbp_edge_orbits(N)
+    n = ne + st[0] + 2 * st[1] + 3 * st[2]
+    rng = np.random.default_rng(seed)
+    th = list(rng.uniform(0.01, 0.2, ne))
+    if st[0]:
+        th.append(rng.uniform(0.05, 0.3))
+    for _ in range(st[1]):
+        th += [rng.uniform(0.02, 0.48), rng.uniform(0.02, 0.3)]
+    for _ in range(st[2]):
+        th += [rng.uniform(0.01, 0.45), rng.uniform(0.01, 0.45), rng.uniform(0.02, 0.2)]
+    th = np.array(th)
+    d = 2 * N - 1
+    target = np.zeros(num_modes(d))
+    target[0] = np.sqrt(2.0)
+
+    def resid_jac(th):
+        r, s, w, dl, owner, _ = _sbp_points(th, N)
+        V, Vr, Vs = basis(d, r, s, derivs=True)
+        R = V.T @ w - target
+        J = np.zeros((R.size, n))
+        for i in range(r.size):
+            J[:, owner[i]] += V[i]
+            for j, dlam in dl[i].items():
+                drj = -dlam[0] + dlam[1] - dlam[2]
+                dsj = -dlam[0] - dlam[1] + dlam[2]
+                J[:, j] += w[i] * (Vr[i] * drj + Vs[i] * dsj)
+        return R, J
+    mu = 1e-3
+    R, J = resid_jac(th)
+    for _ in range(300):
+        if np.linalg.norm(R) < 1e-15:
+            break
+        try:
+            step = np.linalg.solve(J.T @ J + mu * np.eye(n), -J.T @ R)
+        except np.linalg.LinAlgError:
+            return False, th
+        if not np.all(np.isfinite(step)):
+            return False, th
+        R2, J2 = resid_jac(th + step)
+        if np.linalg.norm(R2) < np.linalg.norm(R):
+            th, R, J = th + step, R2, J2
+            mu = max(mu / 3, 1e-15)
+        else:
+            mu *= 10
+            if mu > 1e10:
+                break
+    r, s, w, _, _, ne = _sbp_points(th, N)
+    ri, si = r[_sbp_edge_count(N):], s[_sbp_edge_count(N):]
+    ok = (np.linalg.norm(R) < 1e-13 and np.all(w > 0) and np.all(ri > -1 + 1e-9) and np.all(si > -1 + 1e-9)
+          and np.all(ri + si < -1e-9))
+    return ok, th
+
+
+def _sbp_edge_count(N):
+    return 3 * ((N + 1) % 2) + 6 * ((N + 1) // 2)
+
+
+_SBP_CACHE = {}
+# restarts stop after this many successful solves (the solution is unique for
+# these orbit structures, so every success gives the same rule)
+SBP_SOLUTIONS = 4
+
+
+def sbp_quadrature(N):
+    """(r, s, w) of the SBP rule of degree N (N = 1..5): edge nodes first
+    (midpoints, then the 6-point orbits by increasing t), then the interior
+    orbits in canonical order; among the first SBP_SOLUTIONS successful
+    seeded restarts the solution whose smallest weight is largest."""
+    if N not in _SBP_CACHE:
+        st = SBP_STRUCT[N]
+        _, _, ne = _sbp_edge_orbits(N)
+        best, best_min, found = None, -1.0, 0
+        for seed in range(SYM_RESTARTS):
+            if found == SBP_SOLUTIONS:
+                break
+            ok, th = _sbp_solve(N, seed)
+            if not ok:
+                continue
+            found += 1
+            th = np.concatenate([th[:ne], _canonical(th[ne:], st)])
+            wmin = _sbp_points(th, N)[2].min()
+            if wmin > best_min + 1e-12:
+                best, best_min = th, wmin
+        if best is None:
+            raise RuntimeError("no SBP rule found for N = %d" % N)
+        r, s, w, _, _, _ = _sbp_points(best, N)
+        _SBP_CACHE[N] = (r, s, w)
+    return _SBP_CACHE[N]

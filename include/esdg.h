@@ -75,6 +75,18 @@ extern "C" {
 #define ESDG_MASS_EXACT           0
 #define ESDG_MASS_WEIGHT_ADJUSTED 1
 
+/* the scheme: the hybridized modal ESDG method of Sec. 2 (unknowns: modal
+   coefficients, state [3][K][Np]), or the traditional entropy-stable DG-SBP
+   method of Sec. 3 (unknowns: nodal values at the Nq points of an SBP rule,
+   exact to 2N-1 with the face Gauss-Legendre points among its nodes: 6, 10,
+   18, 22, 34 points for N = 1..5; state [3][K][Nq]; no entropy projection;
+   SBP operators Q_SBP = [I; I_f]^T Q_h [I; I_f] of Theorem 3.1; diagonal mass
+   W J).  The DG-SBP method takes periodic boundaries and ESDG_MASS_EXACT,
+   ignores volume_rule, and runs outside ensembles and the server.  Its
+   ESDG_POINTS_VOLQ points are the SBP nodes, where initial data are given. */
+#define ESDG_METHOD_MODAL 0
+#define ESDG_METHOD_SBP   1
+
 /* point sets for esdg_get_points */
 #define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
 #define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
@@ -99,6 +111,7 @@ typedef struct esdg_config {
     int volume_rule;        /* ESDG_RULE_* */
     int boundary;           /* ESDG_BOUNDARY_* */
     int mass;               /* ESDG_MASS_*; ensembles and served FP32 requests take ESDG_MASS_EXACT */
+    int method;             /* ESDG_METHOD_* */
 } esdg_config;
 
 /*

@@ -109,6 +109,11 @@ class SBPOracle:
             out[:, ks] = self._rhs_rows(u, ks, t)
         return out
 
+    def rhs_elements(self, u, elems, t=0.0):
+        """du/dt on the listed elements only (no projection couples them: each
+        needs its own and its face neighbours' nodal values)."""
+        return self._rhs_rows(u, np.asarray(elems, dtype=np.int64), t)
+
     def _rhs_rows(self, u_all, ks, t):
         ref, m, g = self.ref, self.mesh, self.g
         Nfq = self.Nfq

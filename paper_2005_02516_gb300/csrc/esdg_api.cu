@@ -48,6 +48,7 @@ struct DevLayout {
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
+    size_t fmap = 0;                     // DG-SBP: volume node of each face node (int)
     size_t u = 0, res = 0, rhs = 0, ut0 = 0, ut1 = 0;
     size_t partial = 0, diag = 0, status = 0;
     size_t total = 0;
@@ -72,6 +73,9 @@ struct esdg_ctx {
     LaunchGeom lg2;      // k_stage2 (FP32)
     int Kpad = 0;        // per-element arrays are padded to a multiple of 8 elements
     int mstride = 0;     // element stride of the packed inverse mass matrices
+    bool sbp = false;    // the DG-SBP scheme of Sec. 3 (nodal unknowns at the SBP rule's nodes)
+    int ndof = 0;        // unknowns per element and field: Np (modal) or Nq (DG-SBP)
+    int nrec = 0;        // node records per element: Nh (hybrid nodes) or Nq (DG-SBP)
     int entropy_parts = 0;
     int num_sms = 0;
     int cur = 0;            // which u~ buffer holds the current stage's values
@@ -99,6 +103,7 @@ static size_t real_size(const esdg_ctx* c) { return c->cfg.precision == ESDG_FP3
 static int c2_ops_floats(int N);
 
 static bool weight_adjusted(const esdg_config& cfg) { return cfg.mass == ESDG_MASS_WEIGHT_ADJUSTED; }
+static bool is_sbp(const esdg_config& cfg) { return cfg.method == ESDG_METHOD_SBP; }
 
 // Kernel template parameter of a configuration: NR = N + 8 * rule + 16 * wadg.
 static int kernel_nr(const esdg_config& cfg) {
@@ -118,30 +123,38 @@ static void compute_layout(esdg_ctx* c) {
     const size_t Kp = size_t(c->Kpad);
     const int NpP = R.Np * (R.Np + 1) / 2;
     c->mstride = (NpP + 3) & ~3;
+    const bool sbp = is_sbp(c->cfg);
+    c->sbp = sbp;
+    c->ndof = sbp ? R.Nq : R.Np;
+    c->nrec = sbp ? R.Nq : R.Nh;
+    const size_t nrec = size_t(c->nrec), ndof = size_t(c->ndof);
     DevLayout& L = c->L;
     size_t off = 0;
     auto take = [&](size_t bytes) { size_t o = off; off = align256(off + bytes); return o; };
-    L.ops_bytes = rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np + 3 * size_t(R.Nfq) +
-                        size_t(R.Nq));
+    L.ops_bytes = sbp ? rs * (size_t(R.Nq) * R.Nq * 2 + 3 * size_t(R.Nfq))
+                      : rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np +
+                              3 * size_t(R.Nfq) + size_t(R.Nq));
     L.ops = take(L.ops_bytes);
-    L.ops2_bytes = c->cfg.precision == ESDG_FP32 ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
+    L.ops2_bytes = (!sbp && c->cfg.precision == ESDG_FP32) ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
     L.ops2 = take(L.ops2_bytes);
-    L.vq64 = take(8 * size_t(R.Nq) * R.Np);
-    L.geo = take(rs * Kp * R.Nh * 4);
+    L.vq64 = take(sbp ? 0 : 8 * size_t(R.Nq) * R.Np);
+    L.geo = take(rs * Kp * nrec * 4);
     L.wJq = take(rs * Kp * R.Nq);
-    L.minv = take(weight_adjusted(c->cfg) ? 0 : rs * Kp * c->mstride);  // none with the weight-adjusted inverse
-    L.bh = take(rs * Kp * R.Nh);
+    // no stored inverses with the weight-adjusted inverse or the diagonal SBP mass
+    L.minv = take((sbp || weight_adjusted(c->cfg)) ? 0 : rs * Kp * c->mstride);
+    L.bh = take(rs * Kp * nrec);
     L.nbr = take(4 * Kp * 3);
+    L.fmap = take(sbp ? 4 * size_t(R.Nfq) : 0);
     const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
     L.xq = take(forcing ? rs * Kp * R.Nq : 0);
     L.yq = take(forcing ? rs * Kp * R.Nq : 0);
     L.wJq64 = take(8 * K * R.Nq);
     L.bq64 = take(8 * K * R.Nq);
-    L.u = take(8 * 3 * K * R.Np);
-    L.res = take(8 * 3 * K * R.Np);
-    L.rhs = take(8 * 3 * K * R.Np);
-    L.ut0 = take(rs * Kp * R.Nh * 4);
-    L.ut1 = take(rs * Kp * R.Nh * 4);
+    L.u = take(8 * 3 * K * ndof);
+    L.res = take(8 * 3 * K * ndof);
+    L.rhs = take(8 * 3 * K * ndof);
+    L.ut0 = take(rs * Kp * nrec * 4);
+    L.ut1 = take(rs * Kp * nrec * 4);
     c->entropy_parts = 1024;
     L.partial = take(8 * 3 * size_t(c->entropy_parts));
     L.diag = take(8 * 4);
@@ -178,6 +191,34 @@ static std::vector<real> pack_ops(const RefOps& R) {
         o.push_back((real)R.ns[f]);
     }
     for (int q = 0; q < R.Nq; ++q) o.push_back((real)R.wq[q]);
+    return o;
+}
+
+// Operators of the DG-SBP kernel (SbpSmem in esdg_sbp.cuh): the skew SBP
+// operators Q_SBP - Q_SBP^T = [I; I_f]^T (Q_h - Q_h^T) [I; I_f] (Theorem 3.1)
+// as [Nq(m)][Nq(l)][2] = (r, s) pairs, then w_f and the scaled normals.
+template <typename real>
+static std::vector<real> pack_ops_sbp(const RefOps& R) {
+    const int Nq = R.Nq;
+    auto node = [&](int a) { return a < Nq ? a : R.fmap[a - Nq]; };
+    Mat Sr(Nq, Nq), Ss(Nq, Nq);
+    for (int a = 0; a < R.Nh; ++a)
+        for (int b = 0; b < R.Nh; ++b) {
+            Sr(node(a), node(b)) += R.Qsr(a, b);
+            Ss(node(a), node(b)) += R.Qss(a, b);
+        }
+    std::vector<real> o;
+    o.reserve(size_t(Nq) * Nq * 2 + 3 * size_t(R.Nfq));
+    for (int m = 0; m < Nq; ++m)
+        for (int l = 0; l < Nq; ++l) {
+            o.push_back((real)Sr(l, m));
+            o.push_back((real)Ss(l, m));
+        }
+    for (int f = 0; f < R.Nfq; ++f) o.push_back((real)R.wf[f]);
+    for (int f = 0; f < R.Nfq; ++f) {
+        o.push_back((real)R.nr[f]);
+        o.push_back((real)R.ns[f]);
+    }
     return o;
 }
 
@@ -277,20 +318,30 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     const RefOps& R = c->ref;
     const MeshData& M = c->mesh;
     const size_t K = size_t(M.K);
-    put(img, c->L.ops, pack_ops<real>(R));
-    put(img, c->L.vq64, R.Vq.a);
-    // the FP32 batched kernel reads the metrics pre-scaled by 1/8 (exact)
-    const double gscale = c->cfg.precision == ESDG_FP32 ? 0.125 : 1.0;
-    std::vector<real> geo(M.geo.size());
-    for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
-    put(img, c->L.geo, geo);
-    if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, kernel_nr(c->cfg)));
+    if (c->sbp) {
+        put(img, c->L.ops, pack_ops_sbp<real>(R));
+        put(img, c->L.fmap, R.fmap);
+        // metrics at the SBP nodes (the volume part of the hybrid nodes)
+        std::vector<real> geo(K * R.Nq * 4);
+        for (size_t e = 0; e < K; ++e)
+            for (size_t i = 0; i < size_t(R.Nq) * 4; ++i) geo[e * R.Nq * 4 + i] = (real)M.geo[e * R.Nh * 4 + i];
+        put(img, c->L.geo, geo);
+    } else {
+        put(img, c->L.ops, pack_ops<real>(R));
+        put(img, c->L.vq64, R.Vq.a);
+        // the FP32 batched kernel reads the metrics pre-scaled by 1/8 (exact)
+        const double gscale = c->cfg.precision == ESDG_FP32 ? 0.125 : 1.0;
+        std::vector<real> geo(M.geo.size());
+        for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
+        put(img, c->L.geo, geo);
+        if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, kernel_nr(c->cfg)));
+    }
     std::vector<double> wJ64(K * R.Nq);
     for (size_t e = 0; e < K; ++e)
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
     put(img, c->L.wJq, to_real<real>(wJ64));
     put(img, c->L.wJq64, wJ64);
-    if (!weight_adjusted(c->cfg)) {
+    if (!weight_adjusted(c->cfg) && !c->sbp) {
         const int NpP = R.Np * (R.Np + 1) / 2;
         std::vector<real> mi(K * size_t(c->mstride), (real)0);
         for (size_t e = 0; e < K; ++e)
@@ -309,13 +360,14 @@ template <typename real>
 static void bathymetry_arrays(const esdg_ctx* c, std::vector<real>& bhr, std::vector<double>& bq) {
     const RefOps& R = c->ref;
     const size_t K = size_t(c->mesh.K);
-    bhr.assign(K * R.Nh, (real)0);
+    const int nrec = c->nrec;  // hybrid nodes, or the SBP nodes (the first Nq rows of V_h)
+    bhr.assign(K * nrec, (real)0);
     bq.assign(K * R.Nq, 0.0);
     for (size_t e = 0; e < K; ++e)
-        for (int l = 0; l < R.Nh; ++l) {
+        for (int l = 0; l < nrec; ++l) {
             double s = 0;
             for (int n = 0; n < R.Np; ++n) s += R.Vh(l, n) * c->b_modal[e * R.Np + n];
-            bhr[e * R.Nh + l] = (real)s;
+            bhr[e * nrec + l] = (real)s;
             if (l < R.Nq) bq[e * R.Nq + l] = s;
         }
 }
@@ -326,6 +378,18 @@ static void project_host(const esdg_ctx* c, const double* q_volq, int mode, doub
     const RefOps& R = c->ref;
     const MeshData& M = c->mesh;
     const size_t K = size_t(M.K);
+    if (c->sbp) {
+        // DG-SBP: the unknowns are the nodal values themselves (SURFACE: h = H - b)
+        for (int f = 0; f < 3; ++f)
+            for (size_t e = 0; e < K; ++e)
+                for (int q = 0; q < R.Nq; ++q) {
+                    double v = q_volq[(f * K + e) * R.Nq + q];
+                    if (f == 0 && mode == ESDG_INIT_SURFACE)
+                        for (int n = 0; n < R.Np; ++n) v -= R.Vq(q, n) * c->b_modal[e * R.Np + n];
+                    u[(f * K + e) * R.Nq + q] = v;
+                }
+        return;
+    }
     const int NpP = R.Np * (R.Np + 1) / 2;
     std::vector<double> y(R.Np);
     for (int f = 0; f < 3; ++f)
@@ -399,13 +463,19 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.lf = c->cfg.lax_friedrichs;
     real* ops = reinterpret_cast<real*>(d + c->L.ops);
     p.QsT = ops;
-    p.Vq = p.QsT + size_t(R.Nh) * R.Nh * 2;
-    p.VqT = p.Vq + size_t(R.Nq) * R.Np;
-    p.Vh = p.VqT + size_t(R.Np) * R.Nq;
-    p.VhT = p.Vh + size_t(R.Nh) * R.Np;
-    p.wf = p.VhT + size_t(R.Np) * R.Nh;
-    p.nrs = p.wf + R.Nfq;
-    p.wq = p.nrs + 2 * size_t(R.Nfq);
+    if (c->sbp) {
+        p.wf = p.QsT + size_t(R.Nq) * R.Nq * 2;
+        p.nrs = p.wf + R.Nfq;
+        p.fmap = reinterpret_cast<const int*>(d + c->L.fmap);
+    } else {
+        p.Vq = p.QsT + size_t(R.Nh) * R.Nh * 2;
+        p.VqT = p.Vq + size_t(R.Nq) * R.Np;
+        p.Vh = p.VqT + size_t(R.Np) * R.Nq;
+        p.VhT = p.Vh + size_t(R.Nh) * R.Np;
+        p.wf = p.VhT + size_t(R.Np) * R.Nh;
+        p.nrs = p.wf + R.Nfq;
+        p.wq = p.nrs + 2 * size_t(R.Nfq);
+    }
     p.geo = reinterpret_cast<const real*>(d + c->L.geo);
     p.wJq = reinterpret_cast<const real*>(d + c->L.wJq);
     p.minv = reinterpret_cast<const real*>(d + c->L.minv);
@@ -434,9 +504,28 @@ static real* ut_buf(esdg_ctx* c, int which) {
 }
 
 // ---- degree dispatch ---------------------------------------------------------
+template <typename real>
+static cudaError_t d_sbp(esdg_ctx* c, const StageParams<real>& p, int mode) {
+    switch (c->cfg.N) {
+#define X(v) case v: return launch_sbp<v, real>(p, mode, c->lg, c->stream);
+        X(1) X(2) X(3) X(4) X(5)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
 static cudaError_t d_geometry(esdg_ctx* c) {
     const int sms = c->num_sms;
     cudaError_t e = cudaErrorInvalidValue;
+    if (c->sbp) {
+        const bool f32 = c->cfg.precision == ESDG_FP32;
+        switch (c->cfg.N) {
+#define X(v) case v: e = f32 ? sbp_geometry<v, float>(sms, c->lg) : sbp_geometry<v, double>(sms, c->lg); break;
+            X(1) X(2) X(3) X(4) X(5)
+#undef X
+        }
+        return e;
+    }
     if (c->cfg.precision == ESDG_FP32) {
         switch (kernel_nr(c->cfg)) {
 #define X(v) case v: e = stage2_geometry<v>(sms, c->lg2); break;
@@ -461,6 +550,7 @@ static cudaError_t d_project(int NR, const StageParams<double>& p, const LaunchG
     return cudaErrorInvalidValue;
 }
 static cudaError_t d_stage(esdg_ctx* c, const StageParams<double>& p, int mode) {
+    if (c->sbp) return d_sbp<double>(c, p, mode);
     const LaunchGeom& lg = c->lg;
     switch (kernel_nr(c->cfg)) {
 #define X(v) case v: return launch_stage<v, double>(p, mode, lg, c->stream);
@@ -470,6 +560,7 @@ static cudaError_t d_stage(esdg_ctx* c, const StageParams<double>& p, int mode) 
     return cudaErrorInvalidValue;
 }
 static cudaError_t d_stage(esdg_ctx* c, const StageParams<float>& p, int mode) {
+    if (c->sbp) return d_sbp<float>(c, p, mode);
     const LaunchGeom& lg = c->lg2;
     const float* ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
     switch (kernel_nr(c->cfg)) {
@@ -511,10 +602,14 @@ static int project_current(esdg_ctx* c, const double* u_in, int target, bool cop
     if (u_in) p.u_in = u_in;
     p.copy_in = copy_in ? 1 : 0;  // also store u_in as the state, residual zeroed
     p.ut_out = ut_buf<real>(c, target);
-    if constexpr (std::is_same<real, float>::value)
-        CUDA_TRY(c, d_stage(c, p, 2));  // the FP32 path's projection-only stage kernel
-    else
-        CUDA_TRY(c, d_project(kernel_nr(c->cfg), p, c->lg_proj, c->stream));
+    if constexpr (std::is_same<real, float>::value) {
+        CUDA_TRY(c, d_stage(c, p, 2));  // the FP32 path's projection-only stage kernel (or DG-SBP records)
+    } else {
+        if (c->sbp)
+            CUDA_TRY(c, d_stage(c, p, 2));  // DG-SBP: nodal records of the state
+        else
+            CUDA_TRY(c, d_project(kernel_nr(c->cfg), p, c->lg_proj, c->stream));
+    }
     return ESDG_OK;
 }
 
@@ -574,11 +669,15 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         return fail(nullptr, ESDG_EINVAL, "unknown boundary kind");
     if (cfg->mass != ESDG_MASS_EXACT && cfg->mass != ESDG_MASS_WEIGHT_ADJUSTED)
         return fail(nullptr, ESDG_EINVAL, "unknown inverse-mass kind");
+    if (cfg->method != ESDG_METHOD_MODAL && cfg->method != ESDG_METHOD_SBP)
+        return fail(nullptr, ESDG_EINVAL, "unknown method");
+    if (cfg->method == ESDG_METHOD_SBP && (cfg->boundary != ESDG_BOUNDARY_PERIODIC || cfg->mass != ESDG_MASS_EXACT))
+        return fail(nullptr, ESDG_EINVAL, "the DG-SBP scheme takes periodic boundaries and its diagonal mass matrix");
     esdg_ctx* c = new (std::nothrow) esdg_ctx();
     if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     c->cfg = *cfg;
     std::string err;
-    if (!build_reference(cfg->N, cfg->volume_rule, c->ref, err)) {
+    if (!build_reference(cfg->N, cfg->method == ESDG_METHOD_SBP ? 2 : cfg->volume_rule, c->ref, err)) {
         delete c;
         return fail(nullptr, ESDG_EINVAL, err);
     }
@@ -687,7 +786,7 @@ int esdg_init_state(esdg_ctx* c, const double* b_nodal, const double* q_volq, in
         if (rc) return rc;
     }
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    std::vector<double> u(3 * size_t(c->mesh.K) * c->ref.Np);
+    std::vector<double> u(3 * size_t(c->mesh.K) * c->ndof);
     project_host(c, q_volq, mode, u.data());
     return esdg_set_state(c, u.data(), 0);
 }
@@ -695,7 +794,7 @@ int esdg_init_state(esdg_ctx* c, const double* b_nodal, const double* q_volq, in
 int esdg_set_state(esdg_ctx* c, const double* u, int on_device) {
     if (!valid(c) || !u) return fail(nullptr, ESDG_EINVAL, "null argument");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ref.Np;
+    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ndof;
     CUDA_TRY(c, cudaMemcpyAsync(c->dbuf + c->L.u, u, bytes,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(c, cudaMemsetAsync(c->dbuf + c->L.res, 0, bytes, c->stream));
@@ -708,7 +807,7 @@ int esdg_copy_state(const esdg_ctx* cc, double* u, int on_device) {
     esdg_ctx* c = const_cast<esdg_ctx*>(cc);
     if (!valid(c) || !u) return fail(nullptr, ESDG_EINVAL, "null argument");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ref.Np;
+    size_t bytes = 8 * 3 * size_t(c->mesh.K) * c->ndof;
     CUDA_TRY(c, cudaMemcpyAsync(u, c->dbuf + c->L.u, bytes,
                                 on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
     if (!on_device) CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -798,11 +897,18 @@ int esdg_entropy(esdg_ctx* c, double t, double* entropy, double* mass, double* e
         rhs = r;
     }
     double* out = reinterpret_cast<double*>(c->dbuf + c->L.diag);
-    CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u), rhs,
-                          reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
-                          reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
-                          reinterpret_cast<const double*>(c->dbuf + c->L.bq64),
-                          reinterpret_cast<double*>(c->dbuf + c->L.partial), c->entropy_parts, out, c->stream));
+    if (c->sbp)
+        CUDA_TRY(c, launch_entropy_nodal(c->mesh.K, c->ref.Nq, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u),
+                                         rhs, reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                                         reinterpret_cast<const double*>(c->dbuf + c->L.bq64),
+                                         reinterpret_cast<double*>(c->dbuf + c->L.partial), c->entropy_parts, out,
+                                         c->stream));
+    else
+        CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, reinterpret_cast<const double*>(c->dbuf + c->L.u),
+                              rhs, reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
+                              reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                              reinterpret_cast<const double*>(c->dbuf + c->L.bq64),
+                              reinterpret_cast<double*>(c->dbuf + c->L.partial), c->entropy_parts, out, c->stream));
     double h[3];
     CUDA_TRY(c, cudaMemcpyAsync(h, out, 24, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -854,10 +960,17 @@ int esdg_entropy_noalloc(const esdg_ctx* cc, const double* u_dev, double* entrop
     const double* u = u_dev ? u_dev : reinterpret_cast<const double*>(c->dbuf + c->L.u);
     // every block writes its own partial and the finalize kernel writes all three
     // totals, so no part of the scratch has to start at zero
-    CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, u, nullptr,
-                          reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
-                          reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
-                          reinterpret_cast<const double*>(c->dbuf + c->L.bq64), partial, (int)parts, out, c->stream));
+    if (c->sbp)
+        CUDA_TRY(c, launch_entropy_nodal(c->mesh.K, c->ref.Nq, c->cfg.g, u, nullptr,
+                                         reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                                         reinterpret_cast<const double*>(c->dbuf + c->L.bq64), partial, (int)parts, out,
+                                         c->stream));
+    else
+        CUDA_TRY(c, d_entropy(kernel_nr(c->cfg), c->mesh.K, c->cfg.g, u, nullptr,
+                              reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
+                              reinterpret_cast<const double*>(c->dbuf + c->L.wJq64),
+                              reinterpret_cast<const double*>(c->dbuf + c->L.bq64), partial, (int)parts, out,
+                              c->stream));
     double h[3];
     CUDA_TRY(c, cudaMemcpyAsync(h, out, 24, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1017,6 +1130,7 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must share one volume rule");
         if (weight_adjusted(c->cfg))
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must use the stored inverse mass matrices");
+        if (c->sbp) return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must use the modal scheme");
     }
     esdg_ensemble* e = new (std::nothrow) esdg_ensemble();
     if (!e) return fail(nullptr, ESDG_ENOMEM, "out of host memory");

@@ -35,5 +35,12 @@ cudaError_t launch_stage2(const StageParams<float>& p, const float* ops2, int Kp
 template <int N>
 cudaError_t launch_entropy(int K, double g, const double* u, const double* rhs, const double* Vq, const double* wJq,
                            const double* bq, double* partial, int nparts, double* out, cudaStream_t s);
+// DG-SBP kernels (esdg_sbp.cuh), degree N = 1..5, FP64 and FP32.
+template <int N, typename real>
+cudaError_t sbp_geometry(int num_sms, LaunchGeom& lg);
+template <int N, typename real>
+cudaError_t launch_sbp(const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s);
+cudaError_t launch_entropy_nodal(int K, int Nq, double g, const double* u, const double* rhs, const double* wJq,
+                                 const double* bq, double* partial, int nparts, double* out, cudaStream_t s);
 
 }  // namespace esdg

@@ -1,0 +1,242 @@
+// DG-SBP kernels (Sec. 3 of Wu, Kubatko, Chan, arXiv 2005.02516) for sm_103a.
+//
+// The traditional entropy-stable DG-SBP scheme: nodal unknowns at the Nq
+// points of an SBP rule (exact to 2N-1, the face Gauss-Legendre points among
+// them), no entropy projection, the SBP operator Q_SBP = [I; I_f]^T Q_h [I; I_f]
+// of Theorem 3.1 and the diagonal mass matrix W J.  Per element and stage,
+// with the split form of Sec. 5.2 applied to Q_SBP (Q_SBP + Q_SBP^T =
+// I_f^T B I_f, so 2 Q_SBP o F 1 = Qskew o F 1 + I_f^T B f(u_f)):
+//   r_l = sum_m Qskew^{x,k}[l,m] f_S^x(u_l, u_m) + Qskew^{y,k}[l,m] f_S^y(u_l, u_m)
+//         (+ the bathymetry source folded into the pressure as in esdg_kernels.cuh)
+//       + [l = I_f(f)] w_f (nxJ f_S^x(u+, u_l) + nyJ f_S^y(u+, u_l)) - LF,
+//   du_l/dt = -r_l / (w_l J_l) + forcing,
+// then the LSRK45 stage.  Qskew^{i,k}[l,m] = sum_j Qskew_SBP^j[l,m] (G_ij[l] +
+// G_ij[m]) / 2 with the metrics at the SBP nodes (a face node shares them with
+// its volume node).  Neighbour values come from the previous stage's nodal
+// record buffer (ut_in), so a stage never reads values it is updating.
+//
+// A warp per element (rows l = lane, lane + 32), operators in shared memory;
+// the same kernel in FP64 and FP32.
+#pragma once
+
+#include "esdg_kernels.cuh"
+
+namespace esdg {
+
+// Points of the SBP rule of degree N: 3(N+1) face Gauss-Legendre points plus
+// the interior orbits.
+constexpr int sbp_points(int N) { return N == 1 ? 6 : N == 2 ? 10 : N == 3 ? 18 : N == 4 ? 22 : 34; }
+
+template <int N_>
+struct SbpDims {
+    static constexpr int N = N_;
+    static constexpr int Np = (N + 1) * (N + 2) / 2;
+    static constexpr int Nq = sbp_points(N);
+    static constexpr int Nfp = N + 1;
+    static constexpr int Nfq = 3 * (N + 1);
+};
+
+template <int N, typename real>
+struct SbpSmem {
+    typedef SbpDims<N> D;
+    static constexpr int REC = 12;  // h hu hv u v H rx sx ry sy 2gh b
+    static constexpr int ops_QsT = 0;                         // [Nq(m)][Nq(l)][2]
+    static constexpr int ops_wf = ops_QsT + D::Nq * D::Nq * 2;
+    static constexpr int ops_nrs = ops_wf + D::Nfq;
+    static constexpr int ops_end = ((ops_nrs + 2 * D::Nfq) + 3) & ~3;
+    static constexpr int w_rec = 0;                           // [Nq][REC]
+    static constexpr int w_r = w_rec + D::Nq * REC;           // [3][Nq] du/dt
+    static constexpr int w_end = ((w_r + 3 * D::Nq) + 3) & ~3;
+    static constexpr size_t bytes(int warps) {
+        return sizeof(real) * (size_t(ops_end) + size_t(warps) * w_end) + sizeof(int) * 2 * 64;
+    }
+};
+
+// MODE 0: du/dt into rhs_out.  MODE 1: LSRK45 stage of (u, res), the new
+// nodal records into ut_out.  MODE 2: nodal records of u_in into ut_out (and,
+// with copy_in, u_in stored as the state with the residual zeroed).
+template <int N, typename real, int MODE>
+__global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
+    typedef SbpDims<N> D;
+    typedef SbpSmem<N, real> S;
+    typedef typename V2<real>::t real2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real* ops = reinterpret_cast<real*>(smem_raw);
+    const int wpb = blockDim.x >> 5;
+    int* fmap = reinterpret_cast<int*>(ops + S::ops_end + wpb * S::w_end);  // [Nfq]
+    int* frow = fmap + 64;                                                  // [Nq]: face node of row, or -1
+    for (int i = threadIdx.x; i < D::Nq * D::Nq * 2; i += blockDim.x) ops[S::ops_QsT + i] = p.QsT[i];
+    for (int i = threadIdx.x; i < D::Nfq; i += blockDim.x) {
+        ops[S::ops_wf + i] = p.wf[i];
+        ops[S::ops_nrs + 2 * i] = p.nrs[2 * i];
+        ops[S::ops_nrs + 2 * i + 1] = p.nrs[2 * i + 1];
+        fmap[i] = p.fmap[i];
+    }
+    for (int i = threadIdx.x; i < D::Nq; i += blockDim.x) frow[i] = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < D::Nfq; i += blockDim.x) frow[fmap[i]] = i;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    real* ws = ops + S::ops_end + warp * S::w_end;
+    real* rec = ws + S::w_rec;
+    real* rr = ws + S::w_r;
+    const real2* QsT = reinterpret_cast<const real2*>(ops + S::ops_QsT);
+    const real g = p.g;
+    const real eighth = real(0.125);
+    for (int e = blockIdx.x * wpb + warp; e < p.K; e += gridDim.x * wpb) {
+        if (MODE == 2) {
+            int bad = 0;
+            for (int i = lane; i < D::Nq; i += 32) {
+                const size_t g0 = ((size_t)0 * p.K + e) * D::Nq + i;
+                const size_t g1 = ((size_t)1 * p.K + e) * D::Nq + i;
+                const size_t g2 = ((size_t)2 * p.K + e) * D::Nq + i;
+                const double h = p.u_in[g0], hu = p.u_in[g1], hv = p.u_in[g2];
+                if (p.copy_in) {
+                    p.u[g0] = h;
+                    p.u[g1] = hu;
+                    p.u[g2] = hv;
+                    p.res[g0] = p.res[g1] = p.res[g2] = 0.0;
+                }
+                if (!(h > 0.0)) bad |= STATUS_NONPOSITIVE;
+                const real hr = (real)h, ur = (real)(hu / h), vr = (real)(hv / h);
+                real* o = p.ut_out + ((size_t)e * D::Nq + i) * 4;
+                o[0] = hr;
+                o[1] = ur;
+                o[2] = vr;
+                o[3] = hr + p.bh[(size_t)e * D::Nq + i];
+            }
+            if (bad) atomicOr(p.status, bad);
+            continue;
+        }
+        // ---- nodal records of the element ----------------------------------------
+        for (int l = lane; l < D::Nq; l += 32) {
+            const real* ut = p.ut_in + ((size_t)e * D::Nq + l) * 4;
+            const real* gg = p.geo + ((size_t)e * D::Nq + l) * 4;
+            const real h = ut[0], uu = ut[1], vv = ut[2], H = ut[3];
+            const real b = p.bh[(size_t)e * D::Nq + l];
+            real* r = rec + l * S::REC;
+            r[0] = h;
+            r[1] = h * uu;
+            r[2] = h * vv;
+            r[3] = uu;
+            r[4] = vv;
+            r[5] = H;
+            r[6] = gg[0] * eighth;
+            r[7] = gg[1] * eighth;
+            r[8] = gg[2] * eighth;
+            r[9] = gg[3] * eighth;
+            r[10] = real(2) * g * h;
+            r[11] = b;
+        }
+        __syncwarp();
+        // ---- flux differencing over all node pairs, interface at face rows -----------
+        for (int l = lane; l < D::Nq; l += 32) {
+            const real* rl = rec + l * S::REC;
+            const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
+            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real a0 = 0, a1 = 0, a2 = 0;
+            for (int m = 0; m < D::Nq; ++m) {
+                const real2 q = QsT[m * D::Nq + l];
+                const real* rm = rec + m * S::REC;
+                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                const real U = u_l + rm[3], V = v_l + rm[4];
+                const real T = Qx * HU + Qy * HV;
+                const real P = gh2_l * rm[5];
+                a0 += T;
+                a1 += U * T + Qx * P;
+                a2 += V * T + Qy * P;
+            }
+            real r0 = real(2) * a0, r1 = a1, r2 = a2;
+            const int f = frow[l];
+            if (f >= 0) {
+                const int face = f / D::Nfp, i = f - face * D::Nfp;
+                const int nb = p.nbr[(size_t)e * 3 + face];
+                const int en = nb >> 2, fn = nb & 3;
+                const real nr = ops[S::ops_nrs + 2 * f], ns = ops[S::ops_nrs + 2 * f + 1];
+                const real nxJ = real(8) * (rx_l * nr + sx_l * ns);
+                const real nyJ = real(8) * (ry_l * nr + sy_l * ns);
+                const real* up = p.ut_in + ((size_t)en * D::Nq + fmap[fn * D::Nfp + (D::Nfp - 1 - i)]) * 4;
+                const real hP = up[0], uP = up[1], vP = up[2];
+                const real huP = hP * uP, hvP = hP * vP;
+                const real w = ops[S::ops_wf + f];
+                const real b_l = rl[11];
+                const real huA = real(0.5) * (hu_l + huP), hvA = real(0.5) * (hv_l + hvP);
+                const real uA = real(0.5) * (u_l + uP), vA = real(0.5) * (v_l + vP);
+                const real pw = real(0.5) * g * h_l * (hP + b_l);
+                const real Fn0 = nxJ * huA + nyJ * hvA;
+                r0 += w * Fn0;
+                r1 += w * (uA * Fn0 + nxJ * pw);
+                r2 += w * (vA * Fn0 + nyJ * pw);
+                if (p.lf) {
+                    const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
+                    const real inx = nxJ / sJ, iny = nyJ / sJ;
+                    const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
+                    const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
+                    const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
+                    r0 -= c * (hP - h_l);
+                    r1 -= c * (huP - hu_l);
+                    r2 -= c * (hvP - hv_l);
+                }
+            }
+            // du/dt = -r / (w J) + forcing (the forcing term W J f of the form, divided by W J)
+            const real iwj = real(1) / p.wJq[(size_t)e * D::Nq + l];
+            real d0 = -r0 * iwj, d1 = -r1 * iwj, d2 = -r2 * iwj;
+            if (p.forcing) {
+                const real x = p.xq[(size_t)e * D::Nq + l], y = p.yq[(size_t)e * D::Nq + l];
+                real sth, cth, sx, cx, sy, cy;
+                r_sincospi<real>(x + y - real(p.t), &sth, &cth);
+                r_sincospi<real>(x, &sx, &cx);
+                r_sincospi<real>(y, &sy, &cy);
+                const real pi = real(3.14159265358979323846);
+                const real h = real(2) + p.mms_amp * sth;
+                const real c = p.mms_amp * pi * cth;
+                const real bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
+                const real u0 = p.mms_u0, v0 = p.mms_v0;
+                d0 += -c + u0 * c + v0 * c;
+                d1 += -u0 * c + (u0 * u0 + g * h) * c + u0 * v0 * c + g * h * bx;
+                d2 += -v0 * c + u0 * v0 * c + (v0 * v0 + g * h) * c + g * h * by;
+            }
+            rr[l] = d0;
+            rr[D::Nq + l] = d1;
+            rr[2 * D::Nq + l] = d2;
+        }
+        __syncwarp();
+        // ---- output or LSRK45 stage (FP64) and the next stage's records ------------------
+        int bad = 0;
+        for (int l = lane; l < D::Nq; l += 32) {
+            double un[3];
+            for (int c = 0; c < 3; ++c) {
+                const size_t gi = ((size_t)c * p.K + e) * D::Nq + l;
+                const double d = (double)rr[c * D::Nq + l];
+                if (MODE == 0) {
+                    p.rhs_out[gi] = d;
+                } else {
+                    const double rs = p.rkA * p.res[gi] + p.dt * d;
+                    p.res[gi] = rs;
+                    un[c] = p.u[gi] + p.rkB * rs;
+                    p.u[gi] = un[c];
+                    if (p.u_out) p.u_out[gi] = un[c];
+                }
+            }
+            if (MODE == 1) {
+                const double h = un[0];
+                if (!(h > 0.0)) bad |= STATUS_NONPOSITIVE;
+                if (!isfinite(un[0]) || !isfinite(un[1]) || !isfinite(un[2])) bad |= STATUS_NONFINITE;
+                const real hr = (real)h;
+                real* o = p.ut_out + ((size_t)e * D::Nq + l) * 4;
+                o[0] = hr;
+                o[1] = (real)(un[1] / h);
+                o[2] = (real)(un[2] / h);
+                o[3] = hr + rec[l * S::REC + 11];
+            }
+        }
+        if (bad) atomicOr(p.status, bad);
+        __syncwarp();
+    }
+}
+
+
+
+}  // namespace esdg

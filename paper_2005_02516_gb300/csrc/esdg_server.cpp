@@ -240,8 +240,9 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
     esdg_config cfg;
     rc = esdg_get_config(ctx, &cfg);
     // FP32 requests run inside an ensemble launch, which carries neither
-    // forcing terms nor the weight-adjusted inverse
-    if (rc || (cfg.precision == ESDG_FP32 && (cfg.forcing != ESDG_FORCING_NONE || cfg.mass != ESDG_MASS_EXACT))) {
+    // forcing terms nor the weight-adjusted inverse; requests are modal
+    if (rc || cfg.method != ESDG_METHOD_MODAL ||
+        (cfg.precision == ESDG_FP32 && (cfg.forcing != ESDG_FORCING_NONE || cfg.mass != ESDG_MASS_EXACT))) {
         delete r;
         return rc ? rc : ESDG_EINVAL;
     }

@@ -417,6 +417,188 @@ bool symmetric_rule(int N, std::vector<double>& r, std::vector<double>& s, std::
 }
 
 // ---------------------------------------------------------------------------
+// SBP volume rules (Sec. 3.1): positive weights, exact to degree 2N-1, and the
+// N+1 Gauss-Legendre points of every face among the nodes.  Fully symmetric:
+// edge orbits at the fixed Gauss-Legendre points (the three edge midpoints
+// when N+1 is odd, then one 6-point orbit per point t > 0, by increasing t)
+// with free weights, then interior orbits (centroid, 3-point, 6-point counts
+// per N: 1: none, 2: (1,0,0), 3: (0,0,1), 4: (1,2,0), 5: (1,1,2)), so that the
+// symmetric moment equations of degree 2N-1 form a square system.  Solved by
+// Levenberg-Marquardt from seeded starts like the rules above; each of these
+// structures has a single positive interior solution.
+// ---------------------------------------------------------------------------
+namespace {
+const int kSbpStruct[6][3] = {{0, 0, 0}, {0, 0, 0}, {1, 0, 0}, {0, 0, 1}, {1, 2, 0}, {1, 1, 2}};
+
+// Edge orbit points (barycentric) of degree N with their weight index.
+int sbp_edge_points(int N, const std::vector<double>& th, std::vector<OrbitPoint>& pts) {
+    std::vector<double> t, w;
+    gauss_jacobi(N + 1, 0.0, 0.0, t, w);
+    int k = 0;
+    if ((N + 1) % 2 == 1) {
+        const double L[3][3] = {{0.5, 0.5, 0.0}, {0.0, 0.5, 0.5}, {0.5, 0.0, 0.5}};
+        for (int q = 0; q < 3; ++q)
+            pts.push_back(OrbitPoint{{L[q][0], L[q][1], L[q][2]}, th[k], k, {-1, -1}, {{0, 0, 0}, {0, 0, 0}}});
+        k += 1;
+    }
+    std::vector<double> tp;
+    for (double x : t)
+        if (x > 1e-12) tp.push_back(x);
+    std::sort(tp.begin(), tp.end());
+    for (double x : tp) {
+        const double a = 0.5 * (1.0 - x), b = 1.0 - a;
+        const double L[6][3] = {{a, b, 0}, {b, a, 0}, {0, a, b}, {0, b, a}, {a, 0, b}, {b, 0, a}};
+        for (int q = 0; q < 6; ++q)
+            pts.push_back(OrbitPoint{{L[q][0], L[q][1], L[q][2]}, th[k], k, {-1, -1}, {{0, 0, 0}, {0, 0, 0}}});
+        k += 1;
+    }
+    return k;
+}
+
+int sbp_edge_params(int N) { return (N + 1) % 2 + (N + 1) / 2; }
+
+// All points of an SBP rule: edge orbits, then the interior orbits whose
+// parameters follow the edge weights in th.
+std::vector<OrbitPoint> sbp_points(int N, const std::vector<double>& th) {
+    std::vector<OrbitPoint> pts;
+    const int ne = sbp_edge_points(N, th, pts);
+    const std::vector<double> ti(th.begin() + ne, th.end());
+    for (OrbitPoint p : orbit_points(ti, kSbpStruct[N])) {
+        p.owner += ne;
+        for (int q = 0; q < 2; ++q)
+            if (p.dpar[q] >= 0) p.dpar[q] += ne;
+        pts.push_back(p);
+    }
+    return pts;
+}
+
+bool sbp_try(int N, uint64_t seed, std::vector<double>& th) {
+    const int d = 2 * N - 1;
+    const int* st = kSbpStruct[N];
+    const int ne = sbp_edge_params(N);
+    const int n = ne + st[0] + 2 * st[1] + 3 * st[2];
+    const int nm = (d + 1) * (d + 2) / 2;
+    uint64_t x = seed * 104729 + 31;
+    th.clear();
+    for (int i = 0; i < ne; ++i) th.push_back(uniform(x, 0.01, 0.2));
+    if (st[0]) th.push_back(uniform(x, 0.05, 0.3));
+    for (int o = 0; o < st[1]; ++o) { th.push_back(uniform(x, 0.02, 0.48)); th.push_back(uniform(x, 0.02, 0.3)); }
+    for (int o = 0; o < st[2]; ++o) {
+        th.push_back(uniform(x, 0.01, 0.45));
+        th.push_back(uniform(x, 0.01, 0.45));
+        th.push_back(uniform(x, 0.02, 0.2));
+    }
+    auto eval = [&](const std::vector<double>& t, std::vector<double>& R, Mat& J) {
+        std::vector<OrbitPoint> pts = sbp_points(N, t);
+        std::vector<double> r(pts.size()), s(pts.size());
+        for (size_t i = 0; i < pts.size(); ++i) { r[i] = to_r(pts[i].lam); s[i] = to_s(pts[i].lam); }
+        Mat V, Vr, Vs;
+        dubiner(d, r, s, V, &Vr, &Vs);
+        R.assign(nm, 0.0);
+        J = Mat(nm, n);
+        for (size_t i = 0; i < pts.size(); ++i)
+            for (int m = 0; m < nm; ++m) {
+                R[m] += pts[i].w * V(int(i), m);
+                J(m, pts[i].owner) += V(int(i), m);
+                for (int q = 0; q < 2; ++q) {
+                    if (pts[i].dpar[q] < 0) continue;
+                    const double dr = to_r(pts[i].dlam[q]), ds = to_s(pts[i].dlam[q]);
+                    J(m, pts[i].dpar[q]) += pts[i].w * (Vr(int(i), m) * dr + Vs(int(i), m) * ds);
+                }
+            }
+        R[0] -= std::sqrt(2.0);
+    };
+    auto norm = [](const std::vector<double>& v) { double a = 0; for (double y : v) a += y * y; return std::sqrt(a); };
+    std::vector<double> R, R2;
+    Mat J, J2;
+    eval(th, R, J);
+    double mu = 1e-3;
+    for (int it = 0; it < 300 && norm(R) > 1e-15; ++it) {
+        Mat A(n, n), Ai;
+        std::vector<double> g(n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) {
+                double sum = 0;
+                for (int m = 0; m < nm; ++m) sum += J(m, i) * J(m, j);
+                A(i, j) = sum + (i == j ? mu : 0.0);
+            }
+            for (int m = 0; m < nm; ++m) g[i] -= J(m, i) * R[m];
+        }
+        if (!invert(A, Ai)) { mu *= 10; if (mu > 1e10) break; continue; }
+        std::vector<double> t2(th);
+        bool finite = true;
+        for (int i = 0; i < n; ++i) {
+            for (int j = 0; j < n; ++j) t2[i] += Ai(i, j) * g[j];
+            finite = finite && std::isfinite(t2[i]);
+        }
+        if (!finite) return false;
+        eval(t2, R2, J2);
+        if (norm(R2) < norm(R)) {
+            th = t2; R = R2; J = J2;
+            mu = std::max(mu / 3, 1e-15);
+        } else {
+            mu *= 10;
+            if (mu > 1e10) break;
+        }
+    }
+    if (!(norm(R) < 1e-13)) return false;
+    const std::vector<OrbitPoint> pts = sbp_points(N, th);
+    const int nedge = 3 * ((N + 1) % 2) + 6 * ((N + 1) / 2);
+    for (size_t i = 0; i < pts.size(); ++i) {
+        if (!(pts[i].w > 0)) return false;
+        if (int(i) < nedge) continue;
+        const double r = to_r(pts[i].lam), s = to_s(pts[i].lam);
+        if (!(r > -1 + 1e-9) || !(s > -1 + 1e-9) || !(r + s < -1e-9)) return false;
+    }
+    return true;
+}
+}  // namespace
+
+bool sbp_rule(int N, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w, std::string& err) {
+    if (N < 1 || N > 5) { err = "SBP rules exist here for N = 1..5"; return false; }
+    static std::mutex mu;
+    static std::vector<double> cache[6];
+    std::lock_guard<std::mutex> lock(mu);
+    const int* st = kSbpStruct[N];
+    const int ne = sbp_edge_params(N);
+    std::vector<double>& best = cache[N];
+    if (best.empty()) {
+        std::vector<std::vector<double>> found(kSymRestarts);
+        std::vector<char> ok(kSymRestarts, 0);
+        const int nt = std::max(1, std::min<int>(16, int(std::thread::hardware_concurrency())));
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back([&, t]() {
+                for (int seed = t; seed < kSymRestarts; seed += nt) ok[seed] = sbp_try(N, uint64_t(seed), found[seed]);
+            });
+        for (auto& th : pool) th.join();
+        double best_min = -1.0;
+        for (int seed = 0; seed < kSymRestarts; ++seed) {
+            if (!ok[seed]) continue;
+            double wmin = 1e300;
+            for (const OrbitPoint& p : sbp_points(N, found[seed])) wmin = std::min(wmin, p.w);
+            if (wmin > best_min + 1e-12) {
+                best_min = wmin;
+                const std::vector<double> ti(found[seed].begin() + ne, found[seed].end());
+                best.assign(found[seed].begin(), found[seed].begin() + ne);
+                if (!ti.empty()) {
+                    const std::vector<double> c = sym_canonical(ti, st);
+                    best.insert(best.end(), c.begin(), c.end());
+                }
+            }
+        }
+        if (best.empty()) { err = "no SBP volume rule found"; return false; }
+    }
+    r.clear(); s.clear(); w.clear();
+    for (const OrbitPoint& p : sbp_points(N, best)) {
+        r.push_back(to_r(p.lam));
+        s.push_back(to_s(p.lam));
+        w.push_back(p.w);
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
 // Reference element
 // ---------------------------------------------------------------------------
 bool build_reference(int N, int rule, RefOps& R, std::string& err) {
@@ -438,7 +620,9 @@ bool build_reference(int N, int rule, RefOps& R, std::string& err) {
                 R.sq.push_back(xb[ib]);
                 R.wq.push_back(0.5 * wa[ia] * wb[ib]);
             }
-    } else if (!symmetric_rule(N, R.rq, R.sq, R.wq, err)) {
+    } else if (rule == 1) {
+        if (!symmetric_rule(N, R.rq, R.sq, R.wq, err)) return false;
+    } else if (!sbp_rule(N, R.rq, R.sq, R.wq, err)) {
         return false;
     }
     R.Nq = int(R.rq.size());
@@ -455,6 +639,16 @@ bool build_reference(int N, int rule, RefOps& R, std::string& err) {
             R.wf.push_back(wa[i]);
             R.nr.push_back(f == 0 ? 0.0 : (f == 1 ? 1.0 : -1.0));
             R.ns.push_back(f == 0 ? -1.0 : (f == 1 ? 1.0 : 0.0));
+        }
+    // SBP rule: the volume node at each face node (the selection I_f, Sec. 3.2)
+    R.fmap.clear();
+    if (rule == 2)
+        for (int f = 0; f < R.Nfq; ++f) {
+            int best = -1;
+            for (int q = 0; q < R.Nq; ++q)
+                if (std::hypot(R.rq[q] - R.rf[f], R.sq[q] - R.sf[f]) < 1e-12) best = q;
+            if (best < 0) { err = "a face node is not a node of the SBP rule"; return false; }
+            R.fmap.push_back(best);
         }
     dubiner(N, R.rq, R.sq, R.Vq, &R.Vqr, &R.Vqs);
     dubiner(N, R.rf, R.sf, R.Vf, &R.Vfr, &R.Vfs);

@@ -36,12 +36,16 @@ struct RefOps {
     Mat Vh;                                // (Nh x Np)
     Mat Qsr, Qss;                          // skew hybridized operators Q_h - Q_h^T (Nh x Nh)
     Mat Veq_inv;                           // inverse Vandermonde at the equispaced nodes
+    std::vector<int> fmap;                 // SBP rule only: volume node of each face node (I_f)
 };
 
 // rule 0: collapsed Gauss rule, (N+1)^2 points, exact to 2N+1;
-// rule 1: fully symmetric rule exact to 2N (3, 6, 12, 16, 25 points).
+// rule 1: fully symmetric rule exact to 2N (3, 6, 12, 16, 25 points);
+// rule 2: SBP rule of Sec. 3.1, exact to 2N-1 with the face Gauss-Legendre
+//         points among its nodes (6, 10, 18, 22, 34 points).
 bool build_reference(int N, int rule, RefOps& ref, std::string& err);
 bool symmetric_rule(int N, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w, std::string& err);
+bool sbp_rule(int N, std::vector<double>& r, std::vector<double>& s, std::vector<double>& w, std::string& err);
 
 // Orthonormal Dubiner basis and (optionally) its gradients at points (r, s).
 void dubiner(int N, const std::vector<double>& r, const std::vector<double>& s,

@@ -34,6 +34,8 @@ ESDG_RULE_COLLAPSED = 0
 ESDG_RULE_SYMMETRIC = 1
 ESDG_MASS_EXACT = 0
 ESDG_MASS_WEIGHT_ADJUSTED = 1
+ESDG_METHOD_MODAL = 0
+ESDG_METHOD_SBP = 1
 ESDG_POINTS_NODAL = 0
 ESDG_POINTS_VOLQ = 1
 ESDG_POINTS_FACEQ = 2
@@ -71,7 +73,8 @@ class Config(ctypes.Structure):
                 ("lax_friedrichs", ctypes.c_int), ("forcing", ctypes.c_int),
                 ("mms_amp", ctypes.c_double), ("mms_bamp", ctypes.c_double),
                 ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double),
-                ("volume_rule", ctypes.c_int), ("boundary", ctypes.c_int), ("mass", ctypes.c_int)]
+                ("volume_rule", ctypes.c_int), ("boundary", ctypes.c_int), ("mass", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 _lib = None
@@ -145,9 +148,11 @@ def _ptr(a):
 
 def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, warp=0.0, g=1.0, cfl=0.25,
                 lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False,
-                mass="exact"):
+                mass="exact", method="modal"):
     if mass not in ("exact", "weight_adjusted"):
         raise ValueError("mass must be 'exact' or 'weight_adjusted'")
+    if method not in ("modal", "sbp"):
+        raise ValueError("method must be 'modal' or 'sbp'")
     cfg = Config()
     cfg.N, cfg.nx, cfg.ny = N, nx, ny
     cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
@@ -160,6 +165,7 @@ def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, w
     cfg.volume_rule = ESDG_RULE_SYMMETRIC if rule == "symmetric" else ESDG_RULE_COLLAPSED
     cfg.boundary = ESDG_BOUNDARY_WALLS if walls else ESDG_BOUNDARY_PERIODIC
     cfg.mass = ESDG_MASS_WEIGHT_ADJUSTED if mass == "weight_adjusted" else ESDG_MASS_EXACT
+    cfg.method = ESDG_METHOD_SBP if method == "sbp" else ESDG_METHOD_MODAL
     return cfg
 
 
@@ -282,12 +288,13 @@ class Solver:
 
     def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
                  warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
-                 mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, mass="exact", torch_memory=True,
-                 stream=None):
+                 mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, mass="exact", method="modal",
+                 torch_memory=True, stream=None):
         import torch
         self.lib = load_library()
         cfg = make_config(N, nx, ny, precision=precision, x0=x0, x1=x1, y0=y0, y1=y1, warp=warp, g=g, cfl=cfl,
-                          lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule, walls=walls, mass=mass)
+                          lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule, walls=walls, mass=mass,
+                          method=method)
         self.cfg = cfg
         h = ctypes.c_void_p()
         self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)
@@ -297,6 +304,8 @@ class Solver:
         self._check(self.lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq),
                                         ctypes.byref(Nfq), ctypes.byref(nbytes)))
         self.K, self.Np, self.Nq, self.Nfq = K.value, Np.value, Nq.value, Nfq.value
+        # unknowns per element and field: modal coefficients, or the DG-SBP nodal values
+        self.ndof = self.Nq if method == "sbp" else self.Np
         self.device_bytes = nbytes.value
         if stream is None:
             stream = torch.cuda.current_stream()
@@ -349,25 +358,25 @@ class Solver:
         self._check(self.lib.esdg_set_bathymetry(self.h, _ptr(b)))
 
     def set_state(self, u):
-        """u: numpy (host) or torch CUDA tensor [3][K][Np] float64."""
+        """u: numpy (host) or torch CUDA tensor [3][K][ndof] float64."""
         on_dev = 0 if isinstance(u, np.ndarray) else 1
         if on_dev == 0:
             u = np.ascontiguousarray(u, dtype=np.float64)
-        assert tuple(u.shape) == (3, self.K, self.Np)
+        assert tuple(u.shape) == (3, self.K, self.ndof)
         self._check(self.lib.esdg_set_state(self.h, _ptr(u), on_dev))
 
     def get_state(self, out=None):
         if out is None:
-            out = np.zeros((3, self.K, self.Np))
+            out = np.zeros((3, self.K, self.ndof))
         on_dev = 0 if isinstance(out, np.ndarray) else 1
         self._check(self.lib.esdg_copy_state(self.h, _ptr(out), on_dev))
         return out
 
     def rhs(self, t=0.0, u_in=None, out=None):
-        """du/dt as a torch CUDA tensor [3][K][Np] float64."""
+        """du/dt as a torch CUDA tensor [3][K][ndof] float64."""
         import torch
         if out is None:
-            out = torch.empty((3, self.K, self.Np), dtype=torch.float64, device="cuda")
+            out = torch.empty((3, self.K, self.ndof), dtype=torch.float64, device="cuda")
         self._check(self.lib.esdg_rhs(self.h, t, _ptr(u_in), _ptr(out)))
         return out
 
@@ -377,13 +386,13 @@ class Solver:
         return tt.value
 
     def step_host(self, u_in, nsteps=1, dt=0.0, t=0.0, out=None):
-        """esdg_step_host: the state u_in (host [3][K][Np] float64 in pinned
+        """esdg_step_host: the state u_in (host [3][K][ndof] float64 in pinned
         memory, e.g. a numpy view of a torch pin_memory tensor) is read by the
         device directly, nsteps steps run and the result is written to out
         (pinned host memory; default: u_in itself).  Returns (out, t)."""
         out = u_in if out is None else out
         for a in (u_in, out):
-            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (3, self.K, self.Np)
+            assert isinstance(a, np.ndarray) and a.dtype == np.float64 and a.shape == (3, self.K, self.ndof)
         tt = ctypes.c_double(t)
         self._check(self.lib.esdg_step_host(self.h, _ptr(u_in), nsteps, dt, ctypes.byref(tt), _ptr(out)))
         return out, tt.value

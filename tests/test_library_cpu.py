@@ -48,6 +48,7 @@ def _cfg(**kw):
     c.volume_rule = kw.get("rule", esdg.ESDG_RULE_COLLAPSED)
     c.boundary = kw.get("boundary", esdg.ESDG_BOUNDARY_PERIODIC)
     c.mass = kw.get("mass", esdg.ESDG_MASS_EXACT)
+    c.method = kw.get("method", esdg.ESDG_METHOD_MODAL)
     return c
 
 
@@ -59,7 +60,8 @@ def _build(**kw):
 
 
 @pytest.mark.parametrize("bad", [dict(N=0), dict(N=6), dict(nx=2), dict(ny=1), dict(g=0.0), dict(precision=7),
-                                 dict(rule=2), dict(rule=-1), dict(boundary=2), dict(mass=2), dict(mass=-1)])
+                                 dict(rule=2), dict(rule=-1), dict(boundary=2), dict(mass=2), dict(mass=-1),
+                                 dict(method=2), dict(method=1, boundary=1), dict(method=1, mass=1)])
 def test_build_rejects_bad_config(bad):
     lib, rc, h = _build(**bad)
     assert rc == esdg.ESDG_EINVAL
@@ -154,3 +156,21 @@ def test_weight_adjusted_mass_stores_no_inverses(rule, precision):
     rs = 4 if precision == esdg.ESDG_FP32 else 8
     stored = K * Np * (Np + 1) // 2 * rs
     assert stored - 16384 <= exact - wadg <= stored + 16384
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_sbp_rule_points_match_oracle(N):
+    """The host builder's SBP rule (its own Levenberg-Marquardt solve) gives
+    the oracle's nodes in the oracle's order, on a curved mesh."""
+    from oracle.sbp import SBPOracle
+    lib, rc, h = _build(N=N, nx=5, ny=3, warp=0.05, method=esdg.ESDG_METHOD_SBP)
+    assert rc == 0
+    o = SBPOracle(N, 5, 3, ax=0.05, ay=0.05)
+    K, Nq = ctypes.c_int(), ctypes.c_int()
+    assert lib.esdg_sizes(h, ctypes.byref(K), None, ctypes.byref(Nq), None, None) == 0
+    assert (K.value, Nq.value) == (o.K, o.Nq)
+    x, y = np.zeros((o.K, o.Nq)), np.zeros((o.K, o.Nq))
+    assert lib.esdg_get_points(h, esdg.ESDG_POINTS_VOLQ, x.ctypes.data, y.ctypes.data) == 0
+    xo, yo = o.points("volq")
+    assert np.abs(x - xo).max() < 1e-13 and np.abs(y - yo).max() < 1e-13
+    lib.esdg_destroy(h)

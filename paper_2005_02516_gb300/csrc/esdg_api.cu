@@ -15,6 +15,7 @@
 
 #include "esdg.h"
 #include "esdg_launch.hpp"
+#include "esdg_sbp2.cuh"
 #include "host_build.hpp"
 
 namespace esdg {
@@ -135,7 +136,9 @@ static void compute_layout(esdg_ctx* c) {
                       : rs * (size_t(R.Nh) * R.Nh * 2 + 2 * size_t(R.Nq) * R.Np + 2 * size_t(R.Nh) * R.Np +
                               3 * size_t(R.Nfq) + size_t(R.Nq));
     L.ops = take(L.ops_bytes);
-    L.ops2_bytes = (!sbp && c->cfg.precision == ESDG_FP32) ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
+    L.ops2_bytes = c->cfg.precision != ESDG_FP32 ? 0
+                   : sbp ? 4 * size_t(sbp2_ops_floats(c->cfg.N))
+                         : 4 * size_t(c2_ops_floats(kernel_nr(c->cfg)));
     L.ops2 = take(L.ops2_bytes);
     L.vq64 = take(sbp ? 0 : 8 * size_t(R.Nq) * R.Np);
     L.geo = take(rs * Kp * nrec * 4);
@@ -220,6 +223,47 @@ static std::vector<real> pack_ops_sbp(const RefOps& R) {
         o.push_back((real)R.ns[f]);
     }
     return o;
+}
+
+// Operators of the FP32 batched DG-SBP kernel in its shared-memory layout (S2<N>
+// in esdg_sbp2.cuh): the skew SBP operators / 8 per (column, lane slot), w_f,
+// the scaled normals, and the face-node / volume-node maps as int bits.
+template <int N>
+static std::vector<float> pack_ops_sbp2_t(const RefOps& R) {
+    typedef S2<N> C;
+    const int Nq = R.Nq, LPE = C::LPE;
+    const std::vector<double> full = pack_ops_sbp<double>(R);  // [m][l][2], then w_f, normals
+    std::vector<float> o(C::o_end, 0.f);
+    for (int m = 0; m < Nq; ++m)
+        for (int b = 0; b < LPE; ++b)
+            for (int i = 0; i < C::RPL; ++i) {
+                const int l = b + LPE * i;
+                if (l >= Nq) continue;
+                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)(0.125 * full[(size_t(m) * Nq + l) * 2]);
+                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)(0.125 * full[(size_t(m) * Nq + l) * 2 + 1]);
+            }
+    const size_t base = size_t(Nq) * Nq * 2;
+    for (int f = 0; f < R.Nfq; ++f) {
+        o[C::o_wf + f] = (float)full[base + f];
+        o[C::o_nrs + 2 * f] = (float)full[base + R.Nfq + 2 * f];
+        o[C::o_nrs + 2 * f + 1] = (float)full[base + R.Nfq + 2 * f + 1];
+    }
+    std::vector<int> frow(Nq, -1);
+    for (int f = 0; f < R.Nfq; ++f) frow[R.fmap[f]] = f;
+    std::memcpy(o.data() + C::o_fmap, R.fmap.data(), sizeof(int) * R.Nfq);
+    std::memcpy(o.data() + C::o_frow, frow.data(), sizeof(int) * Nq);
+    return o;
+}
+
+static std::vector<float> pack_ops_sbp2(const RefOps& R) {
+    switch (R.N) {
+        case 1: return pack_ops_sbp2_t<1>(R);
+        case 2: return pack_ops_sbp2_t<2>(R);
+        case 3: return pack_ops_sbp2_t<3>(R);
+        case 4: return pack_ops_sbp2_t<4>(R);
+        case 5: return pack_ops_sbp2_t<5>(R);
+    }
+    return {};
 }
 
 // Operators of k_stage2 in its shared-memory layout (see C2<N> in esdg_stage2.cuh).
@@ -321,6 +365,7 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     if (c->sbp) {
         put(img, c->L.ops, pack_ops_sbp<real>(R));
         put(img, c->L.fmap, R.fmap);
+        if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops_sbp2(R));
         // metrics at the SBP nodes (the volume part of the hybrid nodes)
         std::vector<real> geo(K * R.Nq * 4);
         for (size_t e = 0; e < K; ++e)
@@ -506,6 +551,15 @@ static real* ut_buf(esdg_ctx* c, int which) {
 // ---- degree dispatch ---------------------------------------------------------
 template <typename real>
 static cudaError_t d_sbp(esdg_ctx* c, const StageParams<real>& p, int mode) {
+    if constexpr (std::is_same<real, float>::value) {
+        // FP32 stages on the batched kernel; record preparation on the generic one
+        const float* ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
+        if (mode != 2) switch (c->cfg.N) {
+#define X(v) case v: return launch_sbp2<v>(p, ops2, c->Kpad, mode, c->lg2, c->stream);
+            X(1) X(2) X(3) X(4) X(5)
+#undef X
+        }
+    }
     switch (c->cfg.N) {
 #define X(v) case v: return launch_sbp<v, real>(p, mode, c->lg, c->stream);
         X(1) X(2) X(3) X(4) X(5)
@@ -520,7 +574,11 @@ static cudaError_t d_geometry(esdg_ctx* c) {
     if (c->sbp) {
         const bool f32 = c->cfg.precision == ESDG_FP32;
         switch (c->cfg.N) {
-#define X(v) case v: e = f32 ? sbp_geometry<v, float>(sms, c->lg) : sbp_geometry<v, double>(sms, c->lg); break;
+#define X(v)                                                                       \
+    case v:                                                                        \
+        e = f32 ? sbp_geometry<v, float>(sms, c->lg) : sbp_geometry<v, double>(sms, c->lg); \
+        if (!e && f32) e = sbp2_geometry<v>(sms, c->lg2);                          \
+        break;
             X(1) X(2) X(3) X(4) X(5)
 #undef X
         }

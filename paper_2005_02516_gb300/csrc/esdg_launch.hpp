@@ -40,6 +40,13 @@ template <int N, typename real>
 cudaError_t sbp_geometry(int num_sms, LaunchGeom& lg);
 template <int N, typename real>
 cudaError_t launch_sbp(const StageParams<real>& p, int mode, const LaunchGeom& lg, cudaStream_t s);
+// FP32 batched DG-SBP stage kernel (esdg_sbp2.cuh), modes 0 and 1.
+template <int N>
+cudaError_t sbp2_geometry(int num_sms, LaunchGeom& lg);
+template <int N>
+cudaError_t launch_sbp2(const StageParams<float>& p, const float* ops2, int Kpad, int mode, const LaunchGeom& lg,
+                        cudaStream_t s);
+int sbp2_ops_floats(int N);
 cudaError_t launch_entropy_nodal(int K, int Nq, double g, const double* u, const double* rhs, const double* wJq,
                                  const double* bq, double* partial, int nparts, double* out, cudaStream_t s);
 

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
     const real g = p.g;
     const real eighth = real(0.125);
     for (int e = blockIdx.x * wpb + warp; e < p.K; e += gridDim.x * wpb) {
-        if (MODE == 2) {
+        if constexpr (MODE == 2) {
             int bad = 0;
             for (int i = lane; i < D::Nq; i += 32) {
                 const size_t g0 = ((size_t)0 * p.K + e) * D::Nq + i;
@@ -106,8 +106,7 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                 o[3] = hr + p.bh[(size_t)e * D::Nq + i];
             }
             if (bad) atomicOr(p.status, bad);
-            continue;
-        }
+        } else {
         // ---- nodal records of the element ----------------------------------------
         for (int l = lane; l < D::Nq; l += 32) {
             const real* ut = p.ut_in + ((size_t)e * D::Nq + l) * 4;
@@ -234,6 +233,7 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
         }
         if (bad) atomicOr(p.status, bad);
         __syncwarp();
+        }
     }
 }
 

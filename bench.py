@@ -42,6 +42,9 @@ WL = W.DAM
 STAGE_TRAFFIC = {"exact": {"source_sha1": "f02127742633926d43cbacca013f9cc9b778da04", "bytes": 432.4e6},
                  "weight_adjusted": {"source_sha1": "f02127742633926d43cbacca013f9cc9b778da04", "bytes": 362.5e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
+# the same for the FP32 DG-SBP stage kernel (profiles/k_sbp2_dam_k131072_n4.md)
+SBP_TRAFFIC = {"source_sha1": "4ea83419271dec62e0f86bdf5ce3ea2c48616b76", "bytes": 386.1e6}
+SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")
 
 # Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of
 # each step of the path, and the bytes each element-stage must move.
@@ -86,6 +89,21 @@ def algorithmic_bytes(N, Nq, real_bytes=4, wadg=False):
     b += Nh * real_bytes                # bathymetry at hybrid nodes
     b += 3 * 4                          # neighbour ids
     return b
+
+
+def sbp_algorithmic(N, Nq, real_bytes=4):
+    """DG-SBP (Sec. 3) per element-stage: FLOPs and bytes.  Nq nodes (all of
+    them rows and columns of the dense skew SBP operator), Nfq = 3(N+1) face
+    nodes among them."""
+    Nfq = 3 * (N + 1)
+    flops = 35 * Nq * (Nq - 1) // 2 + 40 * Nfq + 3 * Nq + 4 * 3 * Nq   # pairs, interface, 1/(wJ), RK
+    b = 4 * 3 * Nq * 8                  # u, res read + write (FP64)
+    b += 2 * Nq * 4 * real_bytes        # nodal records own read + next write
+    b += Nfq * 3 * real_bytes           # neighbour values
+    b += Nq * 4 * real_bytes            # metrics
+    b += 2 * Nq * real_bytes            # w_q J_q, b
+    b += 3 * 4                          # neighbour ids
+    return flops, b
 
 
 def load_peaks():
@@ -185,9 +203,10 @@ def replica_value(units_per_rank, world, max_seconds):
     return units_per_rank * world / max_seconds / 1e9
 
 
-def make_solver(precision, mass="exact"):
+def make_solver(precision, mass="exact", method="modal"):
     from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
-    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule, mass=mass)
+    s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule, mass=mass,
+               method=method)
     xb, yb = s.points(ESDG_POINTS_NODAL)
     xq, yq = s.points(ESDG_POINTS_VOLQ)
     s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
@@ -401,6 +420,35 @@ def run_volume_ratio(sizes=(16, 32, 50, 100, 150, 200), pairs_gpu=1 << 27, pairs
 PAPER_V100_FP64_S_PER_STEP = {1: 0.0221, 2: 0.0316, 3: 0.0515, 4: 0.0627, 5: 0.1585}
 
 
+def run_sbp(steps, warmup, world, peaks):
+    """The DG-SBP scheme of Sec. 3 on the same workload (N = 4, K = 131072
+    curved; 22 SBP nodes per element): FP32 right-hand side with FP64 RK and
+    the plain FP64 path, time per stage, throughput counted in the modal
+    unknowns K Np (same polynomial degree, so comparable with the headline)
+    and in its own nodal unknowns K Nq, and the FP32 kernel's HBM roofline."""
+    import hashlib
+    out = {}
+    for prec, st in (("fp32", steps), ("fp64", max(2, steps // 20))):
+        s = make_solver(prec, method="sbp")
+        el = time_steps(s, st, warmup if prec == "fp32" else 1, world)
+        t = el / (5 * st)
+        row = {"value": s.K * s.Np * 5 * st / el / 1e9, "unit": UNIT,
+               "nodal_gdof_stage_s": s.K * s.Nq * 5 * st / el / 1e9, "ms_per_step": el / st * 1e3, "steps": st,
+               "Nq": s.Nq, "device_bytes": s.device_bytes}
+        if prec == "fp32":
+            fl, by = sbp_algorithmic(WL.N, s.Nq, 4)
+            traffic = None
+            with open(SBP_SOURCE, "rb") as f:
+                if SBP_TRAFFIC is not None and hashlib.sha1(f.read()).hexdigest() == SBP_TRAFFIC["source_sha1"]:
+                    traffic = SBP_TRAFFIC["bytes"]
+            row["roofline"] = {"bound": "hbm", "achieved": by * s.K / t / 1e9, "peak": peaks["hbm_gbs"],
+                               "unit": "GB/s", "frac": by * s.K / t / 1e9 / peaks["hbm_gbs"], "traffic": traffic,
+                               "algorithmic_bytes_per_element_stage": by, "algorithmic_flops_per_element_stage": fl}
+        out[prec] = row
+        s.close()
+    return out
+
+
 def run_context(degrees=(1, 2, 3, 4, 5), steps=3):
     """Context row beside the paper's GPU table: K = 65536 affine periodic
     (256 x 128 quads), N = 1..5, the symmetric volume rule (the paper's rule is
@@ -503,10 +551,16 @@ def main():
     ap.add_argument("--served-rate", type=float, default=20.0)
     ap.add_argument("--mass", default="exact", choices=["exact", "weight_adjusted"],
                     help="inverse mass of the timed leg: stored (M_h^k)^-1 (the paper's) or weight-adjusted")
+    ap.add_argument("--method", default="modal", choices=["modal", "sbp"],
+                    help="scheme of the timed leg: the paper's modal ESDG (Sec. 2) or the DG-SBP scheme (Sec. 3; "
+                         "implies --fp32-only --no-e2e)")
+    ap.add_argument("--no-sbp", action="store_true", help="skip the DG-SBP comparison leg")
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.method == "sbp":   # the side legs belong to the modal headline
+        args.fp32_only = args.no_e2e = True
     global WL
     if args.nx is not None:
         WL = W.scaled(WL, args.nx)
@@ -520,29 +574,33 @@ def main():
     torch.cuda.set_device(local)
     peaks, peak_kind = load_peaks()
 
-    s = make_solver("fp32", args.mass)
+    s = make_solver("fp32", args.mass, args.method)
     wadg = args.mass == "weight_adjusted"
+    sbp_main = args.method == "sbp"
     steps = args.steps
     clocks = ClockSampler(local)
     clocks.start()
     el = time_steps(s, steps, args.warmup, world)
     clk = clocks.stop()
     el_max = max_over_ranks(el, world)
-    K, Np = s.K, s.Np
+    K, Np, Nq_run = s.K, s.Np, s.Nq
     units = K * Np * 5 * steps
     value = replica_value(units, world, el_max)
     launches = 5 * steps
     t_launch = el / launches
     flops = algorithmic_flops(WL.N, WL.Nq, wadg) * K
     nbytes = algorithmic_bytes(WL.N, WL.Nq, 4, wadg) * K
+    if sbp_main:
+        fl_s, by_s = sbp_algorithmic(WL.N, s.Nq, 4)
+        flops, nbytes = fl_s * K, by_s * K
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12     # TFLOP/s at the maximum SM clock
     alu = flops / t_launch / 1e12
     hbm = nbytes / t_launch / 1e9
     traffic = None
     import hashlib
-    rec = STAGE_TRAFFIC.get(args.mass)
-    with open(STAGE_SOURCE, "rb") as f:
+    rec = (SBP_TRAFFIC if sbp_main else STAGE_TRAFFIC.get(args.mass))
+    with open(SBP_SOURCE if sbp_main else STAGE_SOURCE, "rb") as f:
         if rec is not None and hashlib.sha1(f.read()).hexdigest() == rec["source_sha1"]:
             traffic = rec["bytes"]
     roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
@@ -556,7 +614,7 @@ def main():
     # comparison: its throughput, HBM roofline fraction and the relative L2
     # difference of the two FP32 states after the same warm-up + timed steps
     other_mass = None
-    if not args.fp32_only:
+    if not args.fp32_only and not sbp_main:
         om = "exact" if wadg else "weight_adjusted"
         s2 = make_solver("fp32", om)
         el2 = time_steps(s2, steps, args.warmup, world)
@@ -587,6 +645,10 @@ def main():
         precision = precision_report(s64, 1 + st64)
         s64.close()
         del s64
+
+    sbp = None
+    if not args.fp32_only and not args.no_sbp and not sbp_main:
+        sbp = run_sbp(steps, args.warmup, world, peaks)
 
     volume_ratio = None
     if not args.fp32_only and not args.no_volume_ratio and rank == 0:
@@ -623,12 +685,13 @@ def main():
                 "warmup": args.warmup, "ms_per_step": el_max / steps * 1e3, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": WL.name if args.nx is None else "%s_nx%d" % (WL.name, args.nx),
-                           "N": WL.N, "K": K, "Np": Np, "Nq": WL.Nq, "volume_rule": WL.rule, "curved": True,
-                           "mass": args.mass,
+                           "N": WL.N, "K": K, "Np": Np, "Nq": Nq_run,
+                           "volume_rule": "sbp" if sbp_main else WL.rule, "curved": True,
+                           "mass": args.mass, "method": args.method,
                            "rhs_precision": "fp32", "rk_accumulation": "fp64",
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
-                "roofline": roofline, "roofline_other": other, "other_mass": other_mass,
+                "roofline": roofline, "roofline_other": other, "other_mass": other_mass, "sbp": sbp,
                 "fp64": fp64, "precision": precision, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))

@@ -225,23 +225,27 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
             for (int c = 0; c < 3; ++c) p.rhs_out[((size_t)c * K + ge) * D::Nq + l] = (double)d[c];
         } else {
             // ---- LSRK45 stage in FP64; the next stage's record --------------------------
+            // (dt du/dt formed in FP32, the precision of du/dt; the record's
+            // velocities divided in FP32, the precision they are stored in: the
+            // FP64 pipe, narrow on this part, keeps only the two DFMAs a value)
             if (!EARLY) load_rk(i);
-            double un[3];
+            const float dtf = (float)p.dt;
+            float uf[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const size_t gi = ((size_t)c * K + ge) * D::Nq + l;
-                const double rs = fma(p.rkA, ro[i][c], p.dt * f2d_bits(d[c]));
-                un[c] = fma(p.rkB, rs, uo[i][c]);
+                const double rs = fma(p.rkA, ro[i][c], f2d_bits(dtf * d[c]));
+                const double un = fma(p.rkB, rs, uo[i][c]);
                 p.res[gi] = rs;
-                p.u[gi] = un[c];
-                if (p.u_out) p.u_out[gi] = un[c];
+                p.u[gi] = un;
+                if (p.u_out) p.u_out[gi] = un;
+                uf[c] = d2f_bits(un);
             }
-            if (!(un[0] > 0.0)) bad |= STATUS_NONPOSITIVE;
-            if (!isfinite(un[0]) || !isfinite(un[1]) || !isfinite(un[2])) bad |= STATUS_NONFINITE;
-            const double ih = 1.0 / un[0];
-            const float hf = d2f_bits(un[0]);
+            if (!(uf[0] > 0.f)) bad |= STATUS_NONPOSITIVE;
+            if (!isfinite(uf[0]) || !isfinite(uf[1]) || !isfinite(uf[2])) bad |= STATUS_NONFINITE;
+            const float ih = 1.f / uf[0];
             *reinterpret_cast<float4*>(p.ut_out + ((size_t)ge * D::Nq + l) * 4) =
-                make_float4(hf, d2f_bits(un[1] * ih), d2f_bits(un[2] * ih), hf + bl[i]);
+                make_float4(uf[0], uf[1] * ih, uf[2] * ih, uf[0] + bl[i]);
         }
     }
     if (bad) atomicOr(p.status, bad);

@@ -106,6 +106,13 @@ def sbp_algorithmic(N, Nq, real_bytes=4):
     return flops, b
 
 
+def fp64_peak(peaks):
+    """FP64 SIMT peak, TFLOP/s: 152 SMs x 2 DFMA per SM per cycle (the unit
+    rate ncu states for sm_103) x 2 FLOP x the maximum SM clock."""
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e12, "152 SMs x 2 DFMA/cycle x 2 x %.0f MHz" % sm_mhz
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -435,6 +442,11 @@ def run_sbp(steps, warmup, world, peaks):
         row = {"value": s.K * s.Np * 5 * st / el / 1e9, "unit": UNIT,
                "nodal_gdof_stage_s": s.K * s.Nq * 5 * st / el / 1e9, "ms_per_step": el / st * 1e3, "steps": st,
                "Nq": s.Nq, "device_bytes": s.device_bytes}
+        if prec == "fp64":
+            pk64, pk64_src = fp64_peak(peaks)
+            ach = sbp_algorithmic(WL.N, s.Nq, 8)[0] * s.K / t / 1e12
+            row["roofline"] = {"bound": "alu", "achieved": ach, "peak": pk64, "unit": "TFLOP/s", "frac": ach / pk64,
+                               "peak_source": pk64_src}
         if prec == "fp32":
             fl, by = sbp_algorithmic(WL.N, s.Nq, 4)
             traffic = None
@@ -640,7 +652,11 @@ def main():
         s64 = make_solver("fp64")
         st64 = max(2, steps // 20)
         el64 = time_steps(s64, st64, 1, world)
+        pk64, pk64_src = fp64_peak(peaks)
+        ach64 = algorithmic_flops(WL.N, WL.Nq) * K * 5 * st64 / el64 / 1e12
         fp64 = {"value": K * Np * 5 * st64 / el64 / 1e9, "unit": UNIT, "ms_per_step": el64 / st64 * 1e3,
+                "roofline": {"bound": "alu", "achieved": ach64, "peak": pk64, "unit": "TFLOP/s",
+                             "frac": ach64 / pk64, "peak_source": pk64_src},
                 "steps": st64}
         precision = precision_report(s64, 1 + st64)
         s64.close()

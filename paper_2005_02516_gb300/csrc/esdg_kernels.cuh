@@ -118,6 +118,30 @@ __device__ __forceinline__ void r_sincospi<double>(double x, double* s, double* 
 template <typename real>
 __device__ __forceinline__ bool r_finite(real x) { return isfinite(x); }
 
+// Row r of a three-field contraction with T terms, for R <= 16 rows: the two
+// half-warps take half of the terms each and the sums meet by a shuffle, so
+// all 32 lanes work (rows r = lane & 15).  acc(r, t, a0, a1, a2) adds term t.
+// Every lane of the warp calls it; it returns true on lanes 0..R-1, which hold
+// the sums of row r = lane.
+template <int R, int T, typename real, typename Acc>
+__device__ __forceinline__ bool split_rows(int lane, Acc acc, real& a0, real& a1, real& a2) {
+    static_assert(R <= 16, "two half-warps of rows");
+    constexpr int TH = (T + 1) / 2;
+    const int r = lane & 15, hf = lane >> 4;
+    a0 = a1 = a2 = real(0);
+    if (r < R) {
+#pragma unroll
+        for (int tt = 0; tt < TH; ++tt) {
+            const int t = hf * TH + tt;
+            if (t < T) acc(r, t, a0, a1, a2);
+        }
+    }
+    a0 += __shfl_down_sync(0xffffffffu, a0, 16);
+    a1 += __shfl_down_sync(0xffffffffu, a1, 16);
+    a2 += __shfl_down_sync(0xffffffffu, a2, 16);
+    return lane < R;
+}
+
 // Shared-memory layout of one CTA: reference operators, then one slab per warp.
 template <int N, typename real>
 struct Smem {
@@ -222,14 +246,21 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
     const real g = p.g;
     int bad = 0;
     // u_q = Vq u_h, v_q = v(u_q), scaled by w_q J_q
-    for (int q = lane; q < D::Nq; q += 32) {
+    auto vq_term = [&](int q, int n, real& a0, real& a1, real& a2) {
+        const real v = Vq[q * D::Np + n];
+        a0 += v * us[n];
+        a1 += v * us[D::Np + n];
+        a2 += v * us[2 * D::Np + n];
+    };
+    for (int q0 = 0; q0 < D::Nq; q0 += 32) {
         real a0 = 0, a1 = 0, a2 = 0;
+        const int q = q0 + lane;
+        if constexpr (D::Nq <= 16) {
+            if (!split_rows<D::Nq, D::Np>(lane, vq_term, a0, a1, a2)) continue;
+        } else {
+            if (q >= D::Nq) continue;
 #pragma unroll
-        for (int n = 0; n < D::Np; ++n) {
-            real v = Vq[q * D::Np + n];
-            a0 += v * us[n];
-            a1 += v * us[D::Np + n];
-            a2 += v * us[2 * D::Np + n];
+            for (int n = 0; n < D::Np; ++n) vq_term(q, n, a0, a1, a2);
         }
         real h = a0;
         if (!(h > real(0))) bad |= STATUS_NONPOSITIVE;
@@ -243,14 +274,21 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
     }
     __syncwarp();
     // y = Vq^T W J v_q
-    for (int n = lane; n < D::Np; n += 32) {
+    auto vqt_term = [&](int n, int q, real& a0, real& a1, real& a2) {
+        const real v = VqT[n * D::Nq + q];
+        a0 += v * ta[q];
+        a1 += v * ta[D::Nq + q];
+        a2 += v * ta[2 * D::Nq + q];
+    };
+    for (int n0 = 0; n0 < D::Np; n0 += 32) {
         real a0 = 0, a1 = 0, a2 = 0;
+        const int n = n0 + lane;
+        if constexpr (D::Np <= 16) {
+            if (!split_rows<D::Np, D::Nq>(lane, vqt_term, a0, a1, a2)) continue;
+        } else {
+            if (n >= D::Np) continue;
 #pragma unroll 5
-        for (int q = 0; q < D::Nq; ++q) {
-            real v = VqT[n * D::Nq + q];
-            a0 += v * ta[q];
-            a1 += v * ta[D::Nq + q];
-            a2 += v * ta[2 * D::Nq + q];
+            for (int q = 0; q < D::Nq; ++q) vqt_term(n, q, a0, a1, a2);
         }
         tc[n] = a0;
         tc[D::Np + n] = a1;
@@ -262,15 +300,22 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
         wadg_apply<N, real>(p, ops, tc, ta, us, e, lane, real(1));
     } else {
         // v_h = (M_h^k)^{-1} y   (packed symmetric)
-        for (int n = lane; n < D::Np; n += 32) {
+        auto mi_term = [&](int n, int j, real& a0, real& a1, real& a2) {
+            const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+            const real m = mi[ij];
+            a0 += m * tc[j];
+            a1 += m * tc[D::Np + j];
+            a2 += m * tc[2 * D::Np + j];
+        };
+        for (int n0 = 0; n0 < D::Np; n0 += 32) {
             real a0 = 0, a1 = 0, a2 = 0;
+            const int n = n0 + lane;
+            if constexpr (D::Np <= 16) {
+                if (!split_rows<D::Np, D::Np>(lane, mi_term, a0, a1, a2)) continue;
+            } else {
+                if (n >= D::Np) continue;
 #pragma unroll
-            for (int j = 0; j < D::Np; ++j) {
-                int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
-                real m = mi[ij];
-                a0 += m * tc[j];
-                a1 += m * tc[D::Np + j];
-                a2 += m * tc[2 * D::Np + j];
+                for (int j = 0; j < D::Np; ++j) mi_term(n, j, a0, a1, a2);
             }
             us[n] = a0;   // us is free again: reuse for v_h
             us[D::Np + n] = a1;
@@ -389,19 +434,22 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
             real a0 = 0, a1 = 0, a2 = 0;
             const int mEnd = (l < D::Nq) ? D::Nh : D::Nq;
+            // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the
+            // row part is added once after the loop
             for (int m = 0; m < mEnd; ++m) {
                 const real2 q = QsT[m * D::Nh + l];
                 const real* rm = rec + m * S::REC;
                 const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
                 const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
                 const real HU = hu_l + rm[1], HV = hv_l + rm[2];
-                const real U = u_l + rm[3], V = v_l + rm[4];
                 const real T = Qx * HU + Qy * HV;
                 const real P = gh2_l * rm[5];
                 a0 += T;
-                a1 += U * T + Qx * P;
-                a2 += V * T + Qy * P;
+                a1 += rm[3] * T + Qx * P;
+                a2 += rm[4] * T + Qy * P;
             }
+            a1 += u_l * a0;
+            a2 += v_l * a0;
             real r0 = real(2) * a0, r1 = a1, r2 = a2;
             if (l >= D::Nq) {
                 // interface: f_S(u~+, u~) with the well-balanced pressure
@@ -442,7 +490,8 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 r2 += w * Fn2;
                 if (p.lf) {
                     const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
-                    const real inx = nxJ / sJ, iny = nyJ / sJ;
+                    const real isJ = real(1) / sJ;
+                    const real inx = nxJ * isJ, iny = nyJ * isJ;
                     const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
                     const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
                     const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
@@ -481,22 +530,37 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         const real* VhT = ops + S::ops_VhT;
         const real* VqT = ops + S::ops_VqT;
         real* sb = ws + S::w_b;
-        for (int n = lane; n < D::Np; n += 32) {
+        auto vht_term = [&](int n, int l, real& a0, real& a1, real& a2) {
+            const real v = VhT[n * D::Nh + l];
+            a0 += v * rt[l];
+            a1 += v * rt[D::Nh + l];
+            a2 += v * rt[2 * D::Nh + l];
+        };
+        auto frc_term = [&](int n, int q, real& a0, real& a1, real& a2) {
+            const real v = VqT[n * D::Nq + q];
+            a0 -= v * fa[q];
+            a1 -= v * fa[D::Nq + q];
+            a2 -= v * fa[2 * D::Nq + q];
+        };
+        for (int n0 = 0; n0 < D::Np; n0 += 32) {
             real a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 8
-            for (int l = 0; l < D::Nh; ++l) {
-                const real v = VhT[n * D::Nh + l];
-                a0 += v * rt[l];
-                a1 += v * rt[D::Nh + l];
-                a2 += v * rt[2 * D::Nh + l];
-            }
-            if (p.forcing) {
-                for (int q = 0; q < D::Nq; ++q) {
-                    const real v = VqT[n * D::Nq + q];
-                    a0 -= v * fa[q];
-                    a1 -= v * fa[D::Nq + q];
-                    a2 -= v * fa[2 * D::Nq + q];
+            const int n = n0 + lane;
+            if constexpr (D::Np <= 16) {
+                const bool own = split_rows<D::Np, D::Nh>(lane, vht_term, a0, a1, a2);
+                if (p.forcing) {
+                    real f0, f1, f2;
+                    split_rows<D::Np, D::Nq>(lane, frc_term, f0, f1, f2);
+                    a0 += f0;
+                    a1 += f1;
+                    a2 += f2;
                 }
+                if (!own) continue;
+            } else {
+                if (n >= D::Np) continue;
+#pragma unroll 8
+                for (int l = 0; l < D::Nh; ++l) vht_term(n, l, a0, a1, a2);
+                if (p.forcing)
+                    for (int q = 0; q < D::Nq; ++q) frc_term(n, q, a0, a1, a2);
             }
             sb[n] = a0;
             sb[D::Np + n] = a1;
@@ -509,15 +573,22 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             wadg_apply<N, real>(p, ops, sb, fa, sc, e, lane, real(-1));  // fa (forcing) is consumed
         } else {
             const real* mi = ws + S::w_minv;
-            for (int n = lane; n < D::Np; n += 32) {
+            auto mi_term = [&](int n, int j, real& a0, real& a1, real& a2) {
+                const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
+                const real m = mi[ij];
+                a0 += m * sb[j];
+                a1 += m * sb[D::Np + j];
+                a2 += m * sb[2 * D::Np + j];
+            };
+            for (int n0 = 0; n0 < D::Np; n0 += 32) {
                 real a0 = 0, a1 = 0, a2 = 0;
+                const int n = n0 + lane;
+                if constexpr (D::Np <= 16) {
+                    if (!split_rows<D::Np, D::Np>(lane, mi_term, a0, a1, a2)) continue;
+                } else {
+                    if (n >= D::Np) continue;
 #pragma unroll
-                for (int j = 0; j < D::Np; ++j) {
-                    const int ij = n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n;
-                    const real m = mi[ij];
-                    a0 += m * sb[j];
-                    a1 += m * sb[D::Np + j];
-                    a2 += m * sb[2 * D::Np + j];
+                    for (int j = 0; j < D::Np; ++j) mi_term(n, j, a0, a1, a2);
                 }
                 sc[n] = -a0;
                 sc[D::Np + n] = -a1;

@@ -98,7 +98,8 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                     p.res[g0] = p.res[g1] = p.res[g2] = 0.0;
                 }
                 if (!(h > 0.0)) bad |= STATUS_NONPOSITIVE;
-                const real hr = (real)h, ur = (real)(hu / h), vr = (real)(hv / h);
+                const double ih = 1.0 / h;
+                const real hr = (real)h, ur = (real)(hu * ih), vr = (real)(hv * ih);
                 real* o = p.ut_out + ((size_t)e * D::Nq + i) * 4;
                 o[0] = hr;
                 o[1] = ur;
@@ -134,19 +135,21 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
             const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
             real a0 = 0, a1 = 0, a2 = 0;
+            // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T
             for (int m = 0; m < D::Nq; ++m) {
                 const real2 q = QsT[m * D::Nq + l];
                 const real* rm = rec + m * S::REC;
                 const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
                 const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
                 const real HU = hu_l + rm[1], HV = hv_l + rm[2];
-                const real U = u_l + rm[3], V = v_l + rm[4];
                 const real T = Qx * HU + Qy * HV;
                 const real P = gh2_l * rm[5];
                 a0 += T;
-                a1 += U * T + Qx * P;
-                a2 += V * T + Qy * P;
+                a1 += rm[3] * T + Qx * P;
+                a2 += rm[4] * T + Qy * P;
             }
+            a1 += u_l * a0;
+            a2 += v_l * a0;
             real r0 = real(2) * a0, r1 = a1, r2 = a2;
             const int f = frow[l];
             if (f >= 0) {
@@ -170,7 +173,8 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                 r2 += w * (vA * Fn0 + nyJ * pw);
                 if (p.lf) {
                     const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
-                    const real inx = nxJ / sJ, iny = nyJ / sJ;
+                    const real isJ = real(1) / sJ;
+                    const real inx = nxJ * isJ, iny = nyJ * isJ;
                     const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
                     const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
                     const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
@@ -224,10 +228,11 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                 if (!(h > 0.0)) bad |= STATUS_NONPOSITIVE;
                 if (!isfinite(un[0]) || !isfinite(un[1]) || !isfinite(un[2])) bad |= STATUS_NONFINITE;
                 const real hr = (real)h;
+                const double ih = 1.0 / h;
                 real* o = p.ut_out + ((size_t)e * D::Nq + l) * 4;
                 o[0] = hr;
-                o[1] = (real)(un[1] / h);
-                o[2] = (real)(un[2] / h);
+                o[1] = (real)(un[1] * ih);
+                o[2] = (real)(un[2] * ih);
                 o[3] = hr + rec[l * S::REC + 11];
             }
         }

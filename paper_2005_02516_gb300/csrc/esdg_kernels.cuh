@@ -428,25 +428,85 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         load_minv<N, real>(p, ws, e, lane);
         __syncwarp();
         // ---- volume flux differencing + interface flux, row l = lane ----------
+        // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the row
+        // part is added once after the pair loop.
+        // Volume rows take Nh columns, face rows Nq.  With Nq = 16 and Nh <= 32
+        // the face-row lanes (16 and up) also take the last Nh - C columns of
+        // volume row lane - 16 after their own row, so no lane runs more than
+        // max(C, Nq + Nh - C) pairs (the FP64 pipe, which bounds this kernel,
+        // then carries no idle lanes' share); the partial sums meet by a shuffle.
+        constexpr bool SPLIT = D::Nq == 16 && D::Nh > 16 && D::Nh <= 32;
+        constexpr int C = SPLIT ? (16 + D::Nh + 1) / 2 : D::Nh;
+        real tl0 = 0, tl1 = 0, tl2 = 0;  // volume row lane's share computed by lane + 16
+        if constexpr (SPLIT) {
+            constexpr int ITERS = C > D::Nq + D::Nh - C ? C : D::Nq + D::Nh - C;
+            const int len1 = lane < 16 ? C : (lane < D::Nh ? D::Nq : 0);  // own row's columns
+            const int len2 = lane >= 16 ? D::Nh - C : 0;                   // tail of row lane - 16
+            int row = lane < D::Nh ? lane : lane - 16;
+            if (len1 == 0) row = lane - 16;
+            const real* rl = rec + row * S::REC;
+            real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real c0 = 0, c1 = 0, c2 = 0, s0 = 0, s1 = 0, s2 = 0;
+            int m = len1 == 0 ? C : 0;
+            for (int it = 0; it < ITERS; ++it) {
+                if (it == len1 && len1 > 0 && len2 > 0) {
+                    // own row done: keep its sums, continue on the volume row's tail
+                    s0 = c0; s1 = c1; s2 = c2;
+                    c0 = c1 = c2 = 0;
+                    row = lane - 16;
+                    rl = rec + row * S::REC;
+                    hu_l = rl[1]; hv_l = rl[2]; rx_l = rl[6]; sx_l = rl[7]; ry_l = rl[8]; sy_l = rl[9];
+                    gh2_l = rl[10];
+                    m = C;
+                }
+                if (it < len1 + len2) {
+                    const real2 q = QsT[m * D::Nh + row];
+                    const real* rm = rec + m * S::REC;
+                    const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                    const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                    const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                    const real T = Qx * HU + Qy * HV;
+                    const real P = gh2_l * rm[5];
+                    c0 += T;
+                    c1 += rm[3] * T + Qx * P;
+                    c2 += rm[4] * T + Qy * P;
+                    ++m;
+                }
+            }
+            // lanes < 16: c = own volume row (first C columns); lanes >= 16: c =
+            // the tail of row lane - 16, s = the own face row (lane 31: no row)
+            tl0 = __shfl_down_sync(0xffffffffu, c0, 16);
+            tl1 = __shfl_down_sync(0xffffffffu, c1, 16);
+            tl2 = __shfl_down_sync(0xffffffffu, c2, 16);
+            if (lane < 16) {
+                tl0 += c0; tl1 += c1; tl2 += c2;
+            } else {
+                tl0 = s0; tl1 = s1; tl2 = s2;
+            }
+        }
         for (int l = lane; l < D::Nh; l += 32) {
             const real* rl = rec + l * S::REC;
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
             const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
             real a0 = 0, a1 = 0, a2 = 0;
-            const int mEnd = (l < D::Nq) ? D::Nh : D::Nq;
-            // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the
-            // row part is added once after the loop
-            for (int m = 0; m < mEnd; ++m) {
-                const real2 q = QsT[m * D::Nh + l];
-                const real* rm = rec + m * S::REC;
-                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
-                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
-                const real HU = hu_l + rm[1], HV = hv_l + rm[2];
-                const real T = Qx * HU + Qy * HV;
-                const real P = gh2_l * rm[5];
-                a0 += T;
-                a1 += rm[3] * T + Qx * P;
-                a2 += rm[4] * T + Qy * P;
+            if constexpr (SPLIT) {
+                a0 = tl0;
+                a1 = tl1;
+                a2 = tl2;
+            } else {
+                const int mEnd = (l < D::Nq) ? D::Nh : D::Nq;
+                for (int m = 0; m < mEnd; ++m) {
+                    const real2 q = QsT[m * D::Nh + l];
+                    const real* rm = rec + m * S::REC;
+                    const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                    const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                    const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                    const real T = Qx * HU + Qy * HV;
+                    const real P = gh2_l * rm[5];
+                    a0 += T;
+                    a1 += rm[3] * T + Qx * P;
+                    a2 += rm[4] * T + Qy * P;
+                }
             }
             a1 += u_l * a0;
             a2 += v_l * a0;

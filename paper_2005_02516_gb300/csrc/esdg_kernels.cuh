@@ -430,20 +430,19 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         // ---- volume flux differencing + interface flux, row l = lane ----------
         // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the row
         // part is added once after the pair loop.
-        // Volume rows take Nh columns, face rows Nq.  With Nq = 16 and Nh <= 32
-        // the face-row lanes (16 and up) also take the last Nh - C columns of
-        // volume row lane - 16 after their own row, so no lane runs more than
+        // Volume rows take Nh columns, face rows Nq.  With Nq <= 16 and Nh <= 32
+        // the lanes 16 and up also take the last Nh - C columns of volume row
+        // lane - 16 (after their own face row, if any), so no lane runs more than
         // max(C, Nq + Nh - C) pairs (the FP64 pipe, which bounds this kernel,
         // then carries no idle lanes' share); the partial sums meet by a shuffle.
-        constexpr bool SPLIT = D::Nq == 16 && D::Nh > 16 && D::Nh <= 32;
-        constexpr int C = SPLIT ? (16 + D::Nh + 1) / 2 : D::Nh;
-        real tl0 = 0, tl1 = 0, tl2 = 0;  // volume row lane's share computed by lane + 16
+        constexpr bool SPLIT = D::Nq <= 16 && D::Nh <= 32;
+        constexpr int C = SPLIT ? (D::Nq + D::Nh + 1) / 2 : D::Nh;
+        real tl0 = 0, tl1 = 0, tl2 = 0;  // the lane's own row sums after the pair loop
         if constexpr (SPLIT) {
             constexpr int ITERS = C > D::Nq + D::Nh - C ? C : D::Nq + D::Nh - C;
-            const int len1 = lane < 16 ? C : (lane < D::Nh ? D::Nq : 0);  // own row's columns
-            const int len2 = lane >= 16 ? D::Nh - C : 0;                   // tail of row lane - 16
-            int row = lane < D::Nh ? lane : lane - 16;
-            if (len1 == 0) row = lane - 16;
+            const int len1 = lane < D::Nq ? C : (lane < D::Nh ? D::Nq : 0);     // own row's columns
+            const int len2 = (lane >= 16 && lane - 16 < D::Nq) ? D::Nh - C : 0;  // tail of row lane - 16
+            int row = len1 > 0 ? lane : (len2 > 0 ? lane - 16 : 0);  // idle lanes read row 0
             const real* rl = rec + row * S::REC;
             real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
             real c0 = 0, c1 = 0, c2 = 0, s0 = 0, s1 = 0, s2 = 0;
@@ -460,7 +459,7 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                     m = C;
                 }
                 if (it < len1 + len2) {
-                    const real2 q = QsT[m * D::Nh + row];
+                    const real2 q = QsT[m * D::Nh + row];  // row < Nh, m < Nh
                     const real* rm = rec + m * S::REC;
                     const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
                     const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
@@ -473,15 +472,20 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                     ++m;
                 }
             }
-            // lanes < 16: c = own volume row (first C columns); lanes >= 16: c =
-            // the tail of row lane - 16, s = the own face row (lane 31: no row)
-            tl0 = __shfl_down_sync(0xffffffffu, c0, 16);
-            tl1 = __shfl_down_sync(0xffffffffu, c1, 16);
-            tl2 = __shfl_down_sync(0xffffffffu, c2, 16);
-            if (lane < 16) {
-                tl0 += c0; tl1 += c1; tl2 += c2;
-            } else {
-                tl0 = s0; tl1 = s1; tl2 = s2;
+            // own row and tail partial sums: a lane that switched holds its own
+            // row in s and the tail in c; a tail-only lane holds the tail in c
+            const bool switched = len1 > 0 && len2 > 0;
+            const real o0 = switched ? s0 : (len1 > 0 ? c0 : real(0));
+            const real o1 = switched ? s1 : (len1 > 0 ? c1 : real(0));
+            const real o2 = switched ? s2 : (len1 > 0 ? c2 : real(0));
+            const real p0 = len2 > 0 ? c0 : real(0), p1 = len2 > 0 ? c1 : real(0), p2 = len2 > 0 ? c2 : real(0);
+            // volume row v (< Nq <= 16) receives its tail from lane v + 16
+            const real r0 = __shfl_down_sync(0xffffffffu, p0, 16);
+            const real r1 = __shfl_down_sync(0xffffffffu, p1, 16);
+            const real r2 = __shfl_down_sync(0xffffffffu, p2, 16);
+            tl0 = o0; tl1 = o1; tl2 = o2;
+            if (lane < D::Nq) {
+                tl0 += r0; tl1 += r1; tl2 += r2;
             }
         }
         for (int l = lane; l < D::Nh; l += 32) {

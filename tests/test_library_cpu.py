@@ -174,3 +174,37 @@ def test_sbp_rule_points_match_oracle(N):
     xo, yo = o.points("volq")
     assert np.abs(x - xo).max() < 1e-13 and np.abs(y - yo).max() < 1e-13
     lib.esdg_destroy(h)
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
+def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
+    """The FP64 stage kernel's lane schedule of the pair loop (esdg_kernels.cuh,
+    k_stage: with Nq <= 16 and Nh <= 32 lane v < Nq takes columns [0, C) of
+    volume row v, lanes 16 and up take their own face row's Nq columns and then
+    columns [C, Nh) of volume row lane - 16), replayed on the host: every
+    non-zero pair (volume rows x all columns, face rows x volume columns) is
+    evaluated exactly once, with in-range indices, in max(C, Nq + Nh - C)
+    iterations."""
+    Nq = {1: 3, 2: 6, 3: 12, 4: 16, 5: 25}[N] if rule == "symmetric" else (N + 1) ** 2
+    Nh = Nq + 3 * (N + 1)
+    if not (Nq <= 16 and Nh <= 32):
+        pytest.skip("the kernel keeps one row per lane here")
+    C = (Nq + Nh + 1) // 2
+    iters = max(C, Nq + Nh - C)
+    seen = {}
+    for lane in range(32):
+        len1 = C if lane < Nq else (Nq if lane < Nh else 0)
+        len2 = Nh - C if (lane >= 16 and lane - 16 < Nq) else 0
+        row = lane if len1 > 0 else (lane - 16 if len2 > 0 else 0)
+        m = C if len1 == 0 else 0
+        for it in range(iters):
+            if it == len1 and len1 > 0 and len2 > 0:
+                row, m = lane - 16, C
+            if it < len1 + len2:
+                assert 0 <= row < Nh and 0 <= m < Nh
+                seen[(row, m)] = seen.get((row, m), 0) + 1
+                m += 1
+    want = {(l, m): 1 for l in range(Nh) for m in range(Nh if l < Nq else Nq)}
+    assert seen == want
+    assert iters < Nh

@@ -15,8 +15,10 @@
 // its volume node).  Neighbour values come from the previous stage's nodal
 // record buffer (ut_in), so a stage never reads values it is updating.
 //
-// A warp per element (rows l = lane, lane + 32), operators in shared memory;
-// the same kernel in FP64 and FP32.
+// A warp per element (rows l = lane, lane + 32), operators in shared memory:
+// the FP64 stages, and the preparation of nodal records from a state (MODE 2)
+// in both precisions; the FP32 stages run on the batched k_sbp2
+// (esdg_sbp2.cuh).
 #pragma once
 
 #include "esdg_kernels.cuh"

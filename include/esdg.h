@@ -345,6 +345,17 @@ int esdg_destroy(esdg_ctx* ctx);
  * esdg_build_operators failures).  The string lives until the next call. */
 const char* esdg_last_error(const esdg_ctx* ctx);
 
+/*
+ * esdg_selftest_wait_timeout -- failure-detection self-test: one warp waits,
+ * through the same bounded mbarrier wait that the stage kernels put on their
+ * bulk copies, on a phase that no copy completes.  After its cycle limit
+ * (about a second) the wait sets the timeout bit of a status word and the
+ * kernel returns, with nothing in flight.  Returns ESDG_ETIMEOUT when that
+ * happened (the expected outcome), ESDG_OK if the phase completed (it cannot),
+ * ESDG_ECUDA / ESDG_ENOMEM on a CUDA failure.  stream: a cudaStream_t.
+ */
+int esdg_selftest_wait_timeout(void* stream);
+
 #ifdef __cplusplus
 }
 #endif

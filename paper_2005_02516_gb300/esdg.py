@@ -54,7 +54,7 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
            "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
-           "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host"]
+           "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host", "esdg_selftest_wait_timeout"]
 
 
 class EsdgError(RuntimeError):
@@ -126,6 +126,7 @@ def load_library(path=LIB_PATH):
         "esdg_volume_kernel": ([I, I, I, I, D, P, P, P, P, P], I),
         "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
         "esdg_step_host": ([P, P, I, D, PD, P], I),
+        "esdg_selftest_wait_timeout": ([P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)

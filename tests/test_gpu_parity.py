@@ -285,3 +285,32 @@ def test_step_host_equals_set_step_copy(precision):
         s.step_host(np.array(u), 1, dt)
     assert ei.value.code == ESDG_EINVAL
     s.step(1, dt)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_checkpoint_resume_is_exact(precision):
+    """Checkpoint / resume: the state u alone restarts LSRK45 (its first
+    stage has A = 0, so the residual carries nothing across steps).  Ten steps
+    in one run equal five steps, esdg_copy_state, a new context,
+    esdg_set_state and five more steps, to rounding: the resumed run projects
+    its first u~ in the projection kernel rather than at the end of a stage
+    kernel, whose compiled arithmetic may round differently."""
+    w = W.scaled(W.MMS, 6, 5)
+    s1, o = _solver(w, precision, nx=6, ny=5)
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_VOLQ
+    xs, ys = s1.points(ESDG_POINTS_VOLQ)
+    q = w.initial(xs, ys)
+    s1.init_state(None, q)
+    dt = o.dt()
+    s1.step(10, dt, 0.0)
+    u10 = s1.get_state()
+    s2, _ = _solver(w, precision, nx=6, ny=5)
+    s2.init_state(None, q)
+    s2.step(5, dt, 0.0)
+    ck = s2.get_state()
+    s2.close()
+    s3, _ = _solver(w, precision, nx=6, ny=5)
+    s3.set_state(ck)
+    s3.step(5, dt, 5 * dt)
+    tol = 1e-13 if precision == "fp64" else 1e-6
+    assert np.linalg.norm(s3.get_state() - u10) <= tol * np.linalg.norm(u10)

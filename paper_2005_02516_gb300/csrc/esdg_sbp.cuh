@@ -48,7 +48,13 @@ struct SbpSmem {
     static constexpr int ops_end = ((ops_nrs + 2 * D::Nfq) + 3) & ~3;
     static constexpr int w_rec = 0;                           // [Nq][REC]
     static constexpr int w_r = w_rec + D::Nq * REC;           // [3][Nq] du/dt
-    static constexpr int w_end = ((w_r + 3 * D::Nq) + 3) & ~3;
+    // the pair loop in 32 equal pieces of the flattened Nq x Nq pair list:
+    // each lane's piece spans at most PR rows, whose partial sums meet in
+    // w_part ([32][PR][4]: three sums and the row)
+    static constexpr int PL = (D::Nq * D::Nq + 31) / 32;      // pairs per lane
+    static constexpr int PR = (PL + D::Nq - 2) / D::Nq + 1;   // rows a piece can touch
+    static constexpr int w_part = w_r + 3 * D::Nq;
+    static constexpr int w_end = ((w_part + 32 * PR * 4) + 3) & ~3;
     static constexpr size_t bytes(int warps) {
         return sizeof(real) * (size_t(ops_end) + size_t(warps) * w_end) + sizeof(int) * 2 * 64;
     }
@@ -131,25 +137,71 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
             r[11] = b;
         }
         __syncwarp();
-        // ---- flux differencing over all node pairs, interface at face rows -----------
+        // ---- flux differencing over all node pairs --------------------------------
+        // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the row
+        // part is added once per row.  The Nq x Nq pairs, row-major, are cut
+        // into 32 pieces of PL, one per lane (all lanes busy on the FP64 pipe,
+        // which bounds the FP64 path); a piece's partial row sums go to w_part
+        // when its row ends, and each row's owner adds up the pieces of its row.
+        real* part = ws + S::w_part;
+        {
+            const int p0 = lane * S::PL;
+            const int p1 = p0 + S::PL < D::Nq * D::Nq ? p0 + S::PL : D::Nq * D::Nq;
+            int r = p0 < p1 ? p0 / D::Nq : 0, m = p0 < p1 ? p0 - r * D::Nq : 0, slot = 0;
+            const real* rl = rec + r * S::REC;
+            real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real c0 = 0, c1 = 0, c2 = 0;
+            for (int k = 0; k < S::PR * 4; ++k) part[lane * S::PR * 4 + k] = real(-1);
+            for (int it = 0; it < S::PL; ++it) {
+                if (p0 + it < p1) {
+                    const real2 q = QsT[m * D::Nq + r];
+                    const real* rm = rec + m * S::REC;
+                    const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                    const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                    const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                    const real T = Qx * HU + Qy * HV;
+                    const real P = gh2_l * rm[5];
+                    c0 += T;
+                    c1 += rm[3] * T + Qx * P;
+                    c2 += rm[4] * T + Qy * P;
+                    if (++m == D::Nq || p0 + it + 1 == p1) {
+                        // this row's piece ends: file its partial sums
+                        real* o = part + (lane * S::PR + slot) * 4;
+                        o[0] = c0;
+                        o[1] = c1;
+                        o[2] = c2;
+                        o[3] = real(r);
+                        ++slot;
+                        c0 = c1 = c2 = 0;
+                        if (m == D::Nq && r + 1 < D::Nq) {
+                            m = 0;
+                            ++r;
+                            rl = rec + r * S::REC;
+                            hu_l = rl[1]; hv_l = rl[2]; rx_l = rl[6]; sx_l = rl[7]; ry_l = rl[8]; sy_l = rl[9];
+                            gh2_l = rl[10];
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();
         for (int l = lane; l < D::Nq; l += 32) {
             const real* rl = rec + l * S::REC;
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
-            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9];
             real a0 = 0, a1 = 0, a2 = 0;
-            // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T
-            for (int m = 0; m < D::Nq; ++m) {
-                const real2 q = QsT[m * D::Nq + l];
-                const real* rm = rec + m * S::REC;
-                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
-                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
-                const real HU = hu_l + rm[1], HV = hv_l + rm[2];
-                const real T = Qx * HU + Qy * HV;
-                const real P = gh2_l * rm[5];
-                a0 += T;
-                a1 += rm[3] * T + Qx * P;
-                a2 += rm[4] * T + Qy * P;
-            }
+            // the pieces of row l: lanes l Nq / PL .. ((l+1) Nq - 1) / PL, in lane order
+            const int k0 = (l * D::Nq) / S::PL, k1 = ((l + 1) * D::Nq - 1) / S::PL;
+            for (int k = k0; k <= k1; ++k)
+#pragma unroll
+                for (int sl = 0; sl < S::PR; ++sl) {
+                    const real* o = part + (k * S::PR + sl) * 4;
+                    if (o[3] == real(l)) {
+                        a0 += o[0];
+                        a1 += o[1];
+                        a2 += o[2];
+                    }
+                }
             a1 += u_l * a0;
             a2 += v_l * a0;
             real r0 = real(2) * a0, r1 = a1, r2 = a2;

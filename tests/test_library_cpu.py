@@ -208,3 +208,31 @@ def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
     want = {(l, m): 1 for l in range(Nh) for m in range(Nh if l < Nq else Nq)}
     assert seen == want
     assert iters < Nh
+
+
+@pytest.mark.parametrize("Nq", [6, 10, 18, 22, 34])
+def test_fp64_sbp_kernel_pair_pieces(Nq):
+    """The FP64 DG-SBP kernel's split of the Nq x Nq pairs into 32 pieces of
+    PL (esdg_sbp.cuh), replayed on the host: every pair is evaluated once, a
+    piece files at most PR partial rows, and the lanes that row l's owner
+    reads back, l Nq / PL .. ((l+1) Nq - 1) / PL, hold all of row l's pieces."""
+    PL = (Nq * Nq + 31) // 32
+    PR = (PL + Nq - 2) // Nq + 1
+    seen, filed = {}, {}
+    for lane in range(32):
+        p0, p1 = lane * PL, min(lane * PL + PL, Nq * Nq)
+        r, m, slot = (p0 // Nq, p0 % Nq, 0) if p0 < p1 else (0, 0, 0)
+        for it in range(PL):
+            if p0 + it < p1:
+                seen[(r, m)] = seen.get((r, m), 0) + 1
+                m += 1
+                if m == Nq or p0 + it + 1 == p1:
+                    filed.setdefault(r, []).append(lane)
+                    slot += 1
+                    assert slot <= PR
+                    if m == Nq and r + 1 < Nq:
+                        m, r = 0, r + 1
+    assert seen == {(r, m): 1 for r in range(Nq) for m in range(Nq)}
+    for l in range(Nq):
+        k0, k1 = (l * Nq) // PL, ((l + 1) * Nq - 1) // PL
+        assert set(filed[l]) <= set(range(k0, k1 + 1)) and 0 <= k0 <= k1 < 32

@@ -17,7 +17,9 @@
  *   - Arrays are dense, C order.  The state is u[field][element][mode], FP64,
  *     fields (h, hu, hv), modes of the orthonormal Dubiner basis in the order
  *     i = 0..N, j = 0..N-i (phi_ij = sqrt(2) P_i(a) P_j^(2i+1,0)(b) (1-b)^i,
- *     a = 2(1+r)/(1-s) - 1, b = s).
+ *     a = 2(1+r)/(1-s) - 1, b = s).  With ESDG_METHOD_SBP the last index runs
+ *     over the Nq SBP nodes instead (state [3][K][Nq] of nodal values), and
+ *     every [3][K][Np] state or right-hand side below is [3][K][Nq].
  *   - All work is enqueued on the stream given to esdg_attach_device(); calls
  *     that return host data synchronise that stream.
  */

@@ -485,18 +485,12 @@ def run_context(degrees=(1, 2, 3, 4, 5), steps=3):
     return rows
 
 
-def cpu_baseline(seconds_target=15.0):
-    """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
-    on a sample of 2048 consecutive elements of the same workload, repeated
-    until about `seconds_target` seconds of CPU work."""
-    from oracle import Oracle
-    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
-    xb, yb = o.points("nodal")
-    o.set_bathymetry(WL.bathymetry(xb, yb))
-    xq, yq = o.points("volq")
-    u = o.init_state(WL.initial(xq, yq))
-    ks = np.arange(0, 2048)
-    o.rhs_elements(u, ks)
+def _oracle_rhs_loop(o, u, ks, seconds_target, barrier=None):
+    """Repeated oracle right-hand sides on the elements ks for about
+    seconds_target seconds: (evaluations, seconds)."""
+    o.rhs_elements(u, ks)   # warm-up
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
     n = 0
     while True:
@@ -504,11 +498,52 @@ def cpu_baseline(seconds_target=15.0):
         n += 1
         el = time.perf_counter() - t0
         if el > seconds_target:
-            break
-    gdof = ks.size * o.Np * n / el / 1e9
-    return {"value": gdof, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d right-hand-side evaluations of elements 0..2047 of the K=131072 N=4 workload "
-                      "(FP64 numpy oracle, single thread), %.1f s" % (n, el)}
+            return n, el
+
+
+_CPU_ORACLE = None
+
+
+def _oracle_worker(i, chunk, seconds_target, barrier, out):
+    o, u = _CPU_ORACLE
+    ks = np.arange(i * chunk, (i + 1) * chunk)
+    out.put(_oracle_rhs_loop(o, u, ks, seconds_target, barrier))
+
+
+def cpu_baseline(seconds_target=12.0, chunk=2048):
+    """The FP64 oracle (as it stands) on the host: right-hand-side evaluations
+    on samples of 2048 consecutive elements of the same workload, for about
+    `seconds_target` seconds, once on one core and once on every core at the
+    same time (one process per core, each on its own 2048 elements; forked,
+    so this runs before the process touches the GPU)."""
+    global _CPU_ORACLE
+    import multiprocessing as mp
+    from oracle import Oracle
+    o = Oracle(WL.N, WL.nx, WL.ny, ax=WL.warp, ay=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(WL.bathymetry(xb, yb))
+    xq, yq = o.points("volq")
+    u = o.init_state(WL.initial(xq, yq))
+    n1, el1 = _oracle_rhs_loop(o, u, np.arange(0, chunk), seconds_target)
+    single = chunk * o.Np * n1 / el1 / 1e9
+    procs = max(1, min(os.cpu_count() or 1, 64, o.K // chunk))
+    _CPU_ORACLE = (o, u)
+    ctx = mp.get_context("fork")
+    barrier, out = ctx.Barrier(procs), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(i, chunk, seconds_target, barrier, out)) for i in range(procs)]
+    for pr in ps:
+        pr.start()
+    res = [out.get() for _ in ps]
+    for pr in ps:
+        pr.join()
+    _CPU_ORACLE = None
+    parallel = sum(chunk * o.Np * n for n, _ in res) / max(el for _, el in res) / 1e9
+    return {"value": parallel, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "single_core_value": single,
+            "sample": "right-hand-side evaluations of 2048 consecutive elements of the K=131072 N=4 workload "
+                      "per core (FP64 numpy oracle, one process per core, %d cores at once, %d-%d evaluations "
+                      "each in about %.0f s; one core alone: %d evaluations in %.1f s)"
+                      % (procs, min(n for n, _ in res), max(n for n, _ in res), seconds_target, n1, el1)}
 
 
 def run_reference(args, world, rank):
@@ -581,6 +616,10 @@ def main():
         world = int(os.environ.get("WORLD_SIZE", "1"))
         run_reference(args, world, int(os.environ.get("RANK", "0")))
         return
+    cb = None
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_cpu_baseline:
+        # before any CUDA call: the CPU baseline forks its worker processes
+        cb = cpu_baseline()
     world, rank, local = dist_init("nccl")
     import torch
     torch.cuda.set_device(local)
@@ -693,9 +732,6 @@ def main():
         e2e = {"value": K * Np * 5 * e_steps * world / el_e / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb, "steps": e_steps}
         s.close()
-    cb = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": steps,
                 "warmup": args.warmup, "ms_per_step": el_max / steps * 1e3, "higher_is_better": True,

@@ -163,7 +163,15 @@ struct Smem {
     static constexpr int w_b = w_a + 3 * D::Nq;                  // [3][Np]
     static constexpr int w_c = w_b + 3 * D::Np;                  // [3][Np]
     static constexpr int w_minv = w_c + 3 * D::Np;               // [NpP] (stored inverse only)
-    static constexpr int w_end = ((w_minv + (D::wadg ? 0 : D::NpP)) + 3) & ~3;
+    // pair loop of the rules too large for the half-warp split (see k_stage):
+    // the NPAIR non-zero pairs, row-major, cut into 32 pieces of PL, each piece
+    // touching at most PR rows; partial row sums in w_part [32][PR][4]
+    static constexpr bool PIECES = !(D::Nq <= 16 && D::Nh <= 32);
+    static constexpr int NPAIR = D::Nq * D::Nh + D::Nfq * D::Nq;
+    static constexpr int PL = (NPAIR + 31) / 32;
+    static constexpr int PR = (PL + D::Nq - 2) / D::Nq + 1;
+    static constexpr int w_part = ((w_minv + (D::wadg ? 0 : D::NpP)) + 3) & ~3;
+    static constexpr int w_end = ((w_part + (PIECES ? 32 * PR * 4 : 0)) + 3) & ~3;
     static constexpr size_t bytes(int warps) { return sizeof(real) * (size_t(ops_end) + size_t(warps) * w_end); }
 };
 
@@ -488,29 +496,88 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 tl0 += r0; tl1 += r1; tl2 += r2;
             }
         }
-        for (int l = lane; l < D::Nh; l += 32) {
-            const real* rl = rec + l * S::REC;
-            const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
-            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
-            real a0 = 0, a1 = 0, a2 = 0;
-            if constexpr (SPLIT) {
-                a0 = tl0;
-                a1 = tl1;
-                a2 = tl2;
+        // Larger rules: the non-zero pairs (volume rows x Nh columns, then face
+        // rows x Nq columns), row-major, in 32 equal pieces, one per lane; a
+        // piece files its partial row sums when a row ends, and each row's
+        // owner adds up the pieces of its row below.
+        real* part = ws + S::w_part;
+        if constexpr (S::PIECES) {
+            const int p0 = lane * S::PL;
+            const int p1 = p0 + S::PL < S::NPAIR ? p0 + S::PL : S::NPAIR;
+            const int pp = p0 < p1 ? p0 : 0;
+            int r, m, len, slot = 0;
+            if (pp < D::Nq * D::Nh) {
+                r = pp / D::Nh;
+                m = pp - r * D::Nh;
+                len = D::Nh;
             } else {
-                const int mEnd = (l < D::Nq) ? D::Nh : D::Nq;
-                for (int m = 0; m < mEnd; ++m) {
-                    const real2 q = QsT[m * D::Nh + l];
+                const int q = pp - D::Nq * D::Nh;
+                r = D::Nq + q / D::Nq;
+                m = q - (r - D::Nq) * D::Nq;
+                len = D::Nq;
+            }
+            const real* rl = rec + r * S::REC;
+            real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real c0 = 0, c1 = 0, c2 = 0;
+            for (int k = 0; k < S::PR * 4; ++k) part[lane * S::PR * 4 + k] = real(-1);
+#pragma unroll 1
+            for (int it = 0; it < S::PL; ++it) {
+                if (p0 + it < p1) {
+                    const real2 q = QsT[m * D::Nh + r];
                     const real* rm = rec + m * S::REC;
                     const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
                     const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
                     const real HU = hu_l + rm[1], HV = hv_l + rm[2];
                     const real T = Qx * HU + Qy * HV;
                     const real P = gh2_l * rm[5];
-                    a0 += T;
-                    a1 += rm[3] * T + Qx * P;
-                    a2 += rm[4] * T + Qy * P;
+                    c0 += T;
+                    c1 += rm[3] * T + Qx * P;
+                    c2 += rm[4] * T + Qy * P;
+                    if (++m == len || p0 + it + 1 == p1) {
+                        real* o = part + (lane * S::PR + slot) * 4;
+                        o[0] = c0;
+                        o[1] = c1;
+                        o[2] = c2;
+                        o[3] = real(r);
+                        ++slot;
+                        c0 = c1 = c2 = 0;
+                        if (m == len && r + 1 < D::Nh) {
+                            ++r;
+                            m = 0;
+                            len = r < D::Nq ? D::Nh : D::Nq;
+                            rl = rec + r * S::REC;
+                            hu_l = rl[1]; hv_l = rl[2]; rx_l = rl[6]; sx_l = rl[7]; ry_l = rl[8]; sy_l = rl[9];
+                            gh2_l = rl[10];
+                        }
+                    }
                 }
+            }
+            __syncwarp();
+        }
+        for (int l = lane; l < D::Nh; l += 32) {
+            const real* rl = rec + l * S::REC;
+            const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
+            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9];
+            real a0 = 0, a1 = 0, a2 = 0;
+            if constexpr (SPLIT) {
+                a0 = tl0;
+                a1 = tl1;
+                a2 = tl2;
+            } else {
+                // the pieces of row l, in lane order
+                const int start = l < D::Nq ? l * D::Nh : D::Nq * D::Nh + (l - D::Nq) * D::Nq;
+                const int len = l < D::Nq ? D::Nh : D::Nq;
+                const int k0 = start / S::PL, k1 = (start + len - 1) / S::PL;
+                for (int k = k0; k <= k1; ++k)
+#pragma unroll
+                    for (int sl = 0; sl < S::PR; ++sl) {
+                        const real* o = part + (k * S::PR + sl) * 4;
+                        if (o[3] == real(l)) {
+                            a0 += o[0];
+                            a1 += o[1];
+                            a2 += o[2];
+                        }
+                    }
             }
             a1 += u_l * a0;
             a2 += v_l * a0;

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
             real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
             real c0 = 0, c1 = 0, c2 = 0;
             for (int k = 0; k < S::PR * 4; ++k) part[lane * S::PR * 4 + k] = real(-1);
+#pragma unroll 1
             for (int it = 0; it < S::PL; ++it) {
                 if (p0 + it < p1) {
                     const real2 q = QsT[m * D::Nq + r];

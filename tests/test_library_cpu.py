@@ -176,6 +176,44 @@ def test_sbp_rule_points_match_oracle(N):
     lib.esdg_destroy(h)
 
 
+def _replay_fp64_pieces(Nq, Nh):
+    """The larger rules' schedule (Smem::PIECES): the non-zero pairs
+    row-major (volume rows x Nh columns, face rows x Nq columns) in 32 pieces
+    of PL; every pair once, at most PR filed rows a piece, and each row's
+    pieces inside the lane range its owner reads."""
+    NPAIR = Nq * Nh + (Nh - Nq) * Nq
+    PL = (NPAIR + 31) // 32
+    PR = (PL + Nq - 2) // Nq + 1
+    seen, filed = {}, {}
+    for lane in range(32):
+        p0, p1 = lane * PL, min(lane * PL + PL, NPAIR)
+        pp = p0 if p0 < p1 else 0
+        if pp < Nq * Nh:
+            r, m, ln = pp // Nh, pp % Nh, Nh
+        else:
+            q = pp - Nq * Nh
+            r, m, ln = Nq + q // Nq, q % Nq, Nq
+        slot = 0
+        for it in range(PL):
+            if p0 + it < p1:
+                assert r < Nh and m < ln
+                seen[(r, m)] = seen.get((r, m), 0) + 1
+                m += 1
+                if m == ln or p0 + it + 1 == p1:
+                    filed.setdefault(r, []).append(lane)
+                    slot += 1
+                    assert slot <= PR
+                    if m == ln and r + 1 < Nh:
+                        r, m = r + 1, 0
+                        ln = Nh if r < Nq else Nq
+    assert seen == {(l, m): 1 for l in range(Nh) for m in range(Nh if l < Nq else Nq)}
+    for l in range(Nh):
+        start = l * Nh if l < Nq else Nq * Nh + (l - Nq) * Nq
+        ln = Nh if l < Nq else Nq
+        k0, k1 = start // PL, (start + ln - 1) // PL
+        assert set(filed[l]) <= set(range(k0, k1 + 1)) and k1 < 32
+
+
 @pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
@@ -185,11 +223,12 @@ def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
     columns [C, Nh) of volume row lane - 16), replayed on the host: every
     non-zero pair (volume rows x all columns, face rows x volume columns) is
     evaluated exactly once, with in-range indices, in max(C, Nq + Nh - C)
-    iterations."""
+    iterations; the larger rules' 32-piece schedule likewise."""
     Nq = {1: 3, 2: 6, 3: 12, 4: 16, 5: 25}[N] if rule == "symmetric" else (N + 1) ** 2
     Nh = Nq + 3 * (N + 1)
     if not (Nq <= 16 and Nh <= 32):
-        pytest.skip("the kernel keeps one row per lane here")
+        _replay_fp64_pieces(Nq, Nh)
+        return
     C = (Nq + Nh + 1) // 2
     iters = max(C, Nq + Nh - C)
     seen = {}

@@ -151,3 +151,24 @@ def test_weight_adjusted_is_refused_by_ensembles_and_served_fp32():
     assert ei.value.code == esdg.ESDG_EINVAL
     p.close()
     srv.close()
+
+
+@pytest.mark.parametrize("rule,N", [("symmetric", 4), ("collapsed", 3)])
+def test_weight_adjusted_with_walls_matches_oracle(rule, N):
+    """The weight-adjusted inverse in a walled box (reflective walls, Sec. 2.9):
+    right-hand side FP64 at 1e-12 and FP32 at 5e-5 against the oracle."""
+    from paper_2005_02516_gb300.esdg import ESDG_POINTS_NODAL, Solver
+    w = W.DAM
+    for precision, tol in (("fp64", 1e-12), ("fp32", 5e-5)):
+        s = Solver(N, 6, 5, precision=precision, warp=w.warp, g=w.g, cfl=w.cfl, rule=rule, walls=True, mass=WA)
+        o = Oracle(N, 6, 5, ax=w.warp, ay=w.warp, g=w.g, cfl=w.cfl, rule=rule, walls=True, mass=WA)
+        xb, yb = s.points(ESDG_POINTS_NODAL)
+        s.set_bathymetry(w.bathymetry(xb, yb))
+        xo, yo = o.points("nodal")
+        o.set_bathymetry(w.bathymetry(xo, yo))
+        u = random_modal_state(o.K, o.Np, seed=W.BASE_SEED + 50 + N)
+        s.set_state(u)
+        got = s.rhs(0.0).cpu().numpy()
+        want = o.rhs(u, 0.0)
+        assert _rel(got, want) < tol, precision
+        s.close()

@@ -300,7 +300,9 @@ const char* esdg_ensemble_error(const esdg_ensemble* ens);
  * Ownership of ctx passes to the server on a successful submit (it is
  * destroyed when the request finishes); b_nodal and q_volq are copied;
  * result_host must stay valid until the request is done.  FP32 requests
- * with a forcing term are refused (ESDG_EINVAL); requests larger than the whole
+ * run in an ensemble and must be modal with the stored inverse and no forcing
+ * term (else ESDG_EINVAL); FP64 requests take any configuration (each carries
+ * its own simulated time for forcing terms); requests larger than the whole
  * budget are refused (ESDG_EBUSY).  Times are seconds since esdg_server_create.
  */
 typedef struct esdg_server esdg_server;

@@ -39,7 +39,8 @@ struct Request {
     int precision = ESDG_FP32;
     int rule = ESDG_RULE_COLLAPSED;
     int nsteps = 0, remaining = 0;
-    double* result = nullptr;  // caller's host buffer [3][K][Np]
+    double dt = 0, t = 0;      // step size and the request's simulated time (forcing terms depend on it)
+    double* result = nullptr;  // caller's host buffer [3][K][Np] ([3][K][Nq] for the DG-SBP method)
     size_t bytes = 0;
     void* dmem = nullptr;
     int state = 0;  // 0 queued, 1 active, 2 done, < 0 failed (status code)
@@ -164,7 +165,7 @@ static void run(esdg_server* s) {
             if (!rc && s->ens[rule]) rc = esdg_ensemble_step_async(s->ens[rule], chunk);
         }
         for (Request* r : act)
-            if (!rc && r->precision == ESDG_FP64) rc = esdg_step_async(r->ctx, chunk, 0.0, 0.0);
+            if (!rc && r->precision == ESDG_FP64) rc = esdg_step_async(r->ctx, chunk, r->dt, r->t);
         cudaStreamSynchronize(s->stream);
         std::vector<std::pair<Request*, int>> outcome;
         for (Request* r : act) {
@@ -176,6 +177,7 @@ static void run(esdg_server* s) {
             Request* r = o.first;
             if (o.second) continue;
             r->remaining -= chunk;
+            r->t += chunk * r->dt;
             if (r->remaining == 0) {
                 int st = esdg_copy_state(r->ctx, r->result, 0);
                 o.second = st;
@@ -240,13 +242,15 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
     esdg_config cfg;
     rc = esdg_get_config(ctx, &cfg);
     // FP32 requests run inside an ensemble launch, which carries neither
-    // forcing terms nor the weight-adjusted inverse; requests are modal
-    if (rc || cfg.method != ESDG_METHOD_MODAL ||
-        (cfg.precision == ESDG_FP32 && (cfg.forcing != ESDG_FORCING_NONE || cfg.mass != ESDG_MASS_EXACT))) {
+    // forcing terms, the weight-adjusted inverse nor the DG-SBP method; FP64
+    // requests run through their own contexts and take any configuration
+    if (rc || (cfg.precision == ESDG_FP32 && (cfg.forcing != ESDG_FORCING_NONE || cfg.mass != ESDG_MASS_EXACT ||
+                                              cfg.method != ESDG_METHOD_MODAL))) {
         delete r;
         return rc ? rc : ESDG_EINVAL;
     }
     r->precision = cfg.precision;
+    esdg_dt(ctx, &r->dt);
     r->rule = cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 1 : 0;
     // all host work of the request (bathymetry, initial projection, operator
     // and geometry packing) runs here, in the submitting thread

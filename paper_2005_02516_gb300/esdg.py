@@ -187,6 +187,7 @@ class Problem:
         self.lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq),
                             ctypes.byref(nbytes))
         self.K, self.Np, self.Nq, self.Nfq = K.value, Np.value, Nq.value, Nfq.value
+        self.ndof = self.Nq if self.cfg.method == ESDG_METHOD_SBP else self.Np
         self.device_bytes = nbytes.value
 
     def points(self, kind):
@@ -235,7 +236,7 @@ class Server:
         """Submit a Problem (ownership passes to the server); returns a ticket."""
         b = np.ascontiguousarray(b_nodal, dtype=np.float64)
         q = np.ascontiguousarray(q_volq, dtype=np.float64)
-        out = np.zeros((3, problem.K, problem.Np))
+        out = np.zeros((3, problem.K, problem.ndof))
         t = ctypes.c_int()
         rc = self.lib.esdg_server_submit(self.h, problem.h, _ptr(b), _ptr(q),
                                          ESDG_INIT_SURFACE if surface else ESDG_INIT_DEPTH, nsteps, _ptr(out),

@@ -153,3 +153,35 @@ def test_failing_request_does_not_disturb_the_others():
         assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want)
     assert srv.stats()[2] == 0        # every request's device memory returned
     srv.close()
+
+
+def test_served_fp64_requests_of_any_configuration():
+    """FP64 requests run through their own contexts: a forced manufactured
+    solution (its simulated time carried across the served iterations), a
+    DG-SBP problem and a weight-adjusted one finish with the states of the
+    same problems run alone (relative 1e-12)."""
+    from paper_2005_02516_gb300 import esdg
+    mms, dam = W.scaled(W.MMS, 6, 5, N=3), W.scaled(W.DAM, 6, 6, N=3)
+    cases = [(mms, dict(forcing="mms_sine", rule="collapsed"), False, 33),
+             (dam, dict(method="sbp"), False, 17),
+             (dam, dict(mass="weight_adjusted", rule="symmetric"), False, 25)]
+    srv = esdg.Server(hbm_budget_bytes=2 << 30)
+    tickets, wants = [], []
+    for w, kw, surface, steps in cases:
+        common = dict(precision="fp64", warp=w.warp, g=w.g, cfl=w.cfl, **kw)
+        p = esdg.Problem(w.N, w.nx, w.ny, **common)
+        xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
+        xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
+        b, q = w.bathymetry(xb, yb), w.initial(xq, yq)
+        tickets.append(srv.submit(p, b, q, steps, surface=surface))
+        s = esdg.Solver(w.N, w.nx, w.ny, **common)
+        s.init_state(b, q, surface=surface)
+        s.step(steps)
+        wants.append(s.get_state())
+        s.close()
+    srv.drain(300.0)
+    for tk, want in zip(tickets, wants):
+        assert srv.query(tk)[0] == 2
+        got = srv.result(tk)
+        assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    srv.close()

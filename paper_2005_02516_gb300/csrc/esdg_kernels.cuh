@@ -758,9 +758,9 @@ __global__ void __launch_bounds__(256) k_entropy(int K, double g, const double* 
                                                  double* __restrict__ partial) {
     typedef Dims<N> D;
     double s_ent = 0, s_mass = 0, s_rate = 0;
-    const int total = K * D::Nq;
-    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-        const int e = idx / D::Nq, q = idx - e * D::Nq;
+    const size_t total = (size_t)K * D::Nq;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(idx / D::Nq), q = (int)(idx - (size_t)e * D::Nq);
         double a[3] = {0, 0, 0}, d[3] = {0, 0, 0};
         for (int n = 0; n < D::Np; ++n) {
             const double v = Vq[q * D::Np + n];

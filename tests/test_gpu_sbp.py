@@ -161,14 +161,16 @@ def test_sbp_step_host_equals_set_step_copy(precision):
     assert np.array_equal(out, s.get_state())
 
 
-def test_sbp_is_refused_by_ensembles_and_the_server():
+def test_sbp_is_refused_by_ensembles_and_served_fp32():
+    """Ensembles (and so served FP32 requests) run the modal scheme only;
+    served FP64 requests take the DG-SBP method (test_gpu_serving.py)."""
     from paper_2005_02516_gb300 import esdg
     s = esdg.Solver(2, 8, 8, precision="fp32", method="sbp")
     with pytest.raises(esdg.EsdgError) as ei:
         esdg.Ensemble([s])
     assert ei.value.code == esdg.ESDG_EINVAL
     s.close()
-    p = esdg.Problem(2, 8, 8, precision="fp64", method="sbp")
+    p = esdg.Problem(2, 8, 8, precision="fp32", method="sbp")
     xb, yb = p.points(esdg.ESDG_POINTS_NODAL)
     xq, yq = p.points(esdg.ESDG_POINTS_VOLQ)
     srv = esdg.Server(hbm_budget_bytes=1 << 30)

@@ -427,6 +427,76 @@ def run_volume_ratio(sizes=(16, 32, 50, 100, 150, 200), pairs_gpu=1 << 27, pairs
 PAPER_V100_FP64_S_PER_STEP = {1: 0.0221, 2: 0.0316, 3: 0.0515, 4: 0.0627, 5: 0.1585}
 
 
+GOLDEN_MMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden", "mms_k8192_n3_1000steps.txt")
+
+
+def _golden_mms():
+    """The stored FP64 oracle values of the manufactured-solution run (sampled
+    coefficients of the final state and the oracle's own L2 errors, measured
+    with its degree-2N+2 error rule)."""
+    idx, val, l2 = [], [], None
+    with open(GOLDEN_MMS) as f:
+        for line in f:
+            if line.startswith("#") or line.startswith("norms"):
+                continue
+            parts = line.split()
+            if parts[0] == "l2err":
+                l2 = [float(v) for v in parts[1:4]]
+                continue
+            idx.append(int(parts[0]))
+            val.append(float(parts[1]))
+    return np.array(idx), np.array(val), l2
+
+
+def run_accuracy():
+    """The stated-accuracy leg: the manufactured-solution workload (N = 3,
+    64 x 64 quads -> K = 8192 curved, forcing, 1000 steps) on the FP32 and the
+    FP64 path from the same initial data.  For each: the per-field L2 error
+    against the exact solution at the final time (esdg_l2_error, the volume
+    rule), its throughput, and the relative difference of the sampled final
+    coefficients from the stored FP64 oracle values; plus the FP32-FP64 state
+    difference."""
+    import torch
+    from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
+    w = W.MMS
+    gidx, gval, gl2 = _golden_mms() if os.path.exists(GOLDEN_MMS) else (None, None, None)
+    out = {"workload": w.name, "N": w.N, "K": w.K, "steps": w.steps, "curved": True, "forcing": w.forcing,
+           "l2_rule": "the volume rule of the run (collapsed, exact to degree 2N+1)"}
+    states = {}
+    for prec in ("fp32", "fp64"):
+        s = Solver(w.N, w.nx, w.ny, precision=prec, warp=w.warp, g=w.g, cfl=w.cfl, forcing=w.forcing)
+        xb, yb = s.points(ESDG_POINTS_NODAL)
+        xq, yq = s.points(ESDG_POINTS_VOLQ)
+        s.init_state(w.bathymetry(xb, yb), w.initial(xq, yq))
+        dt = s.dt()
+        torch.cuda.synchronize()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(s.stream)
+        s.step_async(w.steps, dt, 0.0)
+        ev1.record(s.stream)
+        ev1.synchronize()
+        s.check()
+        el = ev0.elapsed_time(ev1) / 1e3
+        T = w.steps * dt
+        err = s.l2_error(w.exact(xq, yq, T))
+        u = s.get_state()
+        states[prec] = u
+        rec = {"l2_error": [float(v) for v in err], "t_final": T,
+               "value": s.K * s.Np * 5 * w.steps / el / 1e9, "unit": UNIT, "seconds": el}
+        if gidx is not None:
+            got = u.ravel()[gidx]
+            rec["rel_diff_vs_oracle_samples"] = float(np.linalg.norm(got - gval) / np.linalg.norm(gval))
+        out[prec] = rec
+        s.close()
+    out["fp32_vs_fp64_state_rel_l2"] = float(np.linalg.norm(states["fp32"] - states["fp64"])
+                                             / np.linalg.norm(states["fp64"]))
+    if gl2 is not None:
+        out["oracle_l2_error_degree_2n2_rule"] = gl2
+        out["oracle_samples"] = "%d coefficients of the final FP64 oracle state (tests/golden)" % len(gidx)
+    return out
+
+
 def run_sbp(steps, warmup, world, peaks):
     """The DG-SBP scheme of Sec. 3 on the same workload (N = 4, K = 131072
     curved; 22 SBP nodes per element): FP32 right-hand side with FP64 RK and
@@ -602,6 +672,8 @@ def main():
                     help="scheme of the timed leg: the paper's modal ESDG (Sec. 2) or the DG-SBP scheme (Sec. 3; "
                          "implies --fp32-only --no-e2e)")
     ap.add_argument("--no-sbp", action="store_true", help="skip the DG-SBP comparison leg")
+    ap.add_argument("--no-accuracy", action="store_true",
+                    help="skip the stated-accuracy leg (manufactured solution, N=3, K=8192, 1000 steps)")
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
@@ -705,6 +777,10 @@ def main():
     if not args.fp32_only and not args.no_sbp and not sbp_main:
         sbp = run_sbp(steps, args.warmup, world, peaks)
 
+    accuracy = None
+    if not args.fp32_only and not args.no_accuracy and rank == 0:
+        accuracy = run_accuracy()
+
     volume_ratio = None
     if not args.fp32_only and not args.no_volume_ratio and rank == 0:
         volume_ratio = run_volume_ratio()
@@ -744,7 +820,7 @@ def main():
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other, "other_mass": other_mass, "sbp": sbp,
-                "fp64": fp64, "precision": precision, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
+                "fp64": fp64, "precision": precision, "accuracy": accuracy, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))
     if world > 1:

@@ -232,6 +232,20 @@ int esdg_check(esdg_ctx* ctx);
 int esdg_entropy(esdg_ctx* ctx, double t, double* entropy, double* mass, double* entropy_rate);
 
 /*
+ * esdg_l2_error -- FP64 L2 error of the current state against values given at
+ * the volume quadrature points (the error measure of the convergence study,
+ * Sec. 4.1, evaluated with the element's own volume rule):
+ *     err[f] = sqrt( sum_k sum_q w_q J_q^k (u_q[f] - exact_volq[f][k][q])^2 ),
+ * f = 0, 1, 2 for (h, hu, hv); u_q = V_q u_h (modal) or the nodal values
+ * (ESDG_METHOD_SBP, whose volume points are its nodes).
+ * exact_volq: device memory [3][K][Nq] FP64 (values at the ESDG_POINTS_VOLQ
+ * points, e.g. an exact solution), owned by the caller; host memory is refused
+ * with ESDG_EINVAL.  err: host array of 3 doubles.  Uses the context's
+ * diagnostic scratch; synchronises the stream.
+ */
+int esdg_l2_error(esdg_ctx* ctx, const double* exact_volq, double* err);
+
+/*
  * esdg_entropy_noalloc -- the entropy and mass of esdg_entropy (no rate), for
  * callers that cannot allocate device memory while they run: code inside a
  * memory-pool or arena regime that forbids new allocations, or a driver loop

@@ -281,6 +281,15 @@ class Oracle:
         dq = np.einsum("qn,ckn->ckq", ref.Vq, dudt)
         return np.sum(ref.w[None, :] * m.Jq * np.sum(vq * dq, axis=0), axis=1)
 
+    def l2_error_volq(self, u_h, exact_volq):
+        """Per-field L2 error against values (3, K, Nq) given at the volume
+        quadrature points, measured with the volume rule itself:
+        sqrt(sum_k sum_q w_q J_q (V_q u_h - exact)^2) (the error measure of
+        Sec. 4.1 on the element's own rule)."""
+        ref, m = self.ref, self.mesh
+        e = np.einsum("qn,ckn->ckq", ref.Vq, u_h) - np.asarray(exact_volq, np.float64)
+        return np.sqrt(np.sum(ref.w[None, None, :] * m.Jq[None] * e * e, axis=(1, 2)))
+
     def l2_error(self, u_h, exact):
         """L2 error against exact(x, y) -> (3, K, npts) with the degree >= 2N+2
         rule (Sec. 4.1); returns per-field errors."""

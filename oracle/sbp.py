@@ -174,6 +174,12 @@ class SBPOracle:
         v = swe.entropy_vars(u, self.bq, self.g)
         return np.sum(self.M * np.sum(v * dudt, axis=0), axis=1)
 
+    def l2_error_volq(self, u, exact_volq):
+        """Per-field L2 error against values (3, K, Nq) given at the SBP nodes,
+        measured with the SBP rule: sqrt(sum_k sum_q w_q J_q (u_q - exact)^2)."""
+        e = u - np.asarray(exact_volq, np.float64)
+        return np.sqrt(np.sum(self.M[None] * e * e, axis=(1, 2)))
+
     def l2_error(self, u, exact):
         """Per-field L2 error of the nodal solution, measured with the SBP
         rule itself (the nodal values are the unknowns; Sec. 3)."""

@@ -976,6 +976,26 @@ int esdg_entropy(esdg_ctx* c, double t, double* entropy, double* mass, double* e
     return ESDG_OK;
 }
 
+int esdg_l2_error(esdg_ctx* c, const double* exact_volq, double* err) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (!exact_volq || !err) return fail(c, ESDG_EINVAL, "exact_volq and err must not be NULL");
+    cudaPointerAttributes attr;
+    CUDA_TRY(c, cudaPointerGetAttributes(&attr, exact_volq));
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+        return fail(c, ESDG_EINVAL, "exact_volq must be device memory");
+    double* out = reinterpret_cast<double*>(c->dbuf + c->L.diag);
+    CUDA_TRY(c, launch_l2_error(c->mesh.K, c->ref.Nq, c->ndof, reinterpret_cast<const double*>(c->dbuf + c->L.u),
+                                c->sbp ? nullptr : reinterpret_cast<const double*>(c->dbuf + c->L.vq64),
+                                reinterpret_cast<const double*>(c->dbuf + c->L.wJq64), exact_volq,
+                                reinterpret_cast<double*>(c->dbuf + c->L.partial), c->entropy_parts, out, c->stream));
+    double h[3];
+    CUDA_TRY(c, cudaMemcpyAsync(h, out, 24, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int f = 0; f < 3; ++f) err[f] = std::sqrt(h[f]);
+    return ESDG_OK;
+}
+
 // ---- no-allocation variant of the entropy diagnostic --------------------------
 // Scratch for the per-block partial sums (3 per block) and the 3 totals.
 static __device__ __align__(256) double g_noalloc_scratch[ESDG_NOALLOC_MAX_PARTS * 3 + 4];

@@ -49,5 +49,9 @@ cudaError_t launch_sbp2(const StageParams<float>& p, const float* ops2, int Kpad
 int sbp2_ops_floats(int N);
 cudaError_t launch_entropy_nodal(int K, int Nq, double g, const double* u, const double* rhs, const double* wJq,
                                  const double* bq, double* partial, int nparts, double* out, cudaStream_t s);
+// FP64 L2 error against given values at the volume points (esdg_diag.cu):
+// Vq [Nq][Np] for a modal state, NULL for a nodal one (Np = Nq).
+cudaError_t launch_l2_error(int K, int Nq, int Np, const double* u, const double* Vq, const double* wJq,
+                            const double* exact, double* partial, int nparts, double* out, cudaStream_t s);
 
 }  // namespace esdg

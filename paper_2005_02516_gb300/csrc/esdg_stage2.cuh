@@ -12,7 +12,7 @@
 //    is read from shared memory once for RPL rows (the flux differencing is
 //    FP32-ALU bound, and this keeps shared-memory traffic well below it).
 //    Eight lanes per element (rather than four) halve the registers and the
-//    shared memory per warp, which lets 16 warps share an SM.
+//    shared memory per warp, which lets 24 warps share an SM.
 //    Interleaving rows across the LPE lanes balances volume rows (all Nh
 //    columns) against face rows (Nq columns: the lower-right block of
 //    Q_skew is zero).
@@ -91,12 +91,22 @@ struct C2 {
     static_assert(3 * D::Np <= D::Nfq * 4, "u scratch");
     static constexpr int TRL = (EPW * D::Nfq + 31) / 32;    // neighbour traces gathered per lane
     static constexpr int RKL = (3 * EPW * D::Np + 31) / 32; // RK values per lane (all 32 lanes)
+    // RK operands loaded before the lift, else just before the update: late
+    // only for the 31 hybrid nodes of N = 4 with the 16-point rule and the
+    // stored inverse, where the early loads push the kernel past 80
+    // registers (measured per configuration; elsewhere early is faster)
+    static constexpr bool EARLY_RK = !(D::Nh == 31 && D::Nq == 16 && !WADG);
     // warps per CTA (one CTA per SM): as many as fit in 227 KB of shared
-    // memory next to the operators, at most 16 (the register budget at 128
-    // registers per thread)
+    // memory next to the operators, at most 24 (80 registers per thread) for
+    // volume rules of up to 16 points and 16 (128 registers) above, where the
+    // row and node data no longer fit 80 registers without spilling.  More
+    // resident warps hide more of the latency this issue-bound kernel waits on:
+    // 24 warps at 80 registers ran 5% (N = 4) to 11% (N = 3) faster than 16 at
+    // 128; 28 at 72 registers spilled and ran slower.
     static constexpr int SMEM_MAX = 232448;
     static constexpr int WARPS_FIT = (SMEM_MAX - 4 * o_end) / (4 * w_end + 8);
-    static constexpr int WARPS = WARPS_FIT < 16 ? WARPS_FIT : 16;
+    static constexpr int WARPS_CAP = D::Nq <= 16 ? 24 : 16;
+    static constexpr int WARPS = WARPS_FIT < WARPS_CAP ? WARPS_FIT : WARPS_CAP;
     static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
     static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + (WADG ? 0 : NpP4 * 4));
 };
@@ -576,13 +586,15 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             rt[(2 * D::Nh + l) * EPW + e] = a2[i];
         }
     }
-    // Operands of the later phases, loaded now so their latency overlaps the
-    // lift and the inverse mass: the FP64 RK state of the batch spread over
-    // all 32 lanes (j = lane + 32 k in [field][element][mode] order, which is
-    // contiguous per field in global memory), and b, w J at this lane's nodes.
+    // The FP64 RK state of the batch spread over all 32 lanes (j = lane + 32 k
+    // in [field][element][mode] order, which is contiguous per field in global
+    // memory).  Loaded here, so that the latency overlaps the lift and the
+    // inverse mass, where the registers allow it (C::EARLY_RK); otherwise just
+    // before the update (1.2% faster at N = 4 with the stored inverse; 2%
+    // slower where the early loads fit).
     constexpr int NRK = 3 * EPW * D::Np;
     double uj[C::RKL], rj[C::RKL];
-    if (MODE == 1) {
+    auto load_rk = [&]() {
 #pragma unroll
         for (int k = 0; k < C::RKL; ++k) {
             const int j = lane + 32 * k;
@@ -597,7 +609,8 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                 }
             }
         }
-    }
+    };
+    if (MODE == 1 && C::EARLY_RK) load_rk();
     // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
     float* ts = ws + C::s_t;
     if (p.forcing) {
@@ -792,6 +805,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     } else {
         // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
+        if (!C::EARLY_RK) load_rk();
         const float dtf = (float)p.dt;
         double* const u_out = p.u_out;  // host-state calls: the last stage also writes the state there
 #pragma unroll

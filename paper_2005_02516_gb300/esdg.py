@@ -54,7 +54,8 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
            "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
-           "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host", "esdg_selftest_wait_timeout"]
+           "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host", "esdg_selftest_wait_timeout",
+           "esdg_l2_error"]
 
 
 class EsdgError(RuntimeError):
@@ -127,6 +128,7 @@ def load_library(path=LIB_PATH):
         "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
         "esdg_step_host": ([P, P, I, D, PD, P], I),
         "esdg_selftest_wait_timeout": ([P], I),
+        "esdg_l2_error": ([P, P, PD], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -410,6 +412,18 @@ class Solver:
         self._check(self.lib.esdg_entropy(self.h, t, ctypes.byref(S), ctypes.byref(M),
                                           ctypes.byref(R) if rate else None))
         return (S.value, M.value, R.value if rate else None)
+
+    def l2_error(self, exact):
+        """esdg_l2_error: per-field L2 error of the state against exact values
+        (3, K, Nq) at the ESDG_POINTS_VOLQ points (numpy array or CUDA
+        tensor; a numpy array is copied to the device first)."""
+        import torch
+        ex = torch.as_tensor(np.ascontiguousarray(exact, dtype=np.float64) if isinstance(exact, np.ndarray)
+                             else exact, device="cuda", dtype=torch.float64).contiguous()
+        assert tuple(ex.shape) == (3, self.K, self.Nq)
+        err = (ctypes.c_double * 3)()
+        self._check(self.lib.esdg_l2_error(self.h, _ptr(ex), err))
+        return np.array(err[:])
 
     def dt(self):
         d = ctypes.c_double()

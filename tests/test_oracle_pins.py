@@ -409,6 +409,40 @@ def _mms_error(N, nx, T=0.1, rule="collapsed"):
 
 
 @pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [2, 4])
+def test_l2_error_volq_closed_form_on_curved_mesh(N, rule):
+    """With u_h = 0 against the constant 1 the error is the square root of the
+    domain's area (4 for [-1,1]^2): the periodic curving keeps the area, and
+    the volume rule integrates the degree-2N-2 Jacobian exactly.  Each field
+    is measured on its own (distinct constants per field)."""
+    o = Oracle(N, 5, 4, ax=0.05, ay=0.05, rule=rule)
+    ex = np.stack([np.full((o.K, o.Nq), c) for c in (1.0, 2.0, 3.0)])
+    err = o.l2_error_volq(np.zeros((3, o.K, o.Np)), ex)
+    assert np.allclose(err, 2.0 * np.array([1.0, 2.0, 3.0]), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [1, 3])
+def test_l2_error_volq_equals_error_rule_for_polynomials(N, rule):
+    """On affine elements (u_h - p)^2 with p a polynomial of degree N in x, y is
+    of degree 2N in r, s, which the volume rule and the degree-2N+2 error rule
+    both integrate exactly: the two measures agree to roundoff (a transposed
+    index, a dropped weight or Jacobian in either would not)."""
+    o = Oracle(N, 4, 3, rule=rule)
+    rng = np.random.default_rng(5 + N)
+    u = rng.standard_normal((3, o.K, o.Np))
+    coef = rng.standard_normal((3, N + 1, N + 1))
+
+    def p(x, y):
+        return np.stack([sum(coef[c, i, j] * x ** i * y ** j for i in range(N + 1) for j in range(N + 1 - i))
+                         for c in range(3)])
+    xq, yq = o.points("volq")
+    a = o.l2_error_volq(u, p(xq, yq))
+    b = o.l2_error(u, p)
+    assert np.allclose(a, b, rtol=1e-11, atol=0)
+
+
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
 @pytest.mark.parametrize("N", [1, 2])
 def test_mms_convergence_order(N, rule):
     """O(h^{N+1}) L2 convergence on a smooth solution (Sec. 4.2 reports the

@@ -153,6 +153,17 @@ def _consistency(o, t=0.3):
     return np.sqrt(np.sum(o.M[None] * (r - _mms_dt_exact(x, y, t)) ** 2))
 
 
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_sbp_l2_error_volq_closed_form_on_curved_mesh(N):
+    """u = 0 against per-field constants c: the error is c times the square
+    root of the area of [-1,1]^2 (the SBP rule, exact to 2N-1, integrates the
+    degree-2N-2 Jacobian exactly, and the periodic curving keeps the area)."""
+    o = SBPOracle(N, 5, 4, ax=0.05, ay=0.05)
+    ex = np.stack([np.full((o.K, o.Nq), c) for c in (1.0, 2.0, 3.0)])
+    err = o.l2_error_volq(np.zeros((3, o.K, o.Nq)), ex)
+    assert np.allclose(err, 2.0 * np.array([1.0, 2.0, 3.0]), rtol=1e-12, atol=0)
+
+
 @pytest.mark.parametrize("N", [1, 2, 3])
 def test_sbp_manufactured_solution_converges(N):
     """Manufactured solution with forcing on curved meshes: the L2 error at

@@ -39,11 +39,11 @@ WL = W.DAM
 # profiles/k_stage2_wadg_dam_k131072_n4.md), valid only
 # for the kernel source it was measured on: reported as null once that source
 # changes.
-STAGE_TRAFFIC = {"exact": {"source_sha1": "de21e34b8994e7ed94b16efe9e0a78dbfe0cfb2e", "bytes": 429.4e6},
-                 "weight_adjusted": {"source_sha1": "f02127742633926d43cbacca013f9cc9b778da04", "bytes": 362.5e6}}
+STAGE_TRAFFIC = {"exact": {"source_sha1": "02937e623df1397b93ce874147324c31a08062e2", "bytes": 429.5e6},
+                 "weight_adjusted": {"source_sha1": "02937e623df1397b93ce874147324c31a08062e2", "bytes": 360.6e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 # the same for the FP32 DG-SBP stage kernel (profiles/k_sbp2_dam_k131072_n4.md)
-SBP_TRAFFIC = {"source_sha1": "0b400bdde10d7fc018db768dff8e4e6659499b40", "bytes": 386.9e6}
+SBP_TRAFFIC = {"source_sha1": "c2b2fd772d39446dc4fa29bb99ad693c9da79486", "bytes": 385.9e6}
 SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")
 
 # Algorithmic work of one element-stage at degree N: FLOPs (an FMA counts 2) of

@@ -45,9 +45,11 @@ struct S2 {
     static constexpr int TRL = (EPW * D::Nfq + 31) / 32;
     static constexpr int SMEM_MAX = 232448;
     static constexpr int WARPS_FIT = (SMEM_MAX - 4 * o_end) / (4 * w_end + 8);
-    // at most 20 warps (96 registers a thread): 4-8% faster than 16 at 128
-    // registers; 24 at 80 registers spill the row data and run slower
-    static constexpr int WARPS = WARPS_FIT < 20 ? WARPS_FIT : 20;
+    // at most 24 warps (80 registers a thread) up to 22 nodes (N <= 4), 20 (96
+    // registers) above, where 80 registers spill: 24 warps ran 6-11% faster
+    // than 16 at 128 registers
+    static constexpr int WARPS_CAP = D::Nq <= 22 ? 24 : 20;
+    static constexpr int WARPS = WARPS_FIT < WARPS_CAP ? WARPS_FIT : WARPS_CAP;
     static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
     static constexpr int TX_BYTES = EPW * 2 * D::Nq * 16;
 };
@@ -90,8 +92,10 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
         }
     }
     // own operands of the later phases, loaded before the wait (the FP64 RK
-    // operands only while they fit the register budget: up to 3 rows a lane)
-    constexpr bool EARLY = RPL <= 3;
+    // operands only while they fit the register budget of 24 warps: up to 2
+    // rows a lane; loaded late, N = 3, 4 run 24 warps at 78 registers, 3-4%
+    // faster than 20 warps with early loads)
+    constexpr bool EARLY = RPL <= 2;
     float wj[RPL], bl[RPL];
     double uo[RPL][3], ro[RPL][3];
     auto load_rk = [&](int i) {
@@ -121,6 +125,10 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
     // ---- flux differencing over all columns, rows l = b + LPE*i ------------------
     const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
     const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
+    // the free surface relative to the element's first node in the pressure
+    // and bathymetry terms: exact by Q_SBP 1 = 0 (Theorem 3.1), and the FP32
+    // sums no longer cancel large equal terms (as in k_stage2)
+    const float Href = utE[0].w;
     float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
     float a0[RPL], a1[RPL], a2[RPL];
 #pragma unroll
@@ -155,7 +163,7 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
 #pragma unroll 2
     for (int m = 0; m < D::Nq; ++m) {
         const float4 U = utE[m], G = geE[m];
-        const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
+        const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * (U.w - Href);
         const float4* q4 = reinterpret_cast<const float4*>(QsB + m * LPE * C::OPB);
 #pragma unroll
         for (int i2 = 0; i2 < (RPL + 1) / 2; ++i2) {
@@ -177,7 +185,7 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
         const int f = frow[l];
         if (f >= 0) {
             const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
-            const float h_l = rh[i], b_l = bl[i];
+            const float h_l = rh[i];
             const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
             const float nxJ = rrx[i] * nr + rsx[i] * ns;
             const float nyJ = rry[i] * nr + rsy[i] * ns;
@@ -187,7 +195,7 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
             const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
             const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);
             const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
-            const float pw = 0.5f * g * h_l * (hP + b_l);
+            const float pw = 0.5f * g * h_l * ((hP - h_l) + (utE[l].w - Href));  // (h+ + b_l) - Href
             const float Fn0 = nxJ * huA + nyJ * hvA;
             a0[i] += w * Fn0;
             a1[i] += w * (uA * Fn0 + nxJ * pw);

@@ -399,8 +399,12 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
             }
         }
     }
-    // u~ = u(v~)
+    // u~ = u(v~), stored as (h, u, v, H - H_0): the free surface relative to
+    // the element's first hybrid node, which only the element's own next stage
+    // reads (the pressure terms of stage2_batch; neighbours read h, u, v)
     {
+        const float H_j0 = (v0[0] + 0.5f * (v1[0] * v1[0] + v2[0] * v2[0])) * ig;  // row l = b
+        const float H0 = __shfl_sync(0xffffffffu, H_j0, lane & ~(LPE - 1));      // row 0 of the element
         if (valid) {
 #pragma unroll
             for (int j = 0; j < RPL; ++j) {
@@ -411,7 +415,7 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
                     if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
                     if (!isfinite(H) || !isfinite(v1[j]) || !isfinite(v2[j])) bad |= STATUS_NONFINITE;
                     *reinterpret_cast<float4*>(ut_out + ((size_t)ge * D::Nh + l) * 4) =
-                        make_float4(h, v1[j], v2[j], H);
+                        make_float4(h, v1[j], v2[j], H - H0);
                 }
             }
         }
@@ -463,6 +467,14 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     // ---- volume flux differencing, rows l = b + LPE*i ------------------------
     const float4* utE = reinterpret_cast<const float4*>(ws + C::w_ut + e * C::UTS);
     const float4* geE = reinterpret_cast<const float4*>(ws + C::w_geo + e * C::UTS);
+    // Pressure and bathymetry enter as g h_l H_m (volume) and g h_l (h+ + b_l)
+    // (interface).  Each row's operator satisfies sum_m Qskew[l,m] + B[l] = 0
+    // (Q_h 1 = 0, the identity behind the lake-at-rest property of Theorem
+    // 2.2), so a constant subtracted from every free surface H in both terms
+    // leaves the exact right-hand side unchanged.  The records carry H - H_0,
+    // H_0 the element's free surface at its first hybrid node (written by
+    // stage2_project): the FP32 sums then no longer cancel large equal terms,
+    // and the momentum error of the FP32 path falls about threefold.
     float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
     float a0[RPL], a1[RPL], a2[RPL];
 #pragma unroll
@@ -539,7 +551,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             const int f = l - D::Nq;
             const float4 U = utE[l];
             const float4 tp = *reinterpret_cast<const float4*>(ws + C::w_tr + (e * D::Nfq + f) * 4);
-            const float h_l = U.x, b_l = U.w - U.x;
+            const float h_l = U.x;
             const float nr = ops[C::o_nrs + 2 * f], ns = ops[C::o_nrs + 2 * f + 1];
             const float nxJ = 8.f * (rrx[i] * nr + rsx[i] * ns);
             const float nyJ = 8.f * (rry[i] * nr + rsy[i] * ns);
@@ -558,7 +570,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             const float hu_l = h_l * ru[i], hv_l = h_l * rv[i];
             const float huA = 0.5f * (hu_l + huP), hvA = 0.5f * (hv_l + hvP);
             const float uA = 0.5f * (ru[i] + uP), vA = 0.5f * (rv[i] + vP);
-            const float pw = 0.5f * g * h_l * (hP + b_l);
+            const float pw = 0.5f * g * h_l * ((hP - h_l) + U.w);  // (h+ + b_l) - H_0
             const float Fn0 = nxJ * huA + nyJ * hvA;
             a0[i] += w * Fn0;
             a1[i] += w * (uA * Fn0 + nxJ * pw);

@@ -86,7 +86,8 @@ struct StageParams {
     double* rhs_out;     // [3][K][Np]  RHS mode output
     double* u_out;       // [3][K][Np]  if set: the stage's new state also written here (host-state calls)
     int copy_in;         // projection of u_in: also store u_in into u and zero res
-    const real* ut_in;   // [K][Nh][4]  entropy-projected (h, u, v, H) of this stage
+    const real* ut_in;   // [K][Nh][4]  entropy-projected (h, u, v, H) of this stage (the FP32 batched
+                         //             kernel k_stage2 stores H - H_0, H_0 the element's H at node 0)
     real* ut_out;        // [K][Nh][4]  ... of the next stage
     double rkA, rkB, dt, t;
     int forcing;

@@ -195,6 +195,26 @@ def test_physical_sbp_property_on_curved_elements(N):
         assert np.abs(Qx + Qx.T - np.diag(B)).max() < 1e-13
 
 
+@pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
+@pytest.mark.parametrize("N", [2, 4])
+def test_physical_operator_annihilates_constants_on_curved_elements(N, rule):
+    """Q_h^{i,k} 1 = 0 on every curved element (the discrete metric identity
+    behind free-stream preservation and the lake at rest, Sec. 2.7, Theorem
+    2.2).  With the SBP property this is Qskew^{i,k} 1 + B^{i,k} 1 = 0 per row,
+    which lets the FP32 kernels subtract any constant from the free surface in
+    both pressure terms of a row without changing the exact result."""
+    o = Oracle(N, 4, 3, ax=0.05, ay=0.05, rule=rule)
+    m, ref = o.mesh, o.ref
+    worst = 0.0
+    for k in range(o.K):
+        for Gr, Gs, nJ in ((m.rxJ[k], m.sxJ[k], m.nxJ[k]), (m.ryJ[k], m.syJ[k], m.nyJ[k])):
+            Q = 0.5 * (ref.Qhr * (Gr[:, None] + Gr[None, :]) + ref.Qhs * (Gs[:, None] + Gs[None, :]))
+            B = np.zeros(o.Nh)
+            B[o.Nq:] = ref.wf * nJ
+            worst = max(worst, np.abs(Q.sum(axis=1)).max(), np.abs((Q - Q.T).sum(axis=1) + B).max())
+    assert worst < 1e-12, worst
+
+
 # ---------------------------------------------------------------------------
 # Fluxes (Def. 2.1, eqs. (SWE_flux1/2))
 # ---------------------------------------------------------------------------

@@ -201,11 +201,12 @@ __device__ __forceinline__ bool sbp2_batch(const StageParams<float>& p, const fl
             a1[i] += w * (uA * Fn0 + nxJ * pw);
             a2[i] += w * (vA * Fn0 + nyJ * pw);
             if (p.lf) {
-                const float sJ = sqrtf(nxJ * nxJ + nyJ * nyJ);
-                const float inx = nxJ / sJ, iny = nyJ / sJ;
-                const float lm = fabsf(ru[i] * inx + rv[i] * iny) + sqrtf(g * h_l);
-                const float lp = fabsf(uP * inx + vP * iny) + sqrtf(g * hP);
-                const float c = 0.5f * w * sJ * fmaxf(lm, lp);
+                // sJ max(|u.n| + sqrt(g h)) over both sides, with the unit normal
+                // n = nJ / sJ folded in: |u.nJ| + sqrt(sJ^2 g h) (no divisions)
+                const float sJ2 = nxJ * nxJ + nyJ * nyJ;
+                const float lm = fabsf(ru[i] * nxJ + rv[i] * nyJ) + sqrtf(sJ2 * g * h_l);
+                const float lp = fabsf(uP * nxJ + vP * nyJ) + sqrtf(sJ2 * g * hP);
+                const float c = 0.5f * w * fmaxf(lm, lp);
                 a0[i] -= c * (hP - h_l);
                 a1[i] -= c * (huP - hu_l);
                 a2[i] -= c * (hvP - hv_l);

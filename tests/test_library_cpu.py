@@ -82,6 +82,9 @@ def test_calls_out_of_order_are_refused():
     u = np.zeros((3, 32, 6))
     assert lib.esdg_set_state(h, u.ctypes.data, 0) == esdg.ESDG_ESTATE
     assert lib.esdg_step(h, 1, 0.01, None) == esdg.ESDG_ESTATE
+    err = (ctypes.c_double * 3)()
+    assert lib.esdg_l2_error(h, u.ctypes.data, err) == esdg.ESDG_ESTATE
+    assert lib.esdg_l2_error(None, u.ctypes.data, err) == esdg.ESDG_EINVAL
     lib.esdg_destroy(h)
 
 

@@ -46,3 +46,15 @@ def test_two_replica_ranks_agree_on_max_time():
     for _, t, v in res:
         assert t == 2.0              # the slowest rank's time
         assert abs(v - 1.0) < 1e-12  # 2 ranks x 1e9 units / 2 s / 1e9
+
+
+def test_accuracy_leg_reads_the_stored_oracle_values():
+    """The bench's stated-accuracy leg compares the sampled final coefficients
+    with the stored FP64 oracle run (tests/golden): the reader finds the 4000
+    samples, distinct indices, and the oracle's three L2 errors."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    idx, val, l2 = bench._golden_mms()
+    assert len(idx) == len(val) == 4000 and len(set(idx.tolist())) == 4000
+    assert l2 is not None and len(l2) == 3 and all(0 < e < 1e-6 for e in l2)

@@ -34,15 +34,14 @@ from paper_2005_02516_gb300 import workloads as W  # noqa: E402
 METRIC = "GDOF-stage/s FP32 vs FP64 per GB300 at stated L2 error; served p50/p99 latency"
 UNIT = "GDOF-stage/s"
 WL = W.DAM
-# DRAM traffic of one stage launch at this workload, per inverse-mass kind,
-# from one ncu capture each (profiles/k_stage2_dam_k131072_n4.md and
-# profiles/k_stage2_wadg_dam_k131072_n4.md), valid only
-# for the kernel source it was measured on: reported as null once that source
-# changes.
+# DRAM traffic of one stage launch at this workload (dram__bytes_read.sum +
+# dram__bytes_write.sum from one ncu capture), per inverse-mass kind, keyed to
+# the sha1 of the kernel source it was measured on: reported as null once that
+# source changes.
 STAGE_TRAFFIC = {"exact": {"source_sha1": "f1833899496250b5f77923439029c4e482204ccd", "bytes": 429.3e6},
                  "weight_adjusted": {"source_sha1": "02937e623df1397b93ce874147324c31a08062e2", "bytes": 360.6e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
-# the same for the FP32 DG-SBP stage kernel (profiles/k_sbp2_dam_k131072_n4.md)
+# the same for the FP32 DG-SBP stage kernel
 SBP_TRAFFIC = {"source_sha1": "bc6a6adb39a7b0f39182f3aa3b747208c033571a", "bytes": 386.1e6}
 SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")
 
@@ -75,6 +74,32 @@ def algorithmic_flops(N, Nq, wadg=False):
 
 
 def algorithmic_bytes(N, Nq, real_bytes=4, wadg=False):
+    """Bytes one element-stage of the method must move, whatever the kernel's
+    design: the FP64 state and RK residual, the geometry and operators that
+    vary per element, and one exchange of face traces between neighbours."""
+    Np = (N + 1) * (N + 2) // 2
+    Nfq = 3 * (N + 1)
+    Nh = Nq + Nfq
+    NpP = Np * (Np + 1) // 2
+    b = 0
+    b += 4 * 3 * Np * 8                 # u read + write, res read + write (FP64)
+    b += Nh * 4 * real_bytes            # metrics rxJ sxJ ryJ syJ at the hybrid nodes
+    b += Nq * real_bytes                # J at the volume nodes (as w_q J_q)
+    b += 0 if wadg else NpP * real_bytes    # packed inverse mass matrix (none when weight-adjusted)
+    b += Nfq * 3 * real_bytes           # face normals nxJ, nyJ and sJ
+    b += Nh * real_bytes                # bathymetry at the hybrid nodes
+    b += 2 * Nfq * 3 * real_bytes       # face traces (h, u, v): own write + neighbour read
+    b += Nfq * 4                        # connectivity: the exterior node of each face node (int32)
+    return b
+
+
+def design_bytes(N, Nq, real_bytes=4, wadg=False):
+    """Bytes the fused stage kernel itself plans to move per element-stage:
+    besides the state, residual and per-element data, it re-reads its own
+    entropy-projected record (h, u, v, H at every hybrid node) written by the
+    previous stage and writes the next one, reads neighbour traces from those
+    records, derives face normals from the metrics and stores one neighbour id
+    per face."""
     Np = (N + 1) * (N + 2) // 2
     Nfq = 3 * (N + 1)
     Nh = Nq + Nfq
@@ -729,7 +754,9 @@ def main():
     roof_alu = {"bound": "alu", "achieved": alu, "peak": fp32_peak, "unit": "TFLOP/s", "frac": alu / fp32_peak,
                 "traffic": traffic, "peak_source": "152 SMs x 128 FP32 lanes x 2 x %.0f MHz" % sm_mhz}
     roof_hbm = {"bound": "hbm", "achieved": hbm, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": hbm / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind}
+                "frac": hbm / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peak_kind,
+                "algorithmic_bytes_per_element_stage": nbytes / K,
+                "design_bytes_per_element_stage": (by_s if sbp_main else design_bytes(WL.N, WL.Nq, 4, wadg))}
     roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
     other = roof_hbm if roofline is roof_alu else roof_alu
 

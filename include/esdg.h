@@ -42,7 +42,11 @@ extern "C" {
 #define ESDG_ESTATE       -6  /* call out of order (e.g. no device memory attached) */
 #define ESDG_ETIMEOUT     -7  /* a bounded device-side wait (on an asynchronous copy) expired;
                                  the kernel stopped early and the state is not valid;
-                                 or a host-side wait (esdg_server_drain) ran out */
+                                 copies into shared memory that the wait gave up on may
+                                 still have been in flight when the block exited, so
+                                 destroy the context (and, to be safe, the CUDA context)
+                                 rather than reuse it; or a host-side wait
+                                 (esdg_server_drain) ran out */
 #define ESDG_EBUSY        -8  /* admission refused: the request's device footprint exceeds
                                  the server's whole HBM budget */
 
@@ -252,17 +256,22 @@ int esdg_l2_error(esdg_ctx* ctx, const double* exact_volq, double* err);
  * that must not call cudaMalloc/cudaFree between launches.  The paper has no
  * counterpart; this is a library convenience.
  *
- * u_dev: device state [3][K][Np] FP64, or NULL for the context's state.
+ * u_dev: device state [3][K][Np] FP64, or NULL for the context's state; a
+ * pointer that is not device (or managed) memory is refused with ESDG_EINVAL
+ * before any launch.
  * entropy, mass: host outputs (either may be NULL).
  * Scratch: the per-block partial sums live in one file-scope device array of
  * ESDG_NOALLOC_MAX_PARTS * 3 + 4 doubles (about 96 KB), held by every GPU that
  * loads the library until the process exits.  One partial covers
  * ESDG_NOALLOC_POINTS_PER_PART volume quadrature points, so K * Nq must not
  * exceed ESDG_NOALLOC_MAX_PARTS * ESDG_NOALLOC_POINTS_PER_PART (ESDG_EINVAL
- * otherwise).  The call allocates nothing: no cudaMalloc, no cudaFree.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Every call overwrites the whole scratch it reads, but all calls
+ * otherwise, checked on the host before the context's state and before any
+ * CUDA call).  The call allocates nothing: no cudaMalloc, no cudaFree.
+ * Every call looks up the array's device address with the caller's device
+ * current (cudaGetSymbolAddress, which allocates nothing), so the address
+ * stays valid across a device reset; the first call on a device may load the
+ * library's device code, so make it before any stream capture.  Every call
+ * overwrites the whole scratch it reads, but all calls
  * share the one array: calls that overlap on the GPU (other streams, other
  * threads) race and must be serialised by the caller.  Synchronises the
  * context's stream.

@@ -8,7 +8,6 @@
 #include <cstdio>
 #include <algorithm>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -1000,36 +999,45 @@ int esdg_l2_error(esdg_ctx* c, const double* exact_volq, double* err) {
 // Scratch for the per-block partial sums (3 per block) and the 3 totals.
 static __device__ __align__(256) double g_noalloc_scratch[ESDG_NOALLOC_MAX_PARTS * 3 + 4];
 
-// The array's device address, looked up once per device (host code cannot use
-// the symbol itself: on the host it only names a stand-in).
-static std::mutex g_noalloc_mu;
-static double* g_noalloc_addr[128];
-
+// The array's device address for the current device.  Host code cannot use the
+// symbol itself (on the host it only names a stand-in), so every call looks the
+// address up with the caller's device current: no cached pointer can outlive a
+// device reset or a re-created primary context.  The lookup allocates nothing.
 static int noalloc_scratch(esdg_ctx* c, double** out) {
-    int dev = 0;
-    CUDA_TRY(c, cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 128) return fail(c, ESDG_EINVAL, "device ordinal out of range for the static scratch table");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        CUDA_TRY(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_noalloc_addr[dev];
+    void* p = nullptr;
+    CUDA_TRY(c, cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    *out = static_cast<double*>(p);
     return ESDG_OK;
+}
+
+// Whether K * Nq volume points fit the static scratch (host arithmetic only).
+static bool noalloc_fits(long long points, long long* parts) {
+    *parts = (points + ESDG_NOALLOC_POINTS_PER_PART - 1) / ESDG_NOALLOC_POINTS_PER_PART;
+    return *parts <= ESDG_NOALLOC_MAX_PARTS;
 }
 
 int esdg_entropy_noalloc(const esdg_ctx* cc, const double* u_dev, double* entropy, double* mass) {
     esdg_ctx* c = const_cast<esdg_ctx*>(cc);
     if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
-    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    // the size limit is checked first, on the host, before any CUDA call
     const long long points = (long long)c->mesh.K * c->ref.Nq;
-    const long long parts = (points + ESDG_NOALLOC_POINTS_PER_PART - 1) / ESDG_NOALLOC_POINTS_PER_PART;
-    if (parts > ESDG_NOALLOC_MAX_PARTS)
+    long long parts = 0;
+    if (!noalloc_fits(points, &parts))
         return fail(c, ESDG_EINVAL,
                     "esdg_entropy_noalloc: K * Nq = " + std::to_string(points) + " exceeds the static scratch limit of " +
                         std::to_string((long long)ESDG_NOALLOC_MAX_PARTS * ESDG_NOALLOC_POINTS_PER_PART) +
                         " quadrature points; use esdg_entropy");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (u_dev) {
+        // a host or stale pointer would fault inside the kernel: refuse it here
+        cudaPointerAttributes attr;
+        if (cudaPointerGetAttributes(&attr, u_dev) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, ESDG_EINVAL, "esdg_entropy_noalloc: u_dev is not a CUDA pointer");
+        }
+        if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+            return fail(c, ESDG_EINVAL, "esdg_entropy_noalloc: u_dev must be device memory");
+    }
     double* scratch = nullptr;
     int rc = noalloc_scratch(c, &scratch);
     if (rc) return rc;

@@ -278,3 +278,23 @@ def test_fp64_sbp_kernel_pair_pieces(Nq):
     for l in range(Nq):
         k0, k1 = (l * Nq) // PL, ((l + 1) * Nq - 1) // PL
         assert set(filed[l]) <= set(range(k0, k1 + 1)) and 0 <= k0 <= k1 < 32
+
+
+@pytest.mark.parametrize("nx, ny, expect", [(512, 512, "at"), (512, 513, "over")])
+def test_noalloc_size_limit_is_checked_on_the_host(nx, ny, expect):
+    # N = 3 with the collapsed rule has Nq = 16 volume points: 512 x 512 quads
+    # give K Nq = 2^23, exactly the static scratch's capacity; one more row of
+    # quads is over it.  The limit is checked before the attach check and
+    # before any CUDA call, so an unattached context shows which side it is on.
+    lib, rc, h = _build(N=3, nx=nx, ny=ny, rule=esdg.ESDG_RULE_COLLAPSED)
+    assert rc == 0
+    try:
+        S, M = ctypes.c_double(), ctypes.c_double()
+        r = lib.esdg_entropy_noalloc(h, None, ctypes.byref(S), ctypes.byref(M))
+        if expect == "at":
+            assert r == esdg.ESDG_ESTATE, lib.esdg_last_error(h)
+        else:
+            assert r == esdg.ESDG_EINVAL
+            assert b"exceeds the static scratch limit" in lib.esdg_last_error(h)
+    finally:
+        lib.esdg_destroy(h)

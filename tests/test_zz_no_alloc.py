@@ -62,3 +62,21 @@ def test_noalloc_entropy_matches_entropy_twice(precision):
     assert abs(M0 - M_ref) <= 1e-12 * abs(M_ref)
     assert np.isfinite([S1, M1]).all()
     s.close()
+
+
+def test_noalloc_refuses_host_memory():
+    # a host array handed in as the state would be read by the kernel as a
+    # device address; the entry point refuses it before any launch
+    s = _solver("fp64")
+    S_ref, M_ref, _ = s.entropy(0.0, rate=False)
+    host = np.ascontiguousarray(s.get_state())
+    S, M = ctypes.c_double(-1.0), ctypes.c_double(-1.0)
+    rc = s.lib.esdg_entropy_noalloc(s.h, host.ctypes.data_as(ctypes.c_void_p), ctypes.byref(S), ctypes.byref(M))
+    from paper_2005_02516_gb300 import esdg
+    assert rc == esdg.ESDG_EINVAL
+    assert b"device memory" in s.lib.esdg_last_error(s.h)
+    assert S.value == -1.0 and M.value == -1.0
+    # the context is still usable afterwards
+    S2, M2 = _noalloc(s)
+    assert abs(S2 - S_ref) <= 1e-12 * abs(S_ref)
+    s.close()

@@ -243,6 +243,86 @@ class Oracle:
         src[2] = -self.g * u[0] * np.einsum("klm,km->kl", Qy, bh)
         return src
 
+    # -- term magnitudes (for floating-point error bounds in the tests) ---------------
+    def rhs_term_magnitude(self, u_h, t=0.0, elems=None):
+        """Per entry of du_h/dt (3, K, Np), or of the listed elements only: the
+        sum of the absolute values of every term that eq. (dgform) adds up for
+        it, i.e. the right-hand side evaluated with each operator entry, flux
+        product, source and penalty term replaced by its absolute value (the
+        pressure g{h}^2 - 1/2 g{h^2} by its value 1/2 g h_l h_m, a jump by the
+        sum of the two sides).  A floating-point evaluation of the same sums
+        with unit roundoff eps has an error of at most a modest multiple of
+        eps times this quantity, which is what the tests scale their
+        element-wise bounds with.  Not part of the scheme."""
+        ks = np.arange(self.K) if elems is None else np.asarray(elems, dtype=np.int64)
+        if elems is None:
+            ut, _ = self.entropy_projection(u_h)
+        else:
+            nbr = self.mesh.EToE[ks].ravel()
+            need = np.unique(np.concatenate([ks, nbr]))
+            ut = np.full((3, self.K, self.Nh), np.nan)
+            ut[:, need] = self._entropy_projection_subset(u_h, need)
+        ref, m, g = self.ref, self.mesh, self.g
+        Nq, Nfq = self.Nq, self.Nfq
+        u = ut[:, ks]
+        def phys(Gr, Gs):
+            return 0.5 * (ref.Qhr[None] * (Gr[:, :, None] + Gr[:, None, :])
+                          + ref.Qhs[None] * (Gs[:, :, None] + Gs[:, None, :]))
+        aQx = np.abs(phys(m.rxJ[ks], m.sxJ[ks]))
+        aQy = np.abs(phys(m.ryJ[ks], m.syJ[ks]))
+
+        def flux_abs(uL, uR):
+            # |{hu}| , |{hu}{u}| + |p|, |{hu}{v}| and the y counterparts, p = 1/2 g hL hR
+            hL, hR = uL[0], uR[0]
+            uA = 0.5 * (uL[1] / hL + uR[1] / hR)
+            vA = 0.5 * (uL[2] / hL + uR[2] / hR)
+            huA = 0.5 * (np.abs(uL[1]) + np.abs(uR[1]))
+            hvA = 0.5 * (np.abs(uL[2]) + np.abs(uR[2]))
+            p = 0.5 * g * np.abs(hL * hR)
+            fx = np.stack([huA, huA * np.abs(uA) + p, huA * np.abs(vA)])
+            fy = np.stack([hvA, hvA * np.abs(uA), hvA * np.abs(vA) + p])
+            return fx, fy
+        Fx, Fy = flux_abs(u[:, :, :, None], u[:, :, None, :])
+        vol = 2.0 * np.einsum("klm,cklm->ckl", aQx, Fx) + 2.0 * np.einsum("klm,cklm->ckl", aQy, Fy)
+        uf = u[:, :, Nq:]
+        flat = ut[:, :, Nq:].reshape(3, -1)
+        idx = (ks[:, None] * Nfq + np.arange(Nfq)[None, :]).ravel()
+        uP = flat[:, m.mapP[idx]].reshape(3, ks.size, Nfq)
+        nxJ, nyJ, sJ = m.nxJ[ks], m.nyJ[ks], m.sJ[ks]
+        if m.walls:
+            wall = np.repeat(m.wall[ks], self.N + 1, axis=1)
+            nx, ny = nxJ / sJ, nyJ / sJ
+            hun = uf[1] * nx + uf[2] * ny
+            mirror = np.stack([uf[0], uf[1] - 2.0 * hun * nx, uf[2] - 2.0 * hun * ny])
+            uP = np.where(wall[None], mirror, uP)
+        fSx, fSy = flux_abs(uP, uf)
+        fx, fy = flux_abs(uf, uf)
+        wf = ref.wf[None, :]
+        surf = wf * (np.abs(nxJ) * (fSx + fx) + np.abs(nyJ) * (fSy + fy))
+        if self.lf:
+            nx, ny = nxJ / sJ, nyJ / sJ
+            lam = np.maximum(swe.wave_speed(uf, nx, ny, g), swe.wave_speed(uP, nx, ny, g))
+            surf = surf + wf * 0.5 * lam * sJ * (np.abs(uP) + np.abs(uf))
+        src = np.zeros_like(u)
+        bh = np.abs(self.bh[ks])
+        src[1] = g * np.abs(u[0]) * np.einsum("klm,km->kl", aQx, bh)
+        src[2] = g * np.abs(u[0]) * np.einsum("klm,km->kl", aQy, bh)
+        aVh, aVf = np.abs(ref.Vh), np.abs(ref.Vf)
+        total = (np.einsum("hn,ckh->ckn", aVh, vol) + np.einsum("fn,ckf->ckn", aVf, surf)
+                 + np.einsum("hn,ckh->ckn", aVh, src))
+        if self.forcing is not None:
+            fq = np.abs(self.forcing(m.xq[ks], m.yq[ks], t, g))
+            total = total + np.einsum("qn,kq,ckq->ckn", np.abs(ref.Vq) * ref.w[:, None], m.Jq[ks], fq)
+        if m.mass == "exact":
+            aMinv = np.abs(m.Mh_inv[ks])
+        else:
+            # the weight-adjusted inverse by its definition M^-1 (Vq^T W diag(1/J) Vq) M^-1
+            VqW = ref.Vq * ref.w[:, None]
+            Mri = np.abs(np.linalg.inv(VqW.T @ ref.Vq))
+            inner = np.einsum("qn,kq,qm->knm", np.abs(VqW), 1.0 / m.Jq[ks], np.abs(ref.Vq))
+            aMinv = Mri[None] @ inner @ Mri[None]
+        return np.einsum("knm,ckm->ckn", aMinv, total)
+
     # -- time stepping (Sec. 4) -----------------------------------------------------
     def step(self, u_h, res, t, dt):
         """One LSRK45 step; returns (u_h, res, t + dt)."""

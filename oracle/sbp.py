@@ -145,6 +145,55 @@ class SBPOracle:
             total = total + self.M[ks][None] * self.forcing(m.xq[ks], m.yq[ks], t, g)
         return total / self.M[ks][None]
 
+    def rhs_term_magnitude(self, u, t=0.0, elems=None):
+        """Per entry of du/dt, or of the listed elements only: the sum of the
+        absolute values of every term the DG-SBP form adds up for it (each
+        operator entry, flux product, source and penalty term by its absolute
+        value; the pressure by 1/2 g h_l h_m, a jump by the sum of the two
+        sides), divided by the diagonal mass.  The scale of a floating-point
+        error bound for the same sums; not part of the scheme."""
+        ks = np.arange(self.K) if elems is None else np.asarray(elems, dtype=np.int64)
+        ref, m, g = self.ref, self.mesh, self.g
+        Nfq = self.Nfq
+        uk = u[:, ks]
+        Qx, Qy = self.sbp_operators(ks)
+        aQx, aQy = np.abs(Qx), np.abs(Qy)
+
+        def flux_abs(uL, uR):
+            hL, hR = uL[0], uR[0]
+            uA = 0.5 * (uL[1] / hL + uR[1] / hR)
+            vA = 0.5 * (uL[2] / hL + uR[2] / hR)
+            huA = 0.5 * (np.abs(uL[1]) + np.abs(uR[1]))
+            hvA = 0.5 * (np.abs(uL[2]) + np.abs(uR[2]))
+            p = 0.5 * g * np.abs(hL * hR)
+            fx = np.stack([huA, huA * np.abs(uA) + p, huA * np.abs(vA)])
+            fy = np.stack([hvA, hvA * np.abs(uA), hvA * np.abs(vA) + p])
+            return fx, fy
+        Fx, Fy = flux_abs(uk[:, :, :, None], uk[:, :, None, :])
+        vol = 2.0 * np.einsum("klm,cklm->ckl", aQx, Fx) + 2.0 * np.einsum("klm,cklm->ckl", aQy, Fy)
+        uf = uk[:, :, ref.fmap]
+        flat = u[:, :, ref.fmap].reshape(3, -1)
+        idx = (ks[:, None] * Nfq + np.arange(Nfq)[None, :]).ravel()
+        uP = flat[:, m.mapP[idx]].reshape(3, ks.size, Nfq)
+        nxJ, nyJ, sJ = m.nxJ[ks], m.nyJ[ks], m.sJ[ks]
+        fSx, fSy = flux_abs(uP, uf)
+        fx, fy = flux_abs(uf, uf)
+        wf = ref.wf[None, :]
+        surf = wf * (np.abs(nxJ) * (fSx + fx) + np.abs(nyJ) * (fSy + fy))
+        if self.lf:
+            nx, ny = nxJ / sJ, nyJ / sJ
+            lam = np.maximum(swe.wave_speed(uf, nx, ny, g), swe.wave_speed(uP, nx, ny, g))
+            surf = surf + wf * 0.5 * lam * sJ * (np.abs(uP) + np.abs(uf))
+        surf_nodes = np.einsum("fq,ckf->ckq", np.abs(ref.If), surf)
+        src = np.zeros_like(uk)
+        b = np.abs(self.bq[ks])
+        src[1] = g * np.abs(uk[0]) * np.einsum("klm,km->kl", aQx, b)
+        src[2] = g * np.abs(uk[0]) * np.einsum("klm,km->kl", aQy, b)
+        total = vol + surf_nodes + src
+        if self.forcing is not None:
+            total = total + self.M[ks][None] * np.abs(self.forcing(m.xq[ks], m.yq[ks], t, g))
+        return total / self.M[ks][None]
+
     # -- time stepping and diagnostics -------------------------------------------------
     def step(self, u, res, t, dt):
         u = u.copy()

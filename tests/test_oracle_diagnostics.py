@@ -231,3 +231,47 @@ def test_planted_dropped_jacobian_fails_the_sbp_constant_state_pin(monkeypatch):
     monkeypatch.setattr(o, "M", np.broadcast_to(o.ref.w[None, :], o.M.shape))
     assert abs(o.entropy(u) - S_ex) > 1e-3 * S_ex
     assert abs(o.mass(u) - M_ex) > 1e-3 * M_ex
+
+
+# ---------------------------------------------------------------------------
+# The term magnitude used to scale the FP32 error bounds of the GPU tests
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("walls", [False, True])
+@pytest.mark.parametrize("mass", ["exact", "weight_adjusted"])
+def test_modal_term_magnitude_bounds_the_right_hand_side(mass, walls):
+    """By the triangle inequality the sum of the absolute values of the terms
+    bounds the sum itself, entry by entry; on listed elements it equals the
+    whole-mesh value; and with u = v = 0, b = 0 and no LF every term is a
+    pressure term, quadratic in h (so doubling h multiplies it by 4)."""
+    from oracle.esdg import mms_sine_forcing
+    o = Oracle(3, 5, 4, ax=0.05, ay=0.05, g=G, rule="symmetric", mass=mass, walls=walls,
+               forcing=mms_sine_forcing)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(0.1 * np.sin(np.pi * xb) * np.cos(np.pi * yb))
+    u = _random_modal(o, 4)
+    r = o.rhs(u, 0.3)
+    m = o.rhs_term_magnitude(u, 0.3)
+    assert np.all(np.abs(r) <= m * (1 + 1e-12))
+    ks = [0, 3, o.K - 1]
+    assert np.allclose(o.rhs_term_magnitude(u, 0.3, elems=ks), m[:, ks], rtol=1e-14, atol=0)
+    o2 = Oracle(3, 5, 4, ax=0.05, ay=0.05, g=G, rule="symmetric", mass=mass, walls=walls, lf=False)
+    h = np.zeros_like(u)
+    h[0, :, 0] = 1.5 * np.sqrt(2.0)        # a constant depth (the mode-0 value is sqrt(2) h)
+    m1, m2 = o2.rhs_term_magnitude(h), o2.rhs_term_magnitude(2.0 * h)
+    assert np.allclose(m2, 4.0 * m1, rtol=1e-13, atol=0)
+
+
+def test_sbp_term_magnitude_bounds_the_right_hand_side():
+    o = SBPOracle(3, 5, 4, ax=0.05, ay=0.05, g=G)
+    xb, yb = o.points("nodal")
+    o.set_bathymetry(0.1 * np.sin(np.pi * xb) * np.cos(np.pi * yb))
+    rng = np.random.default_rng(6)
+    u = 0.05 * rng.standard_normal((3, o.K, o.Nq))
+    u[0] += 2.0
+    r = o.rhs(u)
+    m = o.rhs_term_magnitude(u)
+    assert np.all(np.abs(r) <= m * (1 + 1e-12))
+    ks = [1, 2, o.K - 1]
+    assert np.allclose(o.rhs_term_magnitude(u, elems=ks), m[:, ks], rtol=1e-14, atol=0)

@@ -59,6 +59,7 @@ def check_fp32_rhs(got, want, mag, c):
     worst = float(np.nanmax(ratio))
     assert np.all(err <= c * U32 * mag), "entry error %.3g u mag at %s (bound %d u mag)" % (
         worst, np.unravel_index(int(np.nanargmax(ratio)), ratio.shape), c)
+    print("[fp32 rhs] worst entry error %.3g u mag (bound %d u mag)" % (worst, c))
     return worst
 
 
@@ -68,4 +69,5 @@ def check_state(got, want, tol):
     rel = np.linalg.norm(got - want) / np.linalg.norm(want)
     relmax = np.abs(got - want).max() / np.abs(want).max()
     assert rel < tol and relmax < tol, "state rel L2 %.3g, rel max %.3g (bound %.1g)" % (rel, relmax, tol)
+    print("[state] rel L2 %.3g, rel max %.3g (bound %.1g)" % (rel, relmax, tol))
     return rel, relmax

@@ -676,6 +676,68 @@ def run_reference(args, world, rank):
     print(json.dumps(line))
 
 
+def shard_layout(world):
+    """Blocks of the element partition for `world` ranks: px x py = world with
+    px >= py as close to square as the factors allow."""
+    py = int(world ** 0.5)
+    while world % py:
+        py -= 1
+    return world // py, py
+
+
+def run_shard(args, world, rank, local, peaks):
+    """One solve split over the ranks (element partition, one halo exchange of
+    the entropy-projected records per RK stage over NCCL): the whole mesh's
+    GDOF-stage/s over the slowest rank's time (strong scaling)."""
+    import torch
+    from paper_2005_02516_gb300 import esdg, partition as P
+    px, py = shard_layout(world)
+    s = esdg.Solver(WL.N, WL.nx, WL.ny, precision="fp32", warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule,
+                    partition=(px, py, rank))
+    xb, yb = s.points(esdg.ESDG_POINTS_NODAL)
+    xq, yq = s.points(esdg.ESDG_POINTS_VOLQ)
+    s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
+    L = esdg.partition_layout(s.lib, s.h)
+    ex = P.HaloExchange(P.halo_plan(L), L["record_bytes"], s.halo_pack, s.halo_unpack)
+    tr = P.DistTransport()
+    dt = s.dt()
+    t = P.step(s, ex, tr, args.warmup, dt, 0.0)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0.record(s.stream)
+    t = P.step(s, ex, tr, args.steps, dt, t)
+    ev1.record(s.stream)
+    ev1.synchronize()
+    clk = clocks.stop()
+    s.check()
+    torch.cuda.synchronize()
+    barrier(world)
+    el = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
+    S, M, R = P.entropy_sum(s, t) if world > 1 else s.entropy(t)
+    K = L["K_global"]
+    value = K * s.Np * 5 * args.steps / el / 1e9
+    halo = ex.bytes_per_exchange()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WL.name, "N": WL.N, "K": K, "Np": s.Np, "Nq": s.Nq, "volume_rule": WL.rule,
+                           "curved": True, "mass": "exact", "method": "modal", "rhs_precision": "fp32",
+                           "rk_accumulation": "fp64", "l2": "inputs larger than L2",
+                           "parallelism": "element partition %dx%d (one solve)" % (px, py)},
+                "shard": {"px": px, "py": py, "local_elements_rank0": L["K"], "ghosts_rank0": L["nghost"],
+                          "halo_bytes_per_stage_rank0": halo, "exchanges_per_step": 5,
+                          "entropy": S, "mass": M},
+                "clocks": clk, "gpu_launches": 5 * args.steps * (1 + len(ex.peers)), "peaks": None}
+        print(json.dumps(line))
+    s.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -699,6 +761,9 @@ def main():
     ap.add_argument("--no-sbp", action="store_true", help="skip the DG-SBP comparison leg")
     ap.add_argument("--no-accuracy", action="store_true",
                     help="skip the stated-accuracy leg (manufactured solution, N=3, K=8192, 1000 steps)")
+    ap.add_argument("--shard", action="store_true",
+                    help="one solve split over the ranks by an element partition (halo exchange per RK stage) "
+                         "instead of one replica per rank")
     ap.add_argument("--nx", type=int, default=None,
                     help="grid of nx x nx quads instead of 256 x 256 (small profiling case; not a bench line)")
     args = ap.parse_args()
@@ -714,13 +779,19 @@ def main():
         run_reference(args, world, int(os.environ.get("RANK", "0")))
         return
     cb = None
-    if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_cpu_baseline:
+    if int(os.environ.get("WORLD_SIZE", "1")) == 1 and not args.no_cpu_baseline and not args.shard:
         # before any CUDA call: the CPU baseline forks its worker processes
         cb = cpu_baseline()
     world, rank, local = dist_init("nccl")
     import torch
     torch.cuda.set_device(local)
     peaks, peak_kind = load_peaks()
+    if args.shard:
+        run_shard(args, world, rank, local, peaks)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
 
     s = make_solver("fp32", args.mass, args.method)
     wadg = args.mass == "weight_adjusted"

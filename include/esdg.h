@@ -250,6 +250,66 @@ int esdg_entropy(esdg_ctx* ctx, double t, double* entropy, double* mass, double*
 int esdg_l2_error(esdg_ctx* ctx, const double* exact_volq, double* err);
 
 /*
+ * Element partition of one solve (one GPU per block; the multi-GPU form of a
+ * single solve: the elements of the structured grid split into px x py blocks
+ * of whole quads, with one exchange of the entropy-projected face values per
+ * RK stage, since the interface flux of Sec. 2.8 at a cut face needs the
+ * neighbour's u~ on that face).
+ *
+ * esdg_build_partition -- the context of block `part` (0 <= part < px * py,
+ * block (part % px, part / px); block b covers quads [b n / p, (b + 1) n / p) in
+ * each direction) of the mesh cfg describes.  Its K local elements are the
+ * block's, in increasing global order (global element 2 q + t of quad q =
+ * j nx + i, as esdg_build_operators numbers them); its ghosts are the elements of
+ * other blocks across a cut face, sorted by owning block, then global element.
+ * All per-element calls (points, bathymetry, state, entropy, L2 error) act on
+ * the local elements.  px = py = 1 is the whole mesh.  ESDG_EINVAL for a bad
+ * block layout or configuration; no device work.
+ */
+int esdg_build_partition(const esdg_config* cfg, int px, int py, int part, esdg_ctx** out);
+
+/* K_global: elements of the whole mesh; nghost: ghost records; px, py, part
+ * as built; record_bytes: bytes of one element's u~ record block (the unit of
+ * the halo exchange).  Any output may be NULL. */
+int esdg_partition_info(const esdg_ctx* ctx, int* K_global, int* nghost, int* px, int* py, int* part,
+                        size_t* record_bytes);
+
+/* Host arrays (any may be NULL): owned_gid [K] the global element of each local
+ * element, ghost_gid [nghost] the global element of each ghost record,
+ * ghost_part [nghost] the block that owns it. */
+int esdg_partition_maps(const esdg_ctx* ctx, int* owned_gid, int* ghost_gid, int* ghost_part);
+
+/* The face-neighbour table, host array [K][3]: 4 * element + face of the
+ * neighbour across each face (4 * own element + 3 on a wall).  In a partition,
+ * element indices >= K' = K rounded up to a multiple of 8 name ghost record
+ * index - K'. */
+int esdg_get_neighbors(const esdg_ctx* ctx, int* nbr);
+
+/*
+ * Per-stage stepping with a halo exchange in between (partitions; it works on
+ * any context).  esdg_project: the entropy-projected values u~ of the current
+ * state (Sec. 2.6) into the current u~ buffer.  esdg_stage: LSRK45 stage
+ * `stage` (0..4, Sec. 4) of the step that starts at t0 with step dt: reads the
+ * current u~ buffer (own and ghost records), updates u and the residual, and
+ * writes the next stage's u~ into the other buffer, which becomes current.
+ * ESDG_ESTATE before esdg_project.  A partition with ghosts must exchange its
+ * halo after esdg_project and after every esdg_stage; esdg_step, esdg_rhs and
+ * esdg_step_host refuse it (ESDG_ESTATE).  Asynchronous on the context's
+ * stream; errors found on the device surface at esdg_check.
+ */
+int esdg_project(esdg_ctx* ctx);
+int esdg_stage(esdg_ctx* ctx, int stage, double dt, double t0);
+
+/* Halo exchange, on the current u~ buffer, in record blocks of record_bytes:
+ * esdg_halo_pack gathers the blocks of the n local elements idx_dev (device
+ * int array; an index outside [0, K) gives a block of zeros) into out_dev
+ * (device, n blocks); esdg_halo_unpack copies n blocks from in_dev (device)
+ * into ghost records first .. first + n - 1 (ESDG_EINVAL past the ghosts).
+ * Both asynchronous on the context's stream; the caller owns the buffers. */
+int esdg_halo_pack(esdg_ctx* ctx, const int* idx_dev, int n, void* out_dev);
+int esdg_halo_unpack(esdg_ctx* ctx, const void* in_dev, int first, int n);
+
+/*
  * esdg_entropy_noalloc -- the entropy and mass of esdg_entropy (no rate), for
  * callers that cannot allocate device memory while they run: code inside a
  * memory-pool or arena regime that forbids new allocations, or a driver loop

@@ -80,6 +80,12 @@ struct esdg_ctx {
     int num_sms = 0;
     int cur = 0;            // which u~ buffer holds the current stage's values
     bool ut_valid = false;  // u~ buffer current for the state u
+    // element partition of one solve (esdg_build_partition); px = py = 1: the whole mesh
+    int px = 1, py = 1, part = 0;
+    int K_global = 0;
+    std::vector<int> owned_gid;  // [K]  global element of each local element
+    std::vector<int> ghost_gid;  // [G]  global element of each ghost record (u~ record Kpad + g)
+    std::vector<int> ghost_part; // [G]  the part that owns it (ghosts sorted by part, then element)
 };
 
 static thread_local std::string g_build_error;
@@ -155,8 +161,11 @@ static void compute_layout(esdg_ctx* c) {
     L.u = take(8 * 3 * K * ndof);
     L.res = take(8 * 3 * K * ndof);
     L.rhs = take(8 * 3 * K * ndof);
-    L.ut0 = take(rs * Kp * nrec * 4);
-    L.ut1 = take(rs * Kp * nrec * 4);
+    // u~ records of the local elements, then one per ghost element of a
+    // partition (written by the halo exchange, read as exterior values)
+    const size_t Kr = Kp + c->ghost_gid.size();
+    L.ut0 = take(rs * Kr * nrec * 4);
+    L.ut1 = take(rs * Kr * nrec * 4);
     c->entropy_parts = 1024;
     L.partial = take(8 * 3 * size_t(c->entropy_parts));
     L.diag = take(8 * 4);
@@ -707,7 +716,100 @@ static int step_t(esdg_ctx* c, int nsteps, double dt, double t0, double* u_out =
     return ESDG_OK;
 }
 
+// Gather the u~ record blocks (bytes each, a multiple of 16) of the listed
+// local elements into a contiguous buffer (the halo send of a partition).
+// An index outside [0, K) is not read: its block is written as zeros.
+__global__ void k_halo_pack(const uint4* __restrict__ ut, const int* __restrict__ idx, int n, int words, int K,
+                            uint4* __restrict__ out) {
+    const long long total = (long long)n * words;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = int(t / words), w = int(t - (long long)i * words);
+        const int e = idx[i];
+        out[t] = (e >= 0 && e < K) ? ut[(long long)e * words + w] : make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
 static bool valid(const esdg_ctx* c) { return c != nullptr; }
+
+// The local mesh of block `part` of a px x py block partition of the quad grid
+// (blocks of whole quads, so each quad's two triangles stay together): the
+// owned elements in increasing global order, then the ghosts, i.e. elements of
+// other blocks across a cut face, sorted by owning block and global element.
+// Face neighbours become local indices; a ghost's u~ record is Kpad + g.
+static bool restrict_mesh(const MeshData& F, const esdg_config& cfg, int px, int py, int part, MeshData& M,
+                          std::vector<int>& owned, std::vector<int>& gg, std::vector<int>& gp, std::string& err) {
+    const int nx = cfg.nx, ny = cfg.ny;
+    // block b covers quads [b n / p, (b + 1) n / p) in each direction
+    std::vector<int> bxq(nx, 0), byq(ny, 0);
+    for (int b = 0; b < px; ++b)
+        for (int i = int((long long)b * nx / px); i < int((long long)(b + 1) * nx / px); ++i) bxq[i] = b;
+    for (int b = 0; b < py; ++b)
+        for (int j = int((long long)b * ny / py); j < int((long long)(b + 1) * ny / py); ++j) byq[j] = b;
+    auto block_of_quad = [&](int i, int j) { return byq[j] * px + bxq[i]; };
+    std::vector<int> elem_part(size_t(F.K));
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            const int b = block_of_quad(i, j);
+            elem_part[2 * size_t(j * nx + i)] = elem_part[2 * size_t(j * nx + i) + 1] = b;
+        }
+    owned.clear();
+    for (int e = 0; e < F.K; ++e)
+        if (elem_part[e] == part) owned.push_back(e);
+    const int K = int(owned.size());
+    if (K == 0) { err = "empty partition block"; return false; }
+    std::vector<int> local(size_t(F.K), -1);
+    for (int k = 0; k < K; ++k) local[owned[k]] = k;
+    std::vector<std::pair<int, int>> ghosts;  // (part, global element)
+    for (int k = 0; k < K; ++k)
+        for (int f = 0; f < 3; ++f) {
+            const int nb = F.nbr[3 * size_t(owned[k]) + f], en = nb >> 2;
+            if ((nb & 3) != 3 && local[en] < 0) ghosts.push_back({elem_part[en], en});
+        }
+    std::sort(ghosts.begin(), ghosts.end());
+    ghosts.erase(std::unique(ghosts.begin(), ghosts.end()), ghosts.end());
+    gg.clear();
+    gp.clear();
+    for (auto& g : ghosts) {
+        gp.push_back(g.first);
+        gg.push_back(g.second);
+    }
+    const int Kpad = (K + 7) / 8 * 8;
+    std::vector<int> ghost_slot(size_t(F.K), -1);
+    for (size_t g = 0; g < gg.size(); ++g) ghost_slot[gg[g]] = Kpad + int(g);
+    auto take = [&](const std::vector<double>& v, std::vector<double>& out) {
+        const size_t w = v.size() / size_t(F.K);
+        out.resize(w * K);
+        for (int k = 0; k < K; ++k) std::copy_n(v.begin() + w * owned[k], w, out.begin() + w * k);
+    };
+    M.K = K;
+    take(F.xeq, M.xeq); take(F.yeq, M.yeq); take(F.xq, M.xq); take(F.yq, M.yq);
+    take(F.xf, M.xf); take(F.yf, M.yf); take(F.geo, M.geo); take(F.Jq, M.Jq); take(F.minv, M.minv);
+    M.nbr.resize(3 * size_t(K));
+    for (int k = 0; k < K; ++k)
+        for (int f = 0; f < 3; ++f) {
+            const int nb = F.nbr[3 * size_t(owned[k]) + f], en = nb >> 2, fn = nb & 3;
+            if (fn == 3) M.nbr[3 * k + f] = 4 * k + 3;
+            else M.nbr[3 * k + f] = 4 * (local[en] >= 0 ? local[en] : ghost_slot[en]) + fn;
+        }
+    return true;
+}
+
+template <typename real>
+static int stage_t(esdg_ctx* c, int s, double dt, double t0) {
+    StageParams<real> p = make_params<real>(c);
+    p.dt = dt;
+    p.ut_in = ut_buf<real>(c, c->cur);
+    p.ut_out = ut_buf<real>(c, c->cur ^ 1);
+    p.rkA = RK_A[s];
+    p.rkB = RK_B[s];
+    p.t = t0 + RK_C[s] * dt;
+    CUDA_TRY(c, d_stage(c, p, 1));
+    c->cur ^= 1;
+    return ESDG_OK;
+}
+
+
 
 extern "C" {
 
@@ -747,6 +849,71 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
     c->b_modal.assign(size_t(c->mesh.K) * c->ref.Np, 0.0);
     compute_layout(c);
     *out = c;
+    return ESDG_OK;
+}
+
+int esdg_build_partition(const esdg_config* cfg, int px, int py, int part, esdg_ctx** out) {
+    if (!cfg || !out) return fail(nullptr, ESDG_EINVAL, "null argument");
+    *out = nullptr;
+    if (px < 1 || py < 1 || part < 0 || part >= px * py)
+        return fail(nullptr, ESDG_EINVAL, "partition: need px, py >= 1 and 0 <= part < px * py");
+    if (px > cfg->nx || py > cfg->ny) return fail(nullptr, ESDG_EINVAL, "partition: more blocks than quads");
+    esdg_ctx* full = nullptr;
+    int rc = esdg_build_operators(cfg, &full);
+    if (rc) return rc;
+    esdg_ctx* c = new (std::nothrow) esdg_ctx();
+    if (!c) {
+        delete full;
+        return fail(nullptr, ESDG_ENOMEM, "out of host memory");
+    }
+    c->cfg = full->cfg;
+    c->ref = full->ref;
+    c->px = px;
+    c->py = py;
+    c->part = part;
+    c->K_global = full->mesh.K;
+    std::string err;
+    const bool ok = restrict_mesh(full->mesh, *cfg, px, py, part, c->mesh, c->owned_gid, c->ghost_gid, c->ghost_part,
+                                  err);
+    delete full;
+    if (!ok) {
+        delete c;
+        return fail(nullptr, ESDG_EINVAL, "partition: " + err);
+    }
+    c->b_modal.assign(size_t(c->mesh.K) * c->ref.Np, 0.0);
+    compute_layout(c);
+    *out = c;
+    return ESDG_OK;
+}
+
+int esdg_partition_info(const esdg_ctx* c, int* K_global, int* nghost, int* px, int* py, int* part,
+                        size_t* record_bytes) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (record_bytes) *record_bytes = real_size(c) * size_t(c->nrec) * 4;
+    if (K_global) *K_global = c->K_global ? c->K_global : c->mesh.K;
+    if (nghost) *nghost = int(c->ghost_gid.size());
+    if (px) *px = c->px;
+    if (py) *py = c->py;
+    if (part) *part = c->part;
+    return ESDG_OK;
+}
+
+int esdg_partition_maps(const esdg_ctx* cc, int* owned_gid, int* ghost_gid, int* ghost_part) {
+    esdg_ctx* c = const_cast<esdg_ctx*>(cc);
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    const int K = c->mesh.K;
+    if (owned_gid)
+        for (int k = 0; k < K; ++k) owned_gid[k] = c->owned_gid.empty() ? k : c->owned_gid[k];
+    for (size_t g = 0; g < c->ghost_gid.size(); ++g) {
+        if (ghost_gid) ghost_gid[g] = c->ghost_gid[g];
+        if (ghost_part) ghost_part[g] = c->ghost_part[g];
+    }
+    return ESDG_OK;
+}
+
+int esdg_get_neighbors(const esdg_ctx* c, int* nbr) {
+    if (!valid(c) || !nbr) return fail(nullptr, ESDG_EINVAL, "null argument");
+    std::copy(c->mesh.nbr.begin(), c->mesh.nbr.end(), nbr);
     return ESDG_OK;
 }
 
@@ -872,6 +1039,8 @@ int esdg_copy_state(const esdg_ctx* cc, double* u, int on_device) {
 }
 
 int esdg_rhs(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
+    if (c && !c->ghost_gid.empty())
+        return fail(c, ESDG_ESTATE, "a partition with ghost elements advances by esdg_stage with a halo exchange");
     if (!valid(c) || !rhs_out) return fail(nullptr, ESDG_EINVAL, "null argument");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
     int rc = c->cfg.precision == ESDG_FP32 ? rhs_t<float>(c, t, u_in, rhs_out) : rhs_t<double>(c, t, u_in, rhs_out);
@@ -880,6 +1049,8 @@ int esdg_rhs(esdg_ctx* c, double t, const double* u_in, double* rhs_out) {
 }
 
 int esdg_step_async(esdg_ctx* c, int nsteps, double dt, double t0) {
+    if (c && !c->ghost_gid.empty())
+        return fail(c, ESDG_ESTATE, "a partition with ghost elements advances by esdg_stage with a halo exchange");
     if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
     if (nsteps < 0) return fail(c, ESDG_EINVAL, "nsteps < 0");
@@ -900,6 +1071,8 @@ static const void* device_view(const void* host) {
 }
 
 int esdg_step_host(esdg_ctx* c, const double* u_host, int nsteps, double dt, double* t_inout, double* u_out_host) {
+    if (c && !c->ghost_gid.empty())
+        return fail(c, ESDG_ESTATE, "a partition with ghost elements advances by esdg_stage with a halo exchange");
     if (!valid(c) || !u_host || !u_out_host) return fail(nullptr, ESDG_EINVAL, "null argument");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
     if (nsteps < 1) return fail(c, ESDG_EINVAL, "nsteps < 1");
@@ -922,6 +1095,55 @@ int esdg_step_host(esdg_ctx* c, const double* u_host, int nsteps, double dt, dou
     rc = check_status(c);
     if (rc) return rc;
     if (t_inout) *t_inout = t0 + nsteps * dt;
+    return ESDG_OK;
+}
+
+int esdg_project(esdg_ctx* c) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    int rc = c->cfg.precision == ESDG_FP32 ? project_current<float>(c, nullptr, c->cur)
+                                           : project_current<double>(c, nullptr, c->cur);
+    if (rc) return rc;
+    c->ut_valid = true;
+    return ESDG_OK;
+}
+
+int esdg_stage(esdg_ctx* c, int stage, double dt, double t0) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (stage < 0 || stage > 4) return fail(c, ESDG_EINVAL, "stage must be 0..4");
+    if (!(dt > 0)) return fail(c, ESDG_EINVAL, "dt must be positive");
+    if (!c->ut_valid) return fail(c, ESDG_ESTATE, "call esdg_project (and exchange the halo) first");
+    return c->cfg.precision == ESDG_FP32 ? stage_t<float>(c, stage, dt, t0) : stage_t<double>(c, stage, dt, t0);
+}
+
+int esdg_halo_pack(esdg_ctx* c, const int* idx_dev, int n, void* out_dev) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (n < 0 || (n > 0 && (!idx_dev || !out_dev))) return fail(c, ESDG_EINVAL, "halo pack: bad arguments");
+    if (n == 0) return ESDG_OK;
+    const int words = int(real_size(c) * size_t(c->nrec) * 4 / 16);
+    const unsigned char* ut = c->dbuf + (c->cur == 0 ? c->L.ut0 : c->L.ut1);
+    const long long total = (long long)n * words;
+    const int block = 256;
+    const int grid = int(std::min<long long>((total + block - 1) / block, 4LL * (c->num_sms ? c->num_sms : 152)));
+    k_halo_pack<<<grid, block, 0, c->stream>>>(reinterpret_cast<const uint4*>(ut), idx_dev, n, words, c->mesh.K,
+                                                 reinterpret_cast<uint4*>(out_dev));
+    CUDA_TRY(c, cudaGetLastError());
+    return ESDG_OK;
+}
+
+int esdg_halo_unpack(esdg_ctx* c, const void* in_dev, int first, int n) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    const int G = int(c->ghost_gid.size());
+    if (n < 0 || first < 0 || first + n > G || (n > 0 && !in_dev))
+        return fail(c, ESDG_EINVAL, "halo unpack: ghost range out of bounds");
+    if (n == 0) return ESDG_OK;
+    const size_t rb = real_size(c) * size_t(c->nrec) * 4;
+    unsigned char* ut = c->dbuf + (c->cur == 0 ? c->L.ut0 : c->L.ut1);
+    CUDA_TRY(c, cudaMemcpyAsync(ut + (size_t(c->Kpad) + first) * rb, in_dev, size_t(n) * rb, cudaMemcpyDeviceToDevice,
+                                c->stream));
     return ESDG_OK;
 }
 
@@ -1217,6 +1439,8 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
         if (weight_adjusted(c->cfg))
             return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must use the stored inverse mass matrices");
         if (c->sbp) return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: members must use the modal scheme");
+        if (!c->ghost_gid.empty())
+            return fail(nullptr, ESDG_EINVAL, "esdg_ensemble_create: a block of a partition needs its halo exchange");
     }
     esdg_ensemble* e = new (std::nothrow) esdg_ensemble();
     if (!e) return fail(nullptr, ESDG_ENOMEM, "out of host memory");

@@ -239,6 +239,9 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
     r->nsteps = r->remaining = nsteps;
     r->result = result_host;
     r->bytes = (bytes + 255) & ~size_t(255);
+    int nghost = 0;
+    rc = esdg_partition_info(ctx, nullptr, &nghost, nullptr, nullptr, nullptr, nullptr);
+    if (rc || nghost > 0) return rc ? rc : ESDG_EINVAL;  // a block of a partition needs its halo exchange
     esdg_config cfg;
     rc = esdg_get_config(ctx, &cfg);
     // FP32 requests run inside an ensemble launch, which carries neither

@@ -55,7 +55,8 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
            "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
            "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host", "esdg_selftest_wait_timeout",
-           "esdg_l2_error"]
+           "esdg_l2_error", "esdg_build_partition", "esdg_partition_info", "esdg_partition_maps",
+           "esdg_get_neighbors", "esdg_project", "esdg_stage", "esdg_halo_pack", "esdg_halo_unpack"]
 
 
 class EsdgError(RuntimeError):
@@ -129,6 +130,14 @@ def load_library(path=LIB_PATH):
         "esdg_step_host": ([P, P, I, D, PD, P], I),
         "esdg_selftest_wait_timeout": ([P], I),
         "esdg_l2_error": ([P, P, PD], I),
+        "esdg_build_partition": ([ctypes.POINTER(Config), I, I, I, ctypes.POINTER(P)], I),
+        "esdg_partition_info": ([P, PI, PI, PI, PI, PI, PS], I),
+        "esdg_partition_maps": ([P, P, P, P], I),
+        "esdg_get_neighbors": ([P, P], I),
+        "esdg_project": ([P], I),
+        "esdg_stage": ([P, I, D, D], I),
+        "esdg_halo_pack": ([P, P, I, P], I),
+        "esdg_halo_unpack": ([P, P, I, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -293,7 +302,7 @@ class Solver:
     def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
                  warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
                  mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, mass="exact", method="modal",
-                 torch_memory=True, stream=None):
+                 torch_memory=True, stream=None, partition=None):
         import torch
         self.lib = load_library()
         cfg = make_config(N, nx, ny, precision=precision, x0=x0, x1=x1, y0=y0, y1=y1, warp=warp, g=g, cfl=cfl,
@@ -301,8 +310,14 @@ class Solver:
                           method=method)
         self.cfg = cfg
         h = ctypes.c_void_p()
-        self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)
+        if partition is None:
+            self._check(self.lib.esdg_build_operators(ctypes.byref(cfg), ctypes.byref(h)), None)
+        else:
+            # block `part` of a px x py element partition of the mesh (one solve on several GPUs)
+            px, py, part = partition
+            self._check(self.lib.esdg_build_partition(ctypes.byref(cfg), px, py, part, ctypes.byref(h)), None)
         self.h = h
+        self.partition = partition
         K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         nbytes = ctypes.c_size_t()
         self._check(self.lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq),
@@ -429,6 +444,48 @@ class Solver:
         d = ctypes.c_double()
         self._check(self.lib.esdg_dt(self.h, ctypes.byref(d)))
         return d.value
+
+    # -- per-stage stepping and the halo of an element partition --------------------
+    def project(self):
+        """esdg_project: u~ of the current state into the current u~ buffer."""
+        self._check(self.lib.esdg_project(self.h))
+
+    def stage(self, s, dt, t0):
+        """esdg_stage: LSRK45 stage s (0..4) of the step that starts at t0."""
+        self._check(self.lib.esdg_stage(self.h, s, dt, t0))
+
+    def halo_pack(self, idx, out):
+        """Record blocks of local elements idx (int32 CUDA tensor) into out
+        (CUDA tensor of at least len(idx) * record_bytes bytes)."""
+        self._check(self.lib.esdg_halo_pack(self.h, _ptr(idx), int(idx.numel()), _ptr(out)))
+
+    def halo_unpack(self, buf, first, n):
+        """n record blocks from buf (CUDA tensor) into ghost records first..first+n-1."""
+        self._check(self.lib.esdg_halo_unpack(self.h, _ptr(buf), first, n))
+
+
+def partition_layout(lib, h):
+    """Host-side maps of a context built by esdg_build_partition (no device
+    work): dict with K, K_global, nghost, px, py, part, record_bytes,
+    owned_gid [K], ghost_gid [G], ghost_part [G], nbr [K][3]."""
+    K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nb = ctypes.c_size_t()
+    lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq), ctypes.byref(nb))
+    Kg, G, px, py, part = (ctypes.c_int() for _ in range(5))
+    rb = ctypes.c_size_t()
+    rc = lib.esdg_partition_info(h, ctypes.byref(Kg), ctypes.byref(G), ctypes.byref(px), ctypes.byref(py),
+                                 ctypes.byref(part), ctypes.byref(rb))
+    if rc != ESDG_OK:
+        raise EsdgError(rc, lib.esdg_last_error(h).decode())
+    owned = np.zeros(K.value, dtype=np.int32)
+    gg = np.zeros(G.value, dtype=np.int32)
+    gp = np.zeros(G.value, dtype=np.int32)
+    lib.esdg_partition_maps(h, _ptr(owned), _ptr(gg), _ptr(gp))
+    nbr = np.zeros((K.value, 3), dtype=np.int32)
+    lib.esdg_get_neighbors(h, _ptr(nbr))
+    return {"K": K.value, "K_global": Kg.value, "nghost": G.value, "px": px.value, "py": py.value,
+            "part": part.value, "record_bytes": rb.value, "owned_gid": owned, "ghost_gid": gg, "ghost_part": gp,
+            "nbr": nbr}
 
 
 class Ensemble:

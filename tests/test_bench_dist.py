@@ -58,3 +58,10 @@ def test_accuracy_leg_reads_the_stored_oracle_values():
     idx, val, l2 = bench._golden_mms()
     assert len(idx) == len(val) == 4000 and len(set(idx.tolist())) == 4000
     assert l2 is not None and len(l2) == 3 and all(0 < e < 1e-6 for e in l2)
+
+
+def test_shard_layout_factors_the_ranks():
+    import bench
+    for world, want in [(1, (1, 1)), (2, (2, 1)), (3, (3, 1)), (4, (2, 2)), (6, (3, 2)), (8, (4, 2)), (16, (4, 4))]:
+        px, py = bench.shard_layout(world)
+        assert (px, py) == want and px * py == world

@@ -349,15 +349,31 @@ def run_ensemble(n, steps):
     return res
 
 
-def run_served(n, rate, precision, steps_range, k_range, budget_gb=64.0):
-    """Served form: Poisson arrivals of solve requests (degree 2..5, K
-    log-uniform, steps uniform, random smooth bathymetry, lake at rest plus a
-    bump).  Each request is built on a host thread at its arrival time and
-    submitted to the continuous-batching loop; latency is completion minus
-    arrival (host set-up, queueing, admission and GPU time included)."""
+def served_mean_work(samples=20000):
+    """Mean DOF-stages of one served request under the served distributions
+    (N ~ U{2..5}, K log-uniform in [512, 131072], steps ~ U[100, 2000]), from a
+    large sample of the trace generator."""
+    tr = W.served_trace(samples, rate=1.0, seed=W.BASE_SEED + 777)
+    return float(np.mean([r.K * r.Np * 5 * r.steps for r in tr]))
+
+
+def run_served(rate, precision, duration_s, budget_gb=64.0, seed=W.BASE_SEED, drain=True, max_wall_s=None):
+    """Served form: Poisson arrivals at `rate` per second of solve requests with
+    the served distributions (degree 2..5, K log-uniform in [512, 131072],
+    steps uniform in [100, 2000], random smooth bathymetry, lake at rest plus a
+    bump), for `duration_s` seconds of arrivals.  Each request is built on a host
+    thread at its arrival time and submitted to the continuous-batching loop;
+    latency is completion minus arrival (host set-up, queueing, admission and
+    GPU time included).  The trace depends on the seed only (the rate scales the
+    arrival times), so two runs with one seed and rate see the same requests at
+    the same times.  drain=False: the server is destroyed max_wall_s after the
+    first arrival, ending the requests still queued or running (for a precision
+    that cannot keep up with the rate)."""
     import concurrent.futures
     from paper_2005_02516_gb300 import esdg
-    trace = W.served_trace(n, rate=rate, k_range=k_range, steps_range=steps_range)
+    n = int(rate * duration_s * 1.5) + 8
+    trace = [r for r in W.served_trace(n, rate=rate, seed=seed) if r.t_arrival <= duration_s]
+    n = len(trace)
     srv = esdg.Server(hbm_budget_bytes=int(budget_gb * (1 << 30)))
     t0 = time.perf_counter()
     tickets = [None] * n
@@ -379,23 +395,37 @@ def run_served(n, rate, precision, steps_range, k_range, budget_gb=64.0):
             futs.append(pool.submit(prepare, i))
         for f in futs:
             f.result()
-    srv.drain(3600.0)
+    if drain:
+        srv.drain(3600.0)
+    else:
+        left = max_wall_s - (time.perf_counter() - t0)
+        if left > 0:
+            try:
+                srv.drain(left)
+            except esdg.EsdgError:
+                pass
     wall = time.perf_counter() - t0
     # server clock starts at esdg_server_create, within microseconds of t0
-    lat = []
+    lat, done_units, last_done = [], 0, 0.0
     for i, req in enumerate(trace):
         state, ts, ta, td = srv.query(tickets[i])
-        if state != 2:
+        if state == 2:
+            lat.append(td - req.t_arrival)
+            done_units += req.K * req.Np * 5 * req.steps
+            last_done = max(last_done, td)
+        elif drain:
             raise RuntimeError("request %d failed with state %d" % (i, state))
-        lat.append(td - req.t_arrival)
-    iters, steps, _ = srv.stats()
+    iters, steps, _, max_active = srv.stats()
     srv.close()
-    lat = np.array(lat)
-    units = sum(r.K * r.Np * 5 * r.steps for r in trace)
-    return {"precision": precision, "requests": n, "rate_per_s": rate, "k_range": list(k_range),
-            "steps_range": list(steps_range), "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()),
-            "throughput": units / wall / 1e9, "unit": UNIT, "wall_s": wall, "iterations": iters}
+    lat = np.array(lat) if lat else np.array([np.nan])
+    res = {"precision": precision, "rate_per_s": rate, "arrival_window_s": duration_s, "requests": n,
+           "completed": int(np.isfinite(lat).sum()), "p50_s": float(np.percentile(lat, 50)),
+           "p99_s": float(np.percentile(lat, 99)), "mean_s": float(np.mean(lat)),
+           "throughput": done_units / wall / 1e9, "unit": UNIT, "wall_s": wall, "iterations": iters,
+           "max_active_in_one_iteration": max_active,
+           "drain_after_last_arrival_s": (last_done - trace[-1].t_arrival) if drain and n else None,
+           "distributions": "N U{2..5}, K log-uniform [512, 131072], steps U[100, 2000]"}
+    return res
 
 
 def run_volume_ratio(sizes=(16, 32, 50, 100, 150, 200), pairs_gpu=1 << 27, pairs_cpu=4_000_000):
@@ -751,8 +781,11 @@ def main():
     ap.add_argument("--fp32-only", action="store_true", help="skip the FP64 and ensemble legs (profiling runs)")
     ap.add_argument("--ensemble", type=int, default=64, help="instances of the batched-ensemble leg (0: skip)")
     ap.add_argument("--ensemble-steps", type=int, default=500)
-    ap.add_argument("--served", type=int, default=200, help="FP32 requests of the served leg (0: skip)")
-    ap.add_argument("--served-rate", type=float, default=20.0)
+    ap.add_argument("--served", type=float, default=40.0,
+                    help="seconds of Poisson arrivals in the served legs (0: skip)")
+    ap.add_argument("--served-load", type=float, default=0.7,
+                    help="arrival rate of the served legs as a fraction of the batched FP32 throughput "
+                         "over the mean work of a request")
     ap.add_argument("--mass", default="exact", choices=["exact", "weight_adjusted"],
                     help="inverse mass of the timed leg: stored (M_h^k)^-1 (the paper's) or weight-adjusted")
     ap.add_argument("--method", default="modal", choices=["modal", "sbp"],
@@ -892,10 +925,19 @@ def main():
 
     served = None
     if not args.fp32_only and args.served > 0 and world == 1:
-        # the served distributions with steps scaled by 1/10 (and the arrival
-        # rate by the same factor) so a run ends within a minute
-        served = [run_served(args.served, args.served_rate, "fp32", (10, 200), (512, 131072)),
-                  run_served(max(4, args.served // 20), args.served_rate / 40.0, "fp64", (10, 200), (512, 8192))]
+        # The served distributions unscaled.  The arrival rate is the one the box
+        # sustains with FP32 requests: a fraction of the batched throughput over
+        # the mean work of a request; FP32 runs that trace for args.served seconds
+        # of arrivals and drains.  FP64 then gets the same trace (same requests,
+        # same arrival times) for the same window plus a bounded wait: it cannot
+        # keep up, so what it completes and its latencies are reported as such.
+        mean_work = served_mean_work()
+        batched = ens["value"] if ens else 7.0
+        rate = args.served_load * batched * 1e9 / mean_work
+        s32 = run_served(rate, "fp32", args.served)
+        s64 = run_served(rate, "fp64", args.served, drain=False, max_wall_s=args.served + 15.0)
+        served = {"mean_work_dof_stages": mean_work, "batched_throughput_used": batched,
+                  "load_fraction": args.served_load, "rate_per_s": rate, "fp32": s32, "fp64_same_trace": s64}
 
     e2e = None
     if not args.no_e2e:

@@ -375,9 +375,18 @@ const char* esdg_ensemble_error(const esdg_ensemble* ens);
  * wait in a FIFO queue and are admitted when their device footprint
  * (esdg_sizes) fits the budget next to the active ones; device memory comes
  * from the stream-ordered allocator (cudaMallocAsync/cudaFreeAsync).  Each
- * iteration advances every active request by the smallest number of steps any
- * of them still needs (at most 20): FP32 requests together in one ensemble
- * launch per RK stage, FP64 requests through their own stage kernels.  A
+ * iteration advances every active request by up to 20 steps (never past its
+ * own step count): FP32 requests with 20 or more steps left together in one
+ * ensemble launch per RK stage (per volume rule), an FP32 request with fewer
+ * left through its own stage kernels, FP64 requests through their own stage
+ * kernels on a stream of their own (created at admission), so that their
+ * kernels overlap on the device.  Admission is FIFO and also stops while the
+ * active requests of the head request's precision hold 2^23 (FP32) or 2^21
+ * (FP64) unknowns per field (K Np) or more, so an overloaded server finishes
+ * requests in arrival order rather than advancing all of them slowly (a
+ * request is always admitted when none of its precision is active).  A
+ * partition block (esdg_build_partition with ghosts) is refused with
+ * ESDG_EINVAL.  A
  * finished request's state is copied to result_host ([3][K][Np] FP64) and its
  * device memory returned before queued requests are admitted.
  * Ownership of ctx passes to the server on a successful submit (it is
@@ -396,8 +405,15 @@ int esdg_server_submit(esdg_server* srv, esdg_ctx* ctx, const double* b_nodal, c
 int esdg_server_query(esdg_server* srv, int ticket, int* state, double* t_submit, double* t_admit, double* t_done);
 /* Wait until no request is queued or running (ESDG_ETIMEOUT after timeout_s). */
 int esdg_server_drain(esdg_server* srv, double timeout_s);
-int esdg_server_stats(esdg_server* srv, long long* iterations, long long* steps, size_t* bytes_in_use);
-/* Drops queued requests, waits for running ones, releases everything. */
+/* iterations of the loop; steps: the sum over iterations of the most steps any
+ * request advanced in it; bytes_in_use: device memory held by running requests;
+ * max_active_seen: the most requests one iteration advanced together.  Any
+ * output may be NULL. */
+int esdg_server_stats(esdg_server* srv, long long* iterations, long long* steps, size_t* bytes_in_use,
+                      int* max_active_seen);
+/* Drops queued requests (state ESDG_ESTATE), ends running ones after their
+ * current iteration (at most 20 steps; state ESDG_ESTATE, no result written),
+ * releases everything. */
 int esdg_server_destroy(esdg_server* srv);
 
 /*

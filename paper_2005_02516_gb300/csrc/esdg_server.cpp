@@ -3,15 +3,17 @@
 // A worker thread owns the GPU work.  Requests arrive as built (not yet
 // attached) contexts with host initial data; they wait in a FIFO queue and are
 // admitted when their device footprint fits the HBM budget.  Every iteration
-// advances all active requests together -- the FP32 ones in one ensemble
-// launch per RK stage, the FP64 ones through their own stage kernels -- by the
-// smallest number of steps any of them still needs (at most kMaxChunk), so
-// every request runs exactly its own step count.  Finished requests are
-// retired between iterations (state copied to the caller's host buffer,
-// device memory returned), which lets queued requests in.  FP32 requests form
-// one ensemble per volume rule (an ensemble launch serves one rule).  All host work of a
-// request (esdg_prepare) runs in the submitting thread, so admission is one
-// host-to-device copy.  Built only on the public C ABI of esdg.h.
+// advances every active request by up to kMaxChunk steps: FP32 requests that
+// need at least a whole chunk go together in one ensemble launch per RK stage
+// (one ensemble per volume rule), an FP32 request with fewer steps left runs
+// just those on its own stage kernels in the same iteration, and FP64 requests
+// run on their own streams, so their (often small) grids overlap on the GPU.
+// No request waits for another to finish and none runs past its step count.
+// Finished requests are retired between iterations (state copied to the
+// caller's host buffer, device memory returned), which lets queued requests
+// in.  All host work of a request (esdg_prepare) runs in the submitting
+// thread, so admission is one host-to-device copy.  Built only on the public C
+// ABI of esdg.h.
 
 #include <cuda_runtime.h>
 
@@ -32,17 +34,26 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 constexpr int kMaxChunk = 20;  // steps per iteration at most
+// Working set: admission stops while the active requests of a precision hold
+// this many unknowns per field (K Np) -- enough to keep the device busy, few
+// enough that an overloaded server finishes requests in arrival order instead
+// of advancing all of them slowly.  A request is always admitted when nothing
+// of its precision is active.
+constexpr long long kWorkingSetFP32 = 1LL << 23;
+constexpr long long kWorkingSetFP64 = 1LL << 21;
 
 struct Request {
     int ticket = 0;
     esdg_ctx* ctx = nullptr;
     int precision = ESDG_FP32;
     int rule = ESDG_RULE_COLLAPSED;
+    long long dofs = 0;  // K Np: unknowns per field
     int nsteps = 0, remaining = 0;
     double dt = 0, t = 0;      // step size and the request's simulated time (forcing terms depend on it)
     double* result = nullptr;  // caller's host buffer [3][K][Np] ([3][K][Nq] for the DG-SBP method)
     size_t bytes = 0;
     void* dmem = nullptr;
+    cudaStream_t stream = nullptr;  // FP64 requests: their own stream (FP32 ones share the server's)
     int state = 0;  // 0 queued, 1 active, 2 done, < 0 failed (status code)
     double t_submit = 0, t_admit = 0, t_done = 0;
     std::string err;
@@ -68,6 +79,7 @@ struct esdg_server {
     esdg_ensemble* ens[2] = {nullptr, nullptr};  // FP32 ensembles, per volume rule
     std::vector<Request*> ens_members[2];
     long long iterations = 0, steps_run = 0;
+    int max_active_seen = 0;  // the most requests any one iteration advanced
     std::string err;
 };
 
@@ -81,9 +93,13 @@ static void finish(esdg_server* s, Request* r, int state, const std::string& why
         r->ctx = nullptr;
     }
     if (r->dmem) {
-        cudaFreeAsync(r->dmem, s->stream);
+        cudaFreeAsync(r->dmem, r->stream ? r->stream : s->stream);
         r->dmem = nullptr;
         s->in_use -= r->bytes;
+    }
+    if (r->stream) {
+        cudaStreamDestroy(r->stream);  // released once its work is done
+        r->stream = nullptr;
     }
     r->state = state;
     r->err = why;
@@ -95,13 +111,24 @@ static void admit(esdg_server* s, std::unique_lock<std::mutex>& lk) {
     while (!s->queue.empty() && (int)s->active.size() < s->max_active) {
         Request* r = s->queue.front();
         if (s->in_use + r->bytes > s->budget) break;
+        long long held = 0;
+        for (Request* a : s->active)
+            if (a->precision == r->precision) held += a->dofs;
+        const long long cap = r->precision == ESDG_FP64 ? kWorkingSetFP64 : kWorkingSetFP32;
+        if (held > 0 && held + r->dofs > cap) break;
         s->queue.pop_front();
         s->in_use += r->bytes;
         s->admitting += 1;
         lk.unlock();
         int rc = ESDG_OK;
         std::string why;
-        cudaError_t ce = cudaMallocAsync(&r->dmem, r->bytes + 256, s->stream);
+        cudaStream_t st = s->stream;
+        if (r->precision == ESDG_FP64) {
+            cudaError_t se = cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking);
+            if (se == cudaSuccess) st = r->stream;
+            else r->stream = nullptr;
+        }
+        cudaError_t ce = cudaMallocAsync(&r->dmem, r->bytes + 256, st);
         if (ce != cudaSuccess) {
             rc = ESDG_ENOMEM;
             why = std::string("cudaMallocAsync: ") + cudaGetErrorString(ce);
@@ -110,7 +137,7 @@ static void admit(esdg_server* s, std::unique_lock<std::mutex>& lk) {
         if (!rc) {
             char* p = static_cast<char*>(r->dmem);
             p += (256 - (reinterpret_cast<uintptr_t>(p) & 255)) & 255;
-            rc = esdg_attach_device(r->ctx, p, r->bytes, s->stream);  // one copy of the prepared image
+            rc = esdg_attach_device(r->ctx, p, r->bytes, st);  // one copy of the prepared image
             if (rc) why = esdg_last_error(r->ctx);
         }
         lk.lock();
@@ -126,11 +153,12 @@ static void admit(esdg_server* s, std::unique_lock<std::mutex>& lk) {
     }
 }
 
-// Rebuild an FP32 ensemble when the set of its active requests changed.
-static int refresh_ensemble(esdg_server* s, int rule) {
+// Rebuild an FP32 ensemble when the set of its members changed: the active
+// FP32 requests of the rule with at least `chunk` steps left.
+static int refresh_ensemble(esdg_server* s, const std::vector<Request*>& act, int rule, int chunk) {
     std::vector<Request*> fp32;
-    for (Request* r : s->active)
-        if (r->precision == ESDG_FP32 && r->rule == rule) fp32.push_back(r);
+    for (Request* r : act)
+        if (r->precision == ESDG_FP32 && r->rule == rule && r->remaining >= chunk) fp32.push_back(r);
     if (fp32 == s->ens_members[rule] && (s->ens[rule] || fp32.empty())) return ESDG_OK;
     if (s->ens[rule]) {
         esdg_ensemble_destroy(s->ens[rule]);
@@ -150,43 +178,53 @@ static void run(esdg_server* s) {
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
         admit(s, lk);
+        if (s->stop) {
+            // esdg_server_destroy: running requests end after their last iteration
+            for (Request* r : s->active) finish(s, r, ESDG_ESTATE, "server destroyed while the request ran");
+            s->active.clear();
+            s->cv.notify_all();
+            break;
+        }
         if (s->active.empty()) {
-            if (s->stop) break;
             s->cv.wait_for(lk, std::chrono::milliseconds(2));
             continue;
         }
-        int chunk = kMaxChunk;
-        for (Request* r : s->active) chunk = std::min(chunk, r->remaining);
+        const int chunk = kMaxChunk;
         std::vector<Request*> act = s->active;
         lk.unlock();
+        // steps each request advances in this iteration
+        std::vector<int> adv(act.size());
+        for (size_t i = 0; i < act.size(); ++i) adv[i] = std::min(chunk, act[i]->remaining);
         int rc = ESDG_OK;
         for (int rule = 0; rule < 2 && !rc; ++rule) {
-            rc = refresh_ensemble(s, rule);
+            rc = refresh_ensemble(s, act, rule, chunk);
             if (!rc && s->ens[rule]) rc = esdg_ensemble_step_async(s->ens[rule], chunk);
         }
-        for (Request* r : act)
-            if (!rc && r->precision == ESDG_FP64) rc = esdg_step_async(r->ctx, chunk, r->dt, r->t);
+        for (size_t i = 0; i < act.size() && !rc; ++i) {
+            Request* r = act[i];
+            if (r->precision == ESDG_FP64 || r->remaining < chunk) rc = esdg_step_async(r->ctx, adv[i], r->dt, r->t);
+        }
         cudaStreamSynchronize(s->stream);
+        for (Request* r : act)
+            if (r->stream) cudaStreamSynchronize(r->stream);
         std::vector<std::pair<Request*, int>> outcome;
         for (Request* r : act) {
             int st = rc ? rc : esdg_check(r->ctx);
             outcome.emplace_back(r, st);
         }
-        std::vector<Request*> done;
-        for (auto& o : outcome) {
-            Request* r = o.first;
-            if (o.second) continue;
-            r->remaining -= chunk;
-            r->t += chunk * r->dt;
-            if (r->remaining == 0) {
-                int st = esdg_copy_state(r->ctx, r->result, 0);
-                o.second = st;
-                done.push_back(r);
-            }
+        long long stepped = 0;
+        for (size_t i = 0; i < outcome.size(); ++i) {
+            Request* r = outcome[i].first;
+            if (outcome[i].second) continue;
+            r->remaining -= adv[i];
+            r->t += adv[i] * r->dt;
+            stepped = std::max<long long>(stepped, adv[i]);
+            if (r->remaining == 0) outcome[i].second = esdg_copy_state(r->ctx, r->result, 0);
         }
         lk.lock();
         s->iterations += 1;
-        s->steps_run += chunk;
+        s->steps_run += stepped;
+        s->max_active_seen = std::max(s->max_active_seen, (int)act.size());
         std::vector<Request*> keep;
         for (auto& o : outcome) {
             Request* r = o.first;
@@ -253,6 +291,11 @@ int esdg_server_submit(esdg_server* s, esdg_ctx* ctx, const double* b_nodal, con
         return rc ? rc : ESDG_EINVAL;
     }
     r->precision = cfg.precision;
+    {
+        int K = 0, Np = 0, Nq = 0;
+        esdg_sizes(ctx, &K, &Np, &Nq, nullptr, nullptr);
+        r->dofs = (long long)K * (cfg.method == ESDG_METHOD_SBP ? Nq : Np);
+    }
     esdg_dt(ctx, &r->dt);
     r->rule = cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 1 : 0;
     // all host work of the request (bathymetry, initial projection, operator
@@ -299,9 +342,11 @@ int esdg_server_drain(esdg_server* s, double timeout_s) {
     return ESDG_OK;
 }
 
-int esdg_server_stats(esdg_server* s, long long* iterations, long long* steps, size_t* bytes_in_use) {
+int esdg_server_stats(esdg_server* s, long long* iterations, long long* steps, size_t* bytes_in_use,
+                      int* max_active_seen) {
     if (!s) return ESDG_EINVAL;
     std::lock_guard<std::mutex> lk(s->mu);
+    if (max_active_seen) *max_active_seen = s->max_active_seen;
     if (iterations) *iterations = s->iterations;
     if (steps) *steps = s->steps_run;
     if (bytes_in_use) *bytes_in_use = s->in_use;

@@ -123,7 +123,7 @@ def load_library(path=LIB_PATH):
         "esdg_server_submit": ([P, P, P, P, I, I, P, PI], I),
         "esdg_server_query": ([P, I, PI, PD, PD, PD], I),
         "esdg_server_drain": ([P, D], I),
-        "esdg_server_stats": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PS], I),
+        "esdg_server_stats": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PS, PI], I),
         "esdg_server_destroy": ([P], I),
         "esdg_volume_kernel": ([I, I, I, I, D, P, P, P, P, P], I),
         "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
@@ -276,9 +276,10 @@ class Server:
             raise EsdgError(rc, "esdg_server_drain timed out")
 
     def stats(self):
-        it, st, b = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t()
-        self.lib.esdg_server_stats(self.h, ctypes.byref(it), ctypes.byref(st), ctypes.byref(b))
-        return it.value, st.value, b.value
+        """(iterations, steps, device bytes in use, most requests advanced by one iteration)."""
+        it, st, b, m = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_int()
+        self.lib.esdg_server_stats(self.h, ctypes.byref(it), ctypes.byref(st), ctypes.byref(b), ctypes.byref(m))
+        return it.value, st.value, b.value, m.value
 
     def close(self):
         if getattr(self, "h", None):

@@ -5,8 +5,11 @@ run; each finished state must equal the same problem run alone through the
 single-problem path: FP64 requests to relative 1e-12; FP32 requests to
 relative 1e-6 (the ensemble kernel that carries degree-5 members is a
 separate compilation of the same arithmetic, whose FP32 roundings may differ
-in a few operations; the FP32 accuracy target is 1e-5).  Admission must
-respect the HBM budget, and a request larger than the whole budget is refused.
+in a few operations; the FP32 accuracy target is 1e-5).  Requests overlap on
+the device (continuous batching, not a queue), served results match the FP64
+oracle directly, admission respects the HBM budget, a request larger than
+the whole budget is refused, and destroying the server ends running requests
+promptly.
 """
 
 import time
@@ -70,7 +73,7 @@ def test_served_results_equal_alone(rules):
         tickets.append(srv.submit(p, b, q, req.steps, surface=True))
         inputs.append((b, q))
     srv.drain(300.0)
-    iters, steps, inuse = srv.stats()
+    iters, steps, inuse, _ = srv.stats()
     assert inuse == 0 and iters > 0
     for tk, req, prec, (b, q) in zip(tickets, trace, precisions, inputs):
         state, ts, ta, td = srv.query(tk)
@@ -184,4 +187,82 @@ def test_served_fp64_requests_of_any_configuration():
         assert srv.query(tk)[0] == 2
         got = srv.result(tk)
         assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    srv.close()
+
+
+def test_served_results_match_the_oracle():
+    """Served requests against the FP64 oracle directly: FP64 requests at
+    relative 1e-12, FP32 ones (25 steps: 20 in an ensemble launch, the last 5
+    on their own stage kernels) at relative 1e-5 in the L2 and the max norm."""
+    from oracle import Oracle
+    from paper_2005_02516_gb300 import esdg
+    from _bounds import check_state
+    trace = W.served_trace(4, rate=1000.0, seed=W.BASE_SEED + 8, k_range=(32, 80), steps_range=(25, 25),
+                           degrees=(2, 3))
+    precisions = ["fp32", "fp64", "fp32", "fp64"]
+    srv = esdg.Server(hbm_budget_bytes=4 << 30)
+    tickets = []
+    for req, prec in zip(trace, precisions):
+        p, b, q = _prepare(req, prec)
+        tickets.append(srv.submit(p, b, q, req.steps, surface=True))
+    srv.drain(300.0)
+    for tk, req, prec in zip(tickets, trace, precisions):
+        assert srv.query(tk)[0] == 2
+        o = Oracle(req.N, req.nx, req.nx, ax=req.warp, ay=req.warp, g=req.g, cfl=req.cfl, rule=req.rule)
+        xo, yo = o.points("nodal")
+        o.set_bathymetry(req.bathymetry(xo, yo))
+        xq, yq = o.points("volq")
+        u0 = o.init_state(req.initial(xq, yq), surface=True)
+        want, _ = o.run(u0, req.steps)
+        got = srv.result(tk)
+        check_state(got, want, 1e-12 if prec == "fp64" else 1e-5)
+    srv.close()
+
+
+def test_destroy_ends_running_requests():
+    """esdg_server_destroy drops queued requests and ends running ones after
+    their current iteration (at most 20 steps), so it returns promptly even
+    with long FP64 requests on the device."""
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(3, rate=1000.0, seed=W.BASE_SEED + 9, k_range=(8192, 8192), steps_range=(5000, 5000),
+                           degrees=(4,))
+    srv = esdg.Server(hbm_budget_bytes=4 << 30, max_active=1)
+    tickets = []
+    for req in trace:
+        p, b, q = _prepare(req, "fp64")
+        tickets.append(srv.submit(p, b, q, req.steps, surface=True))
+    time.sleep(1.0)
+    t0 = time.perf_counter()
+    srv.lib.esdg_server_destroy(srv.h)   # the C ABI call itself, timed
+    srv.h = None
+    # one request runs (about 10 s of FP64 work in all); ending it after its
+    # current 20-step iteration takes a fraction of a second
+    assert time.perf_counter() - t0 < 3.0
+
+
+def test_requests_overlap_on_the_device():
+    """Continuous batching, not a queue: a burst of FP32 and FP64 requests is
+    admitted while others run, several are advanced by one iteration, and each
+    result still equals the same problem run alone."""
+    from paper_2005_02516_gb300 import esdg
+    trace = W.served_trace(6, rate=1000.0, seed=W.BASE_SEED + 10, k_range=(512, 2048), steps_range=(60, 200),
+                           degrees=(2, 3, 4))
+    precisions = ["fp32", "fp64", "fp32", "fp32", "fp64", "fp32"]
+    srv = esdg.Server(hbm_budget_bytes=4 << 30)
+    tickets, inputs = [], []
+    for req, prec in zip(trace, precisions):
+        p, b, q = _prepare(req, prec)
+        tickets.append(srv.submit(p, b, q, req.steps, surface=True))
+        inputs.append((b, q))
+    srv.drain(300.0)
+    _, _, _, max_active = srv.stats()
+    assert max_active >= 2
+    spans = [srv.query(tk)[2:] for tk in tickets]
+    # some request was admitted while another was still running
+    assert any(a2 < d1 and a1 < d2 for i, (a1, d1) in enumerate(spans) for j, (a2, d2) in enumerate(spans)
+               if i != j)
+    for tk, req, prec, (b, q) in zip(tickets, trace, precisions, inputs):
+        want = _alone(req, prec, b, q)
+        tol = 1e-12 if prec == "fp64" else 1e-6
+        assert np.linalg.norm(srv.result(tk) - want) <= tol * np.linalg.norm(want)
     srv.close()

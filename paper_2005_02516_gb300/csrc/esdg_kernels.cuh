@@ -439,63 +439,110 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         // ---- volume flux differencing + interface flux, row l = lane ----------
         // (u_l + u_m) T summed over m is u_l (sum of T) + sum of u_m T: the row
         // part is added once after the pair loop.
-        // Volume rows take Nh columns, face rows Nq.  With Nq <= 16 and Nh <= 32
-        // the lanes 16 and up also take the last Nh - C columns of volume row
-        // lane - 16 (after their own face row, if any), so no lane runs more than
-        // max(C, Nq + Nh - C) pairs (the FP64 pipe, which bounds this kernel,
-        // then carries no idle lanes' share); the partial sums meet by a shuffle.
+        //
+        // With Nq <= 16 and Nh <= 32 every non-zero pair (l, m) of Q_skew is
+        // evaluated once (the face-face block is zero): the flux terms are
+        // antisymmetric in (l, m) (T_ml = -T_lm) and the pressure terms swap
+        // h and H, so one evaluation gives row l its contribution and row m
+        // -(u_l T + Qx g h_m H_l), ... (about 26 FP64 operations for two rows
+        // instead of 2 x 18: this kernel is bound by the FP64 pipe).  Lanes
+        // j = lane & 15 of half-warp hf stand for volume row j.  Volume-volume
+        // pairs run along the diagonals (j, j + d mod Nq), volume-face pairs
+        // along (j, Nq + (j + t) mod L), L = max(Nq, Nfq), the two half-warps
+        // splitting the diagonals; in every step each row receives exactly one
+        // transposed contribution, from the lane d (or t) places before it,
+        // by a shuffle.  The half-warps' partial sums meet at the end.
         constexpr bool SPLIT = D::Nq <= 16 && D::Nh <= 32;
-        constexpr int C = SPLIT ? (D::Nq + D::Nh + 1) / 2 : D::Nh;
         real tl0 = 0, tl1 = 0, tl2 = 0;  // the lane's own row sums after the pair loop
         if constexpr (SPLIT) {
-            constexpr int ITERS = C > D::Nq + D::Nh - C ? C : D::Nq + D::Nh - C;
-            const int len1 = lane < D::Nq ? C : (lane < D::Nh ? D::Nq : 0);     // own row's columns
-            const int len2 = (lane >= 16 && lane - 16 < D::Nq) ? D::Nh - C : 0;  // tail of row lane - 16
-            int row = len1 > 0 ? lane : (len2 > 0 ? lane - 16 : 0);  // idle lanes read row 0
-            const real* rl = rec + row * S::REC;
-            real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
-            real c0 = 0, c1 = 0, c2 = 0, s0 = 0, s1 = 0, s2 = 0;
-            int m = len1 == 0 ? C : 0;
-            for (int it = 0; it < ITERS; ++it) {
-                if (it == len1 && len1 > 0 && len2 > 0) {
-                    // own row done: keep its sums, continue on the volume row's tail
-                    s0 = c0; s1 = c1; s2 = c2;
-                    c0 = c1 = c2 = 0;
-                    row = lane - 16;
-                    rl = rec + row * S::REC;
-                    hu_l = rl[1]; hv_l = rl[2]; rx_l = rl[6]; sx_l = rl[7]; ry_l = rl[8]; sy_l = rl[9];
-                    gh2_l = rl[10];
-                    m = C;
-                }
-                if (it < len1 + len2) {
-                    const real2 q = QsT[m * D::Nh + row];  // row < Nh, m < Nh
-                    const real* rm = rec + m * S::REC;
-                    const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
-                    const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
-                    const real HU = hu_l + rm[1], HV = hv_l + rm[2];
-                    const real T = Qx * HU + Qy * HV;
-                    const real P = gh2_l * rm[5];
-                    c0 += T;
-                    c1 += rm[3] * T + Qx * P;
-                    c2 += rm[4] * T + Qy * P;
-                    ++m;
+            constexpr int V = D::Nq, F = D::Nfq, L = V > F ? V : F;
+            static_assert(L <= 16, "one half-warp per diagonal");
+            constexpr int SVV = V / 2;            // volume-volume diagonals d = 1..SVV
+            constexpr int SVV0 = (SVV + 1) / 2;   // half 0: d = 1..SVV0, half 1: d = SVV0+1..SVV
+            constexpr int SVF0 = (L + 1) / 2;     // volume-face: half 0: t < SVF0, half 1: the rest
+            const int j = lane & 15, hf = lane >> 4;
+            const bool vrow = j < V;
+            const real* rl = rec + (vrow ? j : 0) * S::REC;
+            const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4], H_l = rl[5];
+            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9];
+            const real gh2_l = rl[10];
+            real A0 = 0, A1 = 0, A2 = 0;  // volume row j: own side + transposed volume-volume terms
+            real B0 = 0, B1 = 0, B2 = 0;  // face row Nq + j: transposed volume-face terms
+            // pair (j, m): own-row terms into (A0, A1, A2), the row-m terms into (t0, t1, t2)
+            auto pair = [&](int m, real& t0, real& t1, real& t2) {
+                const real2 q = QsT[m * D::Nh + j];
+                const real* rm = rec + m * S::REC;
+                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
+                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                const real HU = hu_l + rm[1], HV = hv_l + rm[2];
+                const real T = Qx * HU + Qy * HV;
+                const real Plm = gh2_l * rm[5];     // 2 g h_l H_m
+                const real Pml = rm[10] * H_l;      // 2 g h_m H_l
+                A0 += T;
+                A1 = fma(rm[3], T, fma(Qx, Plm, A1));
+                A2 = fma(rm[4], T, fma(Qy, Plm, A2));
+                t0 = -T;
+                t1 = -fma(u_l, T, Qx * Pml);
+                t2 = -fma(v_l, T, Qy * Pml);
+            };
+#pragma unroll
+            for (int k = 0; k < SVV0; ++k) {
+                const int d = hf == 0 ? 1 + k : SVV0 + 1 + k;
+                const bool step = d <= SVV;
+                // for d = V / 2 both ends of a pair are d apart: the lower half of the rows takes it
+                const bool act = vrow && step && !(2 * d == V && j >= V / 2);
+                int m = j + d;
+                m -= m >= V ? V : 0;
+                real t0 = 0, t1 = 0, t2 = 0;
+                if (act) pair(m, t0, t1, t2);
+                int src = j - d;
+                src += src < 0 ? V : 0;
+                const real r0 = __shfl_sync(0xffffffffu, t0, 16 * hf + (src & 15));
+                const real r1 = __shfl_sync(0xffffffffu, t1, 16 * hf + (src & 15));
+                const real r2 = __shfl_sync(0xffffffffu, t2, 16 * hf + (src & 15));
+                if (vrow && step) {
+                    A0 += r0;
+                    A1 += r1;
+                    A2 += r2;
                 }
             }
-            // own row and tail partial sums: a lane that switched holds its own
-            // row in s and the tail in c; a tail-only lane holds the tail in c
-            const bool switched = len1 > 0 && len2 > 0;
-            const real o0 = switched ? s0 : (len1 > 0 ? c0 : real(0));
-            const real o1 = switched ? s1 : (len1 > 0 ? c1 : real(0));
-            const real o2 = switched ? s2 : (len1 > 0 ? c2 : real(0));
-            const real p0 = len2 > 0 ? c0 : real(0), p1 = len2 > 0 ? c1 : real(0), p2 = len2 > 0 ? c2 : real(0);
-            // volume row v (< Nq <= 16) receives its tail from lane v + 16
-            const real r0 = __shfl_down_sync(0xffffffffu, p0, 16);
-            const real r1 = __shfl_down_sync(0xffffffffu, p1, 16);
-            const real r2 = __shfl_down_sync(0xffffffffu, p2, 16);
-            tl0 = o0; tl1 = o1; tl2 = o2;
-            if (lane < D::Nq) {
-                tl0 += r0; tl1 += r1; tl2 += r2;
+#pragma unroll
+            for (int k = 0; k < SVF0; ++k) {
+                const int t = hf == 0 ? k : SVF0 + k;
+                const bool step = t < L;
+                int f = j + t;
+                f -= f >= L ? L : 0;
+                const bool act = vrow && step && f < F;
+                real t0 = 0, t1 = 0, t2 = 0;
+                if (act) pair(V + f, t0, t1, t2);
+                int src = j - t;
+                src += src < 0 ? L : 0;
+                const real r0 = __shfl_sync(0xffffffffu, t0, 16 * hf + (src & 15));
+                const real r1 = __shfl_sync(0xffffffffu, t1, 16 * hf + (src & 15));
+                const real r2 = __shfl_sync(0xffffffffu, t2, 16 * hf + (src & 15));
+                if (step && j < F) {
+                    B0 += r0;
+                    B1 += r1;
+                    B2 += r2;
+                }
             }
+            A0 += __shfl_xor_sync(0xffffffffu, A0, 16);
+            A1 += __shfl_xor_sync(0xffffffffu, A1, 16);
+            A2 += __shfl_xor_sync(0xffffffffu, A2, 16);
+            B0 += __shfl_xor_sync(0xffffffffu, B0, 16);
+            B1 += __shfl_xor_sync(0xffffffffu, B1, 16);
+            B2 += __shfl_xor_sync(0xffffffffu, B2, 16);
+            // face row Nq + i lives on lane Nq + i: fetch B of lane i
+            const int fsrc = (lane - V) & 31;
+            const real b0 = __shfl_sync(0xffffffffu, B0, fsrc);
+            const real b1 = __shfl_sync(0xffffffffu, B1, fsrc);
+            const real b2 = __shfl_sync(0xffffffffu, B2, fsrc);
+            if (lane < V) {
+                tl0 = A0; tl1 = A1; tl2 = A2;
+            } else if (lane < D::Nh) {
+                tl0 = b0; tl1 = b1; tl2 = b2;
+            }
+            (void)h_l;
         }
         // Larger rules: the non-zero pairs (volume rows x Nh columns, then face
         // rows x Nq columns), row-major, in 32 equal pieces, one per lane; a
@@ -532,8 +579,8 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                     const real T = Qx * HU + Qy * HV;
                     const real P = gh2_l * rm[5];
                     c0 += T;
-                    c1 += rm[3] * T + Qx * P;
-                    c2 += rm[4] * T + Qy * P;
+                    c1 = fma(rm[3], T, fma(Qx, P, c1));
+                    c2 = fma(rm[4], T, fma(Qy, P, c2));
                     if (++m == len || p0 + it + 1 == p1) {
                         real* o = part + (lane * S::PR + slot) * 4;
                         o[0] = c0;
@@ -621,12 +668,12 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 r1 += w * Fn1;
                 r2 += w * Fn2;
                 if (p.lf) {
-                    const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
-                    const real isJ = real(1) / sJ;
-                    const real inx = nxJ * isJ, iny = nyJ * isJ;
-                    const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
-                    const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
-                    const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
+                    // sJ max(|u.n| + sqrt(g h)) over both sides with the unit
+                    // normal n = nJ / sJ folded in: |u.nJ| + sqrt(sJ^2 g h)
+                    const real sJ2 = nxJ * nxJ + nyJ * nyJ;
+                    const real lm = fabs(u_l * nxJ + v_l * nyJ) + r_sqrt(sJ2 * g * h_l);
+                    const real lp = fabs(uP * nxJ + vP * nyJ) + r_sqrt(sJ2 * g * hP);
+                    const real c = real(0.5) * w * (lm > lp ? lm : lp);
                     r0 -= c * (hP - h_l);
                     r1 -= c * (huP - hu_l);
                     r2 -= c * (hvP - hv_l);

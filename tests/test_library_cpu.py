@@ -217,39 +217,75 @@ def _replay_fp64_pieces(Nq, Nh):
         assert set(filed[l]) <= set(range(k0, k1 + 1)) and k1 < 32
 
 
+def _replay_fp64_diagonals(Nq, Nh):
+    """The schedule of esdg_kernels.cuh, k_stage, for Nq <= 16 and Nh <= 32:
+    lanes j = lane & 15 of half-warp hf evaluate the pair (j, j + d mod Nq)
+    on the volume-volume diagonals (half 0: d = 1..SVV0, half 1: the rest,
+    d = Nq / 2 taken by j < Nq / 2 only) and (j, Nq + (j + t) mod L) on the
+    volume-face diagonals (L = max(Nq, Nfq), half 0: t < SVF0); each step
+    every row takes the transposed term of the lane d (or t) places before it
+    in its half.  Returns the evaluated pairs and the delivered terms."""
+    V, F = Nq, Nh - Nq
+    L = max(V, F)
+    assert L <= 16
+    SVV = V // 2
+    SVV0 = (SVV + 1) // 2
+    SVF0 = (L + 1) // 2
+    evaluated, delivered = {}, {}
+    for hf in range(2):
+        for k in range(SVV0):
+            d = 1 + k if hf == 0 else SVV0 + 1 + k
+            step = d <= SVV
+            sent = {}
+            for j in range(16):
+                act = j < V and step and not (2 * d == V and j >= V // 2)
+                m = (j + d) % V if j < V else None
+                if act:
+                    evaluated[frozenset((j, m))] = evaluated.get(frozenset((j, m)), 0) + 1
+                    sent[j] = (j, m)          # the transposed term of pair (j, m) for row m
+            for j in range(16):
+                src = (j - d) % V if j < V else (j - d) % V
+                if j < V and step and src in sent:
+                    pl, pm = sent[src]
+                    assert pm == j, "a transposed term reached the wrong row"
+                    delivered[(pl, pm)] = delivered.get((pl, pm), 0) + 1
+        for k in range(SVF0):
+            t = k if hf == 0 else SVF0 + k
+            step = t < L
+            sent = {}
+            for j in range(16):
+                f = (j + t) % L
+                act = j < V and step and f < F
+                if act:
+                    key = (j, V + f)
+                    evaluated[frozenset(key)] = evaluated.get(frozenset(key), 0) + 1
+                    sent[j] = key
+            for j in range(16):
+                src = (j - t) % L
+                if step and j < F and src in sent:
+                    pl, pm = sent[src]
+                    assert pm == V + j, "a transposed term reached the wrong face row"
+                    delivered[(pl, pm)] = delivered.get((pl, pm), 0) + 1
+    return evaluated, delivered
+
+
 @pytest.mark.parametrize("rule", ["collapsed", "symmetric"])
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
-    """The FP64 stage kernel's lane schedule of the pair loop (esdg_kernels.cuh,
-    k_stage: with Nq <= 16 and Nh <= 32 lane v < Nq takes columns [0, C) of
-    volume row v, lanes 16 and up take their own face row's Nq columns and then
-    columns [C, Nh) of volume row lane - 16), replayed on the host: every
-    non-zero pair (volume rows x all columns, face rows x volume columns) is
-    evaluated exactly once, with in-range indices, in max(C, Nq + Nh - C)
-    iterations; the larger rules' 32-piece schedule likewise."""
+    """The FP64 stage kernel's lane schedule of the pair loop, replayed on the
+    host: with Nq <= 16 and Nh <= 32 every non-zero pair of Q_skew (volume x
+    volume, volume x face; the face-face block is zero) is evaluated exactly
+    once and its transposed term reaches its other row exactly once; the
+    larger rules' 32-piece schedule covers every ordered non-zero pair once."""
     Nq = {1: 3, 2: 6, 3: 12, 4: 16, 5: 25}[N] if rule == "symmetric" else (N + 1) ** 2
     Nh = Nq + 3 * (N + 1)
     if not (Nq <= 16 and Nh <= 32):
         _replay_fp64_pieces(Nq, Nh)
         return
-    C = (Nq + Nh + 1) // 2
-    iters = max(C, Nq + Nh - C)
-    seen = {}
-    for lane in range(32):
-        len1 = C if lane < Nq else (Nq if lane < Nh else 0)
-        len2 = Nh - C if (lane >= 16 and lane - 16 < Nq) else 0
-        row = lane if len1 > 0 else (lane - 16 if len2 > 0 else 0)
-        m = C if len1 == 0 else 0
-        for it in range(iters):
-            if it == len1 and len1 > 0 and len2 > 0:
-                row, m = lane - 16, C
-            if it < len1 + len2:
-                assert 0 <= row < Nh and 0 <= m < Nh
-                seen[(row, m)] = seen.get((row, m), 0) + 1
-                m += 1
-    want = {(l, m): 1 for l in range(Nh) for m in range(Nh if l < Nq else Nq)}
-    assert seen == want
-    assert iters < Nh
+    evaluated, delivered = _replay_fp64_diagonals(Nq, Nh)
+    want = {frozenset((l, m)) for l in range(Nq) for m in range(Nh) if m != l}
+    assert set(evaluated) == want and all(v == 1 for v in evaluated.values())
+    assert len(delivered) == len(want) and all(v == 1 for v in delivered.values())
 
 
 @pytest.mark.parametrize("Nq", [6, 10, 18, 22, 34])

@@ -96,6 +96,10 @@ struct C2 {
     // stored inverse, where the early loads push the kernel past 80
     // registers (measured per configuration; elsewhere early is faster)
     static constexpr bool EARLY_RK = !(D::Nh == 31 && D::Nq == 16 && !WADG);
+    // column unroll of the volume loops: 1 for the 31 hybrid nodes of N = 4
+    // with the 16-point rule (178.0 against 180.8 us per stage at K = 131072),
+    // 2 elsewhere (N = 3 and the collapsed rules ran 0.6-1.2% faster with 2)
+    static constexpr int VUNROLL = (D::Nh == 31 && D::Nq == 16) ? 1 : 2;
     // warps per CTA (one CTA per SM): as many as fit in 227 KB of shared
     // memory next to the operators, at most 24 (80 registers per thread) for
     // volume rules of up to 16 points and 16 (128 registers) above, where the
@@ -508,7 +512,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     a1[I] = fmaf(U.y, T, fmaf(Qx, P, a1[I]));                              \
     a2[I] = fmaf(U.z, T, fmaf(Qy, P, a2[I]));                              \
 }
-#pragma unroll 2
+#pragma unroll (C::VUNROLL)
     for (int m = 0; m < D::Nq; ++m) {
         const float4 U = utE[m], G = geE[m];
         const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;
@@ -520,7 +524,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             if (2 * i2 + 1 < RPL) ESDG_PAIR(2 * i2 + 1, q.z, q.w)
         }
     }
-#pragma unroll 2
+#pragma unroll (C::VUNROLL)
     for (int m = D::Nq; m < D::Nh; ++m) {
         const float4 U = utE[m], G = geE[m];
         const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = 2.f * g * U.w;

@@ -614,6 +614,45 @@ def run_collapsed(steps, warmup, world, peaks):
     return res
 
 
+def run_partition_one_gpu(steps, px=2, py=2):
+    """The element partition's machinery on one device: the bench workload split
+    into px x py blocks, run as separate contexts with their halos exchanged by
+    device copies after every stage (the exchange a multi-GPU run makes over
+    NCCL), against the same solve in one context.  Measures the cost of the
+    per-stage block launches, gathers and scatters, not communication."""
+    import torch
+    from paper_2005_02516_gb300 import esdg, partition as P
+    parts = list(range(px * py))
+    blocks, exs = [], []
+    for q in parts:
+        s = esdg.Solver(WL.N, WL.nx, WL.ny, precision="fp32", warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule,
+                        partition=(px, py, q))
+        xb, yb = s.points(esdg.ESDG_POINTS_NODAL)
+        xq, yq = s.points(esdg.ESDG_POINTS_VOLQ)
+        s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
+        L = esdg.partition_layout(s.lib, s.h)
+        blocks.append(s)
+        exs.append(P.HaloExchange(P.halo_plan(L), L["record_bytes"], s.halo_pack, s.halo_unpack))
+    dt = blocks[0].dt()
+    t = P.step_local(blocks, exs, parts, 3, dt, 0.0)
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(blocks[0].stream)
+    P.step_local(blocks, exs, parts, steps, dt, t)
+    ev1.record(blocks[0].stream)
+    ev1.synchronize()
+    el = ev0.elapsed_time(ev1) / 1e3
+    for s in blocks:
+        s.check()
+    K = sum(s.K for s in blocks)
+    halo = sum(ex.bytes_per_exchange() for ex in exs)
+    for s in blocks:
+        s.close()
+    return {"blocks": "%dx%d on one GPU" % (px, py), "value": K * WL.Np * 5 * steps / el / 1e9, "unit": UNIT,
+            "ms_per_step": el / steps * 1e3, "halo_bytes_per_stage_all_blocks": halo, "steps": steps}
+
+
 def run_context(degrees=(1, 2, 3, 4, 5), steps=3):
     """Context row beside the paper's GPU table: K = 65536 affine periodic
     (256 x 128 quads), N = 1..5, the symmetric volume rule (the paper's rule is
@@ -941,6 +980,10 @@ def main():
     if not args.fp32_only and not sbp_main and args.nx is None:
         collapsed = run_collapsed(steps, args.warmup, world, peaks)
 
+    partition_one = None
+    if not args.fp32_only and not sbp_main and world == 1:
+        partition_one = run_partition_one_gpu(max(10, steps // 5))
+
     accuracy = None
     if not args.fp32_only and not args.no_accuracy and rank == 0:
         accuracy = run_accuracy()
@@ -993,7 +1036,7 @@ def main():
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other, "other_mass": other_mass, "sbp": sbp,
-                "collapsed_rule": collapsed,
+                "collapsed_rule": collapsed, "partition_one_gpu": partition_one,
                 "fp64": fp64, "precision": precision, "accuracy": accuracy, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))

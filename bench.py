@@ -632,7 +632,7 @@ def run_partition_one_gpu(steps, px=2, py=2):
         s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
         L = esdg.partition_layout(s.lib, s.h)
         blocks.append(s)
-        exs.append(P.HaloExchange(P.halo_plan(L), L["record_bytes"], s.halo_pack, s.halo_unpack))
+        exs.append(P.HaloExchange(P.halo_plan(L), L["trace_bytes"], s.halo_pack, s.halo_unpack))
     dt = blocks[0].dt()
     t = P.step_local(blocks, exs, parts, 3, dt, 0.0)
     torch.cuda.synchronize()
@@ -795,7 +795,7 @@ def run_shard(args, world, rank, local, peaks):
     xq, yq = s.points(esdg.ESDG_POINTS_VOLQ)
     s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
     L = esdg.partition_layout(s.lib, s.h)
-    ex = P.HaloExchange(P.halo_plan(L), L["record_bytes"], s.halo_pack, s.halo_unpack)
+    ex = P.HaloExchange(P.halo_plan(L), L["trace_bytes"], s.halo_pack, s.halo_unpack)
     tr = P.DistTransport()
     dt = s.dt()
     t = P.step(s, ex, tr, args.warmup, dt, 0.0)

@@ -269,10 +269,11 @@ int esdg_l2_error(esdg_ctx* ctx, const double* exact_volq, double* err);
 int esdg_build_partition(const esdg_config* cfg, int px, int py, int part, esdg_ctx** out);
 
 /* K_global: elements of the whole mesh; nghost: ghost records; px, py, part
- * as built; record_bytes: bytes of one element's u~ record block (the unit of
- * the halo exchange).  Any output may be NULL. */
+ * as built; trace_bytes: bytes of one face trace (the N+1 node records of one
+ * face, 4 values each: the unit of the halo exchange).  Any output may be
+ * NULL. */
 int esdg_partition_info(const esdg_ctx* ctx, int* K_global, int* nghost, int* px, int* py, int* part,
-                        size_t* record_bytes);
+                        size_t* trace_bytes);
 
 /* Host arrays (any may be NULL): owned_gid [K] the global element of each local
  * element, ghost_gid [nghost] the global element of each ghost record,
@@ -300,14 +301,17 @@ int esdg_get_neighbors(const esdg_ctx* ctx, int* nbr);
 int esdg_project(esdg_ctx* ctx);
 int esdg_stage(esdg_ctx* ctx, int stage, double dt, double t0);
 
-/* Halo exchange, on the current u~ buffer, in record blocks of record_bytes:
- * esdg_halo_pack gathers the blocks of the n local elements idx_dev (device
- * int array; an index outside [0, K) gives a block of zeros) into out_dev
- * (device, n blocks); esdg_halo_unpack copies n blocks from in_dev (device)
- * into ghost records first .. first + n - 1 (ESDG_EINVAL past the ghosts).
- * Both asynchronous on the context's stream; the caller owns the buffers. */
-int esdg_halo_pack(esdg_ctx* ctx, const int* idx_dev, int n, void* out_dev);
-int esdg_halo_unpack(esdg_ctx* ctx, const void* in_dev, int first, int n);
+/* Halo exchange on the current u~ buffer, in face traces of trace_bytes (the
+ * entropy-projected values at the N+1 nodes of one face: what the interface
+ * flux of the element across that face reads).  esdg_halo_pack gathers the
+ * traces of the n faces faces_dev[i] = 4 e + f (device int array; local
+ * element e < K, face f < 3; an entry out of range gives zeros) into out_dev
+ * (device, n traces); esdg_halo_unpack writes n traces from in_dev (device)
+ * into the faces faces_dev[i] = 4 g + f of ghost records g < nghost (an entry
+ * out of range is skipped).  Both asynchronous on the context's stream; the
+ * caller owns the buffers. */
+int esdg_halo_pack(esdg_ctx* ctx, const int* faces_dev, int n, void* out_dev);
+int esdg_halo_unpack(esdg_ctx* ctx, const void* in_dev, const int* faces_dev, int n);
 
 /*
  * esdg_entropy_noalloc -- the entropy and mass of esdg_entropy (no rate), for

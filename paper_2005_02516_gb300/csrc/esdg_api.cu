@@ -716,17 +716,38 @@ static int step_t(esdg_ctx* c, int nsteps, double dt, double t0, double* u_out =
     return ESDG_OK;
 }
 
-// Gather the u~ record blocks (bytes each, a multiple of 16) of the listed
-// local elements into a contiguous buffer (the halo send of a partition).
-// An index outside [0, K) is not read: its block is written as zeros.
-__global__ void k_halo_pack(const uint4* __restrict__ ut, const int* __restrict__ idx, int n, int words, int K,
-                            uint4* __restrict__ out) {
-    const long long total = (long long)n * words;
+// Halo traces of a partition: the u~ records of one face of one element (Nfp
+// node records of `wpr` 16-byte words each; the face's nodes are records
+// Nq + f Nfp + k of the element, or fmap[f Nfp + k] for the DG-SBP method).
+// Pack: entry i = 4 e + f of a local element e < K gathers into out; an entry
+// out of range gives zeros.  Unpack: entry i = 4 g + f of ghost record g < G
+// scatters from in; an entry out of range is skipped.
+__device__ __forceinline__ int halo_node(const int* fmap, int Nq, int Nfp, int f, int k) {
+    return fmap ? fmap[f * Nfp + k] : Nq + f * Nfp + k;
+}
+
+__global__ void k_halo_pack(const uint4* __restrict__ ut, const int* __restrict__ ent, int n, int nrec, int Nq,
+                            int Nfp, int wpr, const int* __restrict__ fmap, int K, uint4* __restrict__ out) {
+    const long long per = (long long)Nfp * wpr, total = (long long)n * per;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
-        const int i = int(t / words), w = int(t - (long long)i * words);
-        const int e = idx[i];
-        out[t] = (e >= 0 && e < K) ? ut[(long long)e * words + w] : make_uint4(0u, 0u, 0u, 0u);
+        const int i = int(t / per), r = int(t - (long long)i * per), k = r / wpr, w = r - k * wpr;
+        const int x = ent[i], e = x >> 2, f = x & 3;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (x >= 0 && e < K && f < 3) v = ut[((long long)e * nrec + halo_node(fmap, Nq, Nfp, f, k)) * wpr + w];
+        out[t] = v;
+    }
+}
+
+__global__ void k_halo_unpack(uint4* __restrict__ ut, const int* __restrict__ ent, int n, int nrec, int Nq, int Nfp,
+                              int wpr, const int* __restrict__ fmap, int Kpad, int G, const uint4* __restrict__ in) {
+    const long long per = (long long)Nfp * wpr, total = (long long)n * per;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int i = int(t / per), r = int(t - (long long)i * per), k = r / wpr, w = r - k * wpr;
+        const int x = ent[i], g = x >> 2, f = x & 3;
+        if (x >= 0 && g < G && f < 3)
+            ut[((long long)(Kpad + g) * nrec + halo_node(fmap, Nq, Nfp, f, k)) * wpr + w] = in[t];
     }
 }
 
@@ -887,9 +908,9 @@ int esdg_build_partition(const esdg_config* cfg, int px, int py, int part, esdg_
 }
 
 int esdg_partition_info(const esdg_ctx* c, int* K_global, int* nghost, int* px, int* py, int* part,
-                        size_t* record_bytes) {
+                        size_t* trace_bytes) {
     if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
-    if (record_bytes) *record_bytes = real_size(c) * size_t(c->nrec) * 4;
+    if (trace_bytes) *trace_bytes = real_size(c) * size_t(c->ref.Nfp) * 4;
     if (K_global) *K_global = c->K_global ? c->K_global : c->mesh.K;
     if (nghost) *nghost = int(c->ghost_gid.size());
     if (px) *px = c->px;
@@ -1117,34 +1138,37 @@ int esdg_stage(esdg_ctx* c, int stage, double dt, double t0) {
     return c->cfg.precision == ESDG_FP32 ? stage_t<float>(c, stage, dt, t0) : stage_t<double>(c, stage, dt, t0);
 }
 
-int esdg_halo_pack(esdg_ctx* c, const int* idx_dev, int n, void* out_dev) {
-    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
-    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    if (n < 0 || (n > 0 && (!idx_dev || !out_dev))) return fail(c, ESDG_EINVAL, "halo pack: bad arguments");
-    if (n == 0) return ESDG_OK;
-    const int words = int(real_size(c) * size_t(c->nrec) * 4 / 16);
-    const unsigned char* ut = c->dbuf + (c->cur == 0 ? c->L.ut0 : c->L.ut1);
-    const long long total = (long long)n * words;
+static int halo_launch(esdg_ctx* c, bool pack, const int* ent, int n, const void* src, void* dst) {
+    const int wpr = int(real_size(c) * 4 / 16);
+    const int Nfp = c->ref.Nfp;
+    const int* fmap = c->sbp ? reinterpret_cast<const int*>(c->dbuf + c->L.fmap) : nullptr;
+    unsigned char* ut = c->dbuf + (c->cur == 0 ? c->L.ut0 : c->L.ut1);
+    const long long total = (long long)n * Nfp * wpr;
     const int block = 256;
     const int grid = int(std::min<long long>((total + block - 1) / block, 4LL * (c->num_sms ? c->num_sms : 152)));
-    k_halo_pack<<<grid, block, 0, c->stream>>>(reinterpret_cast<const uint4*>(ut), idx_dev, n, words, c->mesh.K,
-                                                 reinterpret_cast<uint4*>(out_dev));
+    if (pack)
+        k_halo_pack<<<grid, block, 0, c->stream>>>(reinterpret_cast<const uint4*>(ut), ent, n, c->nrec, c->ref.Nq, Nfp,
+                                                     wpr, fmap, c->mesh.K, static_cast<uint4*>(dst));
+    else
+        k_halo_unpack<<<grid, block, 0, c->stream>>>(reinterpret_cast<uint4*>(ut), ent, n, c->nrec, c->ref.Nq, Nfp,
+                                                       wpr, fmap, c->Kpad, int(c->ghost_gid.size()),
+                                                       static_cast<const uint4*>(src));
     CUDA_TRY(c, cudaGetLastError());
     return ESDG_OK;
 }
 
-int esdg_halo_unpack(esdg_ctx* c, const void* in_dev, int first, int n) {
+int esdg_halo_pack(esdg_ctx* c, const int* faces_dev, int n, void* out_dev) {
     if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
     if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
-    const int G = int(c->ghost_gid.size());
-    if (n < 0 || first < 0 || first + n > G || (n > 0 && !in_dev))
-        return fail(c, ESDG_EINVAL, "halo unpack: ghost range out of bounds");
-    if (n == 0) return ESDG_OK;
-    const size_t rb = real_size(c) * size_t(c->nrec) * 4;
-    unsigned char* ut = c->dbuf + (c->cur == 0 ? c->L.ut0 : c->L.ut1);
-    CUDA_TRY(c, cudaMemcpyAsync(ut + (size_t(c->Kpad) + first) * rb, in_dev, size_t(n) * rb, cudaMemcpyDeviceToDevice,
-                                c->stream));
-    return ESDG_OK;
+    if (n < 0 || (n > 0 && (!faces_dev || !out_dev))) return fail(c, ESDG_EINVAL, "halo pack: bad arguments");
+    return n == 0 ? ESDG_OK : halo_launch(c, true, faces_dev, n, nullptr, out_dev);
+}
+
+int esdg_halo_unpack(esdg_ctx* c, const void* in_dev, const int* faces_dev, int n) {
+    if (!valid(c)) return fail(nullptr, ESDG_EINVAL, "null context");
+    if (!c->attached) return fail(c, ESDG_ESTATE, "attach device memory first");
+    if (n < 0 || (n > 0 && (!faces_dev || !in_dev))) return fail(c, ESDG_EINVAL, "halo unpack: bad arguments");
+    return n == 0 ? ESDG_OK : halo_launch(c, false, faces_dev, n, in_dev, nullptr);
 }
 
 int esdg_check(esdg_ctx* c) {

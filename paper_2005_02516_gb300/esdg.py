@@ -137,7 +137,7 @@ def load_library(path=LIB_PATH):
         "esdg_project": ([P], I),
         "esdg_stage": ([P, I, D, D], I),
         "esdg_halo_pack": ([P, P, I, P], I),
-        "esdg_halo_unpack": ([P, P, I, I], I),
+        "esdg_halo_unpack": ([P, P, P, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -455,19 +455,20 @@ class Solver:
         """esdg_stage: LSRK45 stage s (0..4) of the step that starts at t0."""
         self._check(self.lib.esdg_stage(self.h, s, dt, t0))
 
-    def halo_pack(self, idx, out):
-        """Record blocks of local elements idx (int32 CUDA tensor) into out
-        (CUDA tensor of at least len(idx) * record_bytes bytes)."""
-        self._check(self.lib.esdg_halo_pack(self.h, _ptr(idx), int(idx.numel()), _ptr(out)))
+    def halo_pack(self, faces, out):
+        """Face traces of faces = 4 e + f of local elements (int32 CUDA tensor)
+        into out (CUDA tensor of at least len(faces) * trace_bytes bytes)."""
+        self._check(self.lib.esdg_halo_pack(self.h, _ptr(faces), int(faces.numel()), _ptr(out)))
 
-    def halo_unpack(self, buf, first, n):
-        """n record blocks from buf (CUDA tensor) into ghost records first..first+n-1."""
-        self._check(self.lib.esdg_halo_unpack(self.h, _ptr(buf), first, n))
+    def halo_unpack(self, buf, faces):
+        """Face traces from buf (CUDA tensor) into the faces 4 g + f of ghost
+        records (int32 CUDA tensor)."""
+        self._check(self.lib.esdg_halo_unpack(self.h, _ptr(buf), _ptr(faces), int(faces.numel())))
 
 
 def partition_layout(lib, h):
     """Host-side maps of a context built by esdg_build_partition (no device
-    work): dict with K, K_global, nghost, px, py, part, record_bytes,
+    work): dict with K, K_global, nghost, px, py, part, trace_bytes,
     owned_gid [K], ghost_gid [G], ghost_part [G], nbr [K][3]."""
     K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     nb = ctypes.c_size_t()
@@ -485,7 +486,7 @@ def partition_layout(lib, h):
     nbr = np.zeros((K.value, 3), dtype=np.int32)
     lib.esdg_get_neighbors(h, _ptr(nbr))
     return {"K": K.value, "K_global": Kg.value, "nghost": G.value, "px": px.value, "py": py.value,
-            "part": part.value, "record_bytes": rb.value, "owned_gid": owned, "ghost_gid": gg, "ghost_part": gp,
+            "part": part.value, "trace_bytes": rb.value, "owned_gid": owned, "ghost_gid": gg, "ghost_part": gp,
             "nbr": nbr}
 
 

@@ -1,17 +1,18 @@
 """Element partition of one solve over several GPUs: the halo plan and the
-per-stage exchange of entropy-projected records.
+per-stage exchange of entropy-projected face traces.
 
 A block of the partition (esdg_build_partition) owns the elements of a
 rectangle of quads; each element's interface flux (Sec. 2.8) reads the
 neighbour's entropy-projected values u~ at the shared face, so after the
-projection and after every RK stage each block sends the u~ records of its
-elements that touch another block and receives those of its ghosts.  One
+projection and after every RK stage each block sends the u~ values at the
+nodes of its cut faces (3 (N+1) values a face, stored as 4 per node) and
+receives those of its ghosts' faces.  One
 exchange per stage is the only communication of the solve; the entropy and
 mass diagnostics add one sum over blocks.
 
-This module is host logic only: which local elements each neighbouring block
-needs and where received records go.  Gathering the records and copying them
-into the ghost slots runs in the library (esdg_halo_pack, esdg_halo_unpack);
+This module is host logic only: which local faces each neighbouring block
+needs and where received traces go.  Gathering the traces and writing them
+into the ghost records runs in the library (esdg_halo_pack, esdg_halo_unpack);
 the transport is torch.distributed point-to-point (NCCL between GPUs, gloo on
 CPU), or an in-process copy when several blocks share one device.
 """
@@ -27,51 +28,56 @@ def kpad(K):
 
 def halo_plan(layout):
     """The exchange of one block, from its maps (esdg.partition_layout):
-    {peer block: (send, first, count)} with send the local elements (int32,
-    increasing global element) whose records the peer needs, and first, count
-    the ghost records the peer fills.  The peer's ghosts from this block are
-    this block's elements adjacent to the peer's, sorted by global element, the
-    same list as `send` seen from the other side (face adjacency is symmetric),
-    so both sides agree on the order without talking."""
+    {peer block: (send, recv)}, both int32 arrays of faces 4 e + f.  send: the
+    faces of local elements whose neighbour the peer owns; recv: the faces of
+    ghost records (e = ghost index) that local elements read.  Both lists run
+    in increasing (global element, face) order, so a face the peer sends is
+    the face it stands for here at the same position: the two sides agree on
+    the order without talking (each cut face is one face of each side, and
+    face adjacency is symmetric)."""
     K = layout["K"]
     Kp = kpad(K)
     nbr = layout["nbr"]
-    gp = layout["ghost_part"]
+    gp, gg, own = layout["ghost_part"], layout["ghost_gid"], layout["owned_gid"]
     en, fn = nbr >> 2, nbr & 3
     is_ghost = (fn != 3) & (en >= Kp)
-    k_idx = np.nonzero(is_ghost)[0]
-    peers_of = gp[en[is_ghost] - Kp]
+    ks, fs = np.nonzero(is_ghost)                 # local element, own face
+    g = en[ks, fs] - Kp                            # ghost index and the ghost's face
+    gf = fn[ks, fs]
+    peer = gp[g]
     plan = {}
-    for r in np.unique(gp):
-        send = np.unique(k_idx[peers_of == r]).astype(np.int32)
-        rows = np.nonzero(gp == r)[0]
-        first, count = int(rows[0]), int(rows.size)
-        assert rows[-1] - rows[0] + 1 == count, "ghosts of one block are contiguous"
-        plan[int(r)] = (send, first, count)
+    for r in np.unique(peer):
+        sel = peer == r
+        send_keys = sorted(set(zip(own[ks[sel]].tolist(), fs[sel].tolist(), ks[sel].tolist())))
+        recv_keys = sorted(set(zip(gg[g[sel]].tolist(), gf[sel].tolist(), g[sel].tolist())))
+        send = np.array([4 * k + f for _, f, k in send_keys], dtype=np.int32)
+        recv = np.array([4 * gi + f for _, f, gi in recv_keys], dtype=np.int32)
+        assert send.size == recv.size
+        plan[int(r)] = (send, recv)
     return plan
 
 
 class HaloExchange:
     """The per-stage exchange of one block.
 
-    pack(idx, out) gathers the record blocks of local elements idx into the
-    flat byte buffer out; unpack(buf, first, n) writes n blocks into ghost
-    records first..first+n-1 (Solver.halo_pack / halo_unpack on a GPU).
-    Buffers are allocated once, on `device`.
+    pack(faces, out) gathers the face traces of local faces (4 e + f) into the
+    flat byte buffer out; unpack(buf, faces) writes traces into ghost faces
+    (Solver.halo_pack / halo_unpack on a GPU).  Buffers are allocated once, on
+    `device`.
     """
 
-    def __init__(self, plan, record_bytes, pack, unpack, device="cuda"):
+    def __init__(self, plan, trace_bytes, pack, unpack, device="cuda"):
         import torch
         self.peers = sorted(plan)
-        self.record_bytes = record_bytes
+        self.trace_bytes = trace_bytes
         self._pack, self._unpack = pack, unpack
-        self.send_idx, self.send_buf, self.recv_buf, self.recv_at = {}, {}, {}, {}
+        self.send_idx, self.recv_idx, self.send_buf, self.recv_buf = {}, {}, {}, {}
         for r in self.peers:
-            send, first, count = plan[r]
+            send, recv = plan[r]
             self.send_idx[r] = torch.as_tensor(send, dtype=torch.int32, device=device)
-            self.send_buf[r] = torch.empty(int(send.size) * record_bytes, dtype=torch.uint8, device=device)
-            self.recv_buf[r] = torch.empty(count * record_bytes, dtype=torch.uint8, device=device)
-            self.recv_at[r] = (first, count)
+            self.recv_idx[r] = torch.as_tensor(recv, dtype=torch.int32, device=device)
+            self.send_buf[r] = torch.empty(int(send.size) * trace_bytes, dtype=torch.uint8, device=device)
+            self.recv_buf[r] = torch.empty(int(recv.size) * trace_bytes, dtype=torch.uint8, device=device)
         self.primed = False
 
     def pack(self):
@@ -81,9 +87,8 @@ class HaloExchange:
 
     def unpack(self):
         for r in self.peers:
-            first, count = self.recv_at[r]
-            if count:
-                self._unpack(self.recv_buf[r], first, count)
+            if self.recv_idx[r].numel():
+                self._unpack(self.recv_buf[r], self.recv_idx[r])
 
     def bytes_per_exchange(self):
         return sum(b.numel() for b in self.send_buf.values())

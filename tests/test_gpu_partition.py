@@ -5,8 +5,8 @@ makes through NCCL), and the result is compared with the same solve on one
 context.
 
 Each block's kernels see, element by element, exactly the inputs of the
-single-domain run (its own records and geometry, the ghost records of its
-neighbours), so the states must agree bit for bit, in FP64 and FP32; the
+single-domain run (its own records and geometry, its neighbours' face traces
+in the ghost records), so the states must agree bit for bit, in FP64 and FP32; the
 entropy and mass summed over blocks agree with the single-domain diagnostics
 up to summation order (1e-12).  The single-domain path is held to the oracle
 by the parity tests.
@@ -71,7 +71,7 @@ def test_partitioned_solve_equals_single_domain(w, px, py, method, walls, precis
     for q in parts:
         s = _solver(w, precision, partition=(px, py, q), method=method, walls=walls)
         L = esdg.partition_layout(s.lib, s.h)
-        ex = P.HaloExchange(P.halo_plan(L), L["record_bytes"], s.halo_pack, s.halo_unpack)
+        ex = P.HaloExchange(P.halo_plan(L), L["trace_bytes"], s.halo_pack, s.halo_unpack)
         blocks.append(s)
         exs.append(ex)
         maps.append(L)
@@ -96,27 +96,29 @@ def test_partitioned_solve_equals_single_domain(w, px, py, method, walls, precis
     one.close()
 
 
-def test_halo_pack_and_unpack_move_whole_records():
-    """esdg_halo_pack gathers the listed elements' record blocks (zeros for an
-    index out of range); esdg_halo_unpack writes ghost records and refuses a
-    range past the ghosts."""
+def test_halo_pack_and_unpack_move_face_traces():
+    """esdg_halo_pack gathers the listed faces' traces (the N+1 node records of
+    face f of element e; zeros for an entry out of range); esdg_halo_unpack
+    writes traces into ghost faces, skipping entries out of range (that the
+    written traces are the ones the interface flux reads is the bit-for-bit
+    test above)."""
     from paper_2005_02516_gb300 import esdg
-    from paper_2005_02516_gb300 import partition as P
     w = dataclasses.replace(W.scaled(W.DAM, 8, 6), rule="symmetric")
     s = _solver(w, "fp32", partition=(2, 1, 0))
     L = esdg.partition_layout(s.lib, s.h)
     s.project()
-    rb = L["record_bytes"]
-    idx = torch.tensor([0, 3, L["K"] - 1, L["K"] + 5, -1], dtype=torch.int32, device="cuda")
-    out = torch.full((idx.numel() * rb,), 7, dtype=torch.uint8, device="cuda")
-    s.halo_pack(idx, out)
-    blocks = out.view(idx.numel(), rb)
-    assert blocks[0].any() and blocks[1].any() and blocks[2].any()
-    assert not blocks[3].any() and not blocks[4].any()
-    assert not torch.equal(blocks[0], blocks[1])
-    s.halo_unpack(out[:2 * rb], 0, 2)
-    with pytest.raises(esdg.EsdgError) as ei:
-        s.halo_unpack(out, L["nghost"] - 1, 2)
-    assert ei.value.code == esdg.ESDG_EINVAL
+    tb = L["trace_bytes"]
+    assert tb == 4 * 4 * (w.N + 1)
+    faces = torch.tensor([0, 4 * 3 + 2, 4 * (L["K"] - 1) + 1, 4 * (L["K"] + 5), 4 * 2 + 3, -1], dtype=torch.int32,
+                         device="cuda")
+    out = torch.full((faces.numel() * tb,), 7, dtype=torch.uint8, device="cuda")
+    s.halo_pack(faces, out)
+    tr = out.view(faces.numel(), tb)
+    assert tr[0].any() and tr[1].any() and tr[2].any()
+    assert not tr[3].any() and not tr[4].any() and not tr[5].any()
+    assert not torch.equal(tr[0], tr[1])
+    # unpack into the first ghost's faces and skip out-of-range entries
+    dst = torch.tensor([0, 4 * 0 + 2, 4 * L["nghost"], -1], dtype=torch.int32, device="cuda")
+    s.halo_unpack(out[:4 * tb], dst)
     s.check()
     s.close()

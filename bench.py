@@ -39,7 +39,7 @@ WL = W.DAM
 # the sha1 of the kernel source it was measured on: reported as null once that
 # source changes.
 STAGE_TRAFFIC = {"exact": {"source_sha1": "5fe24ebb95a87939dd2fcbeee97a894f26b11c05", "bytes": 429.28e6},
-                 "weight_adjusted": {"source_sha1": "02937e623df1397b93ce874147324c31a08062e2", "bytes": 360.6e6}}
+                 "weight_adjusted": {"source_sha1": "5fe24ebb95a87939dd2fcbeee97a894f26b11c05", "bytes": 361.9e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 # the same for the FP32 DG-SBP stage kernel
 SBP_TRAFFIC = {"source_sha1": "bc6a6adb39a7b0f39182f3aa3b747208c033571a", "bytes": 386.1e6}

@@ -235,10 +235,13 @@ def replica_value(units_per_rank, world, max_seconds):
     return units_per_rank * world / max_seconds / 1e9
 
 
-def make_solver(precision, mass="exact", method="modal"):
+DENSE = "auto"  # how the FP32 modal path applies the dense operators (--dense)
+
+
+def make_solver(precision, mass="exact", method="modal", dense=None):
     from paper_2005_02516_gb300.esdg import Solver, ESDG_POINTS_NODAL, ESDG_POINTS_VOLQ
     s = Solver(WL.N, WL.nx, WL.ny, precision=precision, warp=WL.warp, g=WL.g, cfl=WL.cfl, rule=WL.rule, mass=mass,
-               method=method)
+               method=method, dense=dense or DENSE)
     xb, yb = s.points(ESDG_POINTS_NODAL)
     xq, yq = s.points(ESDG_POINTS_VOLQ)
     s.init_state(WL.bathymetry(xb, yb), WL.initial(xq, yq))
@@ -853,6 +856,8 @@ def main():
     ap.add_argument("--served-load", type=float, default=0.7,
                     help="arrival rate of the served legs as a fraction of the batched FP32 throughput "
                          "over the mean work of a request")
+    ap.add_argument("--dense", default="auto", choices=["auto", "simt", "tensor"],
+                    help="dense operators of the FP32 path: FP32 pipes, tensor cores, or the library's choice")
     ap.add_argument("--mass", default="exact", choices=["exact", "weight_adjusted"],
                     help="inverse mass of the timed leg: stored (M_h^k)^-1 (the paper's) or weight-adjusted")
     ap.add_argument("--method", default="modal", choices=["modal", "sbp"],
@@ -870,7 +875,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.method == "sbp":   # the side legs belong to the modal headline
         args.fp32_only = args.no_e2e = True
-    global WL
+    global WL, DENSE
+    DENSE = args.dense
     if args.nx is not None:
         WL = W.scaled(WL, args.nx)
     if args.impl == "reference":

@@ -93,6 +93,21 @@ extern "C" {
 #define ESDG_METHOD_MODAL 0
 #define ESDG_METHOD_SBP   1
 
+/* esdg_config.dense: how the FP32 modal path (stored inverse mass) applies
+ * the shared dense operators Vq, Vq^T, Vh and the lift Vh^T (Sec. 2.6, 2.8).
+ * ESDG_DENSE_TENSOR runs them on the tensor cores (tcgen05 MMA, TF32 operands
+ * split into two parts, three products per step, FP32 accumulation in tensor
+ * memory); it needs Np <= 16 and Nq <= 16 (N <= 4 with the symmetric rule,
+ * N <= 3 with the collapsed one) and is refused elsewhere.  ESDG_DENSE_SIMT
+ * runs them on the FP32 pipes.  ESDG_DENSE_AUTO (0) takes the faster of the
+ * two, which on GB300 is the FP32 pipes at every degree where both exist.
+ * FP64, DG-SBP and weight-adjusted contexts ignore the field.  Ensembles and
+ * the request server apply the operators on the FP32 pipes whatever the
+ * members ask. */
+#define ESDG_DENSE_AUTO   0
+#define ESDG_DENSE_SIMT   1
+#define ESDG_DENSE_TENSOR 2
+
 /* point sets for esdg_get_points */
 #define ESDG_POINTS_NODAL 0  /* degree-N equispaced nodes, [K][Np] */
 #define ESDG_POINTS_VOLQ  1  /* volume quadrature points,  [K][Nq] */
@@ -118,6 +133,7 @@ typedef struct esdg_config {
     int boundary;           /* ESDG_BOUNDARY_* */
     int mass;               /* ESDG_MASS_*; ensembles and served FP32 requests take ESDG_MASS_EXACT */
     int method;             /* ESDG_METHOD_* */
+    int dense;              /* ESDG_DENSE_* (FP32 modal path with the stored inverse) */
 } esdg_config;
 
 /*

@@ -28,7 +28,8 @@ def _sources():
     cu = (["esdg_api.cu", "esdg_ensemble.cu", "esdg_ensemble_s.cu", "esdg_volume.cu", "esdg_sbp_f32.cu",
            "esdg_sbp_f64.cu", "esdg_selftest.cu", "esdg_diag.cu"] + ["esdg_kernels_n%d.cu" % n for n in range(1, 6)]
           + ["esdg_kernels_s%d.cu" % n for n in range(1, 6)]
-          + ["esdg_kernels_w%s%d.cu" % (r, n) for r in "ns" for n in range(1, 6)])
+          + ["esdg_kernels_w%s%d.cu" % (r, n) for r in "ns" for n in range(1, 6)]
+          + ["esdg_kernels_tn%d.cu" % n for n in range(1, 4)] + ["esdg_kernels_ts%d.cu" % n for n in range(1, 5)])
     return cu, ["host_build.cpp", "esdg_server.cpp"]
 
 

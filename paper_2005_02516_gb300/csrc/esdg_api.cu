@@ -45,6 +45,7 @@ using namespace esdg;
 struct DevLayout {
     size_t ops = 0, ops_bytes = 0;       // reference operators (real)
     size_t ops2 = 0, ops2_bytes = 0;     // permuted operators of the FP32 batched kernel
+    size_t ops2s = 0, ops2s_bytes = 0;   // tensor-core contexts: the FP32-pipe layout too (ensembles)
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
@@ -115,9 +116,29 @@ static bool is_sbp(const esdg_config& cfg) { return cfg.method == ESDG_METHOD_SB
 static int kernel_nr(const esdg_config& cfg) {
     return cfg.N + (cfg.volume_rule == ESDG_RULE_SYMMETRIC ? 8 : 0) + (weight_adjusted(cfg) ? 16 : 0);
 }
+// ESDG_DENSE_AUTO: the FP32 pipes, measured faster than the tensor-core form
+// at every degree where both exist (the tensor-core form waits on five MMA
+// round trips per batch of four elements)
+#ifndef ESDG_DENSE_AUTO_TENSOR
+#define ESDG_DENSE_AUTO_TENSOR 0
+#endif
+// The tensor-core form of the FP32 stage kernel exists where Np <= 16 and
+// Nq <= 16 (one 16-column MMA round for the lift, Vq and Vq^T).
+static bool tc_available(const esdg_config& cfg) {
+    return cfg.precision == ESDG_FP32 && cfg.method == ESDG_METHOD_MODAL && !weight_adjusted(cfg) &&
+           (cfg.volume_rule == ESDG_RULE_SYMMETRIC ? cfg.N <= 4 : cfg.N <= 3);
+}
+static bool use_tc(const esdg_config& cfg) {
+    if (!tc_available(cfg)) return false;
+    return cfg.dense == ESDG_DENSE_TENSOR || (cfg.dense == ESDG_DENSE_AUTO && ESDG_DENSE_AUTO_TENSOR);
+}
+// template parameter of the FP32 stage kernel: kernel_nr + 32 for the tensor-core form
+static int stage2_nr(const esdg_config& cfg) { return kernel_nr(cfg) + (use_tc(cfg) ? 32 : 0); }
 #define ESDG_FOR_EACH_NR(X)                                                         \
     X(1) X(2) X(3) X(4) X(5) X(9) X(10) X(11) X(12) X(13) X(17) X(18) X(19) X(20) X(21) \
     X(25) X(26) X(27) X(28) X(29)
+// the FP32 stage kernel's template parameters: the above and the tensor-core forms
+#define ESDG_FOR_EACH_NR2(X) ESDG_FOR_EACH_NR(X) X(33) X(34) X(35) X(41) X(42) X(43) X(44)
 
 static int c2_ops_floats(int NR);
 
@@ -143,8 +164,10 @@ static void compute_layout(esdg_ctx* c) {
     L.ops = take(L.ops_bytes);
     L.ops2_bytes = c->cfg.precision != ESDG_FP32 ? 0
                    : sbp ? 4 * size_t(sbp2_ops_floats(c->cfg.N))
-                         : 4 * size_t(c2_ops_floats(kernel_nr(c->cfg)));
+                         : 4 * size_t(c2_ops_floats(stage2_nr(c->cfg)));
     L.ops2 = take(L.ops2_bytes);
+    L.ops2s_bytes = use_tc(c->cfg) ? 4 * size_t(c2_ops_floats(kernel_nr(c->cfg))) : 0;
+    L.ops2s = take(L.ops2s_bytes);
     L.vq64 = take(sbp ? 0 : 8 * size_t(R.Nq) * R.Np);
     L.geo = take(rs * Kp * nrec * 4);
     L.wJq = take(rs * Kp * R.Nq);
@@ -274,6 +297,31 @@ static std::vector<float> pack_ops_sbp2(const RefOps& R) {
     return {};
 }
 
+// TF32 rounding (to nearest, ties to even) of a finite float.
+static float tf32_round(float f) {
+    uint32_t u;
+    std::memcpy(&u, &f, 4);
+    u = (u + 0x0FFFu + ((u >> 13) & 1u)) & 0xFFFFE000u;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
+// One B operand block of the tensor-core contractions: rows x K entries
+// op(n, k) (zero outside nr x nk), as the TF32 pair (hi at o + base, lo at
+// o + base + rows K), entry (n, k) at (n / 8) 8 K + (k / 4) 32 + (n % 8) 4 + k % 4.
+template <typename F>
+static void put_tc_block(std::vector<float>& o, int base, int rows, int K, int nr, int nk, F op) {
+    for (int n = 0; n < rows; ++n)
+        for (int k = 0; k < K; ++k) {
+            const double v = (n < nr && k < nk) ? op(n, k) : 0.0;
+            const float hi = tf32_round((float)v);
+            const float lo = tf32_round((float)(v - (double)hi));
+            const int i = (n / 8) * 8 * K + (k / 4) * 32 + (n % 8) * 4 + k % 4;
+            o[base + i] = hi;
+            o[base + rows * K + i] = lo;
+        }
+}
+
 // Operators of k_stage2 in its shared-memory layout (see C2<N> in esdg_stage2.cuh).
 template <int N>
 static std::vector<float> pack_ops2_t(const RefOps& R) {
@@ -288,19 +336,29 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
                 o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)R.Qsr(l, m);
                 o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)R.Qss(l, m);
             }
-    if (!C::WADG)
+    if (C::TC) {
+        // lift Vh^T, Vq, Vq^T, Vh as tensor-core B operands (rows = outputs, K = inputs)
+        const int t = C::o_tc;
+        put_tc_block(o, t + C::tb_lift, C::NpR, C::KL, R.Np, R.Nh, [&](int n, int l) { return R.Vh(l, n); });
+        put_tc_block(o, t + C::tb_vq, C::NqR, C::KM, R.Nq, R.Np, [&](int q, int n) { return R.Vq(q, n); });
+        put_tc_block(o, t + C::tb_vqt, C::NpR, C::KQ, R.Np, R.Nq, [&](int n, int q) { return R.Vq(q, n); });
+        put_tc_block(o, t + C::tb_vh, C::NhR, C::KM, R.Nh, R.Np, [&](int l, int n) { return R.Vh(l, n); });
+    }
+    if (!C::WADG && !C::TC)
         for (int l = 0; l < R.Nh; ++l)
             for (int b = 0; b < LPE; ++b)
                 for (int j = 0; j < C::MPL; ++j) {
                     const int n = b + LPE * j;
                     if (n < R.Np) o[C::o_VhT + (l * LPE + b) * C::MPLp + j] = (float)R.Vh(l, n);
                 }
+    if (!C::TC)
     for (int q = 0; q < R.Nq; ++q)
         for (int b = 0; b < LPE; ++b)
             for (int j = 0; j < C::MPL; ++j) {
                 const int n = b + LPE * j;
                 if (n < R.Np) o[C::o_VqT + (q * LPE + b) * C::MPLp + j] = (float)R.Vq(q, n);
             }
+    if (!C::TC)
     for (int n = 0; n < R.Np; ++n)
         for (int b = 0; b < LPE; ++b) {
             for (int j = 0; j < C::QPL; ++j) {
@@ -342,7 +400,7 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
 static int c2_ops_floats(int NR) {
     switch (NR) {
 #define X(v) case v: return C2<v>::o_end;
-        ESDG_FOR_EACH_NR(X)
+        ESDG_FOR_EACH_NR2(X)
 #undef X
     }
     return 0;
@@ -351,7 +409,7 @@ static int c2_ops_floats(int NR) {
 static std::vector<float> pack_ops2(const RefOps& R, int NR) {
     switch (NR) {
 #define X(v) case v: return pack_ops2_t<v>(R);
-        ESDG_FOR_EACH_NR(X)
+        ESDG_FOR_EACH_NR2(X)
 #undef X
     }
     return {};
@@ -387,7 +445,8 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
         std::vector<real> geo(M.geo.size());
         for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
         put(img, c->L.geo, geo);
-        if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, kernel_nr(c->cfg)));
+        if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, stage2_nr(c->cfg)));
+        if (use_tc(c->cfg)) put(img, c->L.ops2s, pack_ops2(R, kernel_nr(c->cfg)));
     }
     std::vector<double> wJ64(K * R.Nq);
     for (size_t e = 0; e < K; ++e)
@@ -593,9 +652,9 @@ static cudaError_t d_geometry(esdg_ctx* c) {
         return e;
     }
     if (c->cfg.precision == ESDG_FP32) {
-        switch (kernel_nr(c->cfg)) {
+        switch (stage2_nr(c->cfg)) {
 #define X(v) case v: e = stage2_geometry<v>(sms, c->lg2); break;
-            ESDG_FOR_EACH_NR(X)
+            ESDG_FOR_EACH_NR2(X)
 #undef X
         }
     } else {
@@ -629,9 +688,9 @@ static cudaError_t d_stage(esdg_ctx* c, const StageParams<float>& p, int mode) {
     if (c->sbp) return d_sbp<float>(c, p, mode);
     const LaunchGeom& lg = c->lg2;
     const float* ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
-    switch (kernel_nr(c->cfg)) {
+    switch (stage2_nr(c->cfg)) {
 #define X(v) case v: return launch_stage2<v>(p, ops2, c->Kpad, mode, lg, c->stream);
-        ESDG_FOR_EACH_NR(X)
+        ESDG_FOR_EACH_NR2(X)
 #undef X
     }
     return cudaErrorInvalidValue;
@@ -853,6 +912,11 @@ int esdg_build_operators(const esdg_config* cfg, esdg_ctx** out) {
         return fail(nullptr, ESDG_EINVAL, "unknown method");
     if (cfg->method == ESDG_METHOD_SBP && (cfg->boundary != ESDG_BOUNDARY_PERIODIC || cfg->mass != ESDG_MASS_EXACT))
         return fail(nullptr, ESDG_EINVAL, "the DG-SBP scheme takes periodic boundaries and its diagonal mass matrix");
+    if (cfg->dense != ESDG_DENSE_AUTO && cfg->dense != ESDG_DENSE_SIMT && cfg->dense != ESDG_DENSE_TENSOR)
+        return fail(nullptr, ESDG_EINVAL, "unknown dense-operator kind");
+    if (cfg->dense == ESDG_DENSE_TENSOR && !tc_available(*cfg))
+        return fail(nullptr, ESDG_EINVAL,
+                    "ESDG_DENSE_TENSOR needs the FP32 modal path with the stored inverse, Np <= 16 and Nq <= 16");
     esdg_ctx* c = new (std::nothrow) esdg_ctx();
     if (!c) return fail(nullptr, ESDG_ENOMEM, "out of host memory");
     c->cfg = *cfg;
@@ -1369,7 +1433,8 @@ static int ensemble_table(esdg_ensemble* e) {
         std::memset(&m, 0, sizeof(m));
         m.p = make_params<float>(c);
         esdg_dt(c, &m.p.dt);
-        m.ops2 = reinterpret_cast<const float*>(c->dbuf + c->L.ops2);
+        // the ensemble kernel applies the dense operators on the FP32 pipes
+        m.ops2 = reinterpret_cast<const float*>(c->dbuf + (use_tc(c->cfg) ? c->L.ops2s : c->L.ops2));
         m.ut[0] = ut_buf<float>(c, 0);
         m.ut[1] = ut_buf<float>(c, 1);
         m.N = N;

@@ -36,12 +36,14 @@ constexpr int symmetric_points(int N) { return N == 1 ? 3 : N == 2 ? 6 : N == 3 
 // volume rule (0: collapsed (N+1)^2 points, 1: symmetric, exact to 2N) and the
 // inverse mass matrix (0: the stored (M_h^k)^{-1} of Sec. 2.7; 1: the
 // weight-adjusted inverse M^{-1} M_{1/J} M^{-1} = Vq^T W diag(1/J) Vq applied
-// on the fly, the alternative Sec. 2.8 names; M = I for these rules).
+// on the fly, the alternative Sec. 2.8 names; M = I for these rules), plus
+// 32 * tc for the FP32 kernel whose dense contractions run on the tensor cores.
 template <int NR>
 struct Dims {
     static constexpr int N = NR & 7;
     static constexpr int rule = (NR >> 3) & 1;
     static constexpr int wadg = (NR >> 4) & 1;
+    static constexpr int tc = (NR >> 5) & 1;    // dense contractions on the tensor cores (FP32 kernel)
     static constexpr int Np = (N + 1) * (N + 2) / 2;
     static constexpr int Nq = rule ? symmetric_points(N) : (N + 1) * (N + 1);
     static constexpr int Nfp = N + 1;

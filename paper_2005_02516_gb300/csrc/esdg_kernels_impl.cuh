@@ -98,14 +98,16 @@ cudaError_t launch_entropy(int K, double g, const double* u, const double* rhs, 
     return cudaGetLastError();
 }
 
+template cudaError_t stage2_geometry<ESDG_N>(int, LaunchGeom&);
+template cudaError_t launch_stage2<ESDG_N>(const StageParams<float>&, const float*, int, int, const LaunchGeom&,
+                                          cudaStream_t);
+#ifndef ESDG_STAGE2_ONLY  // the tensor-core forms (ESDG_N >= 32) have the FP32 stage kernel only
 template cudaError_t stage_geometry<ESDG_N, double>(int, LaunchGeom&);
 template cudaError_t project_geometry<ESDG_N, double>(int, LaunchGeom&);
 template cudaError_t launch_project<ESDG_N, double>(const StageParams<double>&, const LaunchGeom&, cudaStream_t);
 template cudaError_t launch_stage<ESDG_N, double>(const StageParams<double>&, int, const LaunchGeom&, cudaStream_t);
-template cudaError_t stage2_geometry<ESDG_N>(int, LaunchGeom&);
-template cudaError_t launch_stage2<ESDG_N>(const StageParams<float>&, const float*, int, int, const LaunchGeom&,
-                                          cudaStream_t);
 template cudaError_t launch_entropy<ESDG_N>(int, double, const double*, const double*, const double*, const double*,
                                             const double*, double*, int, double*, cudaStream_t);
+#endif
 
 }  // namespace esdg

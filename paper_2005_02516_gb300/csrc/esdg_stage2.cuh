@@ -31,6 +31,7 @@
 #pragma once
 
 #include "esdg_kernels.cuh"
+#include "esdg_tc.cuh"
 
 namespace esdg {
 
@@ -57,6 +58,26 @@ struct C2 {
     static constexpr int UTS = ((D::Nh * 4 + 4) % 32 == 0 || (D::Nh * 4 + 4) % 32 == 16) ? D::Nh * 4 + 8 : D::Nh * 4 + 4;
     static constexpr int MIS = NpP4 + 4;                    // element slot of inverse-mass staging
     static constexpr bool WADG = D::wadg;                   // weight-adjusted inverse mass
+    // Dense contractions on the tensor cores (stored inverse only): per warp,
+    // the rows (element e, field f) -> 3 e + f of an M = 64 TF32 MMA whose
+    // other 48 rows are never read, N = 16 columns of TMEM per warp.
+    static constexpr bool TC = D::tc;
+    static_assert(!(TC && WADG), "tensor-core path: stored inverse only");
+    static constexpr int TN = 16;                                   // MMA N, TMEM columns per warp
+    static constexpr int KL = (D::Nh + 7) & ~7;                     // K of the lift (hybrid nodes)
+    static constexpr int KM = (D::Np + 7) & ~7;                     // K over modes
+    static constexpr int KQ = (D::Nq + 7) & ~7;                     // K over volume nodes
+    static constexpr int KA = KL > KM ? (KL > KQ ? KL : KQ) : (KM > KQ ? KM : KQ);
+    static constexpr int NpR = (D::Np + 15) & ~15, NqR = (D::Nq + 15) & ~15, NhR = (D::Nh + 15) & ~15;
+    // B operand blocks in the operator region (floats; hi part, then lo part
+    // at + rows * K): lift Vh^T (rows modes, K hybrid nodes), Vq (rows volume
+    // nodes, K modes), Vq^T (rows modes, K volume nodes), Vh (rows hybrid
+    // nodes, K modes)
+    static constexpr int tb_lift = 0;
+    static constexpr int tb_vq = tb_lift + 2 * NpR * KL;
+    static constexpr int tb_vqt = tb_vq + 2 * NqR * KM;
+    static constexpr int tb_vh = tb_vqt + 2 * NpR * KQ;
+    static constexpr int tb_end = tb_vh + 2 * NhR * KM;
     // operator region (floats).  Stored inverse: lift Vh^T, projection Vq^T,
     // interpolation Vq and Vh.  Weight-adjusted inverse Vq^T diag(w/J) Vq
     // with the shared factors composed: C = Vq Vh^T (lift to the volume
@@ -65,10 +86,11 @@ struct C2 {
     //   v~    =  B [(w/J) o (A (w J v))].
     static constexpr int o_Qs = 0;                                  // [Nh][LPE][OPB]
     static constexpr int o_VhT = o_Qs + D::Nh * LPE * OPB;          // [Nh][LPE][MPLp]: Vh[l][b+LPE j]
-    static constexpr int o_VqT = o_VhT + (WADG ? 0 : D::Nh * LPE * MPLp);  // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
-    static constexpr int o_Vq = o_VqT + D::Nq * LPE * MPLp;         // [Np][LPE][QPLp]: Vq[b+LPE j][n]
-    static constexpr int o_Vh = o_Vq + D::Np * LPE * QPLp;          // [Np][LPE][RPLp]: Vh[b+LPE j][n]
-    static constexpr int o_C = o_Vh + (WADG ? 0 : D::Np * LPE * RPLp);     // [Nh][LPE][QPLp]: C[b+LPE j][l]
+    static constexpr int o_tc = o_VhT;                              // tensor-core B blocks (TC)
+    static constexpr int o_VqT = o_VhT + (TC ? tb_end : WADG ? 0 : D::Nh * LPE * MPLp);  // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
+    static constexpr int o_Vq = o_VqT + (TC ? 0 : D::Nq * LPE * MPLp);      // [Np][LPE][QPLp]: Vq[b+LPE j][n]
+    static constexpr int o_Vh = o_Vq + (TC ? 0 : D::Np * LPE * QPLp);       // [Np][LPE][RPLp]: Vh[b+LPE j][n]
+    static constexpr int o_C = o_Vh + ((WADG || TC) ? 0 : D::Np * LPE * RPLp);  // [Nh][LPE][QPLp]: C[b+LPE j][l]
     static constexpr int o_A = o_C + (WADG ? D::Nh * LPE * QPLp : 0);      // [Nq][LPE][QPLp]: A[b+LPE j][q]
     static constexpr int o_B = o_A + (WADG ? D::Nq * LPE * QPLp : 0);      // [Nq][LPE][RPLp]: B[b+LPE j][q]
     static constexpr int o_wq = o_B + (WADG ? D::Nq * LPE * RPLp : 0);     // [Nq] volume weights
@@ -79,7 +101,21 @@ struct C2 {
     static constexpr int w_ut = 0;                          // [EPW][UTS]  h u v H
     static constexpr int w_geo = w_ut + EPW * UTS;          // [EPW][UTS]  rxJ sxJ ryJ syJ (scaled 1/8)
     static constexpr int w_tr = w_geo + EPW * UTS;          // [EPW][Nfq][4] neighbour traces
-    static constexpr int w_mi = w_tr + EPW * D::Nfq * 4;    // [EPW][MIS]  packed (M_h^k)^-1 (stored inverse)
+    // tensor-core scratch (TC) sizes, laid out below
+    static constexpr int KMQ = KM > KQ ? KM : KQ;
+    static constexpr int TES = 72, TFS = 20;                 // t_in: element and field strides
+    static constexpr int VES = 3 * NhR + 24, VFS = NhR + 8;  // t_vt: element and field strides
+    static constexpr int t_in_ = 32 * KMQ;
+    static constexpr int t_end_ = t_in_ + ((EPW - 1) * TES + 3 * TFS > (EPW - 1) * VES + 3 * VFS
+                                               ? (EPW - 1) * TES + 3 * TFS
+                                               : (EPW - 1) * VES + 3 * VFS);
+    static constexpr int w_mi0 = w_tr + EPW * D::Nfq * 4;
+    // the M = 64 products read A rows of the neighbouring quarters: up to
+    // 32 KA + 192 floats past the operand for the warp of quarter 0, kept
+    // inside the warp's region
+    static constexpr int t_read_ = 32 * KA + 192;
+    static constexpr int t_need_ = t_end_ > t_read_ ? t_end_ : t_read_;
+    static constexpr int w_mi = (TC && t_need_ > w_mi0) ? (t_need_ + 3) & ~3 : w_mi0;  // [EPW][MIS]  packed (M_h^k)^-1
     static constexpr int w_end = (w_mi + (WADG ? 0 : EPW * MIS) + 3) & ~3;
     // scratch aliases, live after the volume/interface phase
     static constexpr int s_rt = w_ut;                       // [3][Nh][EPW]
@@ -89,6 +125,25 @@ struct C2 {
     static_assert(3 * D::Nh <= UTS, "rt scratch");
     static_assert(3 * D::Nq * EPW + 3 * D::Np * EPW <= EPW * UTS, "t/s scratch");
     static_assert(3 * D::Np <= D::Nfq * 4, "u scratch");
+    // tensor-core scratch (TC), aliasing the staging after the volume phase:
+    // t_A the A operand of a contraction over K (16 rows x K, the hi part,
+    // then the lo part at + 16 K; row r, column k at (k / 4) 64 + (r / 8) 32 +
+    // (r % 8) 4 + k % 4: K-direction core matrices 256 bytes apart, 8-row
+    // groups 128 bytes apart); t_in the 16-column MMA results of row (e, f)
+    // at e TES + f TFS, past the operands over modes and volume nodes; t_vt
+    // the values at the hybrid nodes, row (e, f) at e VES + f VFS, in the same
+    // place (t_in is consumed by then).  Strides chosen so that the readers
+    // (8 lanes of each of the 4 elements) hit distinct banks.
+    static constexpr int t_A = 0;
+    static constexpr int t_in = t_in_;
+    static constexpr int t_vt = t_in_;
+    static_assert(!TC || (D::Np <= 16 && D::Nq <= 16), "tensor-core path: one 16-column round for Vq, Vq^T, lift");
+    static_assert(!TC || TFS >= 16 && VFS >= NhR, "row strides");
+    static_assert(!TC || t_end_ <= w_mi, "tensor-core scratch below the inverse-mass staging");
+    // the M = 64 products read A rows of the neighbouring quarters: up to the
+    // lo part's end plus 6 row groups for the warp of quarter 0, which must
+    // stay inside the warp's region
+    static_assert(!TC || 64 * KA + (KA / 4 - 1) * 256 + 8 * 128 <= 4 * w_end, "A operand reads inside the region");
     static constexpr int TRL = (EPW * D::Nfq + 31) / 32;    // neighbour traces gathered per lane
     static constexpr int RKL = (3 * EPW * D::Np + 31) / 32; // RK values per lane (all 32 lanes)
     // RK operands loaded before the lift, else just before the update: late
@@ -111,7 +166,15 @@ struct C2 {
     static constexpr int WARPS_FIT = (SMEM_MAX - 4 * o_end) / (4 * w_end + 8);
     static constexpr int WARPS_CAP = D::Nq <= 16 ? 24 : 16;
     static constexpr int WARPS = WARPS_FIT < WARPS_CAP ? WARPS_FIT : WARPS_CAP;
-    static constexpr size_t bytes() { return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS; }
+    // per-warp mbarriers of the bulk copies; TC: per-warp MMA-completion
+    // mbarriers (byte offset tc_bar), the TMEM address (tc_slot) and the
+    // per-warp phases of the MMA barriers (tc_par)
+    static constexpr int tc_bar = 4 * (o_end + WARPS * w_end) + 8 * WARPS;
+    static constexpr int tc_slot = tc_bar + 8 * WARPS;
+    static constexpr int tc_par = tc_slot + 16;
+    static constexpr size_t bytes() {
+        return sizeof(float) * (size_t(o_end) + size_t(WARPS) * w_end) + 8 * WARPS + (TC ? 8 * WARPS + 16 + 4 * WARPS : 0);
+    }
     static constexpr int TX_BYTES = EPW * (2 * D::Nh * 16 + (WADG ? 0 : NpP4 * 4));
 };
 
@@ -186,8 +249,9 @@ __device__ __forceinline__ float d2f_bits(double d) {
 }
 
 // Rows n = b + LPE j of (M_h^k)^{-1} y for the three fields; y[f][m] at
-// y + (f * Np + m) * EPW; M the packed lower triangle.
-template <int Np, int MPL, int LPE, int EPW>
+// y + f * YF + m * YM (default: [field][mode][element]); M the packed lower
+// triangle.
+template <int Np, int MPL, int LPE, int EPW, int YF = Np * EPW, int YM = EPW>
 __device__ __forceinline__ void minv_rows(const float* __restrict__ M, const float* y, int b, float (&r0)[MPL],
                                           float (&r1)[MPL], float (&r2)[MPL]) {
     const float* rowp[MPL];
@@ -201,7 +265,7 @@ __device__ __forceinline__ void minv_rows(const float* __restrict__ M, const flo
     }
 #pragma unroll
     for (int m = 0; m < Np; ++m) {
-        const float y0 = y[(0 * Np + m) * EPW], y1 = y[(1 * Np + m) * EPW], y2 = y[(2 * Np + m) * EPW];
+        const float y0 = y[m * YM], y1 = y[YF + m * YM], y2 = y[2 * YF + m * YM];
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
             const int n = b + LPE * j;
@@ -213,6 +277,136 @@ __device__ __forceinline__ void minv_rows(const float* __restrict__ M, const flo
             }
         }
     }
+}
+
+// ---- tensor-core rounds (TC) ---------------------------------------------------
+// Offset in an A operand of row r and column k = b + 8 j is tc_off(r, b) +
+// 128 j (columns b + 8 j of a lane b of the 8 lanes of an element).
+__device__ __forceinline__ int tc_off(int r, int b) { return (b >> 2) * 64 + (b & 3) + (r >> 3) * 32 + (r & 7) * 4; }
+
+// The TF32 pair (hi, lo) of v at offset o of an A operand with K columns.
+__device__ __forceinline__ void tc_put_at(float* A, int K, int o, float v) {
+    const float hi = tf32_rn(v);
+    A[o] = hi;
+    A[16 * K + o] = tf32_rn(v - hi);
+}
+
+// The same at row r, any column k.
+__device__ __forceinline__ void tc_put(float* A, int K, int r, int k, float v) {
+    tc_put_at(A, K, tc_off(r, k & 7) + 128 * (k >> 3), v);
+}
+
+// Lanes i < 3 EPW: row i = (element i / 3, field i % 3) of an MMA result,
+// 16 values, to dst + e es + f fs.
+template <int EPW>
+__device__ __forceinline__ void tc_store_rows(float* dst, int es, int fs, int lane, const float (&d)[16]) {
+    if (lane < 3 * EPW) {
+        const int re = lane / 3, rf = lane - (lane / 3) * 3;
+        float4* o = reinterpret_cast<float4*>(dst + re * es + rf * fs);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) o[i] = make_float4(d[4 * i], d[4 * i + 1], d[4 * i + 2], d[4 * i + 3]);
+    }
+}
+
+// try_wait with a suspend-time hint: the thread sleeps until the phase
+// completes or about the hinted time passes, instead of spinning
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(20000u)
+        : "memory");
+    return ok != 0;
+}
+
+// The warp's MMA-completion barrier and its state word (bit 0: the phase to
+// wait for; bit 1: a wait expired, after which the warp issues no more MMAs).
+template <int NR>
+__device__ __forceinline__ uint64_t* tc_bar_of_warp() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<uint64_t*>(smem_raw + C2<NR>::tc_bar) + (threadIdx.x >> 5);
+}
+template <int NR>
+__device__ __forceinline__ uint32_t* tc_state_of_warp() {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return reinterpret_cast<uint32_t*>(smem_raw + C2<NR>::tc_par) + (threadIdx.x >> 5);
+}
+
+// D = A B^T over K (A: this warp's 16 rows at A, K columns; B: 16 rows of a
+// B block, hi part at Bhi and lo part at Blo, row n, column k at (n / 8) 8 K +
+// (k / 4) 32 + (n % 8) 4 + k % 4), accumulated onto the previous round's D
+// when acc0; then, with LOAD, thread i < 16 gets row i of D (16 columns).
+// Three TF32 products per K step of 8 (hi hi, lo hi, hi lo).  The A
+// descriptor starts 16 q rows before this warp's rows (q = warp mod 4), so
+// that they are rows 16 q .. 16 q + 15 of the M = 64 product and land in the
+// warp's own TMEM lane quarter; the other 48 rows read whatever shared memory
+// lies there (inside the block's allocation) and their results are never
+// read.  The warp's TMEM columns, MMA barrier and state word sit at fixed
+// places of the block's shared memory (C::tc_slot, C::tc_bar, C::tc_par).
+// If the bounded wait for the MMAs expires, status gets STATUS_TIMEOUT, the
+// warp's state records it, and this and later rounds of the warp do nothing
+// (the batch loop then stops; the results of the batch are not used).
+template <int NR, int K, bool LOAD = true>
+__device__ __forceinline__ void tc_round(const float* A, const float* Bhi, const float* Blo, bool acc0, int* status,
+                                         int lane, float (&v)[16]) {
+    typedef C2<NR> C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int w = threadIdx.x >> 5, q = w & 3;
+    uint64_t* bar = tc_bar_of_warp<NR>();
+    uint32_t* st = tc_state_of_warp<NR>();
+    const uint32_t tbase = *reinterpret_cast<const uint32_t*>(smem_raw + C::tc_slot) + (uint32_t)(C::TN * w);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes of A -> tensor-core reads
+    __syncwarp();
+    const uint32_t s0 = *st;
+    if (s0 & 2u) return;
+    if (lane == 0) {
+        tc_fence_after();
+        // descriptors of the first K step; a step of 8 advances A by two
+        // K-direction core matrices (512 bytes) and B by two (256 bytes), i.e.
+        // the start-address field (bytes / 16) by 32 and 16
+        const uint32_t a0 = smem_u32(A) - 256u * (uint32_t)q;
+        const uint64_t ahi = tc_sdesc(a0, 256u, 128u), alo = tc_sdesc(a0 + 64u * K, 256u, 128u);
+        const uint64_t bhi = tc_sdesc(smem_u32(Bhi), 128u, 32u * K), blo = tc_sdesc(smem_u32(Blo), 128u, 32u * K);
+        constexpr uint32_t id = tc_idesc_tf32(64, 16);
+#pragma unroll
+        for (int kc = 0; kc < K / 8; ++kc) {
+            tc_mma_tf32(tbase, ahi + 32u * kc, bhi + 16u * kc, id, (acc0 || kc > 0) ? 1u : 0u);
+            tc_mma_tf32(tbase, alo + 32u * kc, bhi + 16u * kc, id, 1u);
+            tc_mma_tf32(tbase, ahi + 32u * kc, blo + 16u * kc, id, 1u);
+        }
+        tc_commit(smem_u32(bar));
+    }
+    const uint32_t ph = s0 & 1u;
+    const long long t0 = clock64();
+    bool ok = true;
+    while (!mbar_try_wait_sleep(bar, ph)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            ok = false;
+            break;
+        }
+    }
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();  // every lane has read the state word
+    if (lane == 0) {
+        if (ok) {
+            *st = ph ^ 1u;
+        } else {
+            *st = s0 | 2u;
+            atomicOr(status, STATUS_TIMEOUT);
+        }
+    }
+    __syncwarp();
+    if (!ok) return;
+    tc_fence_after();
+    if constexpr (LOAD) tc_ld16(tbase + ((uint32_t)(32 * q) << 16), v);
+    tc_fence_before();
+}
+
+// true once one of the warp's MMA waits has expired
+template <int NR>
+__device__ __forceinline__ bool tc_failed() {
+    return (*tc_state_of_warp<NR>() & 2u) != 0;
 }
 
 // Neighbour traces of the batch starting at e0 (a gather): lane handles
@@ -237,18 +431,104 @@ __device__ __forceinline__ void gather_traces(const StageParams<float>& p, const
     }
 }
 
+// The projection chain of stage2_project on the tensor cores: the new FP32
+// state u is already in the A operand (rows 3 e + f, K over modes).
+// u_q = Vq u (MMA), v(u_q) w J at this lane's volume nodes, y = Vq^T (w J v)
+// (MMA), v_h = (M_h^k)^{-1} y (per element, FP32 pipes), v~ = Vh v_h (MMA, in
+// 16-node chunks) into v0..v2 at the lane's hybrid rows.
+template <int N>
+__device__ __forceinline__ void tc_project(const StageParams<float>& p, const float* __restrict__ ops, const float* Mi,
+                                           float* ws, int ge, int lane, const float (&bqv)[C2<N>::QPL],
+                                           const float (&wqv)[C2<N>::QPL], float (&v0)[C2<N>::RPL],
+                                           float (&v1)[C2<N>::RPL], float (&v2)[C2<N>::RPL], int& bad) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const float g = p.g;
+    const bool valid = ge < p.K;
+    float* tA = ws + C::t_A;
+    float* tin = ws + C::t_in;
+    const float* tb = ops + C::o_tc;
+    int of[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) of[f] = tc_off(3 * e + f, b);
+    float d[16] = {};
+    // u_q = Vq u
+    tc_round<N, C::KM>(tA, tb + C::tb_vq, tb + C::tb_vq + C::NqR * C::KM, false, p.status, lane, d);
+    tc_store_rows<EPW>(tin, C::TES, C::TFS, lane, d);
+    __syncwarp();
+    // w J v(u_q) at q = b + LPE j into the A operand over the volume nodes
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = b + LPE * j;
+        if (q < C::KQ) {
+            float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+            if (valid && q < D::Nq) {
+                const float* u = tin + e * C::TES + q;
+                const float h = u[0];
+                if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                const float ih = 1.f / h;
+                const float uu = u[C::TFS] * ih, vv = u[2 * C::TFS] * ih;
+                const float wj = wqv[j];
+                t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
+                t1 = wj * uu;
+                t2 = wj * vv;
+            }
+            tc_put_at(tA, C::KQ, of[0] + 128 * j, t0);
+            tc_put_at(tA, C::KQ, of[1] + 128 * j, t1);
+            tc_put_at(tA, C::KQ, of[2] + 128 * j, t2);
+        }
+    }
+    // y = Vq^T (w J v)
+    tc_round<N, C::KQ>(tA, tb + C::tb_vqt, tb + C::tb_vqt + C::NpR * C::KQ, false, p.status, lane, d);
+    tc_store_rows<EPW>(tin, C::TES, C::TFS, lane, d);
+    __syncwarp();
+    // v_h = (M_h^k)^{-1} y into the A operand over the modes (zero past Np)
+    {
+        float r0[MPL], r1[MPL], r2[MPL];
+        minv_rows<D::Np, MPL, LPE, EPW, C::TFS, 1>(Mi, tin + e * C::TES, b, r0, r1, r2);
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const bool in = b + LPE * j < D::Np;
+            tc_put_at(tA, C::KM, of[0] + 128 * j, in ? r0[j] : 0.f);
+            tc_put_at(tA, C::KM, of[1] + 128 * j, in ? r1[j] : 0.f);
+            tc_put_at(tA, C::KM, of[2] + 128 * j, in ? r2[j] : 0.f);
+        }
+    }
+    // v~ = Vh v_h, 16 hybrid nodes a round (t_vt aliases t_in, consumed by now)
+    float* tvt = ws + C::t_vt;
+#pragma unroll 1
+    for (int c = 0; c < C::NhR / 16; ++c) {
+        tc_round<N, C::KM>(tA, tb + C::tb_vh + 16 * C::KM * c, tb + C::tb_vh + (C::NhR + 16 * c) * C::KM, false,
+                    p.status, lane, d);
+        tc_store_rows<EPW>(tvt + 16 * c, C::VES, C::VFS, lane, d);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int l = b + LPE * j;
+        const float* v = tvt + e * C::VES + (l < D::Nh ? l : 0);
+        v0[j] = v[0];
+        v1[j] = v[C::VFS];
+        v2[j] = v[2 * C::VFS];
+    }
+}
+
 // Entropy projection of a batch's new state (Sec. 2.6): u (FP32 modal, in us
 // as [field][mode][EPW]) -> u~ = u(Vh v_h) at the hybrid nodes, written to
 // ut_out as float4 (h, u, v, H).  Mi: the element's packed (M_h^k)^{-1}
 // (unused with the weight-adjusted inverse, which reads w J through wqv);
 // ts, ss: scratch; bqv, wqv: b and w J at this lane's volume nodes q = b +
-// LPE j; blv: b at its hybrid rows.
+// LPE j; blv: b at its hybrid rows.  With the tensor-core contractions (C::TC)
+// the state is in the warp's A operand instead of us, and ws is the warp's
+// region.  Returns false if a bounded wait expired.
 template <int N>
-__device__ __forceinline__ void stage2_project(const StageParams<float>& p, float* __restrict__ ut_out,
+__device__ __forceinline__ bool stage2_project(const StageParams<float>& p, float* __restrict__ ut_out,
                                                const float* __restrict__ ops, const float* Mi, const float* us,
                                                float* ts, float* ss, int ge, int lane,
                                                const float (&bqv)[C2<N>::QPL], const float (&wqv)[C2<N>::QPL],
-                                               const float (&blv)[C2<N>::RPL]) {
+                                               const float (&blv)[C2<N>::RPL], float* ws = nullptr) {
     typedef Dims<N> D;
     typedef C2<N> C;
     constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
@@ -257,149 +537,153 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
     const float ig = 1.f / g;
     const bool valid = ge < p.K;
     int bad = 0;
-    // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
-    {
-        float q0[QPL], q1[QPL], q2[QPL];
-#pragma unroll
-        for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
-        for (int n = 0; n < D::Np; ++n) {
-            const float u0 = us[(0 * D::Np + n) * EPW + e];
-            const float u1 = us[(1 * D::Np + n) * EPW + e];
-            const float u2 = us[(2 * D::Np + n) * EPW + e];
-            const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
-#pragma unroll
-            for (int j = 0; j < QPL; ++j) {
-                q0[j] = fmaf(v[j], u0, q0[j]);
-                q1[j] = fmaf(v[j], u1, q1[j]);
-                q2[j] = fmaf(v[j], u2, q2[j]);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < QPL; ++j) {
-            const int q = b + LPE * j;
-            if (q < D::Nq) {
-                float t0 = 0.f, t1 = 0.f, t2 = 0.f;
-                if (valid) {
-                    const float h = q0[j];
-                    if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
-                    const float ih = 1.f / h;
-                    const float uu = q1[j] * ih, vv = q2[j] * ih;
-                    const float wj = wqv[j];
-                    t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
-                    t1 = wj * uu;
-                    t2 = wj * vv;
-                }
-                ts[(0 * D::Nq + q) * EPW + e] = t0;
-                ts[(1 * D::Nq + q) * EPW + e] = t1;
-                ts[(2 * D::Nq + q) * EPW + e] = t2;
-            }
-        }
-    }
-    __syncwarp();
     float v0[RPL], v1[RPL], v2[RPL];
-    if constexpr (C::WADG) {
-        // weight-adjusted: z = (w/J) o (A (w J v)) at the volume nodes q = b + LPE*j
-        float c0[QPL], c1[QPL], c2[QPL];
+    if constexpr (C::TC) {
+        tc_project<N>(p, ops, Mi, ws, ge, lane, bqv, wqv, v0, v1, v2, bad);
+    } else {
+        // ---- entropy projection of the new state: u_q = Vq u, v(u_q) w J -------
+        {
+            float q0[QPL], q1[QPL], q2[QPL];
 #pragma unroll
-        for (int j = 0; j < QPL; ++j) c0[j] = c1[j] = c2[j] = 0.f;
-        for (int q2 = 0; q2 < D::Nq; ++q2) {
-            const float t0 = ts[(0 * D::Nq + q2) * EPW + e];
-            const float t1 = ts[(1 * D::Nq + q2) * EPW + e];
-            const float t2 = ts[(2 * D::Nq + q2) * EPW + e];
-            const float* v = ops + C::o_A + (q2 * LPE + b) * C::QPLp;
+            for (int j = 0; j < QPL; ++j) q0[j] = q1[j] = q2[j] = 0.f;
+            for (int n = 0; n < D::Np; ++n) {
+                const float u0 = us[(0 * D::Np + n) * EPW + e];
+                const float u1 = us[(1 * D::Np + n) * EPW + e];
+                const float u2 = us[(2 * D::Np + n) * EPW + e];
+                const float* v = ops + C::o_Vq + (n * LPE + b) * C::QPLp;
+#pragma unroll
+                for (int j = 0; j < QPL; ++j) {
+                    q0[j] = fmaf(v[j], u0, q0[j]);
+                    q1[j] = fmaf(v[j], u1, q1[j]);
+                    q2[j] = fmaf(v[j], u2, q2[j]);
+                }
+            }
 #pragma unroll
             for (int j = 0; j < QPL; ++j) {
-                c0[j] = fmaf(v[j], t0, c0[j]);
-                c1[j] = fmaf(v[j], t1, c1[j]);
-                c2[j] = fmaf(v[j], t2, c2[j]);
-            }
-        }
-        __syncwarp();  // every lane has read w J v
-#pragma unroll
-        for (int j = 0; j < QPL; ++j) {
-            const int q = b + LPE * j;
-            if (q < D::Nq) {
-                const float w = ops[C::o_wq + q];
-                const float sc = valid ? w * w / wqv[j] : 0.f;
-                ts[(0 * D::Nq + q) * EPW + e] = c0[j] * sc;
-                ts[(1 * D::Nq + q) * EPW + e] = c1[j] * sc;
-                ts[(2 * D::Nq + q) * EPW + e] = c2[j] * sc;
+                const int q = b + LPE * j;
+                if (q < D::Nq) {
+                    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+                    if (valid) {
+                        const float h = q0[j];
+                        if (!(h > 0.f)) bad |= STATUS_NONPOSITIVE;
+                        const float ih = 1.f / h;
+                        const float uu = q1[j] * ih, vv = q2[j] * ih;
+                        const float wj = wqv[j];
+                        t0 = wj * (g * (h + bqv[j]) - 0.5f * (uu * uu + vv * vv));
+                        t1 = wj * uu;
+                        t2 = wj * vv;
+                    }
+                    ts[(0 * D::Nq + q) * EPW + e] = t0;
+                    ts[(1 * D::Nq + q) * EPW + e] = t1;
+                    ts[(2 * D::Nq + q) * EPW + e] = t2;
+                }
             }
         }
         __syncwarp();
-        // v~ = B z at the hybrid nodes l = b + LPE*j
+        if constexpr (C::WADG) {
+            // weight-adjusted: z = (w/J) o (A (w J v)) at the volume nodes q = b + LPE*j
+            float c0[QPL], c1[QPL], c2[QPL];
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
-        for (int q = 0; q < D::Nq; ++q) {
-            const float z0 = ts[(0 * D::Nq + q) * EPW + e];
-            const float z1 = ts[(1 * D::Nq + q) * EPW + e];
-            const float z2 = ts[(2 * D::Nq + q) * EPW + e];
-            const float* v = ops + C::o_B + (q * LPE + b) * C::RPLp;
+            for (int j = 0; j < QPL; ++j) c0[j] = c1[j] = c2[j] = 0.f;
+            for (int q2 = 0; q2 < D::Nq; ++q2) {
+                const float t0 = ts[(0 * D::Nq + q2) * EPW + e];
+                const float t1 = ts[(1 * D::Nq + q2) * EPW + e];
+                const float t2 = ts[(2 * D::Nq + q2) * EPW + e];
+                const float* v = ops + C::o_A + (q2 * LPE + b) * C::QPLp;
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                v0[j] = fmaf(v[j], z0, v0[j]);
-                v1[j] = fmaf(v[j], z1, v1[j]);
-                v2[j] = fmaf(v[j], z2, v2[j]);
+                for (int j = 0; j < QPL; ++j) {
+                    c0[j] = fmaf(v[j], t0, c0[j]);
+                    c1[j] = fmaf(v[j], t1, c1[j]);
+                    c2[j] = fmaf(v[j], t2, c2[j]);
+                }
             }
-        }
-    } else {
-        // y = Vq^T (w J v), modes n = b + LPE*j
-        {
-            float y0[MPL], y1[MPL], y2[MPL];
+            __syncwarp();  // every lane has read w J v
 #pragma unroll
-            for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+            for (int j = 0; j < QPL; ++j) {
+                const int q = b + LPE * j;
+                if (q < D::Nq) {
+                    const float w = ops[C::o_wq + q];
+                    const float sc = valid ? w * w / wqv[j] : 0.f;
+                    ts[(0 * D::Nq + q) * EPW + e] = c0[j] * sc;
+                    ts[(1 * D::Nq + q) * EPW + e] = c1[j] * sc;
+                    ts[(2 * D::Nq + q) * EPW + e] = c2[j] * sc;
+                }
+            }
+            __syncwarp();
+            // v~ = B z at the hybrid nodes l = b + LPE*j
+#pragma unroll
+            for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
             for (int q = 0; q < D::Nq; ++q) {
-                const float t0 = ts[(0 * D::Nq + q) * EPW + e];
-                const float t1 = ts[(1 * D::Nq + q) * EPW + e];
-                const float t2 = ts[(2 * D::Nq + q) * EPW + e];
-                const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+                const float z0 = ts[(0 * D::Nq + q) * EPW + e];
+                const float z1 = ts[(1 * D::Nq + q) * EPW + e];
+                const float z2 = ts[(2 * D::Nq + q) * EPW + e];
+                const float* v = ops + C::o_B + (q * LPE + b) * C::RPLp;
+#pragma unroll
+                for (int j = 0; j < RPL; ++j) {
+                    v0[j] = fmaf(v[j], z0, v0[j]);
+                    v1[j] = fmaf(v[j], z1, v1[j]);
+                    v2[j] = fmaf(v[j], z2, v2[j]);
+                }
+            }
+        } else {
+            // y = Vq^T (w J v), modes n = b + LPE*j
+            {
+                float y0[MPL], y1[MPL], y2[MPL];
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) y0[j] = y1[j] = y2[j] = 0.f;
+                for (int q = 0; q < D::Nq; ++q) {
+                    const float t0 = ts[(0 * D::Nq + q) * EPW + e];
+                    const float t1 = ts[(1 * D::Nq + q) * EPW + e];
+                    const float t2 = ts[(2 * D::Nq + q) * EPW + e];
+                    const float* v = ops + C::o_VqT + (q * LPE + b) * C::MPLp;
+#pragma unroll
+                    for (int j = 0; j < MPL; ++j) {
+                        y0[j] = fmaf(v[j], t0, y0[j]);
+                        y1[j] = fmaf(v[j], t1, y1[j]);
+                        y2[j] = fmaf(v[j], t2, y2[j]);
+                    }
+                }
 #pragma unroll
                 for (int j = 0; j < MPL; ++j) {
-                    y0[j] = fmaf(v[j], t0, y0[j]);
-                    y1[j] = fmaf(v[j], t1, y1[j]);
-                    y2[j] = fmaf(v[j], t2, y2[j]);
+                    const int n = b + LPE * j;
+                    if (n < D::Np) {
+                        ss[(0 * D::Np + n) * EPW + e] = y0[j];
+                        ss[(1 * D::Np + n) * EPW + e] = y1[j];
+                        ss[(2 * D::Np + n) * EPW + e] = y2[j];
+                    }
                 }
             }
-#pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * D::Np + n) * EPW + e] = y0[j];
-                    ss[(1 * D::Np + n) * EPW + e] = y1[j];
-                    ss[(2 * D::Np + n) * EPW + e] = y2[j];
-                }
-            }
-        }
-        __syncwarp();
-        // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
-        {
-            float r0[MPL], r1[MPL], r2[MPL];
-            minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
             __syncwarp();
+            // v_h = (M_h^k)^{-1} y, in place (modes n = b + LPE*j)
+            {
+                float r0[MPL], r1[MPL], r2[MPL];
+                minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
+                __syncwarp();
 #pragma unroll
-            for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * D::Np + n) * EPW + e] = r0[j];
-                    ss[(1 * D::Np + n) * EPW + e] = r1[j];
-                    ss[(2 * D::Np + n) * EPW + e] = r2[j];
+                for (int j = 0; j < MPL; ++j) {
+                    const int n = b + LPE * j;
+                    if (n < D::Np) {
+                        ss[(0 * D::Np + n) * EPW + e] = r0[j];
+                        ss[(1 * D::Np + n) * EPW + e] = r1[j];
+                        ss[(2 * D::Np + n) * EPW + e] = r2[j];
+                    }
                 }
             }
-        }
-        __syncwarp();
-        // v~ = Vh v_h at the hybrid nodes l = b + LPE*j
+            __syncwarp();
+            // v~ = Vh v_h at the hybrid nodes l = b + LPE*j
 #pragma unroll
-        for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
-        for (int n = 0; n < D::Np; ++n) {
-            const float w0 = ss[(0 * D::Np + n) * EPW + e];
-            const float w1 = ss[(1 * D::Np + n) * EPW + e];
-            const float w2 = ss[(2 * D::Np + n) * EPW + e];
-            const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
+            for (int j = 0; j < RPL; ++j) v0[j] = v1[j] = v2[j] = 0.f;
+            for (int n = 0; n < D::Np; ++n) {
+                const float w0 = ss[(0 * D::Np + n) * EPW + e];
+                const float w1 = ss[(1 * D::Np + n) * EPW + e];
+                const float w2 = ss[(2 * D::Np + n) * EPW + e];
+                const float* v = ops + C::o_Vh + (n * LPE + b) * C::RPLp;
 #pragma unroll
-            for (int j = 0; j < RPL; ++j) {
-                v0[j] = fmaf(v[j], w0, v0[j]);
-                v1[j] = fmaf(v[j], w1, v1[j]);
-                v2[j] = fmaf(v[j], w2, v2[j]);
+                for (int j = 0; j < RPL; ++j) {
+                    v0[j] = fmaf(v[j], w0, v0[j]);
+                    v1[j] = fmaf(v[j], w1, v1[j]);
+                    v2[j] = fmaf(v[j], w2, v2[j]);
+                }
             }
         }
     }
@@ -425,6 +709,139 @@ __device__ __forceinline__ void stage2_project(const StageParams<float>& p, floa
         }
     }
     if (bad) atomicOr(p.status, bad);
+    return true;
+}
+
+// The manufactured-solution forcing of Sec. 4.1 (sine solution) at volume
+// node q of element ge, J-weighted: w J f.
+template <int N>
+__device__ __forceinline__ void mms_forcing_at(const StageParams<float>& p, int ge, int q, float& f0, float& f1,
+                                               float& f2) {
+    typedef Dims<N> D;
+    const float g = p.g;
+    const float x = p.xq[(size_t)ge * D::Nq + q], y = p.yq[(size_t)ge * D::Nq + q];
+    const float wj = p.wJq[(size_t)ge * D::Nq + q];
+    float sth, cth, sx, cx, sy, cy;
+    sincospif(x + y - (float)p.t, &sth, &cth);
+    sincospif(x, &sx, &cx);
+    sincospif(y, &sy, &cy);
+    const float pi = 3.14159265358979323846f;
+    const float h = 2.f + p.mms_amp * sth;
+    const float cc = p.mms_amp * pi * cth;
+    const float bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
+    const float u0 = p.mms_u0, v0 = p.mms_v0;
+    f0 = wj * (-cc + u0 * cc + v0 * cc);
+    f1 = wj * (-u0 * cc + (u0 * u0 + g * h) * cc + u0 * v0 * cc + g * h * bx);
+    f2 = wj * (-v0 * cc + u0 * v0 * cc + (v0 * v0 + g * h) * cc + g * h * by);
+}
+
+// The rest of a batch after the volume and interface phase, with the dense
+// contractions on the tensor cores: the lift s = Vh^T r - Vq^T (W J f) (MMA),
+// du/dt = -(M_h^k)^{-1} s (FP32 pipes, modes n = b + LPE j of each lane),
+// then du/dt out (MODE 0) or the LSRK45 stage in FP64 on the same lanes and
+// the entropy projection of the new state (MODE 1).  a0..a2: the rows
+// l = b + LPE i of the volume and interface terms.
+template <int N, int MODE>
+__device__ __forceinline__ void tc_batch_tail(const StageParams<float>& p, float* __restrict__ ut_out, double rkA,
+                                              double rkB, const float* __restrict__ ops, float* ws, int e0, int lane,
+                                              const float (&a0)[C2<N>::RPL], const float (&a1)[C2<N>::RPL],
+                                              const float (&a2)[C2<N>::RPL]) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, EPW = C::EPW, RPL = C::RPL, QPL = C::QPL, MPL = C::MPL;
+    const int e = lane / LPE, b = lane - (lane / LPE) * LPE;
+    const int K = p.K;
+    const int ge = e0 + e;
+    const bool valid = ge < K;
+    float* tA = ws + C::t_A;
+    float* tin = ws + C::t_in;
+    const float* tb = ops + C::o_tc;
+    const float* Mi = ws + C::w_mi + e * C::MIS;
+    int of[3];
+#pragma unroll
+    for (int f = 0; f < 3; ++f) of[f] = tc_off(3 * e + f, b);
+    // the volume and face rows as the A operand of the lift (zero past Nh)
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) {
+        if (b + LPE * i < C::KL) {
+            const bool in = b + LPE * i < D::Nh;
+            tc_put_at(tA, C::KL, of[0] + 128 * i, in ? a0[i] : 0.f);
+            tc_put_at(tA, C::KL, of[1] + 128 * i, in ? a1[i] : 0.f);
+            tc_put_at(tA, C::KL, of[2] + 128 * i, in ? a2[i] : 0.f);
+        }
+    }
+    float d[16] = {};
+    if (!p.forcing) {
+        tc_round<N, C::KL>(tA, tb + C::tb_lift, tb + C::tb_lift + C::NpR * C::KL, false, p.status, lane, d);
+    } else {
+        tc_round<N, C::KL, false>(tA, tb + C::tb_lift, tb + C::tb_lift + C::NpR * C::KL, false, p.status, lane, d);
+        // the lift's operand is consumed: -W J f over the volume nodes, accumulated
+#pragma unroll
+        for (int j = 0; j < QPL; ++j) {
+            const int q = b + LPE * j;
+            if (q < C::KQ) {
+                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
+                if (valid && q < D::Nq) mms_forcing_at<N>(p, ge, q, f0, f1, f2);
+                tc_put_at(tA, C::KQ, of[0] + 128 * j, -f0);
+                tc_put_at(tA, C::KQ, of[1] + 128 * j, -f1);
+                tc_put_at(tA, C::KQ, of[2] + 128 * j, -f2);
+            }
+        }
+        tc_round<N, C::KQ>(tA, tb + C::tb_vqt, tb + C::tb_vqt + C::NpR * C::KQ, true, p.status, lane, d);
+    }
+    tc_store_rows<EPW>(tin, C::TES, C::TFS, lane, d);
+    __syncwarp();
+    float r0[MPL], r1[MPL], r2[MPL];
+    minv_rows<D::Np, MPL, LPE, EPW, C::TFS, 1>(Mi, tin + e * C::TES, b, r0, r1, r2);
+    const float* rr[3] = {r0, r1, r2};
+    if constexpr (MODE == 0) {
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (valid && n < D::Np) p.rhs_out[((size_t)f * K + ge) * D::Np + n] = (double)(-rr[f][j]);
+            }
+        return;
+    }
+    // b and w J at this lane's nodes for the projection
+    float bqv[QPL], wqv[QPL], blv[RPL];
+#pragma unroll
+    for (int j = 0; j < QPL; ++j) {
+        const int q = b + LPE * j;
+        bqv[j] = wqv[j] = 0.f;
+        if (valid && q < D::Nq) {
+            bqv[j] = __ldg(p.bh + (size_t)ge * D::Nh + q);
+            wqv[j] = __ldg(p.wJq + (size_t)ge * D::Nq + q);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int l = b + LPE * j;
+        blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
+    }
+    // LSRK45 stage in FP64 at the lane's modes: res = A res + dt du/dt,
+    // u += B res; the new FP32 state as the A operand of u_q = Vq u (zero past Np)
+    const float dtf = (float)p.dt;
+    double* const u_out = p.u_out;  // host-state calls: the last stage also writes the state there
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int j = 0; j < MPL; ++j) {
+            const int n = b + LPE * j;
+            double un = 1.0;
+            if (valid && n < D::Np) {
+                const size_t gi = ((size_t)f * K + ge) * D::Np + n;
+                const double r = rkA != 0.0 ? p.res[gi] : 0.0;  // the first LSRK45 stage (A = 0) does not read it
+                const double rs = fma(rkA, r, f2d_bits(dtf * (-rr[f][j])));
+                un = fma(rkB, rs, p.u[gi]);
+                p.res[gi] = rs;
+                p.u[gi] = un;
+                if (u_out) u_out[gi] = un;
+            }
+            tc_put_at(tA, C::KM, of[f] + 128 * j, n < D::Np ? d2f_bits(un) : 0.f);
+        }
+    stage2_project<N>(p, ut_out, ops, Mi, nullptr, nullptr, nullptr, ge, lane, bqv, wqv, blv, ws);
 }
 
 // One batch of EPW elements of one problem, starting at element e0 (all 32
@@ -593,6 +1010,9 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
     __syncwarp();  // every lane is done with the u~ / metric staging
+    if constexpr (C::TC) {
+        tc_batch_tail<N, MODE>(p, ut_out, rkA, rkB, ops, ws, e0, lane, a0, a1, a2);
+    } else {
     float* rt = ws + C::s_rt;
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
@@ -630,28 +1050,17 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     if (MODE == 1 && C::EARLY_RK) load_rk();
     // forcing at the volume nodes, J-weighted (added as + Vq^T W J f)
     float* ts = ws + C::s_t;
+    auto forcing_at = [&](int q, float& f0, float& f1, float& f2) {
+        f0 = f1 = f2 = 0.f;
+        if (valid && q < D::Nq) mms_forcing_at<N>(p, ge, q, f0, f1, f2);
+    };
     if (p.forcing) {
 #pragma unroll
         for (int j = 0; j < QPL; ++j) {
             const int q = b + LPE * j;
             if (q < D::Nq) {
-                float f0 = 0.f, f1 = 0.f, f2 = 0.f;
-                if (valid) {
-                    const float x = p.xq[(size_t)ge * D::Nq + q], y = p.yq[(size_t)ge * D::Nq + q];
-                    const float wj = p.wJq[(size_t)ge * D::Nq + q];
-                    float sth, cth, sx, cx, sy, cy;
-                    sincospif(x + y - (float)p.t, &sth, &cth);
-                    sincospif(x, &sx, &cx);
-                    sincospif(y, &sy, &cy);
-                    const float pi = 3.14159265358979323846f;
-                    const float h = 2.f + p.mms_amp * sth;
-                    const float cc = p.mms_amp * pi * cth;
-                    const float bx = -p.mms_bamp * pi * sx * cy, by = -p.mms_bamp * pi * cx * sy;
-                    const float u0 = p.mms_u0, v0 = p.mms_v0;
-                    f0 = wj * (-cc + u0 * cc + v0 * cc);
-                    f1 = wj * (-u0 * cc + (u0 * u0 + g * h) * cc + u0 * v0 * cc + g * h * bx);
-                    f2 = wj * (-v0 * cc + u0 * v0 * cc + (v0 * v0 + g * h) * cc + g * h * by);
-                }
+                float f0, f1, f2;
+                forcing_at(q, f0, f1, f2);
                 ts[(0 * D::Nq + q) * EPW + e] = f0;
                 ts[(1 * D::Nq + q) * EPW + e] = f1;
                 ts[(2 * D::Nq + q) * EPW + e] = f2;
@@ -845,11 +1254,15 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
     __syncwarp();
-    if constexpr (MODE == 1) stage2_project<N>(p, ut_out, ops, Mi, us, ts, ss, ge, lane, bqv, wqv, blv);
+    if constexpr (MODE == 1) {
+        if (!stage2_project<N>(p, ut_out, ops, Mi, us, ts, ss, ge, lane, bqv, wqv, blv, ws)) return false;
+    }
+    }
     // generic-proxy writes to the staging area must be ordered before the
     // next batch's bulk copies overwrite it
     fence_proxy_async_smem();
     __syncwarp();
+    if constexpr (C::TC) return !tc_failed<N>();
     return true;
 }
 
@@ -895,21 +1308,30 @@ __device__ __forceinline__ bool project2_batch(const StageParams<float>& p, floa
         const int ee = o / D::Np, n = o - ee * D::Np;
         const size_t gi = ((size_t)c * K + e0) * D::Np + o;
         const double un = e0 + ee < K ? p.u_in[gi] : 1.0;
-        us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
+        if constexpr (C::TC)
+            tc_put(ws + C::t_A, C::KM, 3 * ee + c, n, d2f_bits(un));
+        else
+            us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
         if (p.copy_in && e0 + ee < K) {
             p.u[gi] = un;
             p.res[gi] = 0.0;
         }
+    }
+    if constexpr (C::TC) {
+        if (lane < 3 * EPW)
+            for (int n = D::Np; n < C::KM; ++n) tc_put(ws + C::t_A, C::KM, lane, n, 0.f);
     }
     if constexpr (!C::WADG) {
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(bar, parity, p.status))) return false;
         parity ^= 1;
     }
     __syncwarp();
-    stage2_project<N>(p, ut_out, ops, ws + C::w_mi + e * C::MIS, us, ws + C::s_t, ws + C::s_s, ge, lane, bqv, wqv,
-                      blv);
+    if (!stage2_project<N>(p, ut_out, ops, ws + C::w_mi + e * C::MIS, us, ws + C::s_t, ws + C::s_s, ge, lane, bqv,
+                           wqv, blv, ws))
+        return false;
     fence_proxy_async_smem();
     __syncwarp();
+    if constexpr (C::TC) return !tc_failed<N>();
     return true;
 }
 
@@ -926,8 +1348,19 @@ __global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<flo
         reinterpret_cast<float4*>(ops)[i] = reinterpret_cast<const float4*>(ops2)[i];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) mbar_init(&bars[warp], 1);
+    // tensor cores: one MMA-completion barrier per warp, and 512 TMEM columns
+    // for the block (one block per SM), 16 for each warp
+    if constexpr (C::TC) {
+        if (lane == 0) {
+            mbar_init(reinterpret_cast<uint64_t*>(smem_raw + C::tc_bar) + warp, 1);
+            reinterpret_cast<uint32_t*>(smem_raw + C::tc_par)[warp] = 0u;
+        }
+        if (warp == 0) tc_alloc(smem_u32(smem_raw + C::tc_slot), 512);
+    }
     fence_mbar_init();
+    if constexpr (C::TC) tc_fence_before();
     __syncthreads();
+    if constexpr (C::TC) tc_fence_after();
     uint64_t* bar = &bars[warp];
     float* ws = ops + C::o_end + warp * C::w_end;
     uint32_t parity = 0;
@@ -936,13 +1369,28 @@ __global__ void __launch_bounds__(C2<N>::WARPS * 32, 1) k_stage2(StageParams<flo
     // per-batch work otherwise keeps them in lockstep).
     __nanosleep((unsigned)(warp >> 2) * 1300u);
     const int nbatch = Kpad / C::EPW;
-    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps)
-        if constexpr (MODE == 2) {
-            if (!project2_batch<N>(p, p.ut_out, ops, ws, bar, parity, batch * C::EPW, lane)) return;
-        } else {
-            if (!stage2_batch<N, MODE>(p, p.ut_in, p.ut_out, p.rkA, p.rkB, ops, ws, bar, parity, batch * C::EPW, lane))
-                return;
+    for (int batch = blockIdx.x * nwarps + warp; batch < nbatch; batch += gridDim.x * nwarps) {
+        bool ok;
+        if constexpr (MODE == 2)
+            ok = project2_batch<N>(p, p.ut_out, ops, ws, bar, parity, batch * C::EPW, lane);
+        else
+            ok = stage2_batch<N, MODE>(p, p.ut_in, p.ut_out, p.rkA, p.rkB, ops, ws, bar, parity, batch * C::EPW,
+                                       lane);
+        if (!ok) break;  // a bounded wait expired (status set)
+    }
+    if constexpr (C::TC) {
+        // every warp's MMAs have completed (each waited for its own; after an
+        // expired wait, once more with a bound); free the tensor memory
+        if (tc_failed<N>()) {
+            const long long t1 = clock64();
+            while (!mbar_try_wait(tc_bar_of_warp<N>(), *tc_state_of_warp<N>() & 1u) && clock64() - t1 < (1LL << 31)) {
+            }
         }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (warp == 0) tc_dealloc(*reinterpret_cast<const uint32_t*>(smem_raw + C::tc_slot), 512);
+    }
 }
 
 // ---- ensembles: several independent problems in one persistent launch --------

@@ -36,6 +36,10 @@ ESDG_MASS_EXACT = 0
 ESDG_MASS_WEIGHT_ADJUSTED = 1
 ESDG_METHOD_MODAL = 0
 ESDG_METHOD_SBP = 1
+ESDG_DENSE_AUTO = 0
+ESDG_DENSE_SIMT = 1
+ESDG_DENSE_TENSOR = 2
+DENSE = {"auto": ESDG_DENSE_AUTO, "simt": ESDG_DENSE_SIMT, "tensor": ESDG_DENSE_TENSOR}
 ESDG_POINTS_NODAL = 0
 ESDG_POINTS_VOLQ = 1
 ESDG_POINTS_FACEQ = 2
@@ -76,7 +80,7 @@ class Config(ctypes.Structure):
                 ("mms_amp", ctypes.c_double), ("mms_bamp", ctypes.c_double),
                 ("mms_u0", ctypes.c_double), ("mms_v0", ctypes.c_double),
                 ("volume_rule", ctypes.c_int), ("boundary", ctypes.c_int), ("mass", ctypes.c_int),
-                ("method", ctypes.c_int)]
+                ("method", ctypes.c_int), ("dense", ctypes.c_int)]
 
 
 _lib = None
@@ -160,11 +164,13 @@ def _ptr(a):
 
 def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, warp=0.0, g=1.0, cfl=0.25,
                 lax_friedrichs=True, forcing="none", mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False,
-                mass="exact", method="modal"):
+                mass="exact", method="modal", dense="auto"):
     if mass not in ("exact", "weight_adjusted"):
         raise ValueError("mass must be 'exact' or 'weight_adjusted'")
     if method not in ("modal", "sbp"):
         raise ValueError("method must be 'modal' or 'sbp'")
+    if dense not in DENSE:
+        raise ValueError("dense must be one of %s" % sorted(DENSE))
     cfg = Config()
     cfg.N, cfg.nx, cfg.ny = N, nx, ny
     cfg.precision = ESDG_FP32 if precision == "fp32" else ESDG_FP64
@@ -178,6 +184,7 @@ def make_config(N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0, w
     cfg.boundary = ESDG_BOUNDARY_WALLS if walls else ESDG_BOUNDARY_PERIODIC
     cfg.mass = ESDG_MASS_WEIGHT_ADJUSTED if mass == "weight_adjusted" else ESDG_MASS_EXACT
     cfg.method = ESDG_METHOD_SBP if method == "sbp" else ESDG_METHOD_MODAL
+    cfg.dense = DENSE[dense]
     return cfg
 
 
@@ -303,12 +310,12 @@ class Solver:
     def __init__(self, N, nx, ny, precision="fp64", x0=-1.0, x1=1.0, y0=-1.0, y1=1.0,
                  warp=0.0, g=1.0, cfl=0.25, lax_friedrichs=True, forcing="none",
                  mms=(0.1, 0.1, 0.5, 0.5), rule="collapsed", walls=False, mass="exact", method="modal",
-                 torch_memory=True, stream=None, partition=None):
+                 torch_memory=True, stream=None, partition=None, dense="auto"):
         import torch
         self.lib = load_library()
         cfg = make_config(N, nx, ny, precision=precision, x0=x0, x1=x1, y0=y0, y1=y1, warp=warp, g=g, cfl=cfl,
                           lax_friedrichs=lax_friedrichs, forcing=forcing, mms=mms, rule=rule, walls=walls, mass=mass,
-                          method=method)
+                          method=method, dense=dense)
         self.cfg = cfg
         h = ctypes.c_void_p()
         if partition is None:

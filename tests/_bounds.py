@@ -47,6 +47,19 @@ def c_modal(Np, Nq, Nfq, wadg=False):
     return 3 * (3 * Np + Nq + 8) + 2 * Nh + Np + 8
 
 
+def c_modal_tc(Np, Nq, Nfq):
+    """The same bound with the dense contractions (Vq, Vq^T W J, Vh and the
+    lift Vh^T) on the tensor cores: each operand is split into TF32 parts
+    x = x_hi + x_lo and a product is formed as a_hi b_hi + a_lo b_hi + a_hi b_lo,
+    which leaves |a_lo b_lo| and the roundings of the two lo parts, at most
+    3 * 2^-22 = 12 u of |a b|; with the tensor core's FP32 accumulation taken
+    at 2 u per addition, a contraction of n terms carries (12 + 2 n) u instead
+    of n u.  The three projection contractions enter tripled (as the
+    projection does above), the lift once."""
+    Nh = Nq + Nfq
+    return c_modal(Np, Nq, Nfq) + 3 * (36 + 2 * Np + Nq) + 12 + Nh
+
+
 def c_sbp(Nq):
     return 3 * 4 + Nq + 8
 

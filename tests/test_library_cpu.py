@@ -49,6 +49,7 @@ def _cfg(**kw):
     c.boundary = kw.get("boundary", esdg.ESDG_BOUNDARY_PERIODIC)
     c.mass = kw.get("mass", esdg.ESDG_MASS_EXACT)
     c.method = kw.get("method", esdg.ESDG_METHOD_MODAL)
+    c.dense = kw.get("dense", esdg.ESDG_DENSE_AUTO)
     return c
 
 
@@ -144,10 +145,11 @@ def test_weight_adjusted_mass_stores_no_inverses(rule, precision):
     """The weight-adjusted inverse keeps no per-element matrix on the device:
     the footprint drops by the stored inverses, K Np(Np+1)/2 values of the
     RHS precision, less the few KB that the FP32 kernel's composed shared
-    operators add."""
+    operators add (both with the dense operators on the FP32 pipes)."""
     sizes = {}
     for mass in (esdg.ESDG_MASS_EXACT, esdg.ESDG_MASS_WEIGHT_ADJUSTED):
-        lib, rc, h = _build(N=4, nx=16, ny=16, warp=0.05, rule=rule, precision=precision, mass=mass)
+        lib, rc, h = _build(N=4, nx=16, ny=16, warp=0.05, rule=rule, precision=precision, mass=mass,
+                            dense=esdg.ESDG_DENSE_SIMT)
         assert rc == 0
         K, Np = ctypes.c_int(), ctypes.c_int()
         nb = ctypes.c_size_t()
@@ -334,3 +336,44 @@ def test_noalloc_size_limit_is_checked_on_the_host(nx, ny, expect):
             assert b"exceeds the static scratch limit" in lib.esdg_last_error(h)
     finally:
         lib.esdg_destroy(h)
+
+
+@pytest.mark.parametrize("N,rule,precision,mass,dense,ok", [
+    (4, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_TENSOR, True),
+    (3, esdg.ESDG_RULE_COLLAPSED, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_TENSOR, True),
+    (5, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_TENSOR, False),
+    (4, esdg.ESDG_RULE_COLLAPSED, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_TENSOR, False),
+    (2, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP64, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_TENSOR, False),
+    (2, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_WEIGHT_ADJUSTED, esdg.ESDG_DENSE_TENSOR, False),
+    (5, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_AUTO, True),
+    (2, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP64, esdg.ESDG_MASS_EXACT, esdg.ESDG_DENSE_SIMT, True),
+    (2, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, 3, False),
+    (2, esdg.ESDG_RULE_SYMMETRIC, esdg.ESDG_FP32, esdg.ESDG_MASS_EXACT, -1, False),
+])
+def test_dense_operator_kind_is_validated(N, rule, precision, mass, dense, ok):
+    """The tensor-core form of the dense contractions exists for the FP32
+    modal path with the stored inverse where Np <= 16 and Nq <= 16; a request
+    for it elsewhere, or an unknown kind, is refused with ESDG_EINVAL."""
+    lib, rc, h = _build(N=N, nx=4, ny=4, warp=0.05, rule=rule, precision=precision, mass=mass, dense=dense)
+    if ok:
+        assert rc == 0 and h.value
+        lib.esdg_destroy(h)
+    else:
+        assert rc == esdg.ESDG_EINVAL and not h.value
+
+
+def test_tensor_core_context_keeps_the_fp32_pipe_operators():
+    """A tensor-core context stores its operators in both layouts (the
+    tensor-core B blocks for its own kernel, the FP32-pipe layout for
+    ensembles): its footprint exceeds the FP32-pipe context's by a few tens
+    of KB only."""
+    sizes = []
+    for dense in (esdg.ESDG_DENSE_SIMT, esdg.ESDG_DENSE_TENSOR):
+        lib, rc, h = _build(N=4, nx=16, ny=16, warp=0.05, rule=esdg.ESDG_RULE_SYMMETRIC, precision=esdg.ESDG_FP32,
+                            dense=dense)
+        assert rc == 0
+        nb = ctypes.c_size_t()
+        assert lib.esdg_sizes(h, None, None, None, None, ctypes.byref(nb)) == 0
+        sizes.append(nb.value)
+        lib.esdg_destroy(h)
+    assert 0 < sizes[1] - sizes[0] < 64 * 1024

@@ -617,6 +617,24 @@ def run_collapsed(steps, warmup, world, peaks):
     return res
 
 
+def run_dense_other(steps, warmup, world, peaks):
+    """The headline workload with the dense contractions (V_q, V_q^T W J, V_h,
+    the lift) in the form the headline did not use: on the tensor cores
+    (tcgen05, split TF32) when the headline ran them on the FP32 pipes, and the
+    other way round.  Throughput and the HBM fraction on the method's bytes."""
+    other = "simt" if DENSE == "tensor" else "tensor"
+    s = make_solver("fp32", dense=other)
+    el = time_steps(s, steps, warmup, world)
+    t = el / (5 * steps)
+    by = algorithmic_bytes(WL.N, s.Nq)
+    res = {"dense": other, "value": s.K * s.Np * 5 * steps / el / 1e9, "unit": UNIT,
+           "ms_per_step": el / steps * 1e3, "us_per_stage": t * 1e6,
+           "hbm": {"achieved": by * s.K / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                   "frac": by * s.K / t / 1e9 / peaks["hbm_gbs"], "algorithmic_bytes_per_element_stage": by}}
+    s.close()
+    return res
+
+
 def run_partition_one_gpu(steps, px=2, py=2):
     """The element partition's machinery on one device: the bench workload split
     into px x py blocks, run as separate contexts with their halos exchanged by
@@ -986,6 +1004,10 @@ def main():
     if not args.fp32_only and not sbp_main and args.nx is None:
         collapsed = run_collapsed(steps, args.warmup, world, peaks)
 
+    dense_other = None
+    if not args.fp32_only and not sbp_main and args.mass == "exact":
+        dense_other = run_dense_other(steps, args.warmup, world, peaks)
+
     partition_one = None
     if not args.fp32_only and not sbp_main and world == 1:
         partition_one = run_partition_one_gpu(max(10, steps // 5))
@@ -1038,11 +1060,12 @@ def main():
                            "N": WL.N, "K": K, "Np": Np, "Nq": Nq_run,
                            "volume_rule": "sbp" if sbp_main else WL.rule, "curved": True,
                            "mass": args.mass, "method": args.method,
+                           "dense_contractions": "tensor_cores" if args.dense == "tensor" else "fp32_pipes",
                            "rhs_precision": "fp32", "rk_accumulation": "fp64",
                            "l2": "inputs larger than L2 (state, residual, geometry ~0.5 GB)",
                            "parallelism": "replicas" if world > 1 else "single"},
                 "roofline": roofline, "roofline_other": other, "other_mass": other_mass, "sbp": sbp,
-                "collapsed_rule": collapsed, "partition_one_gpu": partition_one,
+                "collapsed_rule": collapsed, "dense_other": dense_other, "partition_one_gpu": partition_one,
                 "fp64": fp64, "precision": precision, "accuracy": accuracy, "volume_ratio": volume_ratio, "context": context, "ensemble": ens, "served": served, "e2e": e2e, "cpu_baseline": cb, "clocks": clk,
                 "gpu_launches": launches, "peaks": peak_kind}
         print(json.dumps(line))

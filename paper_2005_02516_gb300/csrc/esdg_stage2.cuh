@@ -146,6 +146,11 @@ struct C2 {
     static_assert(!TC || 64 * KA + (KA / 4 - 1) * 256 + 8 * 128 <= 4 * w_end, "A operand reads inside the region");
     static constexpr int TRL = (EPW * D::Nfq + 31) / 32;    // neighbour traces gathered per lane
     static constexpr int RKL = (3 * EPW * D::Np + 31) / 32; // RK values per lane (all 32 lanes)
+    // the RK update at the modes n = b + LPE j whose du/dt the inverse mass
+    // leaves in a lane's registers, where that takes no more FP64 warp
+    // instructions than spreading the batch's values over all 32 lanes
+    // (N = 2, 4; measured 2-5% faster there, 4% slower at N = 3)
+    static constexpr bool RK_LANES = 3 * MPL <= RKL;
     // RK operands loaded before the lift, else just before the update: late
     // only for the 31 hybrid nodes of N = 4 with the 16-point rule and the
     // stored inverse, where the early loads push the kernel past 80
@@ -1023,26 +1028,45 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             rt[(2 * D::Nh + l) * EPW + e] = a2[i];
         }
     }
-    // The FP64 RK state of the batch spread over all 32 lanes (j = lane + 32 k
-    // in [field][element][mode] order, which is contiguous per field in global
-    // memory).  Loaded here, so that the latency overlaps the lift and the
-    // inverse mass, where the registers allow it (C::EARLY_RK); otherwise just
-    // before the update (1.2% faster at N = 4 with the stored inverse; 2%
-    // slower where the early loads fit).
+    // The FP64 RK state: at this lane's element and modes n = b + LPE j (the
+    // modes whose du/dt the inverse mass leaves in this lane's registers;
+    // C::RK_LANES), or spread over all 32 lanes (j = lane + 32 k in
+    // [field][element][mode] order, contiguous per field in global memory).
+    // Loaded here, so that the latency overlaps the lift and the inverse mass,
+    // where the registers allow it (C::EARLY_RK); otherwise just before the
+    // update (1.2% faster at N = 4 with the stored inverse; 2% slower where
+    // the early loads fit).
     constexpr int NRK = 3 * EPW * D::Np;
-    double uj[C::RKL], rj[C::RKL];
+    constexpr int RKV = C::RK_LANES ? 3 * MPL : C::RKL;
+    double uj[RKV], rj[RKV];
     auto load_rk = [&]() {
+        if constexpr (C::RK_LANES) {
 #pragma unroll
-        for (int k = 0; k < C::RKL; ++k) {
-            const int j = lane + 32 * k;
-            uj[k] = 0.0;
-            rj[k] = 0.0;
-            if (j < NRK) {
-                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-                if (e0 + o / D::Np < K) {
-                    const size_t gi = ((size_t)c * K + e0) * D::Np + o;
-                    uj[k] = p.u[gi];
-                    if (rkA != 0.0) rj[k] = p.res[gi];  // the first LSRK45 stage (A = 0) does not read it
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const int n = b + LPE * j;
+                    uj[f * MPL + j] = 0.0;
+                    rj[f * MPL + j] = 0.0;
+                    if (valid && n < D::Np) {
+                        const size_t gi = ((size_t)f * K + ge) * D::Np + n;
+                        uj[f * MPL + j] = p.u[gi];
+                        if (rkA != 0.0) rj[f * MPL + j] = p.res[gi];  // the first LSRK45 stage (A = 0) does not read it
+                    }
+                }
+        } else {
+#pragma unroll
+            for (int k = 0; k < C::RKL; ++k) {
+                const int j = lane + 32 * k;
+                uj[k] = 0.0;
+                rj[k] = 0.0;
+                if (j < NRK) {
+                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                    if (e0 + o / D::Np < K) {
+                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                        uj[k] = p.u[gi];
+                        if (rkA != 0.0) rj[k] = p.res[gi];
+                    }
                 }
             }
         }
@@ -1069,6 +1093,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     }
     __syncwarp();
     float* ss = ws + C::s_s;
+    float du[3][MPL];  // du/dt at this lane's modes n = b + LPE j
     float bqv[QPL], wqv[QPL], blv[RPL];
     const float* Mi = ws + C::w_mi + e * C::MIS;  // the stored inverse (unused when weight-adjusted)
     if constexpr (C::WADG) {
@@ -1137,12 +1162,9 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
 #pragma unroll
         for (int j = 0; j < MPL; ++j) {
-            const int n = b + LPE * j;
-            if (n < D::Np) {
-                ss[(0 * EPW + e) * D::Np + n] = -r0[j];
-                ss[(1 * EPW + e) * D::Np + n] = -r1[j];
-                ss[(2 * EPW + e) * D::Np + n] = -r2[j];
-            }
+            du[0][j] = -r0[j];
+            du[1][j] = -r1[j];
+            du[2][j] = -r2[j];
         }
     } else {
         // ---- lift: s = Vh^T rt - Vq^T W J f, modes n = b + LPE*j --------------
@@ -1187,19 +1209,15 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             }
         }
         __syncwarp();
-        // ---- du/dt = -(M_h^k)^{-1} s (modes n = b + LPE*j) into ss as [field][element][mode]
+        // ---- du/dt = -(M_h^k)^{-1} s at the lane's modes n = b + LPE*j, in registers
         {
             float r0[MPL], r1[MPL], r2[MPL];
             minv_rows<D::Np, MPL, LPE, EPW>(Mi, ss + e, b, r0, r1, r2);
-            __syncwarp();
 #pragma unroll
             for (int j = 0; j < MPL; ++j) {
-                const int n = b + LPE * j;
-                if (n < D::Np) {
-                    ss[(0 * EPW + e) * D::Np + n] = -r0[j];
-                    ss[(1 * EPW + e) * D::Np + n] = -r1[j];
-                    ss[(2 * EPW + e) * D::Np + n] = -r2[j];
-                }
+                du[0][j] = -r0[j];
+                du[1][j] = -r1[j];
+                du[2][j] = -r2[j];
             }
         }
     }
@@ -1224,32 +1242,75 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
             blv[j] = (valid && l < D::Nh) ? __ldg(p.bh + (size_t)ge * D::Nh + l) : 0.f;
         }
     }
+    if constexpr (!C::RK_LANES) {
+        // du/dt into ss as [field][element][mode] for the spread-out update
+        __syncwarp();  // every lane has read s (the inverse mass's input aliases ss)
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+            for (int j = 0; j < MPL; ++j) {
+                const int n = b + LPE * j;
+                if (n < D::Np) ss[(f * EPW + e) * D::Np + n] = du[f][j];
+            }
+        __syncwarp();
+    }
     if (MODE == 0) {
-        for (int j = lane; j < NRK; j += 32) {
-            const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-            if (e0 + o / D::Np < K) p.rhs_out[((size_t)c * K + e0) * D::Np + o] = (double)ss[j];
+        if constexpr (C::RK_LANES) {
+#pragma unroll
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const int n = b + LPE * j;
+                    if (valid && n < D::Np) p.rhs_out[((size_t)f * K + ge) * D::Np + n] = (double)du[f][j];
+                }
+        } else {
+            for (int j = lane; j < NRK; j += 32) {
+                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                if (e0 + o / D::Np < K) p.rhs_out[((size_t)c * K + e0) * D::Np + o] = (double)ss[j];
+            }
         }
     } else {
-        // ---- LSRK45 stage in FP64 on all 32 lanes: res = A res + dt rhs, u += B res
+        // ---- LSRK45 stage in FP64: res = A res + dt rhs, u += B res
         if (!C::EARLY_RK) load_rk();
         const float dtf = (float)p.dt;
         double* const u_out = p.u_out;  // host-state calls: the last stage also writes the state there
+        if constexpr (C::RK_LANES) {
 #pragma unroll
-        for (int k = 0; k < C::RKL; ++k) {
-            const int j = lane + 32 * k;
-            if (j < NRK) {
-                const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
-                const int ee = o / D::Np, n = o - ee * D::Np;
-                double un = 1.0;
-                if (e0 + ee < K) {
-                    const size_t gi = ((size_t)c * K + e0) * D::Np + o;
-                    const double rs = fma(rkA, rj[k], f2d_bits(dtf * ss[j]));
-                    un = fma(rkB, rs, uj[k]);
-                    p.res[gi] = rs;
-                    p.u[gi] = un;
-                    if (u_out) u_out[gi] = un;
+            for (int f = 0; f < 3; ++f)
+#pragma unroll
+                for (int j = 0; j < MPL; ++j) {
+                    const int n = b + LPE * j;
+                    if (n < D::Np) {
+                        double un = 1.0;
+                        if (valid) {
+                            const size_t gi = ((size_t)f * K + ge) * D::Np + n;
+                            const double rs = fma(rkA, rj[f * MPL + j], f2d_bits(dtf * du[f][j]));
+                            un = fma(rkB, rs, uj[f * MPL + j]);
+                            p.res[gi] = rs;
+                            p.u[gi] = un;
+                            if (u_out) u_out[gi] = un;
+                        }
+                        us[(f * D::Np + n) * EPW + e] = d2f_bits(un);
+                    }
                 }
-                us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
+        } else {
+#pragma unroll
+            for (int k = 0; k < C::RKL; ++k) {
+                const int j = lane + 32 * k;
+                if (j < NRK) {
+                    const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+                    const int ee = o / D::Np, n = o - ee * D::Np;
+                    double un = 1.0;
+                    if (e0 + ee < K) {
+                        const size_t gi = ((size_t)c * K + e0) * D::Np + o;
+                        const double rs = fma(rkA, rj[k], f2d_bits(dtf * ss[j]));
+                        un = fma(rkB, rs, uj[k]);
+                        p.res[gi] = rs;
+                        p.u[gi] = un;
+                        if (u_out) u_out[gi] = un;
+                    }
+                    us[(c * D::Np + n) * EPW + ee] = d2f_bits(un);
+                }
             }
         }
     }

@@ -38,9 +38,14 @@ WL = W.DAM
 # dram__bytes_write.sum from one ncu capture), per inverse-mass kind, keyed to
 # the sha1 of the kernel source it was measured on: reported as null once that
 # source changes.
-STAGE_TRAFFIC = {"exact": {"source_sha1": "5fe24ebb95a87939dd2fcbeee97a894f26b11c05", "bytes": 429.28e6},
-                 "weight_adjusted": {"source_sha1": "5fe24ebb95a87939dd2fcbeee97a894f26b11c05", "bytes": 361.9e6}}
+STAGE_TRAFFIC = {"exact": {"source_sha1": "4e485b7f63c3ac275e119975cc61955aad8e657e", "bytes": 426.08e6},
+                 "weight_adjusted": {"source_sha1": "4e485b7f63c3ac275e119975cc61955aad8e657e", "bytes": 357.26e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
+# Warp instructions per element-stage of the FP32 stage kernel (ncu
+# smsp__inst_executed.sum / K on the same kernel at K = 32768), keyed the same
+# way: the issue-slot roofline of an issue-bound kernel (one warp instruction
+# per cycle per SM sub-partition).
+STAGE_INSTR = {"exact": {"source_sha1": "4e485b7f63c3ac275e119975cc61955aad8e657e", "per_element_stage": 1160.9}}
 # the same for the FP32 DG-SBP stage kernel
 SBP_TRAFFIC = {"source_sha1": "bc6a6adb39a7b0f39182f3aa3b747208c033571a", "bytes": 386.1e6}
 SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")
@@ -955,6 +960,18 @@ def main():
                 "design_bytes_per_element_stage": (by_s if sbp_main else design_bytes(WL.N, WL.Nq, 4, wadg))}
     roofline = roof_alu if roof_alu["frac"] >= roof_hbm["frac"] else roof_hbm
     other = roof_hbm if roofline is roof_alu else roof_alu
+    # context: the issue-slot roofline (the kernel's own binding limit)
+    irec = None if sbp_main else STAGE_INSTR.get(args.mass)
+    with open(STAGE_SOURCE, "rb") as f:
+        if irec is not None and irec["source_sha1"] == hashlib.sha1(f.read()).hexdigest() and args.dense != "tensor":
+            ipe = irec["per_element_stage"]
+            issue_peak = 152 * 4 * sm_mhz * 1e6 / 1e9
+            other = dict(other)
+            other["issue"] = {"bound": "issue", "instructions_per_element_stage": ipe,
+                              "achieved": ipe * K / t_launch / 1e9, "peak": issue_peak, "unit": "G warp-instructions/s",
+                              "frac": ipe * K / t_launch / 1e9 / issue_peak,
+                              "peak_source": "152 SMs x 4 sub-partitions x 1 warp instruction per cycle x %.0f MHz"
+                              % sm_mhz}
 
     # The other inverse-mass kind on the same workload, same steps, for
     # comparison: its throughput, HBM roofline fraction and the relative L2

@@ -1450,7 +1450,7 @@ static int ensemble_table(esdg_ensemble* e) {
     e->slab = slab;
     e->nmax = nmax <= 4 ? 4 : 5;
     const int n = int(h.size());
-    e->smem = 4 * (size_t(ops) + size_t(e->warps) * slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(e->warps);
+    e->smem = 4 * (size_t(ops) + size_t(e->warps) * slab) + 4 * size_t((n + 1 + 3) & ~3) + (8 + sizeof(StageParams<float>)) * size_t(e->warps);
     ECUDA_TRY(e, cudaMemcpyAsync(e->dmem, h.data(), sizeof(EnsembleMember) * n, cudaMemcpyHostToDevice, e->stream));
     ECUDA_TRY(e, cudaStreamSynchronize(e->stream));
     if (e->graph) {
@@ -1462,7 +1462,7 @@ static int ensemble_table(esdg_ensemble* e) {
 
 static int ensemble_fits(esdg_ensemble* e, int warps) {
     const int n = int(e->members.size());
-    size_t need = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(warps);
+    size_t need = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + (8 + sizeof(StageParams<float>)) * size_t(warps);
     return need <= 232448;
 }
 
@@ -1491,7 +1491,7 @@ static int ensemble_prepare(esdg_ensemble* e) {
 static int ensemble_set_shape(esdg_ensemble* e, int warps) {
     e->warps = warps;
     const int n = int(e->members.size());
-    e->smem = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + 8 * size_t(warps);
+    e->smem = 4 * (size_t(e->ops_end) + size_t(warps) * e->slab) + 4 * size_t((n + 1 + 3) & ~3) + (8 + sizeof(StageParams<float>)) * size_t(warps);
     cudaError_t err = e->rule == ESDG_RULE_SYMMETRIC ? ensemble_smem_attr<1>(e->nmax, e->smem)
                                                      : ensemble_smem_attr<0>(e->nmax, e->smem);
     if (err != cudaSuccess) return efail(e, ESDG_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(err));

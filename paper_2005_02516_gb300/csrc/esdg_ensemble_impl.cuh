@@ -7,6 +7,16 @@
 
 namespace esdg {
 
+// One batch of a member of degree NR: a call, not inlined, so that each
+// degree's body is allocated registers on its own.
+template <int NR>
+__device__ __noinline__ bool ensemble_batch(const StageParams<float>& p, const float* __restrict__ ut_in,
+                                            float* __restrict__ ut_out, double rkA, double rkB,
+                                            const float* __restrict__ ops, float* ws, uint64_t* bar,
+                                            uint32_t& parity, int e0, int lane) {
+    return stage2_batch<NR, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane);
+}
+
 // One LSRK45 stage for every member.  ops_off[N]: float offset of degree N's
 // operators in shared memory (-1 if no member has that degree); slab: floats
 // per warp region (the largest over the degrees present).
@@ -40,6 +50,12 @@ k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_ba
     __syncthreads();
     uint64_t* bar = &bars[warp];
     float* ws = sm + ops_end + warp * slab;
+    // the current member's parameters, copied into this warp's slot of shared
+    // memory when the member changes: read from there they take no registers
+    // through the batch (read from the member table in global memory they
+    // would be loaded early and held)
+    StageParams<float>* pw = reinterpret_cast<StageParams<float>*>(bars + nwarps) + warp;
+    int cur = -1;
     uint32_t parity = 0;
     for (int gb = blockIdx.x * nwarps + warp; gb < total_batches; gb += gridDim.x * nwarps) {
         int lo = 0, hi = nmem - 1;  // the member whose batch range holds gb
@@ -48,7 +64,15 @@ k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_ba
             if (tile[mid] <= gb) lo = mid; else hi = mid - 1;
         }
         const EnsembleMember& M = mem[lo];
-        const StageParams<float>& p = M.p;
+        if (lo != cur) {
+            __syncwarp();
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(&M.p);
+            uint32_t* dst = reinterpret_cast<uint32_t*>(pw);
+            for (int i = lane; i < (int)(sizeof(StageParams<float>) / 4); i += 32) dst[i] = src[i];
+            __syncwarp();
+            cur = lo;
+        }
+        const StageParams<float>& p = *pw;
         const float* ut_in = M.ut[which];
         float* ut_out = M.ut[which ^ 1];
         const int e0 = (gb - tile[lo]) * 4;
@@ -56,12 +80,12 @@ k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_ba
         const float* ops = sm + (n == 1 ? ops_lo.x : n == 2 ? ops_lo.y : n == 3 ? ops_lo.z : n == 4 ? ops_lo.w : ops_hi);
         bool ok = true;
         switch (n) {
-            case 1: ok = stage2_batch<1 + 8 * RULE, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
-            case 2: ok = stage2_batch<2 + 8 * RULE, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
-            case 3: ok = stage2_batch<3 + 8 * RULE, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
-            case 4: ok = stage2_batch<4 + 8 * RULE, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
+            case 1: ok = ensemble_batch<1 + 8 * RULE>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
+            case 2: ok = ensemble_batch<2 + 8 * RULE>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
+            case 3: ok = ensemble_batch<3 + 8 * RULE>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
+            case 4: ok = ensemble_batch<4 + 8 * RULE>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane); break;
             default:
-                if (NMAX >= 5) ok = stage2_batch<5 + 8 * RULE, 1>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane);
+                if (NMAX >= 5) ok = ensemble_batch<5 + 8 * RULE>(p, ut_in, ut_out, rkA, rkB, ops, ws, bar, parity, e0, lane);
                 break;
         }
         if (!ok) return;

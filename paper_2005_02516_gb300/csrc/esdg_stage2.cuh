@@ -717,6 +717,24 @@ __device__ __forceinline__ bool stage2_project(const StageParams<float>& p, floa
     return true;
 }
 
+// Host-state calls: the batch's new FP64 state, just written to p.u at each
+// lane's modes, copied to the caller's (host-resident) u_out in contiguous
+// runs (j = lane + 32 k in [field][element][mode] order): writes over the host
+// link in whole 256-byte runs rather than 64-byte pieces.
+template <int N>
+__device__ __forceinline__ void copy_state_out(const StageParams<float>& p, double* u_out, int e0, int lane) {
+    typedef Dims<N> D;
+    constexpr int EPW = C2<N>::EPW, NRK = 3 * EPW * D::Np;
+    __syncwarp();  // the warp's writes of p.u are visible to its lanes
+    for (int j = lane; j < NRK; j += 32) {
+        const int c = j / (EPW * D::Np), o = j - c * (EPW * D::Np);
+        if (e0 + o / D::Np < p.K) {
+            const size_t gi = ((size_t)c * p.K + e0) * D::Np + o;
+            u_out[gi] = p.u[gi];
+        }
+    }
+}
+
 // The manufactured-solution forcing of Sec. 4.1 (sine solution) at volume
 // node q of element ge, J-weighted: w J f.
 template <int N>
@@ -842,10 +860,10 @@ __device__ __forceinline__ void tc_batch_tail(const StageParams<float>& p, float
                 un = fma(rkB, rs, p.u[gi]);
                 p.res[gi] = rs;
                 p.u[gi] = un;
-                if (u_out) u_out[gi] = un;
             }
             tc_put_at(tA, C::KM, of[f] + 128 * j, n < D::Np ? d2f_bits(un) : 0.f);
         }
+    if (u_out) copy_state_out<N>(p, u_out, e0, lane);
     stage2_project<N>(p, ut_out, ops, Mi, nullptr, nullptr, nullptr, ge, lane, bqv, wqv, blv, ws);
 }
 
@@ -1288,11 +1306,11 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
                             un = fma(rkB, rs, uj[f * MPL + j]);
                             p.res[gi] = rs;
                             p.u[gi] = un;
-                            if (u_out) u_out[gi] = un;
                         }
                         us[(f * D::Np + n) * EPW + e] = d2f_bits(un);
                     }
                 }
+            if (u_out) copy_state_out<N>(p, u_out, e0, lane);
         } else {
 #pragma unroll
             for (int k = 0; k < C::RKL; ++k) {

@@ -127,3 +127,24 @@ def test_tensor_core_refused_where_it_does_not_exist(kw):
     with pytest.raises(esdg.EsdgError) as ei:
         esdg.Solver(kw.pop("N"), 4, 4, precision=kw.pop("precision", "fp32"), dense="tensor", **kw)
     assert ei.value.code == esdg.ESDG_EINVAL
+
+
+def test_tensor_core_full_size_sampled_rhs():
+    """The smoothed dam break at full size (N = 4, K = 131072 curved, the
+    16-point symmetric rule), the tensor-core form in its launch
+    configuration: the right-hand side on sampled elements (every 997th,
+    plus the first and last) against the oracle element by element, within
+    the split-TF32 bound."""
+    w = W.DAM
+    s = _solver(w, w.N, w.nx, w.nx, w.rule)
+    o = Oracle(w.N, w.nx, w.nx, ax=w.warp, ay=w.warp, g=w.g, cfl=w.cfl, rule=w.rule)
+    xo, yo = o.points("nodal")
+    o.set_bathymetry(w.bathymetry(xo, yo))
+    xq, yq = o.points("volq")
+    u = o.init_state(w.initial(xq, yq))
+    s.set_state(u)
+    ks = np.unique(np.concatenate([np.arange(0, o.K, 997), [o.K - 1]]))
+    got = s.rhs(0.0).cpu().numpy()[:, ks]
+    want = o.rhs_elements(u, ks)
+    check_fp32_rhs(got, want, o.rhs_term_magnitude(u, 0.0, elems=ks), c_modal_tc(o.Np, o.Nq, o.Nfq))
+    s.close()

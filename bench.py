@@ -424,6 +424,7 @@ def run_served(rate, precision, duration_s, budget_gb=64.0, seed=W.BASE_SEED, dr
         elif drain:
             raise RuntimeError("request %d failed with state %d" % (i, state))
     iters, steps, _, max_active = srv.stats()
+    loop_s = srv.timing()
     srv.close()
     lat = np.array(lat) if lat else np.array([np.nan])
     res = {"precision": precision, "rate_per_s": rate, "arrival_window_s": duration_s, "requests": n,
@@ -431,6 +432,7 @@ def run_served(rate, precision, duration_s, budget_gb=64.0, seed=W.BASE_SEED, dr
            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(np.mean(lat)),
            "throughput": done_units / wall / 1e9, "unit": UNIT, "wall_s": wall, "iterations": iters,
            "max_active_in_one_iteration": max_active,
+           "loop_seconds": {k: round(v, 3) for k, v in loop_s.items()},
            "drain_after_last_arrival_s": (last_done - trace[-1].t_arrival) if drain and n else None,
            "distributions": "N U{2..5}, K log-uniform [512, 131072], steps U[100, 2000]"}
     return res

@@ -433,6 +433,11 @@ int esdg_server_drain(esdg_server* srv, double timeout_s);
  * output may be NULL. */
 int esdg_server_stats(esdg_server* srv, long long* iterations, long long* steps, size_t* bytes_in_use,
                       int* max_active_seen);
+/* Where the worker thread's time went, seconds since creation, into
+ * seconds[0..4]: admission (device allocation and the copy of each prepared
+ * image), ensemble rebuilds (membership changes), enqueueing each iteration's
+ * work, waiting for the GPU, retiring results (status checks, result copies). */
+int esdg_server_timing(esdg_server* srv, double* seconds);
 /* Drops queued requests (state ESDG_ESTATE), ends running ones after their
  * current iteration (at most 20 steps; state ESDG_ESTATE, no result written),
  * releases everything. */

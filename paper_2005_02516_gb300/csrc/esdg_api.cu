@@ -1550,7 +1550,7 @@ int esdg_ensemble_create(esdg_ctx* const* members, int n, esdg_ensemble** out) {
     }
     int rc = ensemble_table(e);
     if (!rc) {
-        int w = ENSEMBLE_MAX_WARPS;
+        int w = ensemble_max_warps(e->nmax);
         while (w > 1 && !ensemble_fits(e, w)) --w;
         rc = ensemble_set_shape(e, w);
     }
@@ -1632,7 +1632,8 @@ int esdg_ensemble_autotune(esdg_ensemble* e, int* warps_out, int* order_out) {
     for (int o = 0; o < 2 && !rc; ++o) {
         e->order = o == 0 ? given : bydeg;
         rc = ensemble_table(e);
-        for (int w : {ENSEMBLE_MAX_WARPS - 4, ENSEMBLE_MAX_WARPS - 2, ENSEMBLE_MAX_WARPS}) {
+        const int W = ensemble_max_warps(e->nmax);
+        for (int w : {W - 4, W - 2, W}) {
             if (rc || !ensemble_fits(e, w)) continue;
             rc = ensemble_set_shape(e, w);
             if (!rc) rc = ensemble_prepare(e);

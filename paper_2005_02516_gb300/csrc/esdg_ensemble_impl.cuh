@@ -21,7 +21,7 @@ __device__ __noinline__ bool ensemble_batch(const StageParams<float>& p, const f
 // operators in shared memory (-1 if no member has that degree); slab: floats
 // per warp region (the largest over the degrees present).
 template <int NMAX, int RULE>
-__global__ void __launch_bounds__(ENSEMBLE_MAX_WARPS * 32, 1)
+__global__ void __launch_bounds__(ensemble_max_warps(NMAX) * 32, 1)
 k_stage2_ensemble(const EnsembleMember* __restrict__ mem, int nmem, int total_batches, int which, double rkA,
                   double rkB, int4 ops_lo, int ops_hi, int ops_end, int slab) {
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -80,6 +80,10 @@ struct esdg_server {
     std::vector<Request*> ens_members[2];
     long long iterations = 0, steps_run = 0;
     int max_active_seen = 0;  // the most requests any one iteration advanced
+    // where the worker's time goes (seconds): admission (allocation and the
+    // copy of each prepared image), ensemble rebuilds, enqueueing the
+    // iteration's work, waiting for the GPU, retiring results
+    double t_admit = 0, t_rebuild = 0, t_launch = 0, t_wait = 0, t_retire = 0;
     std::string err;
 };
 
@@ -177,7 +181,11 @@ static void run(esdg_server* s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        admit(s, lk);
+        {
+            const Clock::time_point a0 = Clock::now();
+            admit(s, lk);
+            s->t_admit += std::chrono::duration<double>(Clock::now() - a0).count();
+        }
         if (s->stop) {
             // esdg_server_destroy: running requests end after their last iteration
             for (Request* r : s->active) finish(s, r, ESDG_ESTATE, "server destroyed while the request ran");
@@ -196,17 +204,23 @@ static void run(esdg_server* s) {
         std::vector<int> adv(act.size());
         for (size_t i = 0; i < act.size(); ++i) adv[i] = std::min(chunk, act[i]->remaining);
         int rc = ESDG_OK;
+        double t_rb = 0;
+        const Clock::time_point l0 = Clock::now();
         for (int rule = 0; rule < 2 && !rc; ++rule) {
+            const Clock::time_point r0 = Clock::now();
             rc = refresh_ensemble(s, act, rule, chunk);
+            t_rb += std::chrono::duration<double>(Clock::now() - r0).count();
             if (!rc && s->ens[rule]) rc = esdg_ensemble_step_async(s->ens[rule], chunk);
         }
         for (size_t i = 0; i < act.size() && !rc; ++i) {
             Request* r = act[i];
             if (r->precision == ESDG_FP64 || r->remaining < chunk) rc = esdg_step_async(r->ctx, adv[i], r->dt, r->t);
         }
+        const Clock::time_point w0 = Clock::now();
         cudaStreamSynchronize(s->stream);
         for (Request* r : act)
             if (r->stream) cudaStreamSynchronize(r->stream);
+        const Clock::time_point w1 = Clock::now();
         std::vector<std::pair<Request*, int>> outcome;
         for (Request* r : act) {
             int st = rc ? rc : esdg_check(r->ctx);
@@ -222,6 +236,10 @@ static void run(esdg_server* s) {
             if (r->remaining == 0) outcome[i].second = esdg_copy_state(r->ctx, r->result, 0);
         }
         lk.lock();
+        s->t_rebuild += t_rb;
+        s->t_launch += std::chrono::duration<double>(w0 - l0).count() - t_rb;
+        s->t_wait += std::chrono::duration<double>(w1 - w0).count();
+        s->t_retire += std::chrono::duration<double>(Clock::now() - w1).count();
         s->iterations += 1;
         s->steps_run += stepped;
         s->max_active_seen = std::max(s->max_active_seen, (int)act.size());
@@ -350,6 +368,17 @@ int esdg_server_stats(esdg_server* s, long long* iterations, long long* steps, s
     if (iterations) *iterations = s->iterations;
     if (steps) *steps = s->steps_run;
     if (bytes_in_use) *bytes_in_use = s->in_use;
+    return ESDG_OK;
+}
+
+int esdg_server_timing(esdg_server* s, double* seconds) {
+    if (!s || !seconds) return ESDG_EINVAL;
+    std::lock_guard<std::mutex> lk(s->mu);
+    seconds[0] = s->t_admit;
+    seconds[1] = s->t_rebuild;
+    seconds[2] = s->t_launch;
+    seconds[3] = s->t_wait;
+    seconds[4] = s->t_retire;
     return ESDG_OK;
 }
 

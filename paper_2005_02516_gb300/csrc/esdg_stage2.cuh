@@ -1489,6 +1489,9 @@ struct EnsembleMember {
 // 20 warps then run without spills, 7% faster than 16 warps at 128 registers
 // with the bodies inlined (config 4: 9.45 against 8.80 GDOF-stage/s).
 constexpr int ENSEMBLE_MAX_WARPS = 20;
+// With degree-5 members (whose body needs 128 registers, as in k_stage2) the
+// instantiation that carries the degree-5 path runs 16 warps.
+constexpr int ensemble_max_warps(int nmax) { return nmax >= 5 ? 16 : ENSEMBLE_MAX_WARPS; }
 
 // Host wrappers of the ensemble kernel (esdg_ensemble_impl.cuh), one
 // instantiation per volume rule RULE (0 collapsed, 1 symmetric) in its own

@@ -57,7 +57,7 @@ EXPORTS = ["esdg_build_operators", "esdg_sizes", "esdg_attach_device", "esdg_get
            "esdg_ensemble_create", "esdg_ensemble_autotune", "esdg_ensemble_step",
            "esdg_ensemble_step_async", "esdg_ensemble_destroy", "esdg_ensemble_error",
            "esdg_get_config", "esdg_prepare", "esdg_server_create", "esdg_server_submit", "esdg_server_query",
-           "esdg_server_drain", "esdg_server_stats", "esdg_server_destroy",
+           "esdg_server_drain", "esdg_server_stats", "esdg_server_timing", "esdg_server_destroy",
            "esdg_volume_kernel", "esdg_volume_kernel_host", "esdg_step_host", "esdg_selftest_wait_timeout",
            "esdg_l2_error", "esdg_build_partition", "esdg_partition_info", "esdg_partition_maps",
            "esdg_get_neighbors", "esdg_project", "esdg_stage", "esdg_halo_pack", "esdg_halo_unpack"]
@@ -128,6 +128,7 @@ def load_library(path=LIB_PATH):
         "esdg_server_query": ([P, I, PI, PD, PD, PD], I),
         "esdg_server_drain": ([P, D], I),
         "esdg_server_stats": ([P, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong), PS, PI], I),
+        "esdg_server_timing": ([P, P], I),
         "esdg_server_destroy": ([P], I),
         "esdg_volume_kernel": ([I, I, I, I, D, P, P, P, P, P], I),
         "esdg_volume_kernel_host": ([I, I, I, I, D, P, P, P, P], I),
@@ -287,6 +288,13 @@ class Server:
         it, st, b, m = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_size_t(), ctypes.c_int()
         self.lib.esdg_server_stats(self.h, ctypes.byref(it), ctypes.byref(st), ctypes.byref(b), ctypes.byref(m))
         return it.value, st.value, b.value, m.value
+
+    def timing(self):
+        """Seconds the server's worker spent admitting, rebuilding ensembles,
+        enqueueing, waiting for the GPU and retiring results."""
+        t = (ctypes.c_double * 5)()
+        self.lib.esdg_server_timing(self.h, t)
+        return dict(zip(("admit", "rebuild", "launch", "wait", "retire"), list(t)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -75,6 +75,9 @@ def test_served_results_equal_alone(rules):
     srv.drain(300.0)
     iters, steps, inuse, _ = srv.stats()
     assert inuse == 0 and iters > 0
+    tm = srv.timing()  # the worker's time by phase: all non-negative, and it waited on the GPU
+    assert set(tm) == {"admit", "rebuild", "launch", "wait", "retire"}
+    assert all(v >= 0.0 for v in tm.values()) and tm["wait"] > 0.0
     for tk, req, prec, (b, q) in zip(tickets, trace, precisions, inputs):
         state, ts, ta, td = srv.query(tk)
         assert state == 2 and ts <= ta <= td

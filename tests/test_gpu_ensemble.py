@@ -54,7 +54,10 @@ def test_ensemble_matches_members_alone(nsteps, rule):
         u0.append(u)
     ens = esdg.Ensemble(mix)
     warps, order = ens.autotune()
-    assert warps in (12, 14, 16) and order in (0, 1)
+    # the autotuner's candidates: 16, 18, 20 warps, or 12, 14, 16 when a
+    # member has degree 5 (that instantiation runs at most 16 warps)
+    top = 16 if max(N for N, _, _ in MEMBERS) >= 5 else 20
+    assert warps in (top - 4, top - 2, top) and order in (0, 1)
     # the autotuner leaves the states as they were
     for s, u in zip(mix, u0):
         assert np.array_equal(s.get_state(), u)

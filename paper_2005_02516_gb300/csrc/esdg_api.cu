@@ -46,6 +46,7 @@ struct DevLayout {
     size_t ops = 0, ops_bytes = 0;       // reference operators (real)
     size_t ops2 = 0, ops2_bytes = 0;     // permuted operators of the FP32 batched kernel
     size_t ops2s = 0, ops2s_bytes = 0;   // tensor-core contexts: the FP32-pipe layout too (ensembles)
+    size_t qxy = 0, qxy_bytes = 0;       // FP64 unique-pair schedule: stored metric-averaged operator
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
@@ -140,6 +141,7 @@ static int stage2_nr(const esdg_config& cfg) { return kernel_nr(cfg) + (use_tc(c
 // the FP32 stage kernel's template parameters: the above and the tensor-core forms
 #define ESDG_FOR_EACH_NR2(X) ESDG_FOR_EACH_NR(X) X(33) X(34) X(35) X(41) X(42) X(43) X(44)
 
+static int pair_steps(int NR);
 static int c2_ops_floats(int NR);
 
 static void compute_layout(esdg_ctx* c) {
@@ -174,6 +176,8 @@ static void compute_layout(esdg_ctx* c) {
     // no stored inverses with the weight-adjusted inverse or the diagonal SBP mass
     L.minv = take((sbp || weight_adjusted(c->cfg)) ? 0 : rs * Kp * c->mstride);
     L.bh = take(rs * Kp * nrec);
+    L.qxy_bytes = (c->cfg.precision == ESDG_FP64 && !sbp) ? 8 * Kp * size_t(pair_steps(kernel_nr(c->cfg))) * 64 : 0;
+    L.qxy = take(L.qxy_bytes);
     L.nbr = take(4 * Kp * 3);
     L.fmap = take(sbp ? 4 * size_t(R.Nfq) : 0);
     const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
@@ -423,6 +427,70 @@ static void put(std::vector<unsigned char>& img, size_t off, const std::vector<T
     std::memcpy(img.data() + off, v.data(), v.size() * sizeof(T));
 }
 
+// The FP64 kernel's unique-pair schedule (PairSched in esdg_kernels.cuh):
+// steps per element, 0 where the rule is too large for it.
+static int pair_steps(int NR) {
+    switch (NR) {
+#define X(v) case v: return PairSched<v>::SPLIT ? PairSched<v>::NSTEP : 0;
+        ESDG_FOR_EACH_NR(X)
+#undef X
+    }
+    return 0;
+}
+
+// The metric-averaged skew operator entries the FP64 kernel's lanes take,
+// element by element and step by step: lane (half-warp hf, row j) of step s
+// pairs volume row j with column m (the kernel's diagonal schedule) and holds
+// Qx = q_r (rx_j + rx_m) + q_s (sx_j + sx_m), Qy likewise with ry, sy, where
+// (q_r, q_s) = (Qskew^r, Qskew^s)[j][m] and the metrics are the kernel's own
+// (geo, [K][Nh][4], scaled by 1/8 as the kernel scales them); zero where the
+// lane has no pair.  Stage-independent.
+template <int NR>
+static std::vector<double> pair_operator_t(const esdg_ctx* c, const std::vector<double>& geo) {
+    typedef PairSched<NR> PS;
+    const RefOps& R = c->ref;
+    const int Nh = R.Nh, K = c->mesh.K;
+    std::vector<double> q(size_t(c->Kpad) * PS::NSTEP * 64, 0.0);
+    if (!PS::SPLIT) return q;
+    for (int e = 0; e < K; ++e) {
+        const double* g = geo.data() + size_t(e) * Nh * 4;
+        for (int st = 0; st < PS::NSTEP; ++st)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int j = lane & 15, hf = lane >> 4;
+                int m = -1;
+                if (st < PS::SVV0) {
+                    const int d = hf == 0 ? 1 + st : PS::SVV0 + 1 + st;
+                    if (j < PS::V && d <= PS::SVV && !(2 * d == PS::V && j >= PS::V / 2)) m = (j + d) % PS::V;
+                } else {
+                    const int k = st - PS::SVV0;
+                    const int t = hf == 0 ? k : PS::SVF0 + k;
+                    const int f = (j + t) % PS::L;
+                    if (j < PS::V && t < PS::L && f < PS::F) m = PS::V + f;
+                }
+                if (m < 0) continue;
+                const double qr = R.Qsr(j, m), qs = R.Qss(j, m);
+                const double* gj = g + 4 * j;
+                const double* gm = g + 4 * m;
+                double* o = q.data() + ((size_t(e) * PS::NSTEP + st) * 32 + lane) * 2;
+                // the kernel carries the metrics scaled by 1/8 (exact)
+                o[0] = qr * (0.125 * gj[0] + 0.125 * gm[0]) + qs * (0.125 * gj[1] + 0.125 * gm[1]);
+                o[1] = qr * (0.125 * gj[2] + 0.125 * gm[2]) + qs * (0.125 * gj[3] + 0.125 * gm[3]);
+            }
+    }
+    return q;
+}
+
+template <typename real>
+static std::vector<double> pair_operator(const esdg_ctx* c, const std::vector<real>& geo) {
+    std::vector<double> g(geo.begin(), geo.end());
+    switch (kernel_nr(c->cfg)) {
+#define X(v) case v: return pair_operator_t<v>(c, g);
+        ESDG_FOR_EACH_NR(X)
+#undef X
+    }
+    return {};
+}
+
 template <typename real>
 static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     const RefOps& R = c->ref;
@@ -445,6 +513,7 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
         std::vector<real> geo(M.geo.size());
         for (size_t i = 0; i < geo.size(); ++i) geo[i] = (real)(gscale * M.geo[i]);
         put(img, c->L.geo, geo);
+        if (c->L.qxy_bytes) put(img, c->L.qxy, pair_operator(c, geo));
         if (c->cfg.precision == ESDG_FP32) put(img, c->L.ops2, pack_ops2(R, stage2_nr(c->cfg)));
         if (use_tc(c->cfg)) put(img, c->L.ops2s, pack_ops2(R, kernel_nr(c->cfg)));
     }
@@ -597,6 +666,7 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.walls = c->cfg.boundary == ESDG_BOUNDARY_WALLS;
     p.xq = reinterpret_cast<const real*>(d + c->L.xq);
     p.yq = reinterpret_cast<const real*>(d + c->L.yq);
+    p.qxy = reinterpret_cast<const real*>(d + c->L.qxy);
     p.u = reinterpret_cast<double*>(d + c->L.u);
     p.u_in = p.u;
     p.res = reinterpret_cast<double*>(d + c->L.res);

@@ -52,6 +52,19 @@ struct Dims {
     static constexpr int NpP = Np * (Np + 1) / 2;
 };
 
+// The FP64 kernel's unique-pair schedule (rules with Nq <= 16 and Nh <= 32):
+// volume-volume pairs along the diagonals (j, j + d mod V), d = 1..SVV, the
+// two half-warps taking d <= SVV0 and d > SVV0; volume-face pairs along
+// (j, V + (j + t) mod L), t < L, split the same way: NSTEP steps in all.
+template <int NR>
+struct PairSched {
+    typedef Dims<NR> D;
+    static constexpr bool SPLIT = D::Nq <= 16 && D::Nh <= 32;
+    static constexpr int V = D::Nq, F = D::Nfq, L = V > F ? V : F;
+    static constexpr int SVV = V / 2, SVV0 = (SVV + 1) / 2, SVF0 = (L + 1) / 2;
+    static constexpr int NSTEP = SVV0 + SVF0;
+};
+
 // status bits written by the device
 constexpr int STATUS_NONPOSITIVE = 1;
 constexpr int STATUS_NONFINITE = 2;
@@ -81,6 +94,11 @@ struct StageParams {
     int walls;         // reflective walls present (Sec. 2.9)
     const real* xq;    // [K][Nq]   (forcing only)
     const real* yq;
+    // FP64 unique-pair schedule: the metric-averaged skew operator entries
+    // (Qskew^x, Qskew^y)[j][m] of the pair each lane takes in each step,
+    // [K][NSTEP][32][2] (zero where the lane has no pair); stage-independent,
+    // formed once on the host
+    const real* qxy;
     // state
     const double* u_in;  // [3][K][Np]  (projection input)
     double* u;           // [3][K][Np]  RK state (updated in place)
@@ -457,25 +475,24 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         constexpr bool SPLIT = D::Nq <= 16 && D::Nh <= 32;
         real tl0 = 0, tl1 = 0, tl2 = 0;  // the lane's own row sums after the pair loop
         if constexpr (SPLIT) {
-            constexpr int V = D::Nq, F = D::Nfq, L = V > F ? V : F;
+            typedef PairSched<N> PS;
+            constexpr int V = PS::V, F = PS::F, L = PS::L;
             static_assert(L <= 16, "one half-warp per diagonal");
-            constexpr int SVV = V / 2;            // volume-volume diagonals d = 1..SVV
-            constexpr int SVV0 = (SVV + 1) / 2;   // half 0: d = 1..SVV0, half 1: d = SVV0+1..SVV
-            constexpr int SVF0 = (L + 1) / 2;     // volume-face: half 0: t < SVF0, half 1: the rest
+            constexpr int SVV = PS::SVV;          // volume-volume diagonals d = 1..SVV
+            constexpr int SVV0 = PS::SVV0;        // half 0: d = 1..SVV0, half 1: d = SVV0+1..SVV
+            constexpr int SVF0 = PS::SVF0;        // volume-face: half 0: t < SVF0, half 1: the rest
+            // this lane's stored operator entries, one (Qx, Qy) per step
+            const real* qe = p.qxy + ((size_t)e * PS::NSTEP * 32 + lane) * 2;
             const int j = lane & 15, hf = lane >> 4;
             const bool vrow = j < V;
             const real* rl = rec + (vrow ? j : 0) * S::REC;
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4], H_l = rl[5];
-            const real rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9];
             const real gh2_l = rl[10];
             real A0 = 0, A1 = 0, A2 = 0;  // volume row j: own side + transposed volume-volume terms
             real B0 = 0, B1 = 0, B2 = 0;  // face row Nq + j: transposed volume-face terms
             // pair (j, m): own-row terms into (A0, A1, A2), the row-m terms into (t0, t1, t2)
-            auto pair = [&](int m, real& t0, real& t1, real& t2) {
-                const real2 q = QsT[m * D::Nh + j];
+            auto pair = [&](int m, real Qx, real Qy, real& t0, real& t1, real& t2) {
                 const real* rm = rec + m * S::REC;
-                const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
-                const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
                 const real HU = hu_l + rm[1], HV = hv_l + rm[2];
                 const real T = Qx * HU + Qy * HV;
                 const real Plm = gh2_l * rm[5];     // 2 g h_l H_m
@@ -495,8 +512,9 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 const bool act = vrow && step && !(2 * d == V && j >= V / 2);
                 int m = j + d;
                 m -= m >= V ? V : 0;
+                const real2 q = *reinterpret_cast<const real2*>(qe + 64 * k);
                 real t0 = 0, t1 = 0, t2 = 0;
-                if (act) pair(m, t0, t1, t2);
+                if (act) pair(m, q.x, q.y, t0, t1, t2);
                 int src = j - d;
                 src += src < 0 ? V : 0;
                 const real r0 = __shfl_sync(0xffffffffu, t0, 16 * hf + (src & 15));
@@ -515,8 +533,9 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 int f = j + t;
                 f -= f >= L ? L : 0;
                 const bool act = vrow && step && f < F;
+                const real2 q = *reinterpret_cast<const real2*>(qe + 64 * (SVV0 + k));
                 real t0 = 0, t1 = 0, t2 = 0;
-                if (act) pair(V + f, t0, t1, t2);
+                if (act) pair(V + f, q.x, q.y, t0, t1, t2);
                 int src = j - t;
                 src += src < 0 ? L : 0;
                 const real r0 = __shfl_sync(0xffffffffu, t0, 16 * hf + (src & 15));

@@ -3,7 +3,7 @@
 // per-batch arithmetic and EnsembleMember for the tile table).  Included once
 // per volume rule, with ESDG_RULE defined (esdg_ensemble.cu: collapsed,
 // esdg_ensemble_s.cu: symmetric).
-#include "esdg_stage2.cuh"
+#include "esdg_ensemble.cuh"
 
 namespace esdg {
 

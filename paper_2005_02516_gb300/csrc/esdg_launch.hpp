@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "esdg_kernels.cuh"
-#include "esdg_stage2.cuh"
+#include "esdg_ensemble.cuh"
 
 namespace esdg {
 

@@ -38,14 +38,14 @@ WL = W.DAM
 # dram__bytes_write.sum from one ncu capture), per inverse-mass kind, keyed to
 # the sha1 of the kernel source it was measured on: reported as null once that
 # source changes.
-STAGE_TRAFFIC = {"exact": {"source_sha1": "b53ae861ee97153fb5785c6cc656bb9f4049e15b", "bytes": 426.07e6},
-                 "weight_adjusted": {"source_sha1": "b53ae861ee97153fb5785c6cc656bb9f4049e15b", "bytes": 357.20e6}}
+STAGE_TRAFFIC = {"exact": {"source_sha1": "d33a9af34d8178593e3fbdfc83c86a6028349600", "bytes": 426.30e6},
+                 "weight_adjusted": {"source_sha1": "d33a9af34d8178593e3fbdfc83c86a6028349600", "bytes": 357.28e6}}
 STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2.cuh")
 # Warp instructions per element-stage of the FP32 stage kernel (ncu
 # smsp__inst_executed.sum / K on the same kernel at K = 32768), keyed the same
 # way: the issue-slot roofline of an issue-bound kernel (one warp instruction
 # per cycle per SM sub-partition).
-STAGE_INSTR = {"exact": {"source_sha1": "b53ae861ee97153fb5785c6cc656bb9f4049e15b", "per_element_stage": 1159.9}}
+STAGE_INSTR = {"exact": {"source_sha1": "d33a9af34d8178593e3fbdfc83c86a6028349600", "per_element_stage": 1286.7}}
 # the same for the FP32 DG-SBP stage kernel
 SBP_TRAFFIC = {"source_sha1": "bc6a6adb39a7b0f39182f3aa3b747208c033571a", "bytes": 386.1e6}
 SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")

@@ -44,8 +44,10 @@ STAGE_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_stage2
 # Warp instructions per element-stage of the FP32 stage kernel (ncu
 # smsp__inst_executed.sum / K on the same kernel at K = 32768), keyed the same
 # way: the issue-slot roofline of an issue-bound kernel (one warp instruction
-# per cycle per SM sub-partition).
-STAGE_INSTR = {"exact": {"source_sha1": "d33a9af34d8178593e3fbdfc83c86a6028349600", "per_element_stage": 1286.7}}
+# per cycle per SM sub-partition).  Polling of the bulk-copy barrier adds 0-11%
+# that varies from capture to capture (38.0 M and 42.2 M warp instructions
+# for the same binary); the lower count is the one used.
+STAGE_INSTR = {"exact": {"source_sha1": "d33a9af34d8178593e3fbdfc83c86a6028349600", "per_element_stage": 1159.9}}
 # the same for the FP32 DG-SBP stage kernel
 SBP_TRAFFIC = {"source_sha1": "bc6a6adb39a7b0f39182f3aa3b747208c033571a", "bytes": 386.1e6}
 SBP_SOURCE = os.path.join(ROOT, "paper_2005_02516_gb300", "csrc", "esdg_sbp2.cuh")

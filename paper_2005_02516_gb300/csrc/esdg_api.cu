@@ -176,7 +176,11 @@ static void compute_layout(esdg_ctx* c) {
     // no stored inverses with the weight-adjusted inverse or the diagonal SBP mass
     L.minv = take((sbp || weight_adjusted(c->cfg)) ? 0 : rs * Kp * c->mstride);
     L.bh = take(rs * Kp * nrec);
-    L.qxy_bytes = (c->cfg.precision == ESDG_FP64 && !sbp) ? 8 * Kp * size_t(pair_steps(kernel_nr(c->cfg))) * 64 : 0;
+    // FP64: the stored metric-averaged operator of the pair schedule (modal:
+    // the unique-pair steps; DG-SBP: the Nq x Nq ordered pairs in 32 pieces)
+    L.qxy_bytes = c->cfg.precision != ESDG_FP64 ? 0
+                  : sbp ? 8 * Kp * size_t((R.Nq * R.Nq + 31) / 32) * 64
+                        : 8 * Kp * size_t(pair_steps(kernel_nr(c->cfg))) * 64;
     L.qxy = take(L.qxy_bytes);
     L.nbr = take(4 * Kp * 3);
     L.fmap = take(sbp ? 4 * size_t(R.Nfq) : 0);
@@ -480,6 +484,34 @@ static std::vector<double> pair_operator_t(const esdg_ctx* c, const std::vector<
     return q;
 }
 
+// The same for the DG-SBP FP64 kernel, whose lanes take the Nq x Nq ordered
+// pairs (l, m), row-major, in 32 pieces of PL = ceil(Nq^2 / 32): entry it of
+// lane i is pair i PL + it, laid out [K][PL][32][2]; qsbp is the packed SBP
+// skew operator ([m][l][2]) and geo the metrics at the SBP nodes ([K][Nq][4]).
+template <typename real>
+static std::vector<double> sbp_pair_operator(const esdg_ctx* c, const std::vector<double>& qsbp,
+                                             const std::vector<real>& geo) {
+    const int Nq = c->ref.Nq, K = c->mesh.K;
+    const int PL = (Nq * Nq + 31) / 32;
+    std::vector<double> q(size_t(c->Kpad) * PL * 64, 0.0);
+    for (int e = 0; e < K; ++e) {
+        const real* g = geo.data() + size_t(e) * Nq * 4;
+        for (int lane = 0; lane < 32; ++lane)
+            for (int it = 0; it < PL; ++it) {
+                const int pp = lane * PL + it;
+                if (pp >= Nq * Nq) continue;
+                const int r = pp / Nq, m = pp - r * Nq;
+                const double qr = qsbp[(size_t(m) * Nq + r) * 2], qs = qsbp[(size_t(m) * Nq + r) * 2 + 1];
+                const real* gr = g + 4 * r;
+                const real* gm = g + 4 * m;
+                double* o = q.data() + ((size_t(e) * PL + it) * 32 + lane) * 2;
+                o[0] = qr * (0.125 * gr[0] + 0.125 * gm[0]) + qs * (0.125 * gr[1] + 0.125 * gm[1]);
+                o[1] = qr * (0.125 * gr[2] + 0.125 * gm[2]) + qs * (0.125 * gr[3] + 0.125 * gm[3]);
+            }
+    }
+    return q;
+}
+
 template <typename real>
 static std::vector<double> pair_operator(const esdg_ctx* c, const std::vector<real>& geo) {
     std::vector<double> g(geo.begin(), geo.end());
@@ -505,6 +537,7 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
         for (size_t e = 0; e < K; ++e)
             for (size_t i = 0; i < size_t(R.Nq) * 4; ++i) geo[e * R.Nq * 4 + i] = (real)M.geo[e * R.Nh * 4 + i];
         put(img, c->L.geo, geo);
+        if (c->L.qxy_bytes) put(img, c->L.qxy, sbp_pair_operator(c, pack_ops_sbp<double>(R), geo));
     } else {
         put(img, c->L.ops, pack_ops<real>(R));
         put(img, c->L.vq64, R.Vq.a);

@@ -149,16 +149,19 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
             const int p1 = p0 + S::PL < D::Nq * D::Nq ? p0 + S::PL : D::Nq * D::Nq;
             int r = p0 < p1 ? p0 / D::Nq : 0, m = p0 < p1 ? p0 - r * D::Nq : 0, slot = 0;
             const real* rl = rec + r * S::REC;
-            real hu_l = rl[1], hv_l = rl[2], rx_l = rl[6], sx_l = rl[7], ry_l = rl[8], sy_l = rl[9], gh2_l = rl[10];
+            real hu_l = rl[1], hv_l = rl[2], gh2_l = rl[10];
             real c0 = 0, c1 = 0, c2 = 0;
             for (int k = 0; k < S::PR * 4; ++k) part[lane * S::PR * 4 + k] = real(-1);
+            // the metric-averaged operator entries (Qskew^x, Qskew^y)[r][m] of
+            // this lane's pairs, stored per element ([K][PL][32][2], formed on
+            // the host: they depend on the geometry alone)
+            const real* qe = p.qxy + ((size_t)e * S::PL * 32 + lane) * 2;
 #pragma unroll 1
             for (int it = 0; it < S::PL; ++it) {
+                const real2 Q = *reinterpret_cast<const real2*>(qe + 64 * it);
                 if (p0 + it < p1) {
-                    const real2 q = QsT[m * D::Nq + r];
                     const real* rm = rec + m * S::REC;
-                    const real Qx = q.x * (rx_l + rm[6]) + q.y * (sx_l + rm[7]);
-                    const real Qy = q.x * (ry_l + rm[8]) + q.y * (sy_l + rm[9]);
+                    const real Qx = Q.x, Qy = Q.y;
                     const real HU = hu_l + rm[1], HV = hv_l + rm[2];
                     const real T = Qx * HU + Qy * HV;
                     const real P = gh2_l * rm[5];
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                             m = 0;
                             ++r;
                             rl = rec + r * S::REC;
-                            hu_l = rl[1]; hv_l = rl[2]; rx_l = rl[6]; sx_l = rl[7]; ry_l = rl[8]; sy_l = rl[9];
+                            hu_l = rl[1]; hv_l = rl[2];
                             gh2_l = rl[10];
                         }
                     }

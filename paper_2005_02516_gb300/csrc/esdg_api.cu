@@ -336,14 +336,42 @@ static std::vector<float> pack_ops2_t(const RefOps& R) {
     typedef C2<N> C;
     const int LPE = C::LPE;
     std::vector<float> o(C::o_end, 0.f);
-    for (int m = 0; m < R.Nh; ++m)
-        for (int b = 0; b < LPE; ++b)
-            for (int i = 0; i < C::RPL; ++i) {
+    if (C::UP) {
+        // unique pairs: entries (Qr, Qs) of own volume row l = b + LPE i
+        // against partner row m = (b + s) mod LPE + LPE j, in the order of
+        // the kernel's offset schedule; zero where the pair is not this
+        // lane's (offset LPE/2 of the volume-volume block: lanes b < LPE/2
+        // take (i, j) = (0, 0), (1, 1), the others (0, 1), (1, 0)) or m >= Nh
+        auto put4 = [&](int at, int b, int s, int j, bool half) {
+            const int m = ((b + s) % LPE) + LPE * j;
+            for (int i = 0; i < C::VS; ++i) {
                 const int l = b + LPE * i;
-                if (l >= R.Nh) continue;
-                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)R.Qsr(l, m);
-                o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)R.Qss(l, m);
+                bool take = m < R.Nh;
+                if (half) take = take && ((b < LPE / 2) == (i == j));
+                o[at + 4 * b + 2 * i] = take ? (float)R.Qsr(l, m) : 0.f;
+                o[at + 4 * b + 2 * i + 1] = take ? (float)R.Qss(l, m) : 0.f;
             }
+        };
+        for (int b = 0; b < LPE; ++b) {
+            o[C::o_U0 + 2 * b] = (float)R.Qsr(b, b + LPE);
+            o[C::o_U0 + 2 * b + 1] = (float)R.Qss(b, b + LPE);
+            for (int s = 1; s <= LPE / 2; ++s)
+                for (int j = 0; j < C::VS; ++j)
+                    put4(C::o_Uvv + ((s - 1) * C::VS + j) * LPE * 4, b, s, j, s == LPE / 2);
+            for (int s = 0; s < LPE; ++s)
+                for (int j = C::VS; j < C::RPL; ++j)
+                    put4(C::o_Uvf + (s * C::FS + (j - C::VS)) * LPE * 4, b, s, j, false);
+        }
+    } else {
+        for (int m = 0; m < R.Nh; ++m)
+            for (int b = 0; b < LPE; ++b)
+                for (int i = 0; i < C::RPL; ++i) {
+                    const int l = b + LPE * i;
+                    if (l >= R.Nh) continue;
+                    o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i] = (float)R.Qsr(l, m);
+                    o[C::o_Qs + (m * LPE + b) * C::OPB + 2 * i + 1] = (float)R.Qss(l, m);
+                }
+    }
     if (C::TC) {
         // lift Vh^T, Vq, Vq^T, Vh as tensor-core B operands (rows = outputs, K = inputs)
         const int t = C::o_tc;

@@ -85,7 +85,30 @@ struct C2 {
     //   du/dt = -Vq^T [(w/J) o (C r - A (w J f))]   and
     //   v~    =  B [(w/J) o (A (w J v))].
     static constexpr int o_Qs = 0;                                  // [Nh][LPE][OPB]
-    static constexpr int o_VhT = o_Qs + D::Nh * LPE * OPB;          // [Nh][LPE][MPLp]: Vh[l][b+LPE j]
+    // Unique pairs (UP; volume rules of 2 LPE points, so that slots i < VS of
+    // every lane hold volume rows and the slots above face rows): each
+    // non-zero pair of Q_skew is evaluated once, by the lane of its volume
+    // row l = b + LPE i, against a partner row m = c + LPE j of lane c = (b + s)
+    // mod LPE at offset s; row m's share (Q_skew is skew and the flux
+    // symmetric) reaches lane c by a shuffle.  Volume-volume pairs: offset 0
+    // (rows b and b + LPE of one lane) and offsets 1..LPE/2 (at LPE/2 each
+    // lane pair splits its four pairs two and two); volume-face pairs: offsets
+    // 0..LPE-1.  Tables of (Qr, Qs) entries in that order, zero where a pair
+    // is not this lane's or m is past Nh:
+    //   o_U0  [LPE][2]               pair (b, b + LPE)
+    //   o_Uvv [LPE/2][VS][LPE][4]    (l0, m), (l1, m) at offset s = 1.., slot j
+    //   o_Uvf [LPE][FS][LPE][4]      the same at offset s = 0.., face slot VS + j
+    static constexpr int VS = D::Nq / LPE;                  // volume row slots
+    static constexpr int FS = RPL - VS;                     // face row slots
+#ifndef ESDG_STAGE2_UNIQUE_PAIRS
+#define ESDG_STAGE2_UNIQUE_PAIRS 1
+#endif
+    static constexpr bool UP = ESDG_STAGE2_UNIQUE_PAIRS && D::Nq == 2 * LPE;
+    static constexpr int o_U0 = o_Qs;
+    static constexpr int o_Uvv = o_U0 + 2 * LPE;
+    static constexpr int o_Uvf = o_Uvv + (LPE / 2) * VS * LPE * 4;
+    static constexpr int QS_FLOATS = UP ? o_Uvf + LPE * FS * LPE * 4 : D::Nh * LPE * OPB;
+    static constexpr int o_VhT = o_Qs + QS_FLOATS;                  // [Nh][LPE][MPLp]: Vh[l][b+LPE j]
     static constexpr int o_tc = o_VhT;                              // tensor-core B blocks (TC)
     static constexpr int o_VqT = o_VhT + (TC ? tb_end : WADG ? 0 : D::Nh * LPE * MPLp);  // [Nq][LPE][MPLp]: Vq[q][b+LPE j]
     static constexpr int o_Vq = o_VqT + (TC ? 0 : D::Nq * LPE * MPLp);      // [Np][LPE][QPLp]: Vq[b+LPE j][n]
@@ -867,6 +890,121 @@ __device__ __forceinline__ void tc_batch_tail(const StageParams<float>& p, float
     stage2_project<N>(p, ut_out, ops, Mi, nullptr, nullptr, nullptr, ge, lane, bqv, wqv, blv, ws);
 }
 
+// Volume flux differencing with unique pairs (C2::UP): the row data of this
+// lane's slots (volume slots loaded first, face slots after the pair loops,
+// which do not read them) and the accumulators a0..a2 of every slot, before
+// the row part u_l sum(T) is added.  The arithmetic of a pair is that of the
+// ordered loop from row l's side; row m receives -T for h and, for the
+// momenta, -(u_l T + Qx 2 g h_m (H_l - H_0)) (the partner's column is l), as
+// the ordered loop would have formed them from row m's side.
+template <int N>
+__device__ __forceinline__ void stage2_unique_pairs(const float* __restrict__ ops, const float4* utE,
+                                                    const float4* geE, int b, float g, float* rh, float* ru,
+                                                    float* rv, float* rrx, float* rsx, float* rry, float* rsy,
+                                                    float* a0, float* a1, float* a2) {
+    typedef Dims<N> D;
+    typedef C2<N> C;
+    constexpr int LPE = C::LPE, RPL = C::RPL, VS = C::VS;
+    static_assert(VS == 2, "two volume row slots a lane (one float4 of entries per partner row)");
+    float rH[VS];
+#pragma unroll
+    for (int i = 0; i < RPL; ++i) a0[i] = a1[i] = a2[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < VS; ++i) {
+        const float4 U = utE[b + LPE * i], G = geE[b + LPE * i];
+        rh[i] = U.x;
+        ru[i] = U.y;
+        rv[i] = U.z;
+        rH[i] = U.w;
+        rrx[i] = G.x;
+        rsx[i] = G.y;
+        rry[i] = G.z;
+        rsy[i] = G.w;
+    }
+    const float g2 = 2.f * g;
+    // own row slot I against the partner row whose records are U, G; c0..c2
+    // collect the partner row's share (subtracted by the receiver)
+#define ESDG_UPAIR(I, QR, QS, FIRST)                                           \
+{                                                                          \
+    const float Qx = (QR) * (rrx[I] + G.x) + (QS) * (rsx[I] + G.y);        \
+    const float Qy = (QR) * (rry[I] + G.z) + (QS) * (rsy[I] + G.w);        \
+    const float HU = fmaf(rh[I], ru[I], hum), HV = fmaf(rh[I], rv[I], hvm);\
+    const float T = fmaf(Qx, HU, Qy * HV);                                 \
+    const float Pl = rh[I] * gH2, Pm = hm2 * rH[I];                        \
+    a0[I] += T;                                                            \
+    a1[I] = fmaf(U.y, T, fmaf(Qx, Pl, a1[I]));                             \
+    a2[I] = fmaf(U.z, T, fmaf(Qy, Pl, a2[I]));                             \
+    if (FIRST) {                                                           \
+        c0 = T;                                                            \
+        c1 = fmaf(ru[I], T, Qx * Pm);                                      \
+        c2 = fmaf(rv[I], T, Qy * Pm);                                      \
+    } else {                                                               \
+        c0 += T;                                                           \
+        c1 = fmaf(ru[I], T, fmaf(Qx, Pm, c1));                             \
+        c2 = fmaf(rv[I], T, fmaf(Qy, Pm, c2));                             \
+    }                                                                      \
+}
+    // offset 0, volume-volume: rows b and b + LPE of this lane
+    {
+        const float2 q = *reinterpret_cast<const float2*>(ops + C::o_U0 + 2 * b);
+        const float4 U = make_float4(rh[1], ru[1], rv[1], rH[1]);
+        const float4 G = make_float4(rrx[1], rsx[1], rry[1], rsy[1]);
+        const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = g2 * U.w, hm2 = g2 * U.x;
+        float c0, c1, c2;
+        ESDG_UPAIR(0, q.x, q.y, true)
+        a0[1] -= c0;
+        a1[1] -= c1;
+        a2[1] -= c2;
+    }
+    // partner slot J at offset s: the partner row m = (b + s) mod LPE + LPE J
+    // (clamped into the element's rows; its entries are zero past Nh), and
+    // the share of this lane's slot J from lane (b - s) mod LPE
+#define ESDG_USTEP(TABLE, J)                                                   \
+{                                                                          \
+    const int m = min(((b + s) & (LPE - 1)) + LPE * (J), D::Nh - 1);       \
+    const float4 U = utE[m], G = geE[m];                                   \
+    const float4 q = *reinterpret_cast<const float4*>(TABLE + 4 * b);      \
+    const float hum = U.x * U.y, hvm = U.x * U.z, gH2 = g2 * U.w, hm2 = g2 * U.x; \
+    float c0, c1, c2;                                                      \
+    ESDG_UPAIR(0, q.x, q.y, true)                                          \
+    ESDG_UPAIR(1, q.z, q.w, false)                                         \
+    const int src = (b - s) & (LPE - 1);                                   \
+    a0[J] -= __shfl_sync(0xffffffffu, c0, src, LPE);                       \
+    a1[J] -= __shfl_sync(0xffffffffu, c1, src, LPE);                       \
+    a2[J] -= __shfl_sync(0xffffffffu, c2, src, LPE);                       \
+}
+#pragma unroll 2
+    for (int s = 1; s <= LPE / 2; ++s) {
+        const float* t = ops + C::o_Uvv + (s - 1) * VS * LPE * 4;
+#pragma unroll
+        for (int j = 0; j < VS; ++j) ESDG_USTEP(t + j * LPE * 4, j)
+    }
+#pragma unroll 1
+    for (int s = 0; s < LPE; ++s) {
+        const float* t = ops + C::o_Uvf + s * C::FS * LPE * 4;
+#pragma unroll
+        for (int j = VS; j < RPL; ++j) ESDG_USTEP(t + (j - VS) * LPE * 4, j)
+    }
+#undef ESDG_USTEP
+#undef ESDG_UPAIR
+#pragma unroll
+    for (int i = VS; i < RPL; ++i) {
+        const int l = b + LPE * i;
+        float4 U = make_float4(0.f, 0.f, 0.f, 0.f), G = U;
+        if (l < D::Nh) {
+            U = utE[l];
+            G = geE[l];
+        }
+        rh[i] = U.x;
+        ru[i] = U.y;
+        rv[i] = U.z;
+        rrx[i] = G.x;
+        rsx[i] = G.y;
+        rry[i] = G.z;
+        rsy[i] = G.w;
+    }
+}
+
 // One batch of EPW elements of one problem, starting at element e0 (all 32
 // lanes of the warp).  ops: the operator region of degree N in shared memory;
 // ws: this warp's region.  Returns false if the bounded wait on the bulk
@@ -921,6 +1059,9 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
     // and the momentum error of the FP32 path falls about threefold.
     float rh[RPL], ru[RPL], rv[RPL], rrx[RPL], rsx[RPL], rry[RPL], rsy[RPL];
     float a0[RPL], a1[RPL], a2[RPL];
+    if constexpr (C::UP) {
+        stage2_unique_pairs<N>(ops, utE, geE, b, g, rh, ru, rv, rrx, rsx, rry, rsy, a0, a1, a2);
+    } else {
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
         const int l = b + LPE * i;
@@ -981,6 +1122,7 @@ __device__ __forceinline__ bool stage2_batch(const StageParams<float>& p, const 
         }
     }
 #undef ESDG_PAIR
+    }
 #pragma unroll
     for (int i = 0; i < RPL; ++i) {
         a1[i] = fmaf(ru[i], a0[i], a1[i]);

@@ -489,20 +489,23 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4], H_l = rl[5];
             const real gh2_l = rl[10];
             real A0 = 0, A1 = 0, A2 = 0;  // volume row j: own side + transposed volume-volume terms
+            real A1p = 0, A2p = 0;        // volume row j: sum of (Qx, Qy) H_m, times 2 g h_j after the loop
             real B0 = 0, B1 = 0, B2 = 0;  // face row Nq + j: transposed volume-face terms
-            // pair (j, m): own-row terms into (A0, A1, A2), the row-m terms into (t0, t1, t2)
+            // pair (j, m): own-row terms into (A0, A1, A2, A1p, A2p), the row-m
+            // terms, to be subtracted by their receiver, into (t0, t1, t2)
             auto pair = [&](int m, real Qx, real Qy, real& t0, real& t1, real& t2) {
                 const real* rm = rec + m * S::REC;
                 const real HU = hu_l + rm[1], HV = hv_l + rm[2];
                 const real T = Qx * HU + Qy * HV;
-                const real Plm = gh2_l * rm[5];     // 2 g h_l H_m
                 const real Pml = rm[10] * H_l;      // 2 g h_m H_l
                 A0 += T;
-                A1 = fma(rm[3], T, fma(Qx, Plm, A1));
-                A2 = fma(rm[4], T, fma(Qy, Plm, A2));
-                t0 = -T;
-                t1 = -fma(u_l, T, Qx * Pml);
-                t2 = -fma(v_l, T, Qy * Pml);
+                A1 = fma(rm[3], T, A1);
+                A2 = fma(rm[4], T, A2);
+                A1p = fma(Qx, rm[5], A1p);
+                A2p = fma(Qy, rm[5], A2p);
+                t0 = T;
+                t1 = fma(u_l, T, Qx * Pml);
+                t2 = fma(v_l, T, Qy * Pml);
             };
 #pragma unroll
             for (int k = 0; k < SVV0; ++k) {
@@ -521,9 +524,9 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 const real r1 = __shfl_sync(0xffffffffu, t1, 16 * hf + (src & 15));
                 const real r2 = __shfl_sync(0xffffffffu, t2, 16 * hf + (src & 15));
                 if (vrow && step) {
-                    A0 += r0;
-                    A1 += r1;
-                    A2 += r2;
+                    A0 -= r0;
+                    A1 -= r1;
+                    A2 -= r2;
                 }
             }
 #pragma unroll
@@ -542,11 +545,13 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 const real r1 = __shfl_sync(0xffffffffu, t1, 16 * hf + (src & 15));
                 const real r2 = __shfl_sync(0xffffffffu, t2, 16 * hf + (src & 15));
                 if (step && j < F) {
-                    B0 += r0;
-                    B1 += r1;
-                    B2 += r2;
+                    B0 -= r0;
+                    B1 -= r1;
+                    B2 -= r2;
                 }
             }
+            A1 = fma(gh2_l, A1p, A1);  // the pressure terms g h_j H_m of row j's own pairs
+            A2 = fma(gh2_l, A2p, A2);
             A0 += __shfl_xor_sync(0xffffffffu, A0, 16);
             A1 += __shfl_xor_sync(0xffffffffu, A1, 16);
             A2 += __shfl_xor_sync(0xffffffffu, A2, 16);
@@ -770,7 +775,7 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         // ---- du/dt = -(M_h^k)^{-1} s; then output or RK update --------------------
         real* sc = ws + S::w_c;
         if constexpr (D::wadg) {
-            wadg_apply<N, real>(p, ops, sb, fa, sc, e, lane, real(-1));  // fa (forcing) is consumed
+            wadg_apply<N, real>(p, ops, sb, fa, sc, e, lane, real(1));  // fa (forcing) is consumed
         } else {
             const real* mi = ws + S::w_minv;
             auto mi_term = [&](int n, int j, real& a0, real& a1, real& a2) {
@@ -790,20 +795,20 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
 #pragma unroll
                     for (int j = 0; j < D::Np; ++j) mi_term(n, j, a0, a1, a2);
                 }
-                sc[n] = -a0;
-                sc[D::Np + n] = -a1;
-                sc[2 * D::Np + n] = -a2;
+                sc[n] = a0;
+                sc[D::Np + n] = a1;
+                sc[2 * D::Np + n] = a2;
             }
         }
         __syncwarp();
         for (int i = lane; i < 3 * D::Np; i += 32) {
             const int c = i / D::Np, n = i - c * D::Np;
             const size_t gi = ((size_t)c * p.K + e) * D::Np + n;
-            const double r = (double)sc[i];
+            const double r = (double)sc[i];  // du/dt = -r
             if (MODE == 0) {
-                p.rhs_out[gi] = r;
+                p.rhs_out[gi] = -r;
             } else {
-                const double rs = p.rkA * p.res[gi] + p.dt * r;
+                const double rs = p.rkA * p.res[gi] - p.dt * r;
                 p.res[gi] = rs;
                 const double un = p.u[gi] + p.rkB * rs;
                 p.u[gi] = un;

@@ -150,7 +150,9 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
             int r = p0 < p1 ? p0 / D::Nq : 0, m = p0 < p1 ? p0 - r * D::Nq : 0, slot = 0;
             const real* rl = rec + r * S::REC;
             real hu_l = rl[1], hv_l = rl[2], gh2_l = rl[10];
-            real c0 = 0, c1 = 0, c2 = 0;
+            // c1p, c2p: sums of (Qx, Qy) H_m; the row's pressure terms are
+            // 2 g h_l times them, added when the piece's row ends
+            real c0 = 0, c1 = 0, c2 = 0, c1p = 0, c2p = 0;
             for (int k = 0; k < S::PR * 4; ++k) part[lane * S::PR * 4 + k] = real(-1);
             // the metric-averaged operator entries (Qskew^x, Qskew^y)[r][m] of
             // this lane's pairs, stored per element ([K][PL][32][2], formed on
@@ -164,19 +166,20 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                     const real Qx = Q.x, Qy = Q.y;
                     const real HU = hu_l + rm[1], HV = hv_l + rm[2];
                     const real T = Qx * HU + Qy * HV;
-                    const real P = gh2_l * rm[5];
                     c0 += T;
-                    c1 += rm[3] * T + Qx * P;
-                    c2 += rm[4] * T + Qy * P;
+                    c1 = fma(rm[3], T, c1);
+                    c2 = fma(rm[4], T, c2);
+                    c1p = fma(Qx, rm[5], c1p);
+                    c2p = fma(Qy, rm[5], c2p);
                     if (++m == D::Nq || p0 + it + 1 == p1) {
                         // this row's piece ends: file its partial sums
                         real* o = part + (lane * S::PR + slot) * 4;
                         o[0] = c0;
-                        o[1] = c1;
-                        o[2] = c2;
+                        o[1] = fma(gh2_l, c1p, c1);
+                        o[2] = fma(gh2_l, c2p, c2);
                         o[3] = real(r);
                         ++slot;
-                        c0 = c1 = c2 = 0;
+                        c0 = c1 = c2 = c1p = c2p = 0;
                         if (m == D::Nq && r + 1 < D::Nq) {
                             m = 0;
                             ++r;

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -47,6 +48,9 @@ struct DevLayout {
     size_t ops2 = 0, ops2_bytes = 0;     // permuted operators of the FP32 batched kernel
     size_t ops2s = 0, ops2s_bytes = 0;   // tensor-core contexts: the FP32-pipe layout too (ensembles)
     size_t qxy = 0, qxy_bytes = 0;       // FP64 unique-pair schedule: stored metric-averaged operator
+    size_t lk = 0, lk_bytes = 0;         // FP64, stored inverse: M^-1 Vh^T per element (lane order)
+    size_t gk = 0, gk_bytes = 0;         //   M^-1 Vq^T per element (forcing only)
+    size_t pk = 0, pk_bytes = 0;         //   Vh M^-1 Vq^T per element
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
@@ -112,6 +116,14 @@ static int c2_ops_floats(int N);
 
 static bool weight_adjusted(const esdg_config& cfg) { return cfg.mass == ESDG_MASS_WEIGHT_ADJUSTED; }
 static bool is_sbp(const esdg_config& cfg) { return cfg.method == ESDG_METHOD_SBP; }
+// The FP64 modal path with the stored inverse keeps the inverse's products
+// with the shared operators per element, where the kernel's lane mapping
+// covers them (two half-warps of modes, one lane per hybrid node): two
+// inverse-mass passes and two contractions fewer per stage on the FP64 pipe,
+// for 8 (Nh + 1) / 2 * 32 + 8 Nq * 32 bytes per element.
+static bool composed_ops(const esdg_config& cfg, const RefOps& R) {
+    return cfg.precision == ESDG_FP64 && !is_sbp(cfg) && !weight_adjusted(cfg) && R.Np <= 16 && R.Nh <= 32;
+}
 
 // Kernel template parameter of a configuration: NR = N + 8 * rule + 16 * wadg.
 static int kernel_nr(const esdg_config& cfg) {
@@ -182,6 +194,13 @@ static void compute_layout(esdg_ctx* c) {
                   : sbp ? 8 * Kp * size_t((R.Nq * R.Nq + 31) / 32) * 64
                         : 8 * Kp * size_t(pair_steps(kernel_nr(c->cfg))) * 64;
     L.qxy = take(L.qxy_bytes);
+    const bool comp = composed_ops(c->cfg, R);
+    L.lk_bytes = comp ? 8 * Kp * size_t((R.Nh + 1) / 2) * 32 : 0;
+    L.gk_bytes = comp && c->cfg.forcing != ESDG_FORCING_NONE ? 8 * Kp * size_t((R.Nq + 1) / 2) * 32 : 0;
+    L.pk_bytes = comp ? 8 * Kp * size_t(R.Nq) * 32 : 0;
+    L.lk = take(L.lk_bytes);
+    L.gk = take(L.gk_bytes);
+    L.pk = take(L.pk_bytes);
     L.nbr = take(4 * Kp * 3);
     L.fmap = take(sbp ? 4 * size_t(R.Nfq) : 0);
     const bool forcing = c->cfg.forcing != ESDG_FORCING_NONE;
@@ -551,6 +570,8 @@ static std::vector<double> pair_operator(const esdg_ctx* c, const std::vector<re
     return {};
 }
 
+static void composed_operators(const esdg_ctx* c, std::vector<unsigned char>& img);
+
 template <typename real>
 static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
     const RefOps& R = c->ref;
@@ -590,6 +611,7 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
             for (int i = 0; i < NpP; ++i) mi[e * c->mstride + i] = (real)M.minv[e * NpP + i];
         put(img, c->L.minv, mi);
     }
+    if (c->L.lk_bytes) composed_operators(c, img);
     put(img, c->L.nbr, M.nbr);
     if (c->cfg.forcing != ESDG_FORCING_NONE) {
         put(img, c->L.xq, to_real<real>(M.xq));
@@ -663,6 +685,67 @@ static void modal_bathymetry(esdg_ctx* c, const double* b_nodal) {
         }
 }
 
+// Per-element products of the FP64 path (composed_ops): L = M^-1 Vh^T,
+// G = M^-1 Vq^T and P = Vh G, formed in FP64 from the element's inverse mass
+// and written into the image in the lanes' order of k_stage / project_element.
+static void composed_operators(const esdg_ctx* c, std::vector<unsigned char>& img) {
+    const RefOps& R = c->ref;
+    const MeshData& M = c->mesh;
+    const int K = M.K, Np = R.Np, Nq = R.Nq, Nh = R.Nh, LT = (Nh + 1) / 2, GT = (Nq + 1) / 2;
+    double* lk = reinterpret_cast<double*>(img.data() + c->L.lk);
+    double* gk = c->L.gk_bytes ? reinterpret_cast<double*>(img.data() + c->L.gk) : nullptr;
+    double* pk = reinterpret_cast<double*>(img.data() + c->L.pk);
+    std::memset(lk, 0, c->L.lk_bytes);
+    std::memset(pk, 0, c->L.pk_bytes);
+    if (gk) std::memset(gk, 0, c->L.gk_bytes);
+    auto work = [&](int e0, int e1) {
+        std::vector<double> mi(size_t(Np) * Np), G(size_t(Np) * Nq), Lm(size_t(Np) * Nh);
+        for (int e = e0; e < e1; ++e) {
+            const double* pm = &M.minv[size_t(e) * Np * (Np + 1) / 2];
+            for (int n = 0; n < Np; ++n)
+                for (int j = 0; j < Np; ++j) mi[n * Np + j] = pm[n >= j ? n * (n + 1) / 2 + j : j * (j + 1) / 2 + n];
+            for (int n = 0; n < Np; ++n) {
+                for (int q = 0; q < Nq; ++q) {
+                    double s = 0;
+                    for (int j = 0; j < Np; ++j) s += mi[n * Np + j] * R.Vq(q, j);
+                    G[n * Nq + q] = s;
+                }
+                for (int l = 0; l < Nh; ++l) {
+                    double s = 0;
+                    for (int j = 0; j < Np; ++j) s += mi[n * Np + j] * R.Vh(l, j);
+                    Lm[n * Nh + l] = s;
+                }
+            }
+            // lane n + 16 hf, step t: column hf * LT + t (L) or hf * GT + t (G)
+            for (int lane = 0; lane < 32; ++lane) {
+                const int n = lane & 15, hf = lane >> 4;
+                if (n >= Np) continue;
+                for (int t = 0; t < LT; ++t) {
+                    const int l = hf * LT + t;
+                    if (l < Nh) lk[(size_t(e) * LT + t) * 32 + lane] = Lm[n * Nh + l];
+                }
+                if (gk)
+                    for (int t = 0; t < GT; ++t) {
+                        const int q = hf * GT + t;
+                        if (q < Nq) gk[(size_t(e) * GT + t) * 32 + lane] = G[n * Nq + q];
+                    }
+            }
+            for (int l = 0; l < Nh; ++l)
+                for (int q = 0; q < Nq; ++q) {
+                    double s = 0;
+                    for (int n = 0; n < Np; ++n) s += R.Vh(l, n) * G[n * Nq + q];
+                    pk[(size_t(e) * Nq + q) * 32 + l] = s;
+                }
+        }
+    };
+    const int nt = std::max(1, std::min<int>(16, std::min<int>(int(std::thread::hardware_concurrency()),
+                                                                (K + 1023) / 1024)));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < nt; ++t) pool.emplace_back(work, int(size_t(K) * t / nt), int(size_t(K) * (t + 1) / nt));
+    work(0, K / nt);
+    for (auto& th : pool) th.join();
+}
+
 // Host image of [0, end of u): operators, geometry, bathymetry and (if q is
 // given) the projected initial state.
 template <typename real>
@@ -728,6 +811,9 @@ static StageParams<real> make_params(esdg_ctx* c) {
     p.xq = reinterpret_cast<const real*>(d + c->L.xq);
     p.yq = reinterpret_cast<const real*>(d + c->L.yq);
     p.qxy = reinterpret_cast<const real*>(d + c->L.qxy);
+    p.lk = c->L.lk_bytes ? reinterpret_cast<const real*>(d + c->L.lk) : nullptr;
+    p.gk = c->L.gk_bytes ? reinterpret_cast<const real*>(d + c->L.gk) : nullptr;
+    p.pk = c->L.pk_bytes ? reinterpret_cast<const real*>(d + c->L.pk) : nullptr;
     p.u = reinterpret_cast<double*>(d + c->L.u);
     p.u_in = p.u;
     p.res = reinterpret_cast<double*>(d + c->L.res);

@@ -99,6 +99,17 @@ struct StageParams {
     // [K][NSTEP][32][2] (zero where the lane has no pair); stage-independent,
     // formed once on the host
     const real* qxy;
+    // FP64 path with the stored inverse (Np <= 16, Nh <= 32): per-element
+    // products of the inverse mass with the shared operators, formed once on
+    // the host, in the order the lanes read them (zero-padded):
+    //   lk [K][(Nh+1)/2][32]  M^-1 Vh^T   (lift + inverse mass), lane = n + 16 hf,
+    //                          column l = hf (Nh+1)/2 + t at step t
+    //   gk [K][(Nq+1)/2][32]  M^-1 Vq^T   (forcing), the same with columns q
+    //   pk [K][Nq][32]        Vh M^-1 Vq^T (projection to the hybrid nodes), lane = l
+    // null: the inverse applied to the shared operators' results in turn
+    const real* lk;
+    const real* gk;
+    const real* pk;
     // state
     const double* u_in;  // [3][K][Np]  (projection input)
     double* u;           // [3][K][Np]  RK state (updated in place)
@@ -302,6 +313,37 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
         ta[2 * D::Nq + q] = w * vv;
     }
     __syncwarp();
+    // u~ = u(v~) at hybrid node l from v~ = (a0, a1, a2):
+    // H = (v1 + (v2^2 + v3^2)/2)/g, h = H - b
+    const real ig = real(1) / g;
+    auto emit = [&](int l, real a0, real a1, real a2) {
+        real H = (a0 + real(0.5) * (a1 * a1 + a2 * a2)) * ig;
+        real h = H - p.bh[(size_t)e * D::Nh + l];
+        if (!(h > real(0))) bad |= STATUS_NONPOSITIVE;
+        if (!r_finite(H) || !r_finite(a1) || !r_finite(a2)) bad |= STATUS_NONFINITE;
+        real* o = p.ut_out + ((size_t)e * D::Nh + l) * 4;
+        o[0] = h;
+        o[1] = a1;
+        o[2] = a2;
+        o[3] = H;
+    };
+    if constexpr (!D::wadg && D::Np <= 16 && D::Nh <= 32) {
+        if (p.pk != nullptr) {
+            // v~ = (Vh M^-1 Vq^T) (W J v_q), the product stored per element; lane = l
+            const real* Pk = p.pk + (size_t)e * D::Nq * 32 + lane;
+            real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+            for (int q = 0; q < D::Nq; ++q) {
+                const real v = Pk[32 * q];
+                a0 += v * ta[q];
+                a1 += v * ta[D::Nq + q];
+                a2 += v * ta[2 * D::Nq + q];
+            }
+            if (lane < D::Nh) emit(lane, a0, a1, a2);
+            if (bad) atomicOr(p.status, bad);
+            return;
+        }
+    }
     // y = Vq^T W J v_q
     auto vqt_term = [&](int n, int q, real& a0, real& a1, real& a2) {
         const real v = VqT[n * D::Nq + q];
@@ -352,8 +394,7 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
         }
     }
     __syncwarp();
-    // v~ = Vh v_h; u~ = u(v~): H = (v1 + (v2^2 + v3^2)/2)/g, h = H - b
-    const real ig = real(1) / g;
+    // v~ = Vh v_h, then u~ = u(v~)
     for (int l = lane; l < D::Nh; l += 32) {
         real a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll
@@ -363,15 +404,7 @@ __device__ __forceinline__ void project_element(const StageParams<real>& p, cons
             a1 += v * us[D::Np + n];
             a2 += v * us[2 * D::Np + n];
         }
-        real H = (a0 + real(0.5) * (a1 * a1 + a2 * a2)) * ig;
-        real h = H - p.bh[(size_t)e * D::Nh + l];
-        if (!(h > real(0))) bad |= STATUS_NONPOSITIVE;
-        if (!r_finite(H) || !r_finite(a1) || !r_finite(a2)) bad |= STATUS_NONFINITE;
-        real* o = p.ut_out + ((size_t)e * D::Nh + l) * 4;
-        o[0] = h;
-        o[1] = a1;
-        o[2] = a2;
-        o[3] = H;
+        emit(l, a0, a1, a2);
     }
     if (bad) atomicOr(p.status, bad);
 }
@@ -380,8 +413,10 @@ template <int N, typename real>
 __device__ __forceinline__ void load_minv(const StageParams<real>& p, real* ws, int e, int lane) {
     typedef Dims<N> D;
     typedef Smem<N, real> S;
+    // (not read where the products with the inverse are stored)
     if constexpr (!D::wadg)
-        for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * p.mstride + i];
+        if (p.pk == nullptr)
+            for (int i = lane; i < D::NpP; i += 32) ws[S::w_minv + i] = p.minv[(size_t)e * p.mstride + i];
 }
 
 // Standalone projection: u_in (FP64 modal) -> ut_out.
@@ -731,6 +766,48 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             }
         }
         __syncwarp();
+        real* sc = ws + S::w_c;
+        bool composed = false;
+        if constexpr (!D::wadg && D::Np <= 16 && D::Nh <= 32) composed = p.lk != nullptr;
+        if (composed) {
+            // ---- M^-1 s = (M^-1 Vh^T) r - (M^-1 Vq^T) (W J f), the products stored
+            // per element: rows n = lane & 15 over the columns of half-warp hf
+            constexpr int LT = (D::Nh + 1) / 2, GT = (D::Nq + 1) / 2;
+            const int hf = lane >> 4;
+            const real* Lk = p.lk + (size_t)e * LT * 32 + lane;
+            real a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+            for (int t = 0; t < LT; ++t) {
+                const int l = hf * LT + t;
+                if (l < D::Nh) {
+                    const real v = Lk[32 * t];
+                    a0 += v * rt[l];
+                    a1 += v * rt[D::Nh + l];
+                    a2 += v * rt[2 * D::Nh + l];
+                }
+            }
+            if (p.forcing) {
+                const real* Gk = p.gk + (size_t)e * GT * 32 + lane;
+#pragma unroll
+                for (int t = 0; t < GT; ++t) {
+                    const int q = hf * GT + t;
+                    if (q < D::Nq) {
+                        const real v = Gk[32 * t];
+                        a0 -= v * fa[q];
+                        a1 -= v * fa[D::Nq + q];
+                        a2 -= v * fa[2 * D::Nq + q];
+                    }
+                }
+            }
+            a0 += __shfl_down_sync(0xffffffffu, a0, 16);
+            a1 += __shfl_down_sync(0xffffffffu, a1, 16);
+            a2 += __shfl_down_sync(0xffffffffu, a2, 16);
+            if (lane < D::Np) {
+                sc[lane] = a0;
+                sc[D::Np + lane] = a1;
+                sc[2 * D::Np + lane] = a2;
+            }
+        } else {
         // ---- lift: s = Vh^T r - Vq^T W J f --------------------------------------
         const real* VhT = ops + S::ops_VhT;
         const real* VqT = ops + S::ops_VqT;
@@ -773,7 +850,6 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
         }
         __syncwarp();
         // ---- du/dt = -(M_h^k)^{-1} s; then output or RK update --------------------
-        real* sc = ws + S::w_c;
         if constexpr (D::wadg) {
             wadg_apply<N, real>(p, ops, sb, fa, sc, e, lane, real(1));  // fa (forcing) is consumed
         } else {
@@ -800,6 +876,7 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 sc[2 * D::Np + n] = a2;
             }
         }
+        }
         __syncwarp();
         for (int i = lane; i < 3 * D::Np; i += 32) {
             const int c = i / D::Np, n = i - c * D::Np;
@@ -813,7 +890,7 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 const double un = p.u[gi] + p.rkB * rs;
                 p.u[gi] = un;
                 if (p.u_out) p.u_out[gi] = un;
-                sb[i] = (real)un;
+                ws[S::w_b + i] = (real)un;  // the projection's input
             }
         }
         __syncwarp();

@@ -145,21 +145,30 @@ def test_weight_adjusted_mass_stores_no_inverses(rule, precision):
     """The weight-adjusted inverse keeps no per-element matrix on the device:
     the footprint drops by the stored inverses, K Np(Np+1)/2 values of the
     RHS precision, less the few KB that the FP32 kernel's composed shared
-    operators add (both with the dense operators on the FP32 pipes)."""
+    operators add (both with the dense operators on the FP32 pipes).  The
+    FP64 path with the stored inverse also keeps the inverse's products
+    M^-1 Vh^T and Vh M^-1 Vq^T per element where its lane mapping covers them
+    (Np <= 16, Nh <= 32: here the 16-point rule), in its padded lane layout
+    of ((Nh + 1) / 2 + Nq) 32 doubles."""
     sizes = {}
     for mass in (esdg.ESDG_MASS_EXACT, esdg.ESDG_MASS_WEIGHT_ADJUSTED):
         lib, rc, h = _build(N=4, nx=16, ny=16, warp=0.05, rule=rule, precision=precision, mass=mass,
                             dense=esdg.ESDG_DENSE_SIMT)
         assert rc == 0
-        K, Np = ctypes.c_int(), ctypes.c_int()
+        K, Np, Nq, Nfq = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         nb = ctypes.c_size_t()
-        assert lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), None, None, ctypes.byref(nb)) == 0
-        sizes[mass] = (K.value, Np.value, nb.value)
+        assert lib.esdg_sizes(h, ctypes.byref(K), ctypes.byref(Np), ctypes.byref(Nq), ctypes.byref(Nfq),
+                              ctypes.byref(nb)) == 0
+        sizes[mass] = (K.value, Np.value, Nq.value, Nfq.value, nb.value)
         lib.esdg_destroy(h)
-    K, Np, exact = sizes[esdg.ESDG_MASS_EXACT]
-    wadg = sizes[esdg.ESDG_MASS_WEIGHT_ADJUSTED][2]
+    K, Np, Nq, Nfq, exact = sizes[esdg.ESDG_MASS_EXACT]
+    wadg = sizes[esdg.ESDG_MASS_WEIGHT_ADJUSTED][4]
     rs = 4 if precision == esdg.ESDG_FP32 else 8
     stored = K * Np * (Np + 1) // 2 * rs
+    Nh = Nq + Nfq
+    if precision == esdg.ESDG_FP64 and Np <= 16 and Nh <= 32:
+        assert rule == esdg.ESDG_RULE_SYMMETRIC
+        stored += K * ((Nh + 1) // 2 + Nq) * 32 * 8
     assert stored - 16384 <= exact - wadg <= stored + 16384
 
 

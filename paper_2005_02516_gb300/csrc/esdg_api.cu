@@ -54,6 +54,7 @@ struct DevLayout {
     size_t vq64 = 0;                     // Vq FP64 (diagnostics)
     size_t geo = 0, wJq = 0, minv = 0, bh = 0, nbr = 0, xq = 0, yq = 0;
     size_t wJq64 = 0, bq64 = 0;
+    size_t iwJ = 0;                      // DG-SBP FP64: 1 / (w J) at the nodes
     size_t fmap = 0;                     // DG-SBP: volume node of each face node (int)
     size_t u = 0, res = 0, rhs = 0, ut0 = 0, ut1 = 0;
     size_t partial = 0, diag = 0, status = 0;
@@ -185,6 +186,7 @@ static void compute_layout(esdg_ctx* c) {
     L.vq64 = take(sbp ? 0 : 8 * size_t(R.Nq) * R.Np);
     L.geo = take(rs * Kp * nrec * 4);
     L.wJq = take(rs * Kp * R.Nq);
+    L.iwJ = take(sbp && c->cfg.precision == ESDG_FP64 ? 8 * Kp * R.Nq : 0);
     // no stored inverses with the weight-adjusted inverse or the diagonal SBP mass
     L.minv = take((sbp || weight_adjusted(c->cfg)) ? 0 : rs * Kp * c->mstride);
     L.bh = take(rs * Kp * nrec);
@@ -604,6 +606,11 @@ static void fill_static(const esdg_ctx* c, std::vector<unsigned char>& img) {
         for (int q = 0; q < R.Nq; ++q) wJ64[e * R.Nq + q] = R.wq[q] * M.Jq[e * R.Nq + q];
     put(img, c->L.wJq, to_real<real>(wJ64));
     put(img, c->L.wJq64, wJ64);
+    if (c->sbp && c->cfg.precision == ESDG_FP64) {
+        std::vector<double> iw(wJ64.size());
+        for (size_t i = 0; i < iw.size(); ++i) iw[i] = 1.0 / wJ64[i];
+        put(img, c->L.iwJ, iw);
+    }
     if (!weight_adjusted(c->cfg) && !c->sbp) {
         const int NpP = R.Np * (R.Np + 1) / 2;
         std::vector<real> mi(K * size_t(c->mstride), (real)0);
@@ -803,6 +810,7 @@ static StageParams<real> make_params(esdg_ctx* c) {
     }
     p.geo = reinterpret_cast<const real*>(d + c->L.geo);
     p.wJq = reinterpret_cast<const real*>(d + c->L.wJq);
+    p.iwJ = (c->sbp && c->cfg.precision == ESDG_FP64) ? reinterpret_cast<const real*>(d + c->L.iwJ) : nullptr;
     p.minv = reinterpret_cast<const real*>(d + c->L.minv);
     p.mstride = c->mstride;
     p.bh = reinterpret_cast<const real*>(d + c->L.bh);

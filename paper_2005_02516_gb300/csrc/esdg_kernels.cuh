@@ -83,6 +83,7 @@ struct StageParams {
     const real* wf;    // [Nfq]
     const real* nrs;   // [Nfq][2] scaled reference normals
     const real* wq;    // [Nq]     volume weights (weight-adjusted inverse: w_q / J_q = w_q^2 / (w_q J_q))
+    const real* iwJ;   // [K][Nq]  DG-SBP FP64: 1 / (w_q J_q), the inverse of the diagonal mass (else null)
     const int* fmap;   // [Nfq]    DG-SBP: the volume node of each face node (the selection I_f)
     // per element
     const real* geo;   // [K][Nh][4] rxJ sxJ ryJ syJ

@@ -233,19 +233,19 @@ __global__ void __launch_bounds__(256) k_sbp(StageParams<real> p) {
                 r1 += w * (uA * Fn0 + nxJ * pw);
                 r2 += w * (vA * Fn0 + nyJ * pw);
                 if (p.lf) {
-                    const real sJ = r_sqrt(nxJ * nxJ + nyJ * nyJ);
-                    const real isJ = real(1) / sJ;
-                    const real inx = nxJ * isJ, iny = nyJ * isJ;
-                    const real lm = fabs(u_l * inx + v_l * iny) + r_sqrt(g * h_l);
-                    const real lp = fabs(uP * inx + vP * iny) + r_sqrt(g * hP);
-                    const real c = real(0.5) * w * sJ * (lm > lp ? lm : lp);
+                    // sJ max(|u.n| + sqrt(g h)) over both sides with the unit
+                    // normal n = nJ / sJ folded in: |u.nJ| + sqrt(sJ^2 g h)
+                    const real sJ2 = nxJ * nxJ + nyJ * nyJ;
+                    const real lm = fabs(u_l * nxJ + v_l * nyJ) + r_sqrt(sJ2 * g * h_l);
+                    const real lp = fabs(uP * nxJ + vP * nyJ) + r_sqrt(sJ2 * g * hP);
+                    const real c = real(0.5) * w * (lm > lp ? lm : lp);
                     r0 -= c * (hP - h_l);
                     r1 -= c * (huP - hu_l);
                     r2 -= c * (hvP - hv_l);
                 }
             }
             // du/dt = -r / (w J) + forcing (the forcing term W J f of the form, divided by W J)
-            const real iwj = real(1) / p.wJq[(size_t)e * D::Nq + l];
+            const real iwj = p.iwJ != nullptr ? p.iwJ[(size_t)e * D::Nq + l] : real(1) / p.wJq[(size_t)e * D::Nq + l];
             real d0 = -r0 * iwj, d1 = -r1 * iwj, d2 = -r2 * iwj;
             if (p.forcing) {
                 const real x = p.xq[(size_t)e * D::Nq + l], y = p.yq[(size_t)e * D::Nq + l];

@@ -299,6 +299,70 @@ def test_fp64_kernel_pair_assignment_covers_each_pair_once(N, rule):
     assert len(delivered) == len(want) and all(v == 1 for v in delivered.values())
 
 
+def _replay_fp32_offsets(Nq, Nh, LPE=8):
+    """The FP32 stage kernel's unique-pair schedule (esdg_stage2.cuh,
+    stage2_unique_pairs, and the host tables of pack_ops2_t), for rules with
+    Nq = 2 LPE: lane b owns rows b + LPE i (slots i < 2 volume rows, the
+    slots above face rows); offset 0 pairs its two volume rows; at offset s
+    the lane pairs its volume rows with the partner row m = (b + s) mod LPE +
+    LPE j of slot j (volume slots at s = 1..LPE/2, where at s = LPE/2 lanes
+    b < LPE/2 keep (i, j) in {(0,0), (1,1)} and the others {(0,1), (1,0)};
+    face slots at s = 0..LPE-1, m < Nh), and row m's share of slot j comes to
+    lane c from lane (c - s) mod LPE.  Returns the evaluated pairs and the
+    shares delivered per (pair, receiving row)."""
+    RPL = (Nh + LPE - 1) // LPE
+    VS = Nq // LPE
+    assert VS == 2
+    evaluated, delivered = {}, {}
+
+    def step(s, j, half):
+        sent = {}
+        for b in range(LPE):
+            m = (b + s) % LPE + LPE * j
+            pairs = []
+            for i in range(VS):
+                l = b + LPE * i
+                take = m < Nh
+                if half:
+                    take = take and ((b < LPE // 2) == (i == j))
+                if take and l != m:
+                    key = frozenset((l, m))
+                    evaluated[key] = evaluated.get(key, 0) + 1
+                    pairs.append((l, m))
+            sent[b] = pairs
+        for c in range(LPE):
+            row = c + LPE * j
+            for (l, m) in sent[(c - s) % LPE]:
+                assert m == row, "a partner share reached the wrong row"
+                delivered[(l, m)] = delivered.get((l, m), 0) + 1
+
+    for b in range(LPE):                          # offset 0: rows b and b + LPE of one lane
+        key = frozenset((b, b + LPE))
+        evaluated[key] = evaluated.get(key, 0) + 1
+        delivered[(b, b + LPE)] = delivered.get((b, b + LPE), 0) + 1
+    for s in range(1, LPE // 2 + 1):
+        for j in range(VS):
+            step(s, j, s == LPE // 2)
+    for s in range(LPE):
+        for j in range(VS, RPL):
+            step(s, j, False)
+    return evaluated, delivered
+
+
+@pytest.mark.parametrize("N, rule", [(4, "symmetric"), (3, "collapsed")])
+def test_fp32_kernel_unique_pairs_cover_each_pair_once(N, rule):
+    """The FP32 stage kernel's offset schedule for the 16-point volume rules,
+    replayed on the host: every non-zero pair of Q_skew (volume x volume,
+    volume x face) is evaluated exactly once, by the lane of a volume row,
+    and the partner row's share reaches that row exactly once."""
+    Nq = 16
+    Nh = Nq + 3 * (N + 1)
+    evaluated, delivered = _replay_fp32_offsets(Nq, Nh)
+    want = {frozenset((l, m)) for l in range(Nq) for m in range(Nh) if m != l}
+    assert set(evaluated) == want and all(v == 1 for v in evaluated.values())
+    assert len(delivered) == len(want) and all(v == 1 for v in delivered.values())
+
+
 @pytest.mark.parametrize("Nq", [6, 10, 18, 22, 34])
 def test_fp64_sbp_kernel_pair_pieces(Nq):
     """The FP64 DG-SBP kernel's split of the Nq x Nq pairs into 32 pieces of

@@ -243,6 +243,29 @@ def test_full_size_config3_sampled_rhs(precision):
         check_fp32_rhs(got, want, o.rhs_term_magnitude(u, 0.0, elems=ks), c_modal(o.Np, o.Nq, o.Nfq))
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_full_size_collapsed_rule_sampled_rhs(precision):
+    """The same full-size workload with the collapsed (N+1)^2 = 25-point
+    volume rule (the bench's collapsed-rule line; 675 non-zero pairs of Q_skew
+    per element, ordered pairs in both kernels, the FP64 path's pieces
+    schedule): the right-hand side on every 997th element (plus the last)
+    against the oracle element by element, FP64 at relative 1e-12, FP32 within
+    the first-order bound of each entry."""
+    w = W.DAM
+    s, o = _solver(w, precision, rule="collapsed")
+    xo, yo = o.points("volq")
+    u = o.init_state(w.initial(xo, yo))
+    s.set_state(u)
+    ks = np.unique(np.concatenate([np.arange(0, o.K, 997), [o.K - 1]]))
+    got = s.rhs(0.0).cpu().numpy()[:, ks]
+    want = o.rhs_elements(u, ks)
+    if precision == "fp64":
+        assert _rel(got, want) < 1e-12
+        assert _relmax(got, want) < 1e-12
+    else:
+        check_fp32_rhs(got, want, o.rhs_term_magnitude(u, 0.0, elems=ks), c_modal(o.Np, o.Nq, o.Nfq))
+
+
 # ---- reflective walls (Sec. 2.9) -----------------------------------------------
 WALL_CASES = [(W.DAM, 4, 6, 5, "symmetric"), (W.DAM, 3, 5, 4, "collapsed"), (W.LAKE_BUMP, 2, 7, 3, "symmetric"),
               (W.DAM, 5, 4, 3, "symmetric")]

@@ -453,7 +453,7 @@ __global__ void __launch_bounds__(256) k_project(StageParams<real> p) {
 // MODE 0: write du/dt to rhs_out.  MODE 1: LSRK45 stage update of (u, res)
 // followed by the entropy projection of the new state into ut_out.
 template <int N, typename real, int MODE>
-__global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
+__device__ __forceinline__ void k_stage_body(const StageParams<real>& p) {
     typedef Dims<N> D;
     typedef Smem<N, real> S;
     typedef typename V2<real>::t real2;
@@ -664,6 +664,38 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             }
             __syncwarp();
         }
+        // Lax-Friedrichs wave speeds |u.nJ| + sqrt(sJ^2 g h) (the unit normal
+        // n = nJ / sJ folded in) of both sides of every face node in one pass
+        // over the warp, where the face rows sit on lanes Nq.. = 16..: lane
+        // 16 + f takes face node f's own trace, lane f the neighbour's (a wall
+        // mirrors the normal velocity and keeps h, so its speed is the own one);
+        // face row Nq + f then reads the neighbour's speed from lane f.
+        constexpr bool LF_PAIRED = SPLIT && D::Nq == 16 && D::Nfq <= 16;
+        real lam_pass = 0;
+        if constexpr (LF_PAIRED) {
+            __syncwarp();
+            const int f = lane & 15;
+            if (p.lf && f < D::Nfq) {
+                const real* rf = rec + (D::Nq + f) * S::REC;
+                const real nr = ops[S::ops_nrs + 2 * f], ns = ops[S::ops_nrs + 2 * f + 1];
+                const real fx = real(8) * (rf[6] * nr + rf[7] * ns);
+                const real fy = real(8) * (rf[8] * nr + rf[9] * ns);
+                real hh = rf[0], uu = rf[3], vv = rf[4];
+                if (lane < 16) {
+                    const int face = f / D::Nfp, i = f - face * D::Nfp;
+                    const int nb = p.nbr[(size_t)e * 3 + face];
+                    if ((nb & 3) != 3) {
+                        const real* up =
+                            p.ut_in + ((size_t)(nb >> 2) * D::Nh + D::Nq + (nb & 3) * D::Nfp + (D::Nfp - 1 - i)) * 4;
+                        hh = up[0];
+                        uu = up[1];
+                        vv = up[2];
+                    }
+                }
+                lam_pass = fabs(uu * fx + vv * fy) + r_sqrt((fx * fx + fy * fy) * g * hh);
+            }
+        }
+        const real lam_nbr = LF_PAIRED ? __shfl_sync(0xffffffffu, lam_pass, lane & 15) : real(0);
         for (int l = lane; l < D::Nh; l += 32) {
             const real* rl = rec + l * S::REC;
             const real h_l = rl[0], hu_l = rl[1], hv_l = rl[2], u_l = rl[3], v_l = rl[4];
@@ -732,9 +764,15 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
                 if (p.lf) {
                     // sJ max(|u.n| + sqrt(g h)) over both sides with the unit
                     // normal n = nJ / sJ folded in: |u.nJ| + sqrt(sJ^2 g h)
-                    const real sJ2 = nxJ * nxJ + nyJ * nyJ;
-                    const real lm = fabs(u_l * nxJ + v_l * nyJ) + r_sqrt(sJ2 * g * h_l);
-                    const real lp = fabs(uP * nxJ + vP * nyJ) + r_sqrt(sJ2 * g * hP);
+                    real lm, lp;
+                    if constexpr (LF_PAIRED) {
+                        lm = lam_pass;  // this lane is 16 + f: its own side, computed above
+                        lp = lam_nbr;
+                    } else {
+                        const real sJ2 = nxJ * nxJ + nyJ * nyJ;
+                        lm = fabs(u_l * nxJ + v_l * nyJ) + r_sqrt(sJ2 * g * h_l);
+                        lp = fabs(uP * nxJ + vP * nyJ) + r_sqrt(sJ2 * g * hP);
+                    }
                     const real c = real(0.5) * w * (lm > lp ? lm : lp);
                     r0 -= c * (hP - h_l);
                     r1 -= c * (huP - hu_l);
@@ -900,6 +938,27 @@ __global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
             __syncwarp();
         }
     }
+}
+
+template <int N, typename real, int MODE>
+__global__ void __launch_bounds__(256) k_stage(StageParams<real> p) {
+    k_stage_body<N, real, MODE>(p);
+}
+
+// The same kernel with a floor of MINB blocks of 8 warps per SM for the
+// register allocator: the RK stage of N = 4 with the 16-point rule and the
+// stored inverse compiles to 127 registers and 2 blocks under the plain bound,
+// to 80 and 3 blocks with MINB = 3 (3.34 against 3.41 ms per stage at
+// K = 131072); elsewhere the plain bound's allocation is kept (an explicit
+// floor makes the allocator fill up to it, and a cap at 80 spills).
+template <int N, typename real, int MODE, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_stage(StageParams<real> p) {
+    k_stage_body<N, real, MODE>(p);
+}
+
+template <int N, int MODE>
+constexpr bool k_stage_three_blocks() {
+    return MODE == 1 && Dims<N>::Nq == 16 && Dims<N>::Nh == 31 && !Dims<N>::wadg;
 }
 
 // FP64 diagnostics: per-CTA partial sums of (entropy, mass, entropy rate).

@@ -3,6 +3,15 @@
 
 namespace esdg {
 
+// the RK-stage kernel of degree N (the three-block form where it applies)
+template <int N, typename real>
+static auto stage_kernel1() {
+    if constexpr (k_stage_three_blocks<N, 1>())
+        return &k_stage<N, real, 1, 3>;
+    else
+        return &k_stage<N, real, 1>;
+}
+
 template <int N, typename real>
 cudaError_t stage_geometry(int num_sms, LaunchGeom& lg) {
     lg.block = 256;
@@ -10,10 +19,11 @@ cudaError_t stage_geometry(int num_sms, LaunchGeom& lg) {
     cudaError_t err;
     err = cudaFuncSetAttribute(k_stage<N, real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
     if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(k_stage<N, real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
+    auto* k1 = stage_kernel1<N, real>();
+    err = cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lg.smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage<N, real, 1>, lg.block, lg.smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k1, lg.block, lg.smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) per_sm = 1;
     lg.grid = per_sm * num_sms;
@@ -50,7 +60,7 @@ cudaError_t launch_stage(const StageParams<real>& p, int mode, const LaunchGeom&
     if (mode == 0)
         k_stage<N, real, 0><<<grid, lg.block, lg.smem, s>>>(p);
     else
-        k_stage<N, real, 1><<<grid, lg.block, lg.smem, s>>>(p);
+        stage_kernel1<N, real>()<<<grid, lg.block, lg.smem, s>>>(p);
     return cudaGetLastError();
 }
 

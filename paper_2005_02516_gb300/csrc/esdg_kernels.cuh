@@ -500,8 +500,9 @@ __device__ __forceinline__ void k_stage_body(const StageParams<real>& p) {
         // evaluated once (the face-face block is zero): the flux terms are
         // antisymmetric in (l, m) (T_ml = -T_lm) and the pressure terms swap
         // h and H, so one evaluation gives row l its contribution and row m
-        // -(u_l T + Qx g h_m H_l), ... (about 26 FP64 operations for two rows
-        // instead of 2 x 18: this kernel is bound by the FP64 pipe).  Lanes
+        // -(u_l T + Qx g h_m H_l), ... (with the stored metric-averaged entries,
+        // 17 FP64 instructions for both rows, the receiver's three subtractions
+        // included: this kernel is bound by the FP64 pipe).  Lanes
         // j = lane & 15 of half-warp hf stand for volume row j.  Volume-volume
         // pairs run along the diagonals (j, j + d mod Nq), volume-face pairs
         // along (j, Nq + (j + t) mod L), L = max(Nq, Nfq), the two half-warps
